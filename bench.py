@@ -1,0 +1,361 @@
+"""Benchmark: one supremacy circuit per step through the whole hot path.
+
+A step = generate the circuit (host), schedule it into clusters and build the
+FP64 cluster unitaries (host), prepare |0...0>, apply every op (one HBM sweep
+each), and reduce the output distribution (norm, entropy, Porter-Thomas moments).
+The default workload is the 30-qubit 5x6-grid circuit with 25 CZ cycles in
+complex128, fused into clusters of k <= 5 plus merged CZ/T phase diagonals.
+
+Prints one JSON line.  `value` is the job's wall time per circuit (device-timed,
+max over ranks, divided by the circuits all ranks simulated).
+With --gpus N > 1 (under torchrun) every rank simulates its own circuits
+(replicas; no data exchange between GPUs).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "circuit wall time and effective HBM GB/s per cluster sweep (fraction of roofline) vs plain"
+
+WORKLOADS = {
+    # name: (rows, cols, removed, cz_cycles, dtype, k_max)
+    "5x6_d25_c128": (5, 6, (), 25, "c128", 5),
+    "5x6_d25_c64": (5, 6, (), 25, "c64", 5),
+    "4x8_d25_c64": (4, 8, (), 25, "c64", 5),
+    "4x4_d10_c128": (4, 4, (), 10, "c128", 5),
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1704_01127_gb300 import build as _build
+    _build.build()
+    import paper_1704_01127_gb300.qs as qs
+
+    world, rank, local, dist = dist_setup(args)
+    qs.qs_set_device(local)
+    torch.cuda.set_device(local)
+    rows, cols, removed, cycles, dt, k_max = WORKLOADS[args.workload]
+    dtype = qs.QS_C128 if dt == "c128" else qs.QS_C64
+    amp_bytes = 16 if dtype == qs.QS_C128 else 8
+    hbm_gbs, sm_max_mhz, peak_src = load_peaks()
+
+    stream = torch.cuda.Stream()
+    n, _ = qs.qs_supremacy_circuit(rows, cols, cycles, 0, removed=removed)
+    h = qs.qs_alloc(n, dtype, stream)
+    state_bytes = amp_bytes << n
+
+    kernel_ms = {}      # (kind, k) -> list of per-launch ms in the timed region
+    launches = [0]
+
+    def one_step(seed, record):
+        nq, gates = qs.qs_supremacy_circuit(rows, cols, cycles, seed, removed=removed)       # a1
+        sc = qs.qs_schedule_build(nq, gates, k_max=k_max, fuse=not args.plain)                # a2, a3
+        try:
+            qs.qs_init_basis(h, 0)
+            op_ms = qs.qs_run_circuit_timed(h, sc)                                            # a4-a6
+            st = qs.qs_stats(h)                                                               # a7
+            if record:
+                for i in range(qs.qs_schedule_num_ops(sc)):
+                    op = qs.qs_schedule_op(sc, i)
+                    key = (op["kind"], len(op.get("qubits", ())) if op["kind"] == "dense" else 0)
+                    kernel_ms.setdefault(key, []).append(float(op_ms[i]))
+                launches[0] += qs.qs_schedule_num_ops(sc) + 2 + 2
+            return st, len(op_ms)
+        finally:
+            qs.qs_schedule_free(sc)
+
+    seeds = [rank * 1000 + s for s in range(args.warmup + args.steps)]
+    for s in seeds[:args.warmup]:
+        one_step(s, False)
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        stats = None
+        for s in seeds[args.warmup:]:
+            stats, nops = one_step(s, True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier(dist)
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    elapsed = max_over_ranks(dist, max(dev_s, wall))
+    per_circuit = elapsed / (args.steps * world)
+
+    # dominant kernel: the (kind, k) class with the most device time
+    dom_key = max(kernel_ms, key=lambda kk: sum(kernel_ms[kk]))
+    dom_ms = statistics.mean(kernel_ms[dom_key])
+    sweep_bytes = 2 * state_bytes
+    achieved_gbs = sweep_bytes / (dom_ms * 1e-3) / 1e9
+    kind, k = dom_key
+    flops = (1 << n) * (8 * (1 << k) - 2) if kind == "dense" else 0
+    if dtype == qs.QS_C128 and kind == "dense":
+        # native FP64: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock
+        fp64_peak = 152 * 2 * 2 * sm_max_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / (dom_ms * 1e-3) / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "peak_source": "derived FP64 (152 SM x 2 FMA/clk x 2 x %.0f MHz)" % sm_max_mhz}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "peak_source": peak_src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "%s k=%d" % (kind, k) if kind == "dense" else kind
+    roof["kernel_ms"] = dom_ms
+    roof["effective_hbm_gbs"] = achieved_gbs
+    roof["hbm_frac"] = achieved_gbs / hbm_gbs
+
+    sweeps = {("%s_k%d" % kk if kk[0] == "dense" else kk[0]): {
+        "launches": len(v), "mean_ms": statistics.mean(v),
+        "gbs": sweep_bytes / (statistics.mean(v) * 1e-3) / 1e9,
+        "hbm_frac": sweep_bytes / (statistics.mean(v) * 1e-3) / 1e9 / hbm_gbs}
+        for kk, v in sorted(kernel_ms.items())}
+
+    # plain gate-by-gate form of the same circuit (the comparison of the metric)
+    plain = None
+    if not args.plain and not args.no_plain and rank == 0:
+        nq, gates = qs.qs_supremacy_circuit(rows, cols, cycles, seeds[-1], removed=removed)
+        sc = qs.qs_schedule_build(nq, gates, fuse=False)
+        try:
+            qs.qs_init_basis(h, 0)
+            qs.qs_run_circuit(h, sc)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            qs.qs_init_basis(h, 0)
+            e0.record(stream)
+            qs.qs_run_circuit(h, sc)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            plain = {"s_per_circuit": e0.elapsed_time(e1) / 1e3, "ops": qs.qs_schedule_num_ops(sc),
+                     "dtype": dt}
+        finally:
+            qs.qs_schedule_free(sc)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        m = 1 << 20
+        times, h2d = [], 0
+        for s in seeds[:3]:
+            t0 = time.perf_counter()
+            nq, gates = qs.qs_supremacy_circuit(rows, cols, cycles, s, removed=removed)
+            sc = qs.qs_schedule_build(nq, gates, k_max=k_max, fuse=not args.plain)
+            try:
+                h2d = qs.qs_schedule_upload_bytes(sc, dtype)
+                qs.qs_init_basis(h, 0)
+                qs.qs_run_circuit(h, sc)
+                qs.qs_stats(h)
+                qs.qs_sample(h, s, m)
+            finally:
+                qs.qs_schedule_free(sc)
+            times.append(time.perf_counter() - t0)
+        e2e = {"value": statistics.median(times), "unit": "s/circuit", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 4 * 8 + 8 * m,
+               "what": "host gate list -> schedule -> matrices to device -> run -> stats and 2^20 samples to host"}
+
+    qs.qs_free(h)
+    if rank != 0:
+        return None
+    cpu = None if args.no_cpu_baseline else cpu_baseline(args, n_steps=1)[0]
+    line = {
+        "metric": METRIC, "value": per_circuit, "unit": "s/circuit", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if dtype == qs.QS_C128 else "f32", "data": "synthetic",
+        "config": {"workload": "%dx%d grid, %d qubits, %d CZ cycles, %s, %s" % (
+            rows, cols, n, cycles, dt, "gate by gate" if args.plain else "fused k<=%d + phase diagonals" % k_max),
+            "seeds": "rank*1000 + step", "l2": "state %.1f GiB > L2 129 MB (no flush needed)" % (state_bytes / 2**30),
+            "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof, "sweeps": sweeps, "plain": plain,
+        "speedup_vs_plain": (plain["s_per_circuit"] / per_circuit) if plain else None,
+        "porter_thomas": {"sum_p": stats[0], "entropy": stats[1], "m2": stats[3]},
+        "e2e": e2e, "gpu_launches": launches[0], "clocks": clk.summary(), "cpu_baseline": cpu,
+    }
+    return line
+
+
+# ------------------------------------------------------------ oracle (CPU) leg
+
+def cpu_baseline(args, n_steps):
+    """The oracle, as it stands, on a bounded sample of the workload: a few gates
+    of the circuit applied to the full state on the host; the per-circuit time is
+    scaled from the per-gate times."""
+    import numpy as np
+    from oracle import circuit as ocircuit
+    from oracle import sim as osim
+    rows, cols, removed, cycles, dt, k_max = WORKLOADS[args.workload]
+    n, gates = ocircuit.supremacy_circuit(rows, cols, cycles, 0, removed=removed)
+    n1 = sum(1 for g in gates if g[1] != "cz")
+    n2 = len(gates) - n1
+    psi = osim.basis_state(n, 0)
+    one = [g for g in gates if g[1] != "cz"]
+    two = [g for g in gates if g[1] == "cz"]
+    values = []
+    for step in range(n_steps):
+        g1, g2 = one[step % len(one)], two[step % len(two)]
+        t0 = time.perf_counter()
+        osim.apply_gate(psi, g1[1], g1[2])
+        t1 = time.perf_counter()
+        osim.apply_gate(psi, g2[1], g2[2])
+        t2 = time.perf_counter()
+        values.append(n1 * (t1 - t0) + n2 * (t2 - t1))
+    del psi
+    return [{"value": v, "unit": "s/circuit", "cores": 1, "kind": "oracle",
+             "sample": "one single-qubit gate and one CZ of the %dx%d circuit applied to the full "
+                       "2^%d-amplitude complex128 state; scaled by the circuit's %d single-qubit "
+                       "gates and %d CZs" % (rows, cols, n, n1, n2)} for v in values]
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    res = cpu_baseline(args, args.warmup + args.steps)[args.warmup:]
+    vals = [r["value"] for r in res]
+    v = statistics.median(vals)
+    rows, cols, removed, cycles, dt, k_max = WORKLOADS[args.workload]
+    cb = dict(res[0])
+    cb["value"] = v
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/circuit", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "%dx%d grid, %d CZ cycles, gate-by-gate complex128 oracle on the host" % (
+                rows, cols, cycles)},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "s/circuit", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="5x6_d25_c128")
+    ap.add_argument("--plain", action="store_true", help="gate-by-gate form instead of fused")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison run")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("note: warmup raised to 3", file=sys.stderr)
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * qs -- GB300 (sm_103a) state-vector simulator for fused k-qubit cluster sweeps
+ * over low-depth random ("supremacy") circuits, after Haener & Steiger,
+ * "0.5 Petabyte Simulation of a 45-Qubit Quantum Circuit".
+ *
+ * C ABI.  All functions return QS_OK (0) or a negative QS_E* code and never
+ * abort; qs_last_error() gives a thread-local message for the last failure.
+ * Pointers are host pointers unless a parameter says "device".  Every call is
+ * ordered on the state's CUDA stream; calls that return results to host memory
+ * (qs_norm, qs_stats, qs_probabilities to host, qs_sample, qs_get_amplitudes)
+ * synchronise that stream before returning.  The caller keeps ownership of every
+ * array it passes; the library copies what it needs before returning.
+ *
+ * State layout (Sec. 2): 2^n amplitudes alpha_i, qubit q = bit q of the index i
+ * (qubit 0 least significant), stored contiguously in device memory as
+ * interleaved (re, im) pairs: double2 for QS_C128, float2 for QS_C64.
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    QS_OK = 0,
+    QS_EINVAL = -1,        /* bad argument (range, duplicate qubit, size) */
+    QS_ENOMEM = -2,        /* device or host allocation failed */
+    QS_ECUDA = -3,         /* a CUDA runtime call failed */
+    QS_ETIMEOUT = -4,      /* a bounded device wait ran out */
+    QS_EUNSUPPORTED = -5   /* valid request this build does not handle */
+};
+
+enum { QS_C64 = 0, QS_C128 = 1 };   /* amplitude type: complex float / double */
+
+#define QS_MAX_K 5          /* largest dense cluster (2^5 x 2^5 unitary) */
+#define QS_MAX_DIAG_K 12    /* largest table diagonal */
+#define QS_MAX_QUBITS 36    /* largest state this build addresses */
+
+typedef struct qs_state qs_state;   /* opaque, owned by the library */
+
+const char *qs_last_error(void);
+
+/* Allocate a state of 2^n amplitudes of the given dtype on the current CUDA
+ * device (Sec. 2; in place, one buffer, Sec. 3.2).  stream: a cudaStream_t or
+ * NULL for the legacy default stream.  Contents are undefined until an init
+ * call.  Errors: QS_EINVAL (n < 1 or n > QS_MAX_QUBITS, bad dtype),
+ * QS_ENOMEM (cudaMalloc failed). */
+int qs_alloc(int n, int dtype, void *stream, qs_state **out);
+
+/* Adopt an existing device buffer of 2^n amplitudes (e.g. a torch tensor's
+ * storage; 16-byte aligned).  The library never frees dev_ptr.  Errors as
+ * qs_alloc, plus QS_EINVAL for a NULL or misaligned pointer. */
+int qs_wrap(void *dev_ptr, int n, int dtype, void *stream, qs_state **out);
+
+/* Release a state and the library's scratch buffers (not a wrapped buffer).
+ * NULL is ignored. */
+void qs_free(qs_state *s);
+
+/* Make `device` the current CUDA device of the calling thread for later
+ * qs_alloc / qs_wrap calls.  QS_ECUDA if the device does not exist. */
+int qs_set_device(int device);
+
+int qs_num_qubits(const qs_state *s);
+int qs_dtype(const qs_state *s);
+void *qs_device_ptr(const qs_state *s);        /* device pointer to amplitude 0 */
+int qs_set_stream(qs_state *s, void *stream);
+
+/* |x>: amplitude x = 1, all others 0 (Sec. 2).  QS_EINVAL if x >= 2^n. */
+int qs_init_basis(qs_state *s, uint64_t x);
+
+/* (2^{-n/2}, ..., 2^{-n/2}): the state after the H layer of cycle 0, which a
+ * simulator may prepare directly (Sec. 3.6). */
+int qs_init_uniform(qs_state *s);
+
+/* Copy 2^n complex128 amplitudes (interleaved re, im; host memory) into the
+ * state, rounding to the state's dtype; and back (widening for QS_C64). */
+int qs_set_amplitudes(qs_state *s, const double *host_c128);
+int qs_get_amplitudes(qs_state *s, double *host_c128);
+
+/* Apply a dense k-qubit gate in place (Sec. 3.2): for every assignment c of the
+ * n-k other bits, the 2^k amplitudes whose target bits spell x (x_j = bit
+ * qubits[j] of the index) form a vector v, replaced by U v.  There are 2^{n-k}
+ * such products.  qubits: k distinct values in [0, n), any order; the library
+ * permutes U to ascending qubit order (Sec. 3.2).  U: 2^k x 2^k row-major,
+ * complex128 interleaved (re, im), FP64 for both dtypes (rounded to float for
+ * QS_C64).  1 <= k <= QS_MAX_K.  Errors: QS_EINVAL. */
+int qs_apply_cluster(qs_state *s, const int *qubits, int k, const double *U);
+
+/* Apply a diagonal k-qubit gate: amplitude i is multiplied by d[x], x gathered
+ * from the bits qubits[0..k-1] of i as in qs_apply_cluster.  d: 2^k complex128
+ * interleaved.  1 <= k <= QS_MAX_DIAG_K. */
+int qs_apply_diag(qs_state *s, const int *qubits, int k, const double *d);
+
+/* Apply a product of T-type phases and CZ gates (Sec. 2, Sec. 3.5: both are
+ * diagonal): amplitude i is multiplied by e^{i pi m(i)/4} with
+ *   m(i) = sum_q coeff[q] i_q + 4 sum_{e < n_edges} i_{edges[2e]} i_{edges[2e+1]}
+ * (mod 8).  coeff: n integers (taken mod 8); edges: 2*n_edges qubit indices in
+ * [0, n) (a pair may repeat; a == b is rejected). */
+int qs_apply_phase(qs_state *s, const int *coeff, int n_edges, const int *edges);
+
+/* sum_i |alpha_i|^2, accumulated in FP64 (Sec. 2).  out: host double. */
+int qs_norm(qs_state *s, double *out);
+
+/* p_i = |alpha_i|^2 in FP64, each product and the sum rounded separately
+ * (Sec. 2).  out: 2^n doubles, device memory if out_on_device, else host. */
+int qs_probabilities(qs_state *s, double *out, int out_on_device);
+
+/* Output-distribution statistics in FP64 (Sec. 4.2 computes the entropy with a
+ * final reduction): out[0] = sum p, out[1] = -sum p ln p, out[2] = mean of N p,
+ * out[3] = mean of (N p)^2 (N = 2^n; Porter-Thomas gives 1 and 2). */
+int qs_stats(qs_state *s, double out[4]);
+
+/* Draw m outcomes (not in the paper; this library's rule): u_j = (SplitMix64
+ * output j of seed >> 11) * 2^-53 and outcome j = the first x whose cumulative
+ * probability exceeds u_j, the cumulative sums taken in FP64 in a fixed order
+ * (pairwise within blocks of 1024 outcomes and super-blocks of 1024 blocks,
+ * sequential across them).  out: m uint64 in host memory.  m >= 0. */
+int qs_sample(qs_state *s, uint64_t seed, int64_t m, uint64_t *out);
+
+/* Wait for all work queued on the state's stream. */
+int qs_synchronize(qs_state *s);
+
+/* ------------------------------------------------------------------------
+ * Circuits (Fig. 1 caption; Sec. 3.6).
+ * ---------------------------------------------------------------------- */
+enum {
+    QS_GATE_H = 0, QS_GATE_T = 1, QS_GATE_SQRT_X = 2, QS_GATE_SQRT_Y = 3,
+    QS_GATE_CZ = 4, QS_GATE_X = 5, QS_GATE_TDG = 6, QS_GATE_SQRT_XDG = 7,
+    QS_GATE_SQRT_YDG = 8
+};
+
+typedef struct {
+    int32_t cycle;   /* clock cycle (0 = H layer) */
+    int32_t kind;    /* QS_GATE_* */
+    int32_t q0;      /* qubit */
+    int32_t q1;      /* second qubit of CZ, else -1 */
+} qs_gate;
+
+/* Generate a supremacy circuit on a rows x cols grid with some sites removed
+ * (removed_rc: n_removed (row, col) pairs), cz_cycles CZ cycles after the H
+ * layer, seed for the single-qubit gate choices.  Fig. 1 caption: H on every
+ * qubit in cycle 0; eight staggered CZ layouts repeated; a qubit that left a CZ
+ * gets T first, later a uniform choice among {T, X^1/2, Y^1/2} minus its
+ * previous gate.  Readings where the paper is silent: qubit = row-major index of
+ * the remaining sites; layouts H(1,0) V(0,0) H(0,0) V(1,0) V(0,1) H(1,1) V(1,1)
+ * H(0,1), where H(a,b) couples (r,c)-(r,c+1) with c%2 == a, r%2 == b and V(a,b)
+ * couples (r,c)-(r+1,c) with r%2 == a, c%2 == b; choice j takes the
+ * ((SplitMix64 output j) >> 63)-th allowed gate.  Gates are written to
+ * gates[0..max_gates); *n_gates receives the count (QS_EINVAL, with *n_gates
+ * set, if max_gates is too small).  *n_qubits receives the qubit count. */
+int qs_supremacy_circuit(int rows, int cols, const int *removed_rc, int n_removed,
+                         int cz_cycles, uint64_t seed, int *n_qubits,
+                         qs_gate *gates, int max_gates, int *n_gates);
+
+/* ------------------------------------------------------------------------
+ * Schedules (Sec. 3.6 step 2: clusters of k <= k_max qubits; Sec. 3.2 matrix
+ * pre-permutation; Sec. 3.5 diagonal gates).
+ * ---------------------------------------------------------------------- */
+typedef struct qs_schedule qs_schedule;   /* opaque, owned by the library */
+
+enum { QS_OP_DENSE = 0, QS_OP_PHASE = 1, QS_OP_DIAG = 2 };
+
+typedef struct {
+    int32_t k_max;        /* 2..QS_MAX_K when fuse != 0 */
+    int32_t fuse;         /* 0: one op per gate (plain form); 1: greedy clusters */
+    int32_t merge_phase;  /* 1: merge neighbouring all-diagonal ops into one phase op */
+    int32_t reserved;
+} qs_sched_opts;
+
+/* Build a schedule for an n-qubit gate list.  With fuse, gates are packed into
+ * clusters by the greedy closure rule (each cluster: the gates that can run on a
+ * qubit set S, S grown from a seed gate while |S| <= k_max, the largest cluster
+ * taken first), an all-diagonal cluster becomes a phase op, and every dense
+ * cluster's unitary is the FP64 product of its gates in ascending qubit order.
+ * Errors: QS_EINVAL (bad gate, opts). */
+int qs_schedule_build(int n, const qs_gate *gates, int n_gates, const qs_sched_opts *opts,
+                      qs_schedule **out);
+
+/* A schedule from explicit ops (the caller's own clustering): op i is dense
+ * (kinds[i] = QS_OP_DENSE: ks[i] qubits in qubits[5i..5i+ks[i]), unitary at
+ * pool[offsets[i]], 2^k x 2^k complex128 interleaved) or a table diagonal
+ * (QS_OP_DIAG, 2^k complex128 at pool[offsets[i]]). */
+int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const int *ks,
+                         const int *qubits, const int64_t *offsets,
+                         const double *pool, int64_t pool_len, qs_schedule **out);
+
+void qs_schedule_free(qs_schedule *sc);
+
+/* Bytes qs_run_circuit copies host -> device the first time it runs this
+ * schedule on a state of the given dtype (op matrices, tables, phase masks). */
+int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype);
+int qs_schedule_num_qubits(const qs_schedule *sc);
+int qs_schedule_num_ops(const qs_schedule *sc);
+
+typedef struct {
+    int32_t kind;                /* QS_OP_* */
+    int32_t k;                   /* qubits touched (dense/diag); phase: qubits in its support */
+    int32_t qubits[QS_MAX_K];    /* ascending (dense/diag) */
+    int32_t n_gates;             /* gates of the circuit in this op */
+    int32_t n_edges;             /* phase: CZ pairs */
+    int32_t reserved;
+} qs_op_info;
+
+/* Describe op i.  Optional outputs (NULL to skip): matrix (dense: 2^{2k}
+ * complex128 interleaved, qubits[j] <-> bit j; diag: 2^k), gate_idx (n_gates
+ * circuit indices in the order multiplied), coeff (phase: n integers mod 8),
+ * edges (phase: 2*n_edges). */
+int qs_schedule_op(const qs_schedule *sc, int i, qs_op_info *info, double *matrix,
+                   int32_t *gate_idx, int32_t *coeff, int32_t *edges);
+
+/* Apply every op of a schedule, in order, to the state (one HBM sweep per op). */
+int qs_run_circuit(qs_state *s, const qs_schedule *sc);
+
+/* As qs_run_circuit, recording a CUDA event before and after every op on the
+ * state's stream; waits for the stream and writes op i's device time in
+ * milliseconds to op_ms[i] (host, qs_schedule_num_ops entries). */
+int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *op_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_H */

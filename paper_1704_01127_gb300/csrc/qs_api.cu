@@ -1,0 +1,540 @@
+// State management, initial states, FP64 reductions (norm, probabilities,
+// entropy / Porter-Thomas moments) and sampling.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <vector>
+
+#include "qs_internal.h"
+
+namespace {
+thread_local char g_err[512] = "";
+
+int sm_count_dev()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return qs_fail(e == cudaErrorMemoryAllocation ? QS_ENOMEM : QS_ECUDA, "%s: %s", what,
+                   cudaGetErrorString(e));
+}
+
+#define QS_CUDA(call, what)                          \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t amp_bytes(int dtype) { return dtype == QS_C128 ? 16 : 8; }
+
+// ------------------------------------------------------------------ kernels
+
+template <typename C>
+__global__ void k_fill_zero(C *psi, uint64_t N)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        C z;
+        z.x = 0;
+        z.y = 0;
+        psi[i] = z;
+    }
+}
+
+template <typename C, typename R>
+__global__ void k_fill_uniform(C *psi, uint64_t N, R a)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        C z;
+        z.x = a;
+        z.y = 0;
+        psi[i] = z;
+    }
+}
+
+template <typename C>
+__global__ void k_set_one(C *psi, uint64_t x)
+{
+    C o;
+    o.x = 1;
+    o.y = 0;
+    psi[x] = o;
+}
+
+// p = fl(fl(re^2) + fl(im^2)) in FP64 (no contraction into an FMA).
+__device__ __forceinline__ double prob(double2 a)
+{
+    return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
+}
+__device__ __forceinline__ double prob(float2 a)
+{
+    double x = a.x, y = a.y;
+    return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
+}
+
+template <typename C>
+__global__ void k_probs(const C *__restrict__ psi, uint64_t first, uint64_t count, double *__restrict__ p)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        p[i] = prob(psi[first + i]);
+}
+
+// Per-block FP64 partial sums of (p, -p ln p, N p, (N p)^2); NSTAT = 1 or 4.
+template <typename C, int NSTAT>
+__global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *__restrict__ part)
+{
+    double acc[NSTAT];
+#pragma unroll
+    for (int j = 0; j < NSTAT; j++) acc[j] = 0;
+    const double Nd = (double)N;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        double p = prob(psi[i]);
+        acc[0] += p;
+        if (NSTAT == 4) {
+            if (p > 0) acc[1] -= p * log(p);
+            double np = Nd * p;
+            acc[2] += np;
+            acc[3] += np * np;
+        }
+    }
+    __shared__ double red[NSTAT][32];
+#pragma unroll
+    for (int j = 0; j < NSTAT; j++) {
+        double v = acc[j];
+        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int j = 0; j < NSTAT; j++) {
+            double v = threadIdx.x < nw ? red[j][threadIdx.x] : 0.0;
+            for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (threadIdx.x == 0) part[(size_t)blockIdx.x * NSTAT + j] = v;
+        }
+    }
+}
+
+template <int NSTAT>
+__global__ void k_stats_final(const double *__restrict__ part, int nblocks, double *__restrict__ out)
+{
+    // one warp; fixed order for reproducibility
+    double acc[NSTAT];
+#pragma unroll
+    for (int j = 0; j < NSTAT; j++) acc[j] = 0;
+    for (int b = threadIdx.x; b < nblocks; b += 32)
+#pragma unroll
+        for (int j = 0; j < NSTAT; j++) acc[j] += part[(size_t)b * NSTAT + j];
+#pragma unroll
+    for (int j = 0; j < NSTAT; j++) {
+        double v = acc[j];
+        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) out[j] = v;
+    }
+}
+
+// ------------------------------------------------------------------ sampling
+// Pairwise sums over fixed power-of-two blocks: lane l of a warp reduces its
+// contiguous len/32 values as a perfect binary tree, then the 32 lane results
+// combine as the top five tree levels (lane pairs (0,1), (2,3), ... first).
+
+template <typename C>
+__device__ double load_p(const C *psi, uint64_t i) { return prob(psi[i]); }
+__device__ double load_p(const double *v, uint64_t i) { return v[i]; }
+
+template <typename T>
+__device__ double tree_sum_serial(const T *src, uint64_t start, int len)
+{
+    double buf[32];
+    for (int i = 0; i < len; i++) buf[i] = load_p(src, start + i);
+    for (int w = len; w > 1; w >>= 1)
+        for (int i = 0; i < w / 2; i++) buf[i] = buf[2 * i] + buf[2 * i + 1];
+    return buf[0];
+}
+
+// One warp per segment of `len` (power of two, >= 32) values.
+template <typename T>
+__global__ void k_segment_sums(const T *__restrict__ src, uint64_t nseg, int len, double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int per = len >> 5;
+    for (uint64_t seg = warp; seg < nseg; seg += nwarps) {
+        double v = tree_sum_serial(src, seg * (uint64_t)len + (uint64_t)lane * per, per);
+        for (int o = 1; o < 32; o <<= 1) {
+            double w = __shfl_down_sync(0xffffffffu, v, o);
+            if ((lane & (2 * o - 1)) == 0) v = v + w;
+        }
+        if (lane == 0) out[seg] = v;
+    }
+}
+
+// Segments shorter than a warp: one thread per segment.
+template <typename T>
+__global__ void k_segment_sums_small(const T *__restrict__ src, uint64_t nseg, int len, double *__restrict__ out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t seg = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; seg < nseg; seg += stride)
+        out[seg] = tree_sum_serial(src, seg * (uint64_t)len, len);
+}
+
+// Q_0 = 0, Q_{s+1} = Q_s + T_s (one thread); R_{s,0} = Q_s, R_{s,j+1} = R_{s,j} + S_{sG+j}.
+__global__ void k_prefix_super(const double *__restrict__ T, uint64_t ns, double *__restrict__ Q)
+{
+    double q = 0.0;
+    for (uint64_t s = 0; s < ns; s++) {
+        Q[s] = q;
+        q = q + T[s];
+    }
+}
+
+__global__ void k_prefix_blocks(const double *__restrict__ S, const double *__restrict__ Q, uint64_t ns,
+                                uint64_t G, double *__restrict__ R)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += stride) {
+        double r = Q[s];
+        for (uint64_t j = 0; j < G; j++) {
+            R[s * G + j] = r;
+            r = r + S[s * G + j];
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t j)
+{
+    uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// last index in [0, len) with a[idx] <= u (a non-decreasing, a[0] <= u)
+__device__ uint64_t last_le(const double *a, uint64_t len, double u)
+{
+    uint64_t lo = 0, hi = len;   // invariant: a[lo] <= u, answer in [lo, hi)
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename C>
+__global__ void k_draw(const C *__restrict__ psi, const double *__restrict__ Q, const double *__restrict__ R,
+                       uint64_t ns, uint64_t G, uint64_t B, uint64_t seed, int64_t m, uint64_t *__restrict__ out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        double u = (double)(splitmix64(seed, (uint64_t)j) >> 11) * 0x1.0p-53;
+        uint64_t s = last_le(Q, ns, u);
+        uint64_t jb = last_le(R + s * G, G, u);
+        uint64_t b = s * G + jb;
+        double c = R[b];
+        uint64_t i = B - 1;
+        for (uint64_t x = 0; x < B; x++) {
+            c = c + prob(psi[b * B + x]);
+            if (c > u) { i = x; break; }
+        }
+        out[j] = b * B + i;
+    }
+}
+
+template <typename C>
+int stats_impl(qs_state *s, double *out, int nstat)
+{
+    uint64_t N = 1ULL << s->n;
+    const int block = 256;
+    int grid = (int)std::min<uint64_t>((N + block - 1) / block, (uint64_t)sm_count_dev() * 4);
+    void *scr;
+    int rc = qs_state_scratch(s, sizeof(double) * (size_t)(grid + 1) * 4, &scr);
+    if (rc) return rc;
+    double *part = (double *)scr, *res = part + (size_t)grid * 4;
+    cudaStream_t st = (cudaStream_t)s->stream;
+    if (nstat == 1) {
+        k_stats_partial<C, 1><<<grid, block, 0, st>>>((const C *)s->amp, N, part);
+        k_stats_final<1><<<1, 32, 0, st>>>(part, grid, res);
+    } else {
+        k_stats_partial<C, 4><<<grid, block, 0, st>>>((const C *)s->amp, N, part);
+        k_stats_final<4><<<1, 32, 0, st>>>(part, grid, res);
+    }
+    QS_CUDA(cudaGetLastError(), "stats launch");
+    QS_CUDA(cudaMemcpyAsync(out, res, sizeof(double) * nstat, cudaMemcpyDeviceToHost, st), "stats copy");
+    QS_CUDA(cudaStreamSynchronize(st), "stats sync");
+    if (nstat == 4) {
+        out[2] /= (double)N;
+        out[3] /= (double)N;
+    }
+    return QS_OK;
+}
+
+template <typename C>
+int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out)
+{
+    const uint64_t N = 1ULL << s->n;
+    const uint64_t B = std::min<uint64_t>(N, 1024), nb = N / B;
+    const uint64_t G = std::min<uint64_t>(nb, 1024), ns = nb / G;
+    size_t bytes = sizeof(double) * (2 * nb + 2 * ns) + sizeof(uint64_t) * (size_t)std::max<int64_t>(m, 1);
+    void *scr;
+    int rc = qs_state_scratch(s, bytes, &scr);
+    if (rc) return rc;
+    double *S = (double *)scr, *R = S + nb, *T = R + nb, *Q = T + ns;
+    uint64_t *dout = (uint64_t *)(Q + ns);
+    cudaStream_t st = (cudaStream_t)s->stream;
+    const int sms = sm_count_dev();
+    const C *psi = (const C *)s->amp;
+    if (B >= 32)
+        k_segment_sums<C><<<(int)std::min<uint64_t>((nb * 32 + 255) / 256, (uint64_t)sms * 16), 256, 0, st>>>(
+            psi, nb, (int)B, S);
+    else
+        k_segment_sums_small<C><<<1, 32, 0, st>>>(psi, nb, (int)B, S);
+    if (G >= 32)
+        k_segment_sums<double><<<(int)std::min<uint64_t>((ns * 32 + 255) / 256, (uint64_t)sms * 16), 256, 0, st>>>(
+            S, ns, (int)G, T);
+    else
+        k_segment_sums_small<double><<<1, 32, 0, st>>>(S, ns, (int)G, T);
+    k_prefix_super<<<1, 1, 0, st>>>(T, ns, Q);
+    k_prefix_blocks<<<(int)std::min<uint64_t>((ns + 127) / 128, 1024), 128, 0, st>>>(S, Q, ns, G, R);
+    if (m > 0)
+        k_draw<C><<<(int)std::min<int64_t>((m + 255) / 256, (int64_t)sms * 16), 256, 0, st>>>(
+            psi, Q, R, ns, G, B, seed, m, dout);
+    QS_CUDA(cudaGetLastError(), "sampling launch");
+    if (m > 0)
+        QS_CUDA(cudaMemcpyAsync(out, dout, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, st), "sample copy");
+    QS_CUDA(cudaStreamSynchronize(st), "sampling sync");
+    return QS_OK;
+}
+
+int make_state(int n, int dtype, void *stream, void *ptr, bool owned, qs_state **out)
+{
+    qs_state *s = new (std::nothrow) qs_state();
+    if (!s) return qs_fail(QS_ENOMEM, "out of host memory");
+    s->n = n;
+    s->dtype = dtype;
+    s->amp = ptr;
+    s->owned = owned;
+    s->stream = stream;
+    cudaGetDevice(&s->device);
+    *out = s;
+    return QS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- internals
+
+int qs_fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int qs_state_scratch(qs_state *s, size_t bytes, void **out)
+{
+    if (bytes > s->scratch_bytes) {
+        if (s->scratch) {
+            cudaStreamSynchronize((cudaStream_t)s->stream);
+            cudaFree(s->scratch);
+            s->scratch = nullptr;
+            s->scratch_bytes = 0;
+        }
+        size_t want = std::max<size_t>(bytes, 1 << 20);
+        cudaError_t e = cudaMalloc(&s->scratch, want);
+        if (e != cudaSuccess) {
+            s->scratch = nullptr;
+            return cuda_fail(e, "scratch allocation");
+        }
+        s->scratch_bytes = want;
+    }
+    *out = s->scratch;
+    return QS_OK;
+}
+
+// ------------------------------------------------------------------- C ABI
+
+extern "C" const char *qs_last_error(void) { return g_err; }
+
+extern "C" int qs_alloc(int n, int dtype, void *stream, qs_state **out)
+{
+    if (!out || n < 1 || n > QS_MAX_QUBITS || (dtype != QS_C64 && dtype != QS_C128))
+        return qs_fail(QS_EINVAL, "qs_alloc: n = %d, dtype = %d not supported", n, dtype);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, amp_bytes(dtype) << n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return qs_fail(QS_ENOMEM, "qs_alloc: %zu bytes: %s", amp_bytes(dtype) << n, cudaGetErrorString(e));
+    }
+    int rc = make_state(n, dtype, stream, p, true, out);
+    if (rc) cudaFree(p);
+    return rc;
+}
+
+extern "C" int qs_wrap(void *dev_ptr, int n, int dtype, void *stream, qs_state **out)
+{
+    if (!out || !dev_ptr || ((uintptr_t)dev_ptr & 15) || n < 1 || n > QS_MAX_QUBITS ||
+        (dtype != QS_C64 && dtype != QS_C128))
+        return qs_fail(QS_EINVAL, "qs_wrap: bad pointer, n or dtype");
+    return make_state(n, dtype, stream, dev_ptr, false, out);
+}
+
+extern "C" void qs_free(qs_state *s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize((cudaStream_t)s->stream);
+    else cudaDeviceSynchronize();
+    if (s->owned && s->amp) cudaFree(s->amp);
+    if (s->scratch) cudaFree(s->scratch);
+    if (s->pinned) cudaFreeHost(s->pinned);
+    delete s;
+}
+
+extern "C" int qs_num_qubits(const qs_state *s) { return s ? s->n : 0; }
+extern "C" int qs_dtype(const qs_state *s) { return s ? s->dtype : -1; }
+extern "C" void *qs_device_ptr(const qs_state *s) { return s ? s->amp : nullptr; }
+extern "C" int qs_set_stream(qs_state *s, void *stream)
+{
+    if (!s) return qs_fail(QS_EINVAL, "qs_set_stream: null state");
+    s->stream = stream;
+    return QS_OK;
+}
+
+extern "C" int qs_init_basis(qs_state *s, uint64_t x)
+{
+    if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_basis: null state");
+    if (x >> s->n) return qs_fail(QS_EINVAL, "qs_init_basis: index out of range");
+    uint64_t N = 1ULL << s->n;
+    int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count_dev() * 8);
+    cudaStream_t st = (cudaStream_t)s->stream;
+    if (s->dtype == QS_C128) {
+        k_fill_zero<double2><<<grid, 256, 0, st>>>((double2 *)s->amp, N);
+        k_set_one<double2><<<1, 1, 0, st>>>((double2 *)s->amp, x);
+    } else {
+        k_fill_zero<float2><<<grid, 256, 0, st>>>((float2 *)s->amp, N);
+        k_set_one<float2><<<1, 1, 0, st>>>((float2 *)s->amp, x);
+    }
+    QS_CUDA(cudaGetLastError(), "qs_init_basis");
+    return QS_OK;
+}
+
+extern "C" int qs_init_uniform(qs_state *s)
+{
+    if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_uniform: null state");
+    uint64_t N = 1ULL << s->n;
+    int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count_dev() * 8);
+    cudaStream_t st = (cudaStream_t)s->stream;
+    // 2^{-n/2}: exact power of two for even n; sqrt(0.5) * 2^{-(n-1)/2} for odd n
+    double a = (s->n % 2 == 0) ? ldexp(1.0, -s->n / 2) : sqrt(0.5) * ldexp(1.0, -(s->n - 1) / 2);
+    if (s->dtype == QS_C128)
+        k_fill_uniform<double2, double><<<grid, 256, 0, st>>>((double2 *)s->amp, N, a);
+    else
+        k_fill_uniform<float2, float><<<grid, 256, 0, st>>>((float2 *)s->amp, N, (float)a);
+    QS_CUDA(cudaGetLastError(), "qs_init_uniform");
+    return QS_OK;
+}
+
+extern "C" int qs_set_amplitudes(qs_state *s, const double *host)
+{
+    if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_set_amplitudes: null argument");
+    uint64_t N = 1ULL << s->n;
+    cudaStream_t st = (cudaStream_t)s->stream;
+    if (s->dtype == QS_C128) {
+        QS_CUDA(cudaMemcpyAsync(s->amp, host, 16 * N, cudaMemcpyHostToDevice, st), "qs_set_amplitudes");
+    } else {
+        std::vector<float> f(2 * N);
+        for (uint64_t i = 0; i < 2 * N; i++) f[i] = (float)host[i];
+        QS_CUDA(cudaMemcpyAsync(s->amp, f.data(), 8 * N, cudaMemcpyHostToDevice, st), "qs_set_amplitudes");
+    }
+    QS_CUDA(cudaStreamSynchronize(st), "qs_set_amplitudes sync");
+    return QS_OK;
+}
+
+extern "C" int qs_get_amplitudes(qs_state *s, double *host)
+{
+    if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_get_amplitudes: null argument");
+    uint64_t N = 1ULL << s->n;
+    cudaStream_t st = (cudaStream_t)s->stream;
+    if (s->dtype == QS_C128) {
+        QS_CUDA(cudaMemcpyAsync(host, s->amp, 16 * N, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes");
+        QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes sync");
+    } else {
+        std::vector<float> f(2 * N);
+        QS_CUDA(cudaMemcpyAsync(f.data(), s->amp, 8 * N, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes");
+        QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes sync");
+        for (uint64_t i = 0; i < 2 * N; i++) host[i] = (double)f[i];
+    }
+    return QS_OK;
+}
+
+extern "C" int qs_norm(qs_state *s, double *out)
+{
+    if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_norm: null argument");
+    return s->dtype == QS_C128 ? stats_impl<double2>(s, out, 1) : stats_impl<float2>(s, out, 1);
+}
+
+extern "C" int qs_stats(qs_state *s, double out[4])
+{
+    if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_stats: null argument");
+    return s->dtype == QS_C128 ? stats_impl<double2>(s, out, 4) : stats_impl<float2>(s, out, 4);
+}
+
+extern "C" int qs_probabilities(qs_state *s, double *out, int out_on_device)
+{
+    if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_probabilities: null argument");
+    const uint64_t N = 1ULL << s->n;
+    cudaStream_t st = (cudaStream_t)s->stream;
+    const int sms = sm_count_dev();
+    auto launch = [&](uint64_t first, uint64_t count, double *dst) {
+        int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)sms * 8);
+        if (s->dtype == QS_C128)
+            k_probs<double2><<<grid, 256, 0, st>>>((const double2 *)s->amp, first, count, dst);
+        else
+            k_probs<float2><<<grid, 256, 0, st>>>((const float2 *)s->amp, first, count, dst);
+    };
+    if (out_on_device) {
+        launch(0, N, out);
+        QS_CUDA(cudaGetLastError(), "qs_probabilities");
+        return QS_OK;
+    }
+    // host output: chunks of at most 2^25 values through the scratch buffer
+    const uint64_t chunk = std::min<uint64_t>(N, 1ULL << 25);
+    void *scr;
+    int rc = qs_state_scratch(s, sizeof(double) * chunk, &scr);
+    if (rc) return rc;
+    for (uint64_t first = 0; first < N; first += chunk) {
+        launch(first, chunk, (double *)scr);
+        QS_CUDA(cudaGetLastError(), "qs_probabilities");
+        QS_CUDA(cudaMemcpyAsync(out + first, scr, sizeof(double) * chunk, cudaMemcpyDeviceToHost, st),
+                "qs_probabilities copy");
+    }
+    QS_CUDA(cudaStreamSynchronize(st), "qs_probabilities sync");
+    return QS_OK;
+}
+
+extern "C" int qs_sample(qs_state *s, uint64_t seed, int64_t m, uint64_t *out)
+{
+    if (!s || !s->amp || m < 0 || (m > 0 && !out)) return qs_fail(QS_EINVAL, "qs_sample: bad arguments");
+    return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out) : sample_impl<float2>(s, seed, m, out);
+}
+
+extern "C" int qs_synchronize(qs_state *s)
+{
+    if (!s) return qs_fail(QS_EINVAL, "qs_synchronize: null state");
+    QS_CUDA(cudaStreamSynchronize((cudaStream_t)s->stream), "qs_synchronize");
+    return QS_OK;
+}

@@ -1,0 +1,509 @@
+// State sweeps of the hot path: dense k-qubit cluster apply (Sec. 3.2), table
+// diagonals and CZ/T phase products (Sec. 2, Sec. 3.5), and the schedule runner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "qs_internal.h"
+
+namespace {
+
+template <typename R> struct cplx;
+template <> struct cplx<double> { using t = double2; };
+template <> struct cplx<float> { using t = float2; };
+
+struct Targets {
+    int q[QS_MAX_K];   // ascending
+};
+
+int g_sms = 0;
+int sm_count()
+{
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 1;
+    }
+    return g_sms;
+}
+
+// Insert a zero bit at each (ascending) target position: group id -> index of
+// the group's x = 0 member (Sec. 3.2: the c bits fill the non-target positions).
+template <int K>
+__device__ __forceinline__ uint64_t group_base(uint64_t g, const Targets &t)
+{
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        uint64_t lo = g & ((1ULL << t.q[j]) - 1);
+        g = ((g ^ lo) << 1) | lo;
+    }
+    return g;
+}
+
+template <int K>
+__device__ __forceinline__ uint64_t member_offset(int x, const Targets &t)
+{
+    uint64_t o = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++)
+        if ((x >> j) & 1) o |= 1ULL << t.q[j];
+    return o;
+}
+
+// Dense k-qubit cluster: one thread per group c, the 2^K amplitudes gathered at
+// strides 2^{q_j} into registers, v <- U v, scattered back in place.  Each
+// complex multiply-accumulate is the pair of real FMA updates of Eqs. (2)-(3):
+// acc += (v_R m_R, v_I m_R) then acc += (-v_I m_I, v_R m_I).  U (row-major,
+// ascending qubit order) is staged once per CTA in shared memory and read as a
+// warp-uniform broadcast.  Consecutive threads take consecutive groups, so for
+// targets above bit 4 every gathered row of a warp is one contiguous segment.
+template <typename R, int K>
+__global__ void __launch_bounds__(128)
+k_dense(typename cplx<R>::t *__restrict__ psi, uint64_t n_groups, Targets t,
+        const R *__restrict__ Ug)
+{
+    using C = typename cplx<R>::t;
+    constexpr int D = 1 << K;
+    __shared__ C Us[D * D];
+    for (int i = threadIdx.x; i < D * D; i += blockDim.x)
+        Us[i] = reinterpret_cast<const C *>(Ug)[i];
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += stride) {
+        C *p = psi + group_base<K>(g, t);
+        C v[D];
+#pragma unroll
+        for (int x = 0; x < D; x++) v[x] = p[member_offset<K>(x, t)];
+#pragma unroll
+        for (int l = 0; l < D; l++) {
+            R ar = 0, ai = 0;
+#pragma unroll
+            for (int x = 0; x < D; x++) {
+                C m = Us[l * D + x];
+                ar = fma(v[x].x, m.x, ar);
+                ai = fma(v[x].y, m.x, ai);
+                ar = fma(-v[x].y, m.y, ar);
+                ai = fma(v[x].x, m.y, ai);
+            }
+            C o;
+            o.x = ar;
+            o.y = ai;
+            p[member_offset<K>(l, t)] = o;
+        }
+    }
+}
+
+// Table diagonal on up to QS_MAX_DIAG_K qubits: psi_i *= d[x(i)].
+template <typename R>
+__global__ void k_diag(typename cplx<R>::t *__restrict__ psi, uint64_t N, int k, const int *__restrict__ qg,
+                       const R *__restrict__ dg)
+{
+    using C = typename cplx<R>::t;
+    __shared__ int q[QS_MAX_DIAG_K];
+    if (threadIdx.x < k) q[threadIdx.x] = qg[threadIdx.x];
+    __syncthreads();
+    const C *d = reinterpret_cast<const C *>(dg);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        int x = 0;
+        for (int j = 0; j < k; j++) x |= (int)((i >> q[j]) & 1) << j;
+        C m = __ldg(&d[x]);
+        C a = psi[i], o;
+        o.x = a.x * m.x - a.y * m.y;
+        o.y = a.x * m.y + a.y * m.x;
+        psi[i] = o;
+    }
+}
+
+// Multiply by e^{i pi m / 4}: an odd m first takes one factor
+// e^{i pi/4} = (1 + i)/sqrt(2), the rest is a quarter turn (no arithmetic).
+template <typename C, typename R>
+__device__ __forceinline__ C rotate8(C a, int m)
+{
+    if (m & 1) {
+        const R r = (R)0.70710678118654752440;
+        C b;
+        b.x = (a.x - a.y) * r;
+        b.y = (a.x + a.y) * r;
+        a = b;
+    }
+    C o;
+    switch ((m >> 1) & 3) {
+    case 0: o = a; break;
+    case 1: o.x = -a.y; o.y = a.x; break;
+    case 2: o.x = -a.x; o.y = -a.y; break;
+    default: o.x = a.y; o.y = -a.x; break;
+    }
+    return o;
+}
+
+// Product of T-type phases and CZ signs (Sec. 2, Sec. 3.5): the exponent
+// m(i) = sum_q c_q i_q + 4 sum_{(a,b)} i_a i_b mod 8 is evaluated with popcounts
+// on the index bits; CZ-only ops cost no floating-point work.
+template <typename R>
+__global__ void k_phase(typename cplx<R>::t *__restrict__ psi, uint64_t N,
+                        const qs_phase_dev *__restrict__ ph, int n_act)
+{
+    using C = typename cplx<R>::t;
+    __shared__ uint64_t cm[3];
+    __shared__ uint64_t part[64];
+    __shared__ int act[64];
+    if (threadIdx.x < 3) cm[threadIdx.x] = ph->cmask[threadIdx.x];
+    const qs_phase_term *terms = reinterpret_cast<const qs_phase_term *>(ph + 1);
+    for (int i = threadIdx.x; i < n_act; i += blockDim.x) {
+        part[i] = terms[i].partners;
+        act[i] = terms[i].a;
+    }
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        int m = __popcll(i & cm[0]) + 2 * __popcll(i & cm[1]) + 4 * __popcll(i & cm[2]);
+        int par = 0;
+        for (int t = 0; t < n_act; t++)
+            if ((i >> act[t]) & 1) par ^= __popcll(i & part[t]);
+        m = (m + 4 * (par & 1)) & 7;
+        if (m) psi[i] = rotate8<C, R>(psi[i], m);
+    }
+}
+
+int grid_for(uint64_t work, int block, int per_sm)
+{
+    uint64_t want = (work + block - 1) / block;
+    uint64_t cap = (uint64_t)sm_count() * per_sm;
+    if (want < 1) want = 1;
+    return (int)std::min<uint64_t>(want, cap);
+}
+
+template <typename R, int K>
+int launch_dense_t(qs_state *s, const int *q, const void *U)
+{
+    Targets t;
+    for (int j = 0; j < K; j++) t.q[j] = q[j];
+    uint64_t groups = 1ULL << (s->n - K);
+    const int block = 128;
+    int grid = grid_for(groups, block, 8);
+    k_dense<R, K><<<grid, block, 0, (cudaStream_t)s->stream>>>(
+        reinterpret_cast<typename cplx<R>::t *>(s->amp), groups, t, reinterpret_cast<const R *>(U));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "k_dense launch: %s", cudaGetErrorString(e));
+}
+
+template <typename R>
+int launch_dense_r(qs_state *s, const int *q, int k, const void *U)
+{
+    switch (k) {
+    case 1: return launch_dense_t<R, 1>(s, q, U);
+    case 2: return launch_dense_t<R, 2>(s, q, U);
+    case 3: return launch_dense_t<R, 3>(s, q, U);
+    case 4: return launch_dense_t<R, 4>(s, q, U);
+    case 5: return launch_dense_t<R, 5>(s, q, U);
+    default: return qs_fail(QS_EINVAL, "dense cluster of %d qubits", k);
+    }
+}
+
+}  // namespace
+
+int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix)
+{
+    return s->dtype == QS_C128 ? launch_dense_r<double>(s, sorted_qubits, k, dev_matrix)
+                               : launch_dense_r<float>(s, sorted_qubits, k, dev_matrix);
+}
+
+int qs_launch_diag(qs_state *s, const int *dev_qubits, int k, const void *dev_table)
+{
+    uint64_t N = 1ULL << s->n;
+    const int block = 256;
+    int grid = grid_for(N, block, 8);
+    cudaStream_t st = (cudaStream_t)s->stream;
+    if (s->dtype == QS_C128)
+        k_diag<double><<<grid, block, 0, st>>>((double2 *)s->amp, N, k, dev_qubits, (const double *)dev_table);
+    else
+        k_diag<float><<<grid, block, 0, st>>>((float2 *)s->amp, N, k, dev_qubits, (const float *)dev_table);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "k_diag launch: %s", cudaGetErrorString(e));
+}
+
+int qs_launch_phase(qs_state *s, const void *dev_phase, int n_act)
+{
+    uint64_t N = 1ULL << s->n;
+    const int block = 256;
+    int grid = grid_for(N, block, 8);
+    cudaStream_t st = (cudaStream_t)s->stream;
+    if (s->dtype == QS_C128)
+        k_phase<double><<<grid, block, 0, st>>>((double2 *)s->amp, N, (const qs_phase_dev *)dev_phase, n_act);
+    else
+        k_phase<float><<<grid, block, 0, st>>>((float2 *)s->amp, N, (const qs_phase_dev *)dev_phase, n_act);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "k_phase launch: %s", cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+// Sorted copy of (qubits, matrix): ascending qubit order, the matrix permuted so
+// that bit j of its index belongs to the j-th smallest qubit (Sec. 3.2).
+void sort_targets(const int *qubits, int k, const double *U, bool dense, int *qs_out,
+                  std::vector<double> &M)
+{
+    int perm[QS_MAX_DIAG_K];
+    for (int j = 0; j < k; j++) perm[j] = j;
+    std::sort(perm, perm + k, [&](int a, int b) { return qubits[a] < qubits[b]; });
+    for (int j = 0; j < k; j++) qs_out[j] = qubits[perm[j]];
+    auto remap = [&](int xn) {
+        int xo = 0;
+        for (int j = 0; j < k; j++) xo |= ((xn >> j) & 1) << perm[j];
+        return xo;
+    };
+    const int d = 1 << k;
+    if (dense) {
+        M.resize(2 * d * d);
+        for (int r = 0; r < d; r++)
+            for (int c = 0; c < d; c++) {
+                int ro = remap(r), co = remap(c);
+                M[2 * (r * d + c)] = U[2 * (ro * d + co)];
+                M[2 * (r * d + c) + 1] = U[2 * (ro * d + co) + 1];
+            }
+    } else {
+        M.resize(2 * d);
+        for (int x = 0; x < d; x++) {
+            M[2 * x] = U[2 * remap(x)];
+            M[2 * x + 1] = U[2 * remap(x) + 1];
+        }
+    }
+}
+
+// Pack FP64 values into the state's real type.
+std::vector<uint8_t> to_real(const std::vector<double> &v, int dtype)
+{
+    std::vector<uint8_t> out;
+    if (dtype == QS_C128) {
+        out.resize(v.size() * sizeof(double));
+        std::memcpy(out.data(), v.data(), out.size());
+    } else {
+        out.resize(v.size() * sizeof(float));
+        float *f = reinterpret_cast<float *>(out.data());
+        for (size_t i = 0; i < v.size(); i++) f[i] = (float)v[i];
+    }
+    return out;
+}
+
+int check_state(qs_state *s, const char *who)
+{
+    if (!s || !s->amp) return qs_fail(QS_EINVAL, "%s: null state", who);
+    return QS_OK;
+}
+
+// Stage a small operand block in the state's scratch (stream-ordered: the copy
+// runs after earlier kernels on the stream have finished reading the slot).
+int stage(qs_state *s, const void *host, size_t bytes, void **dev)
+{
+    void *p;
+    int rc = qs_state_scratch(s, bytes, &p);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(p, host, bytes, cudaMemcpyHostToDevice, (cudaStream_t)s->stream);
+    if (e != cudaSuccess) return qs_fail(QS_ECUDA, "operand copy: %s", cudaGetErrorString(e));
+    *dev = p;
+    return QS_OK;
+}
+
+int check_qubits(qs_state *s, const int *qubits, int k, int kmax, const char *who)
+{
+    if (!qubits || k < 1 || k > kmax || k > s->n)
+        return qs_fail(QS_EINVAL, "%s: k = %d not in [1, %d] or above n", who, k, kmax);
+    uint64_t seen = 0;
+    for (int j = 0; j < k; j++) {
+        if (qubits[j] < 0 || qubits[j] >= s->n)
+            return qs_fail(QS_EINVAL, "%s: qubit %d out of range", who, qubits[j]);
+        if ((seen >> qubits[j]) & 1) return qs_fail(QS_EINVAL, "%s: qubit %d repeated", who, qubits[j]);
+        seen |= 1ULL << qubits[j];
+    }
+    return QS_OK;
+}
+
+// Device image of a schedule for one dtype: every op's data, 256-byte aligned.
+std::vector<uint8_t> schedule_blob(const qs_schedule *sc, int dtype, std::vector<size_t> &offset,
+                                   std::vector<int> &n_act)
+{
+    std::vector<uint8_t> blob;
+    offset.assign(sc->ops.size(), 0);
+    n_act.assign(sc->ops.size(), 0);
+    for (size_t i = 0; i < sc->ops.size(); i++) {
+        const qs_op_host &op = sc->ops[i];
+        std::vector<uint8_t> part;
+        if (op.kind == QS_OP_PHASE) {
+            part = qs_pack_phase(sc->n, op.coeff, op.edges, &n_act[i]);
+        } else if (op.kind == QS_OP_DIAG) {
+            std::vector<uint8_t> tab = to_real(op.matrix, dtype);
+            part.resize(64 + tab.size());
+            std::memcpy(part.data(), op.qubits, sizeof(int) * op.k);
+            std::memcpy(part.data() + 64, tab.data(), tab.size());
+        } else {
+            part = to_real(op.matrix, dtype);
+        }
+        size_t at = (blob.size() + 255) & ~(size_t)255;
+        blob.resize(at + part.size());
+        std::memcpy(blob.data() + at, part.data(), part.size());
+        offset[i] = at;
+    }
+    if (blob.empty()) blob.resize(256);
+    return blob;
+}
+
+int ensure_dev_schedule(qs_state *s, const qs_schedule *csc)
+{
+    qs_schedule *sc = const_cast<qs_schedule *>(csc);
+    qs_dev_sched &d = sc->dev[s->dtype];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (d.pool && d.device == dev) return QS_OK;
+    if (d.pool) {
+        cudaFree(d.pool);
+        d.pool = nullptr;
+    }
+    std::vector<uint8_t> blob = schedule_blob(sc, s->dtype, d.offset, d.n_act);
+    cudaError_t e = cudaMalloc(&d.pool, blob.size());
+    if (e != cudaSuccess) {
+        d.pool = nullptr;
+        return qs_fail(QS_ENOMEM, "schedule upload: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(d.pool, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return qs_fail(QS_ECUDA, "schedule upload: %s", cudaGetErrorString(e));
+    d.bytes = blob.size();
+    d.device = dev;
+    return QS_OK;
+}
+
+}  // namespace
+
+extern "C" int qs_apply_cluster(qs_state *s, const int *qubits, int k, const double *U)
+{
+    int rc = check_state(s, "qs_apply_cluster");
+    if (rc) return rc;
+    if ((rc = check_qubits(s, qubits, k, QS_MAX_K, "qs_apply_cluster"))) return rc;
+    if (!U) return qs_fail(QS_EINVAL, "qs_apply_cluster: null matrix");
+    int q[QS_MAX_K];
+    std::vector<double> M;
+    sort_targets(qubits, k, U, true, q, M);
+    std::vector<uint8_t> packed = to_real(M, s->dtype);
+    void *dU;
+    if ((rc = stage(s, packed.data(), packed.size(), &dU))) return rc;
+    return qs_launch_dense(s, q, k, dU);
+}
+
+extern "C" int qs_apply_diag(qs_state *s, const int *qubits, int k, const double *d)
+{
+    int rc = check_state(s, "qs_apply_diag");
+    if (rc) return rc;
+    if ((rc = check_qubits(s, qubits, k, QS_MAX_DIAG_K, "qs_apply_diag"))) return rc;
+    if (!d) return qs_fail(QS_EINVAL, "qs_apply_diag: null table");
+    int q[QS_MAX_DIAG_K];
+    std::vector<double> M;
+    sort_targets(qubits, k, d, false, q, M);
+    std::vector<uint8_t> tab = to_real(M, s->dtype);
+    std::vector<uint8_t> blob(64 + tab.size());
+    std::memcpy(blob.data(), q, sizeof(int) * k);
+    std::memcpy(blob.data() + 64, tab.data(), tab.size());
+    void *dev;
+    if ((rc = stage(s, blob.data(), blob.size(), &dev))) return rc;
+    return qs_launch_diag(s, (const int *)dev, k, (const uint8_t *)dev + 64);
+}
+
+extern "C" int qs_apply_phase(qs_state *s, const int *coeff, int n_edges, const int *edges)
+{
+    int rc = check_state(s, "qs_apply_phase");
+    if (rc) return rc;
+    if (!coeff || n_edges < 0 || (n_edges > 0 && !edges))
+        return qs_fail(QS_EINVAL, "qs_apply_phase: bad arguments");
+    std::vector<int32_t> c(coeff, coeff + s->n);
+    std::vector<std::pair<int, int>> e;
+    for (int i = 0; i < n_edges; i++) {
+        int a = edges[2 * i], b = edges[2 * i + 1];
+        if (a < 0 || a >= s->n || b < 0 || b >= s->n || a == b)
+            return qs_fail(QS_EINVAL, "qs_apply_phase: bad edge %d", i);
+        e.push_back({a, b});
+    }
+    int n_act;
+    std::vector<uint8_t> blob = qs_pack_phase(s->n, c, e, &n_act);
+    void *dev;
+    if ((rc = stage(s, blob.data(), blob.size(), &dev))) return rc;
+    return qs_launch_phase(s, dev, n_act);
+}
+
+extern "C" int qs_run_circuit(qs_state *s, const qs_schedule *sc)
+{
+    int rc = check_state(s, "qs_run_circuit");
+    if (rc) return rc;
+    if (!sc || sc->n != s->n) return qs_fail(QS_EINVAL, "qs_run_circuit: schedule/state qubit mismatch");
+    if ((rc = ensure_dev_schedule(s, sc))) return rc;
+    const qs_dev_sched &d = sc->dev[s->dtype];
+    for (size_t i = 0; i < sc->ops.size(); i++) {
+        const qs_op_host &op = sc->ops[i];
+        const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
+        if (op.kind == QS_OP_DENSE) {
+            rc = qs_launch_dense(s, op.qubits, op.k, data);
+        } else if (op.kind == QS_OP_DIAG) {
+            rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
+        } else {
+            rc = qs_launch_phase(s, data, d.n_act[i]);
+        }
+        if (rc) return rc;
+    }
+    return QS_OK;
+}
+
+extern "C" int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *op_ms)
+{
+    int rc = check_state(s, "qs_run_circuit_timed");
+    if (rc) return rc;
+    if (!sc || sc->n != s->n || !op_ms)
+        return qs_fail(QS_EINVAL, "qs_run_circuit_timed: bad schedule or output");
+    if ((rc = ensure_dev_schedule(s, sc))) return rc;
+    const qs_dev_sched &d = sc->dev[s->dtype];
+    cudaStream_t st = (cudaStream_t)s->stream;
+    size_t nops = sc->ops.size();
+    std::vector<cudaEvent_t> ev(nops + 1);
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return qs_fail(QS_ECUDA, "event create");
+    cudaEventRecord(ev[0], st);
+    for (size_t i = 0; i < nops && !rc; i++) {
+        const qs_op_host &op = sc->ops[i];
+        const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
+        if (op.kind == QS_OP_DENSE) rc = qs_launch_dense(s, op.qubits, op.k, data);
+        else if (op.kind == QS_OP_DIAG) rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
+        else rc = qs_launch_phase(s, data, d.n_act[i]);
+        cudaEventRecord(ev[i + 1], st);
+    }
+    if (!rc) {
+        cudaError_t e = cudaEventSynchronize(ev[nops]);
+        if (e != cudaSuccess) rc = qs_fail(QS_ECUDA, "qs_run_circuit_timed: %s", cudaGetErrorString(e));
+        for (size_t i = 0; i < nops && !rc; i++) cudaEventElapsedTime(&op_ms[i], ev[i], ev[i + 1]);
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
+extern "C" int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype)
+{
+    if (!sc || (dtype != QS_C64 && dtype != QS_C128)) return qs_fail(QS_EINVAL, "qs_schedule_upload_bytes");
+    std::vector<size_t> off;
+    std::vector<int> na;
+    return (int64_t)schedule_blob(sc, dtype, off, na).size();
+}
+
+extern "C" int qs_set_device(int device)
+{
+    cudaError_t e = cudaSetDevice(device);
+    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_set_device(%d): %s", device, cudaGetErrorString(e));
+}
+
+extern "C" void qs_schedule_free(qs_schedule *sc)
+{
+    if (!sc) return;
+    for (auto &d : sc->dev)
+        if (d.pool) cudaFree(d.pool);
+    delete sc;
+}

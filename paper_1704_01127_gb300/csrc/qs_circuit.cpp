@@ -1,0 +1,531 @@
+// Host side of the hot path: supremacy-circuit generation (Fig. 1 caption),
+// greedy gate clustering (Sec. 3.6, step 2), FP64 cluster unitaries in sorted
+// qubit order (Sec. 3.2) and diagonal phase ops (Sec. 3.5).
+#include <algorithm>
+#include <cstring>
+#include <set>
+#include <vector>
+
+#include "qs_internal.h"
+
+namespace {
+
+// ----------------------------------------------------------------- gates (Sec. 2)
+// 2x2 matrices, row-major (re, im) pairs.
+constexpr double kR = 0.70710678118654752440;   // 1/sqrt(2), correctly rounded
+
+void gate_matrix(int kind, double m[8])
+{
+    static const double H[8] = {kR, 0, kR, 0, kR, 0, -kR, 0};
+    static const double T[8] = {1, 0, 0, 0, 0, 0, kR, kR};          // diag(1, e^{i pi/4})
+    static const double TD[8] = {1, 0, 0, 0, 0, 0, kR, -kR};
+    static const double SX[8] = {0.5, 0.5, 0.5, -0.5, 0.5, -0.5, 0.5, 0.5};
+    static const double SY[8] = {0.5, 0.5, -0.5, -0.5, 0.5, 0.5, 0.5, 0.5};
+    static const double X[8] = {0, 0, 1, 0, 1, 0, 0, 0};
+    const double *src = H;
+    switch (kind) {
+    case QS_GATE_H: src = H; break;
+    case QS_GATE_T: src = T; break;
+    case QS_GATE_TDG: src = TD; break;
+    case QS_GATE_SQRT_X: src = SX; break;
+    case QS_GATE_SQRT_Y: src = SY; break;
+    case QS_GATE_X: src = X; break;
+    case QS_GATE_SQRT_XDG:    // adjoint: transpose and conjugate
+    case QS_GATE_SQRT_YDG: {
+        const double *b = kind == QS_GATE_SQRT_XDG ? SX : SY;
+        const int tr[4] = {0, 2, 1, 3};
+        for (int e = 0; e < 4; e++) { m[2 * e] = b[2 * tr[e]]; m[2 * e + 1] = -b[2 * tr[e] + 1]; }
+        return;
+    }
+    default: break;
+    }
+    std::memcpy(m, src, sizeof(double) * 8);
+}
+
+bool is_diagonal(int kind) { return kind == QS_GATE_T || kind == QS_GATE_TDG || kind == QS_GATE_CZ; }
+
+// ------------------------------------------------------- SplitMix64 (Steele et al.)
+uint64_t splitmix64(uint64_t seed, uint64_t j)
+{
+    uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// -------------------------------------------------------------- clustering helpers
+struct Clusterer {
+    int n;
+    const std::vector<qs_gate> &g;
+    std::vector<std::vector<int>> queue;   // per qubit, gate indices in order
+    std::vector<uint64_t> gmask;
+
+    Clusterer(int n_, const std::vector<qs_gate> &gates) : n(n_), g(gates), queue(n_)
+    {
+        gmask.resize(g.size());
+        for (size_t i = 0; i < g.size(); i++) {
+            gmask[i] = 1ULL << g[i].q0;
+            queue[g[i].q0].push_back((int)i);
+            if (g[i].q1 >= 0) {
+                gmask[i] |= 1ULL << g[i].q1;
+                queue[g[i].q1].push_back((int)i);
+            }
+        }
+    }
+
+    bool ready(const std::vector<int> &pos, int gi) const
+    {
+        uint64_t m = gmask[gi];
+        while (m) {
+            int q = __builtin_ctzll(m);
+            m &= m - 1;
+            if (pos[q] >= (int)queue[q].size() || queue[q][pos[q]] != gi) return false;
+        }
+        return true;
+    }
+
+    void advance(std::vector<int> &pos, int gi) const
+    {
+        uint64_t m = gmask[gi];
+        while (m) {
+            int q = __builtin_ctzll(m);
+            m &= m - 1;
+            pos[q]++;
+        }
+    }
+
+    std::vector<int> heads(const std::vector<int> &pos) const
+    {
+        std::vector<int> h;
+        for (int q = 0; q < n; q++)
+            if (pos[q] < (int)queue[q].size()) h.push_back(queue[q][pos[q]]);
+        std::sort(h.begin(), h.end());
+        h.erase(std::unique(h.begin(), h.end()), h.end());
+        return h;
+    }
+
+    // Gates runnable on qubit set S: ascending-qubit sweeps taking ready heads
+    // that act only inside S, repeated until a sweep takes nothing.
+    void closure(uint64_t S, const std::vector<int> &pos0, std::vector<int> &members,
+                 std::vector<int> &pos) const
+    {
+        pos = pos0;
+        members.clear();
+        bool changed = true;
+        while (changed) {
+            changed = false;
+            for (int q = 0; q < n; q++) {
+                if (!((S >> q) & 1)) continue;
+                while (pos[q] < (int)queue[q].size()) {
+                    int gi = queue[q][pos[q]];
+                    if ((gmask[gi] & ~S) || !ready(pos, gi)) break;
+                    members.push_back(gi);
+                    advance(pos, gi);
+                    changed = true;
+                }
+            }
+        }
+    }
+
+    void grow(const std::vector<int> &pos, int seed, int k_max, std::vector<int> &members,
+              uint64_t &S) const
+    {
+        S = gmask[seed];
+        std::vector<int> after;
+        closure(S, pos, members, after);
+        std::vector<int> m2, a2, best_m, best_a;
+        for (;;) {
+            bool have = false;
+            int best_len = 0, best_bits = 0, best_g = 0;
+            uint64_t best_S = 0;
+            for (int gi : heads(after)) {
+                uint64_t qs = gmask[gi];
+                if (!(qs & ~S)) continue;
+                uint64_t S2 = S | qs;
+                int bits = __builtin_popcountll(S2);
+                if (bits > k_max) continue;
+                closure(S2, pos, m2, a2);
+                int len = (int)m2.size();
+                // key (len, -bits, -g), larger wins
+                bool better = !have || len > best_len ||
+                              (len == best_len && (bits < best_bits ||
+                                                   (bits == best_bits && gi < best_g)));
+                if (better) {
+                    have = true;
+                    best_len = len; best_bits = bits; best_g = gi; best_S = S2;
+                    best_m = m2; best_a = a2;
+                }
+            }
+            if (!have || best_len <= (int)members.size()) break;
+            S = best_S;
+            members = best_m;
+            after = best_a;
+        }
+    }
+
+    std::vector<std::vector<int>> run(int k_max) const
+    {
+        std::vector<int> pos(n, 0);
+        size_t remaining = g.size();
+        std::vector<std::vector<int>> out;
+        std::vector<int> members;
+        while (remaining) {
+            bool have = false;
+            std::vector<int> best;
+            int best_len = 0, best_bits = 0, best_s = 0;
+            for (int s : heads(pos)) {
+                if (!ready(pos, s)) continue;
+                uint64_t S;
+                grow(pos, s, k_max, members, S);
+                int len = (int)members.size(), bits = __builtin_popcountll(S);
+                bool better = !have || len > best_len ||
+                              (len == best_len && (bits < best_bits ||
+                                                   (bits == best_bits && s < best_s)));
+                if (better) {
+                    have = true;
+                    best = members; best_len = len; best_bits = bits; best_s = s;
+                }
+            }
+            for (int gi : best) advance(pos, gi);
+            remaining -= best.size();
+            out.push_back(best);
+        }
+        return out;
+    }
+};
+
+// U <- G U for a 1-qubit gate on position j of a 2^k space (columns of U are
+// updated pairwise, Sec. 2 Kronecker rule restricted to the cluster's qubits).
+void left_apply_1q(std::vector<double> &U, int k, int j, const double m[8])
+{
+    const int d = 1 << k;
+    for (int r0 = 0; r0 < d; r0++) {
+        if ((r0 >> j) & 1) continue;
+        int r1 = r0 | (1 << j);
+        for (int c = 0; c < d; c++) {
+            double ar = U[2 * (r0 * d + c)], ai = U[2 * (r0 * d + c) + 1];
+            double br = U[2 * (r1 * d + c)], bi = U[2 * (r1 * d + c) + 1];
+            U[2 * (r0 * d + c)] = (m[0] * ar - m[1] * ai) + (m[2] * br - m[3] * bi);
+            U[2 * (r0 * d + c) + 1] = (m[0] * ai + m[1] * ar) + (m[2] * bi + m[3] * br);
+            U[2 * (r1 * d + c)] = (m[4] * ar - m[5] * ai) + (m[6] * br - m[7] * bi);
+            U[2 * (r1 * d + c) + 1] = (m[4] * ai + m[5] * ar) + (m[6] * bi + m[7] * br);
+        }
+    }
+}
+
+void left_apply_cz(std::vector<double> &U, int k, int ja, int jb)
+{
+    const int d = 1 << k;
+    for (int r = 0; r < d; r++) {
+        if (((r >> ja) & 1) && ((r >> jb) & 1)) {
+            for (int c = 0; c < 2 * d; c++) U[2 * r * d + c] = -U[2 * r * d + c];
+        }
+    }
+}
+
+bool check_gate(int n, const qs_gate &g)
+{
+    if (g.kind < QS_GATE_H || g.kind > QS_GATE_SQRT_YDG) return false;
+    if (g.q0 < 0 || g.q0 >= n) return false;
+    if (g.kind == QS_GATE_CZ) return g.q1 >= 0 && g.q1 < n && g.q1 != g.q0;
+    return g.q1 < 0;
+}
+
+void make_phase(int n, const std::vector<qs_gate> &g, const std::vector<int> &members,
+                qs_op_host &op)
+{
+    op.kind = QS_OP_PHASE;
+    op.gates.assign(members.begin(), members.end());
+    op.coeff.assign(n, 0);
+    op.edges.clear();
+    uint64_t support = 0;
+    for (int gi : members) {
+        const qs_gate &x = g[gi];
+        support |= 1ULL << x.q0;
+        if (x.kind == QS_GATE_CZ) {
+            support |= 1ULL << x.q1;
+            op.edges.push_back({x.q0, x.q1});
+        } else {
+            op.coeff[x.q0] = (op.coeff[x.q0] + (x.kind == QS_GATE_T ? 1 : 7)) & 7;
+        }
+    }
+    op.k = __builtin_popcountll(support);
+    int j = 0;
+    for (int q = 0; q < n && j < QS_MAX_K; q++)
+        if ((support >> q) & 1) op.qubits[j++] = q;
+}
+
+void make_dense(const std::vector<qs_gate> &g, const std::vector<int> &members, qs_op_host &op)
+{
+    op.kind = QS_OP_DENSE;
+    op.gates.assign(members.begin(), members.end());
+    uint64_t support = 0;
+    for (int gi : members) {
+        support |= 1ULL << g[gi].q0;
+        if (g[gi].q1 >= 0) support |= 1ULL << g[gi].q1;
+    }
+    int k = 0, where[64];
+    for (int q = 0; q < 64; q++)
+        if ((support >> q) & 1) { where[q] = k; op.qubits[k++] = q; }
+    op.k = k;
+    const int d = 1 << k;
+    op.matrix.assign(2 * d * d, 0.0);
+    for (int r = 0; r < d; r++) op.matrix[2 * (r * d + r)] = 1.0;
+    for (int gi : members) {
+        const qs_gate &x = g[gi];
+        if (x.kind == QS_GATE_CZ) {
+            left_apply_cz(op.matrix, k, where[x.q0], where[x.q1]);
+        } else {
+            double m[8];
+            gate_matrix(x.kind, m);
+            left_apply_1q(op.matrix, k, where[x.q0], m);
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ public API
+
+extern "C" int qs_supremacy_circuit(int rows, int cols, const int *removed_rc, int n_removed,
+                                    int cz_cycles, uint64_t seed, int *n_qubits,
+                                    qs_gate *gates, int max_gates, int *n_gates)
+{
+    if (rows < 1 || cols < 1 || rows * cols > 4096 || cz_cycles < 0 || n_removed < 0 ||
+        (n_removed > 0 && !removed_rc) || !n_qubits || !n_gates || max_gates < 0 ||
+        (max_gates > 0 && !gates))
+        return qs_fail(QS_EINVAL, "qs_supremacy_circuit: bad arguments");
+    std::vector<int> id(rows * cols, 0);
+    for (int i = 0; i < n_removed; i++) {
+        int r = removed_rc[2 * i], c = removed_rc[2 * i + 1];
+        if (r < 0 || r >= rows || c < 0 || c >= cols)
+            return qs_fail(QS_EINVAL, "qs_supremacy_circuit: removed site out of the grid");
+        id[r * cols + c] = -1;
+    }
+    int n = 0;
+    for (int i = 0; i < rows * cols; i++)
+        if (id[i] == 0) id[i] = n++; else id[i] = -1;
+    if (n > QS_MAX_QUBITS || n < 1)
+        return qs_fail(QS_EINVAL, "qs_supremacy_circuit: %d qubits out of range", n);
+    *n_qubits = n;
+    std::vector<qs_gate> out;
+    for (int q = 0; q < n; q++) out.push_back({0, QS_GATE_H, q, -1});
+    // layouts: {horizontal?, a, b}
+    static const int L[8][3] = {{1, 1, 0}, {0, 0, 0}, {1, 0, 0}, {0, 1, 0},
+                                {0, 0, 1}, {1, 1, 1}, {0, 1, 1}, {1, 0, 1}};
+    std::vector<int> last(n, -1);          // previous single-qubit gate kind
+    std::vector<char> prev_cz(n, 0), in_cz(n, 0);
+    uint64_t draw = 0;
+    for (int t = 1; t <= cz_cycles; t++) {
+        const int *lay = L[(t - 1) % 8];
+        std::vector<std::pair<int, int>> edges;
+        for (int r = 0; r < rows; r++)
+            for (int c = 0; c < cols; c++) {
+                int a = id[r * cols + c];
+                if (a < 0) continue;
+                int r2 = r, c2 = c;
+                if (lay[0]) { if (c % 2 != lay[1] || r % 2 != lay[2]) continue; c2 = c + 1; }
+                else { if (r % 2 != lay[1] || c % 2 != lay[2]) continue; r2 = r + 1; }
+                if (r2 >= rows || c2 >= cols) continue;
+                int b = id[r2 * cols + c2];
+                if (b < 0) continue;
+                edges.push_back({std::min(a, b), std::max(a, b)});
+            }
+        std::sort(edges.begin(), edges.end());
+        std::fill(in_cz.begin(), in_cz.end(), 0);
+        for (auto &e : edges) in_cz[e.first] = in_cz[e.second] = 1;
+        for (int q = 0; q < n; q++) {
+            if (!prev_cz[q] || in_cz[q]) continue;
+            int kind;
+            if (last[q] < 0) {
+                kind = QS_GATE_T;
+            } else {
+                int allowed[2], na = 0;
+                const int order[3] = {QS_GATE_T, QS_GATE_SQRT_X, QS_GATE_SQRT_Y};
+                for (int o = 0; o < 3; o++)
+                    if (order[o] != last[q]) allowed[na++] = order[o];
+                kind = allowed[splitmix64(seed, draw++) >> 63];
+            }
+            out.push_back({t, kind, q, -1});
+            last[q] = kind;
+        }
+        for (auto &e : edges) out.push_back({t, QS_GATE_CZ, e.first, e.second});
+        prev_cz = in_cz;
+    }
+    *n_gates = (int)out.size();
+    if ((int)out.size() > max_gates)
+        return qs_fail(QS_EINVAL, "qs_supremacy_circuit: need room for %d gates", (int)out.size());
+    std::memcpy(gates, out.data(), sizeof(qs_gate) * out.size());
+    return QS_OK;
+}
+
+extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
+                                 const qs_sched_opts *opts, qs_schedule **out)
+{
+    if (!out || n < 1 || n > QS_MAX_QUBITS || n_gates < 0 || (n_gates > 0 && !gates) || !opts)
+        return qs_fail(QS_EINVAL, "qs_schedule_build: bad arguments");
+    if (opts->fuse && (opts->k_max < 2 || opts->k_max > QS_MAX_K))
+        return qs_fail(QS_EINVAL, "qs_schedule_build: k_max %d not in [2, %d]", opts->k_max, QS_MAX_K);
+    std::vector<qs_gate> g(gates, gates + n_gates);
+    for (int i = 0; i < n_gates; i++)
+        if (!check_gate(n, g[i])) return qs_fail(QS_EINVAL, "qs_schedule_build: bad gate %d", i);
+    std::vector<std::vector<int>> groups;
+    if (opts->fuse) {
+        Clusterer cl(n, g);
+        groups = cl.run(opts->k_max);
+    } else {
+        for (int i = 0; i < n_gates; i++) groups.push_back({i});
+    }
+    qs_schedule *sc = new (std::nothrow) qs_schedule();
+    if (!sc) return qs_fail(QS_ENOMEM, "qs_schedule_build: out of host memory");
+    sc->n = n;
+    for (auto &members : groups) {
+        bool diag = true;
+        for (int gi : members) diag = diag && is_diagonal(g[gi].kind);
+        qs_op_host op;
+        if (diag) {
+            if (opts->fuse && opts->merge_phase && !sc->ops.empty() &&
+                sc->ops.back().kind == QS_OP_PHASE) {
+                std::vector<int> all(sc->ops.back().gates.begin(), sc->ops.back().gates.end());
+                all.insert(all.end(), members.begin(), members.end());
+                sc->ops.pop_back();
+                make_phase(n, g, all, op);
+            } else {
+                make_phase(n, g, members, op);
+            }
+        } else {
+            make_dense(g, members, op);
+        }
+        sc->ops.push_back(std::move(op));
+    }
+    *out = sc;
+    return QS_OK;
+}
+
+extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const int *ks,
+                                    const int *qubits, const int64_t *offsets,
+                                    const double *pool, int64_t pool_len, qs_schedule **out)
+{
+    if (!out || n < 1 || n > QS_MAX_QUBITS || n_ops < 0 ||
+        (n_ops > 0 && (!kinds || !ks || !qubits || !offsets || !pool)))
+        return qs_fail(QS_EINVAL, "qs_schedule_from_ops: bad arguments");
+    qs_schedule *sc = new (std::nothrow) qs_schedule();
+    if (!sc) return qs_fail(QS_ENOMEM, "qs_schedule_from_ops: out of host memory");
+    sc->n = n;
+    for (int i = 0; i < n_ops; i++) {
+        int k = ks[i];
+        bool dense = kinds[i] == QS_OP_DENSE;
+        if ((!dense && kinds[i] != QS_OP_DIAG) || k < 1 || k > (dense ? QS_MAX_K : QS_MAX_K) || k > n) {
+            delete sc;
+            return qs_fail(QS_EINVAL, "qs_schedule_from_ops: bad op %d", i);
+        }
+        // sort qubits ascending and permute the matrix accordingly (Sec. 3.2)
+        int q[QS_MAX_K], perm[QS_MAX_K];
+        uint64_t seen = 0;
+        for (int j = 0; j < k; j++) {
+            q[j] = qubits[QS_MAX_K * i + j];
+            perm[j] = j;
+            if (q[j] < 0 || q[j] >= n || ((seen >> q[j]) & 1)) {
+                delete sc;
+                return qs_fail(QS_EINVAL, "qs_schedule_from_ops: bad qubits in op %d", i);
+            }
+            seen |= 1ULL << q[j];
+        }
+        std::sort(perm, perm + k, [&](int a, int b) { return q[a] < q[b]; });
+        const int d = 1 << k;
+        int64_t need = dense ? 2LL * d * d : 2LL * d;
+        if (offsets[i] < 0 || offsets[i] + need > pool_len) {
+            delete sc;
+            return qs_fail(QS_EINVAL, "qs_schedule_from_ops: op %d reads past the pool", i);
+        }
+        qs_op_host op;
+        op.kind = dense ? QS_OP_DENSE : QS_OP_DIAG;
+        op.k = k;
+        for (int j = 0; j < k; j++) op.qubits[j] = q[perm[j]];
+        // new index bit j <-> old bit perm[j]
+        auto remap = [&](int xn) {
+            int xo = 0;
+            for (int j = 0; j < k; j++) xo |= ((xn >> j) & 1) << perm[j];
+            return xo;
+        };
+        const double *src = pool + offsets[i];
+        if (dense) {
+            op.matrix.resize(2 * d * d);
+            for (int r = 0; r < d; r++)
+                for (int c = 0; c < d; c++) {
+                    int ro = remap(r), co = remap(c);
+                    op.matrix[2 * (r * d + c)] = src[2 * (ro * d + co)];
+                    op.matrix[2 * (r * d + c) + 1] = src[2 * (ro * d + co) + 1];
+                }
+        } else {
+            op.matrix.resize(2 * d);
+            for (int x = 0; x < d; x++) {
+                op.matrix[2 * x] = src[2 * remap(x)];
+                op.matrix[2 * x + 1] = src[2 * remap(x) + 1];
+            }
+        }
+        sc->ops.push_back(std::move(op));
+    }
+    *out = sc;
+    return QS_OK;
+}
+
+extern "C" int qs_schedule_num_qubits(const qs_schedule *sc) { return sc ? sc->n : 0; }
+extern "C" int qs_schedule_num_ops(const qs_schedule *sc) { return sc ? (int)sc->ops.size() : 0; }
+
+extern "C" int qs_schedule_op(const qs_schedule *sc, int i, qs_op_info *info, double *matrix,
+                              int32_t *gate_idx, int32_t *coeff, int32_t *edges)
+{
+    if (!sc || i < 0 || i >= (int)sc->ops.size())
+        return qs_fail(QS_EINVAL, "qs_schedule_op: bad schedule or index");
+    const qs_op_host &op = sc->ops[i];
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->kind = op.kind;
+        info->k = op.k;
+        for (int j = 0; j < QS_MAX_K && j < op.k; j++) info->qubits[j] = op.qubits[j];
+        info->n_gates = (int32_t)op.gates.size();
+        info->n_edges = (int32_t)op.edges.size();
+    }
+    if (matrix && !op.matrix.empty())
+        std::memcpy(matrix, op.matrix.data(), sizeof(double) * op.matrix.size());
+    if (gate_idx && !op.gates.empty())
+        std::memcpy(gate_idx, op.gates.data(), sizeof(int32_t) * op.gates.size());
+    if (coeff && op.kind == QS_OP_PHASE)
+        std::memcpy(coeff, op.coeff.data(), sizeof(int32_t) * op.coeff.size());
+    if (edges && op.kind == QS_OP_PHASE)
+        for (size_t e = 0; e < op.edges.size(); e++) {
+            edges[2 * e] = op.edges[e].first;
+            edges[2 * e + 1] = op.edges[e].second;
+        }
+    return QS_OK;
+}
+
+// Phase op device layout: three coefficient bit-masks and, per qubit a with CZ
+// partners b > a (pairs counted mod 2), the mask of those partners.
+std::vector<uint8_t> qs_pack_phase(int n, const std::vector<int32_t> &coeff,
+                                   const std::vector<std::pair<int, int>> &edges, int *n_act)
+{
+    qs_phase_dev hdr;
+    std::memset(&hdr, 0, sizeof(hdr));
+    for (int q = 0; q < n; q++) {
+        int c = ((coeff[q] % 8) + 8) % 8;
+        for (int b = 0; b < 3; b++)
+            if ((c >> b) & 1) hdr.cmask[b] |= 1ULL << q;
+    }
+    std::vector<uint64_t> partners(n, 0);
+    for (auto &e : edges) {
+        int a = std::min(e.first, e.second), b = std::max(e.first, e.second);
+        partners[a] ^= 1ULL << b;
+    }
+    std::vector<qs_phase_term> terms;
+    for (int a = 0; a < n; a++)
+        if (partners[a]) terms.push_back({partners[a], a, 0});
+    hdr.n_act = (int32_t)terms.size();
+    *n_act = hdr.n_act;
+    std::vector<uint8_t> buf(sizeof(hdr) + terms.size() * sizeof(qs_phase_term));
+    std::memcpy(buf.data(), &hdr, sizeof(hdr));
+    if (!terms.empty())
+        std::memcpy(buf.data() + sizeof(hdr), terms.data(), terms.size() * sizeof(qs_phase_term));
+    return buf;
+}

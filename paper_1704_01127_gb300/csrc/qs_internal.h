@@ -1,0 +1,77 @@
+// Internal declarations shared by the translation units of libqs.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include <utility>
+
+#include "../../include/qs.h"
+
+// Thread-local error message; returns `code` so callers can `return qs_fail(...)`.
+int qs_fail(int code, const char *fmt, ...);
+
+struct qs_state {
+    int n = 0;
+    int dtype = QS_C128;
+    void *amp = nullptr;          // device, 2^n amplitudes
+    bool owned = false;
+    void *stream = nullptr;       // cudaStream_t
+    int device = 0;
+    // scratch, grown on demand and freed with the state
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    void *pinned = nullptr;       // small pinned host buffer for results
+    size_t pinned_bytes = 0;
+};
+
+// One op of a schedule, host side.
+struct qs_op_host {
+    int kind = QS_OP_DENSE;
+    int k = 0;
+    int qubits[QS_MAX_DIAG_K] = {0};
+    std::vector<int32_t> gates;          // circuit gate indices, in multiplication order
+    std::vector<double> matrix;          // dense: 2^{2k} complex interleaved; diag: 2^k
+    std::vector<int32_t> coeff;          // phase: n values mod 8
+    std::vector<std::pair<int, int>> edges;   // phase: CZ pairs
+};
+
+// Device copy of a schedule's op data for one amplitude type.
+struct qs_dev_sched {
+    int device = -1;
+    void *pool = nullptr;                // device
+    size_t bytes = 0;
+    std::vector<size_t> offset;          // byte offset of op i's data in pool
+    std::vector<int> n_act;              // phase ops: number of CZ partner terms
+};
+
+struct qs_schedule {
+    int n = 0;
+    std::vector<qs_op_host> ops;
+    qs_dev_sched dev[2];                 // indexed by dtype
+};
+
+// Device layout of a phase op (see qs_apply.cu).
+struct qs_phase_dev {
+    uint64_t cmask[3];     // bit q of cmask[b] = bit b of coeff[q]
+    int32_t n_act;         // qubits a with a non-empty partner mask
+    int32_t pad;
+    // followed by n_act entries of { uint64 partners; int32 a; int32 pad }
+};
+struct qs_phase_term {
+    uint64_t partners;
+    int32_t a;
+    int32_t pad;
+};
+
+// Launchers (qs_apply.cu).  All validate nothing: callers check arguments.
+int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix);
+int qs_launch_diag(qs_state *s, const int *qubits, int k, const void *dev_table);
+int qs_launch_phase(qs_state *s, const void *dev_phase, int n_act);
+
+// Pack a phase op into its device layout (qs_circuit.cpp).
+std::vector<uint8_t> qs_pack_phase(int n, const std::vector<int32_t> &coeff,
+                                   const std::vector<std::pair<int, int>> &edges, int *n_act);
+
+// Device scratch of at least `bytes` on the state (qs_api.cu).
+int qs_state_scratch(qs_state *s, size_t bytes, void **out);

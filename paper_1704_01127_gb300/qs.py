@@ -1,0 +1,359 @@
+"""Python binding of the qs C ABI (include/qs.h): argument marshalling only.
+
+Every computation runs in libqs.so (host C++ for circuit generation and
+scheduling, CUDA kernels for every state sweep and reduction).  Importing this
+module fails loudly if the library has not been built; there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqs.so")
+
+QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+QS_C64, QS_C128 = 0, 1
+QS_MAX_K = 5
+QS_OP_DENSE, QS_OP_PHASE, QS_OP_DIAG = 0, 1, 2
+GATE_KIND = {"h": 0, "t": 1, "x_1_2": 2, "y_1_2": 3, "cz": 4, "x": 5, "tdg": 6,
+             "x_1_2dg": 7, "y_1_2dg": 8}
+GATE_NAME = {v: k for k, v in GATE_KIND.items()}
+
+GATE_DTYPE = np.dtype([("cycle", np.int32), ("kind", np.int32), ("q0", np.int32), ("q1", np.int32)])
+
+
+class QSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("qs error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _SchedOpts(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int32), ("fuse", ctypes.c_int32),
+                ("merge_phase", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _OpInfo(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("qubits", ctypes.c_int32 * QS_MAX_K), ("n_gates", ctypes.c_int32),
+                ("n_edges", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_VP, _DP, _IP = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+_U64P, _I64P, _I32P = (ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int64),
+                       ctypes.POINTER(ctypes.c_int32))
+
+_SIGS = {
+    "qs_last_error": ([], ctypes.c_char_p),
+    "qs_alloc": ([ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qs_wrap": ([_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qs_free": ([_VP], None),
+    "qs_num_qubits": ([_VP], ctypes.c_int),
+    "qs_dtype": ([_VP], ctypes.c_int),
+    "qs_device_ptr": ([_VP], _VP),
+    "qs_set_stream": ([_VP, _VP], ctypes.c_int),
+    "qs_init_basis": ([_VP, ctypes.c_uint64], ctypes.c_int),
+    "qs_init_uniform": ([_VP], ctypes.c_int),
+    "qs_set_amplitudes": ([_VP, _DP], ctypes.c_int),
+    "qs_get_amplitudes": ([_VP, _DP], ctypes.c_int),
+    "qs_apply_cluster": ([_VP, _IP, ctypes.c_int, _DP], ctypes.c_int),
+    "qs_apply_diag": ([_VP, _IP, ctypes.c_int, _DP], ctypes.c_int),
+    "qs_apply_phase": ([_VP, _IP, ctypes.c_int, _IP], ctypes.c_int),
+    "qs_norm": ([_VP, _DP], ctypes.c_int),
+    "qs_probabilities": ([_VP, _DP, ctypes.c_int], ctypes.c_int),
+    "qs_stats": ([_VP, _DP], ctypes.c_int),
+    "qs_sample": ([_VP, ctypes.c_uint64, ctypes.c_int64, _U64P], ctypes.c_int),
+    "qs_synchronize": ([_VP], ctypes.c_int),
+    "qs_supremacy_circuit": ([ctypes.c_int, ctypes.c_int, _IP, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_uint64, _IP, _VP, ctypes.c_int, _IP], ctypes.c_int),
+    "qs_schedule_build": ([ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(_SchedOpts),
+                           ctypes.POINTER(_VP)], ctypes.c_int),
+    "qs_schedule_from_ops": ([ctypes.c_int, ctypes.c_int, _IP, _IP, _IP, _I64P, _DP,
+                              ctypes.c_int64, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qs_schedule_free": ([_VP], None),
+    "qs_schedule_num_qubits": ([_VP], ctypes.c_int),
+    "qs_schedule_num_ops": ([_VP], ctypes.c_int),
+    "qs_schedule_op": ([_VP, ctypes.c_int, ctypes.POINTER(_OpInfo), _DP, _I32P, _I32P, _I32P],
+                       ctypes.c_int),
+    "qs_run_circuit": ([_VP, _VP], ctypes.c_int),
+    "qs_run_circuit_timed": ([_VP, _VP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "qs_set_device": ([ctypes.c_int], ctypes.c_int),
+    "qs_schedule_upload_bytes": ([_VP, ctypes.c_int], ctypes.c_int64),
+}
+
+
+def lib():
+    """The loaded libqs.so; raises ImportError if it was never built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libqs.so is not built (run paper_1704_01127_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _check(rc):
+    if rc != QS_OK:
+        raise QSError(rc, lib().qs_last_error().decode())
+    return rc
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_IP)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream   # torch.cuda.Stream
+
+
+# ----------------------------------------------------------------- state API
+
+def qs_alloc(n, dtype=QS_C128, stream=None):
+    h = _VP()
+    _check(lib().qs_alloc(int(n), int(dtype), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def qs_wrap(dev_ptr, n, dtype=QS_C128, stream=None):
+    """Adopt a device buffer (int pointer or a CUDA torch tensor); not freed by qs_free."""
+    if hasattr(dev_ptr, "data_ptr"):
+        dev_ptr = dev_ptr.data_ptr()
+    h = _VP()
+    _check(lib().qs_wrap(_VP(dev_ptr), int(n), int(dtype), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def qs_free(h):
+    lib().qs_free(h)
+
+
+def qs_num_qubits(h):
+    return lib().qs_num_qubits(h)
+
+
+def qs_dtype(h):
+    return lib().qs_dtype(h)
+
+
+def qs_device_ptr(h):
+    return lib().qs_device_ptr(h)
+
+
+def qs_set_stream(h, stream):
+    _check(lib().qs_set_stream(h, _stream_ptr(stream)))
+
+
+def qs_init_basis(h, x=0):
+    _check(lib().qs_init_basis(h, ctypes.c_uint64(int(x))))
+
+
+def qs_init_uniform(h):
+    _check(lib().qs_init_uniform(h))
+
+
+def qs_set_amplitudes(h, psi):
+    a = _c128(psi)
+    assert a.size == 1 << qs_num_qubits(h)
+    _check(lib().qs_set_amplitudes(h, _dp(a.view(np.float64))))
+
+
+def qs_get_amplitudes(h):
+    out = np.empty(1 << qs_num_qubits(h), dtype=np.complex128)
+    _check(lib().qs_get_amplitudes(h, _dp(out.view(np.float64))))
+    return out
+
+
+def qs_apply_cluster(h, qubits, U):
+    q = np.ascontiguousarray(qubits, dtype=np.int32)
+    u = _c128(U)
+    d = 1 << q.size
+    assert u.shape == (d, d)
+    _check(lib().qs_apply_cluster(h, _ip(q), int(q.size), _dp(u.reshape(-1).view(np.float64))))
+
+
+def qs_apply_diag(h, qubits, d):
+    q = np.ascontiguousarray(qubits, dtype=np.int32)
+    dd = _c128(d)
+    assert dd.size == 1 << q.size
+    _check(lib().qs_apply_diag(h, _ip(q), int(q.size), _dp(dd.view(np.float64))))
+
+
+def qs_apply_phase(h, coeff, edges):
+    c = np.ascontiguousarray(coeff, dtype=np.int32)
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    _check(lib().qs_apply_phase(h, _ip(c), int(e.size // 2), _ip(e) if e.size else None))
+
+
+def qs_norm(h):
+    out = ctypes.c_double()
+    _check(lib().qs_norm(h, ctypes.byref(out)))
+    return out.value
+
+
+def qs_stats(h):
+    out = np.zeros(4, dtype=np.float64)
+    _check(lib().qs_stats(h, _dp(out)))
+    return tuple(float(x) for x in out)
+
+
+def qs_probabilities(h, out=None, out_on_device=False):
+    """FP64 probabilities: into a new host array, a given host array, or (with
+    out_on_device) a device pointer / CUDA tensor."""
+    if out_on_device:
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else int(out)
+        _check(lib().qs_probabilities(h, ctypes.cast(ptr, _DP), 1))
+        return out
+    if out is None:
+        out = np.empty(1 << qs_num_qubits(h), dtype=np.float64)
+    _check(lib().qs_probabilities(h, _dp(out), 0))
+    return out
+
+
+def qs_sample(h, seed, m):
+    out = np.zeros(int(m), dtype=np.uint64)
+    _check(lib().qs_sample(h, ctypes.c_uint64(int(seed)), int(m), out.ctypes.data_as(_U64P)))
+    return out
+
+
+def qs_synchronize(h):
+    _check(lib().qs_synchronize(h))
+
+
+# --------------------------------------------------------------- circuit API
+
+def qs_supremacy_circuit(rows, cols, cz_cycles, seed, removed=()):
+    """(n, gates) with gates a structured array of (cycle, kind, q0, q1)."""
+    rem = np.ascontiguousarray(np.asarray(removed, dtype=np.int32).reshape(-1))
+    n = ctypes.c_int()
+    cnt = ctypes.c_int()
+    cap = 64 + 2 * rows * cols * (cz_cycles + 1)
+    gates = np.zeros(cap, dtype=GATE_DTYPE)
+    _check(lib().qs_supremacy_circuit(int(rows), int(cols), _ip(rem) if rem.size else None,
+                                      int(rem.size // 2), int(cz_cycles), ctypes.c_uint64(int(seed)),
+                                      ctypes.byref(n), gates.ctypes.data_as(_VP), cap, ctypes.byref(cnt)))
+    return n.value, gates[:cnt.value].copy()
+
+
+def gates_from_tuples(gates):
+    """Structured gate array from (cycle, name, qubits) tuples."""
+    out = np.zeros(len(gates), dtype=GATE_DTYPE)
+    for i, (cyc, name, qs) in enumerate(gates):
+        out[i] = (cyc, GATE_KIND[name], qs[0], qs[1] if len(qs) > 1 else -1)
+    return out
+
+
+def gates_to_tuples(gates):
+    return [(int(g["cycle"]), GATE_NAME[int(g["kind"])],
+             (int(g["q0"]),) if int(g["q1"]) < 0 else (int(g["q0"]), int(g["q1"])))
+            for g in gates]
+
+
+def qs_schedule_build(n, gates, k_max=5, fuse=True, merge_phase=True):
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    opts = _SchedOpts(int(k_max), int(bool(fuse)), int(bool(merge_phase)), 0)
+    h = _VP()
+    _check(lib().qs_schedule_build(int(n), g.ctypes.data_as(_VP), int(g.size), ctypes.byref(opts),
+                                   ctypes.byref(h)))
+    return h
+
+
+def qs_schedule_from_ops(n, ops):
+    """ops: list of (kind, qubits, complex matrix or diagonal)."""
+    kinds, ks, qubits, offsets, pool = [], [], [], [], []
+    at = 0
+    for kind, qs, m in ops:
+        kinds.append(kind)
+        ks.append(len(qs))
+        qubits.extend(list(qs) + [0] * (QS_MAX_K - len(qs)))
+        flat = _c128(m).reshape(-1).view(np.float64)
+        offsets.append(at)
+        pool.append(flat)
+        at += flat.size
+    pool = np.ascontiguousarray(np.concatenate(pool) if pool else np.zeros(1))
+    kinds, ks, qubits = (np.ascontiguousarray(x, dtype=np.int32) for x in (kinds, ks, qubits))
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    h = _VP()
+    _check(lib().qs_schedule_from_ops(int(n), int(kinds.size), _ip(kinds), _ip(ks), _ip(qubits),
+                                      offsets.ctypes.data_as(_I64P), _dp(pool), int(pool.size),
+                                      ctypes.byref(h)))
+    return h
+
+
+def qs_schedule_free(h):
+    lib().qs_schedule_free(h)
+
+
+def qs_schedule_num_ops(h):
+    return lib().qs_schedule_num_ops(h)
+
+
+def qs_schedule_op(h, i):
+    """Op i as a dict: kind, qubits, gates, and matrix (dense/diag) or coeff/edges (phase)."""
+    info = _OpInfo()
+    _check(lib().qs_schedule_op(h, int(i), ctypes.byref(info), None, None, None, None))
+    k, kind = info.k, info.kind
+    gidx = np.zeros(max(info.n_gates, 1), dtype=np.int32)
+    out = {"kind": {QS_OP_DENSE: "dense", QS_OP_PHASE: "phase", QS_OP_DIAG: "diag"}[kind]}
+    n = lib().qs_schedule_num_qubits(h)
+    if kind == QS_OP_PHASE:
+        coeff = np.zeros(n, dtype=np.int32)
+        edges = np.zeros(max(2 * info.n_edges, 1), dtype=np.int32)
+        _check(lib().qs_schedule_op(h, int(i), None, None, gidx.ctypes.data_as(_I32P),
+                                    coeff.ctypes.data_as(_I32P), edges.ctypes.data_as(_I32P)))
+        out["coeff"] = coeff
+        out["edges"] = [(int(edges[2 * e]), int(edges[2 * e + 1])) for e in range(info.n_edges)]
+        out["support"] = k
+    else:
+        d = 1 << k
+        m = np.zeros(d * d if kind == QS_OP_DENSE else d, dtype=np.complex128)
+        _check(lib().qs_schedule_op(h, int(i), None, _dp(m.view(np.float64)),
+                                    gidx.ctypes.data_as(_I32P), None, None))
+        out["qubits"] = tuple(int(x) for x in info.qubits[:k])
+        out["matrix"] = m.reshape(d, d) if kind == QS_OP_DENSE else m
+    out["gates"] = tuple(int(x) for x in gidx[:info.n_gates])
+    return out
+
+
+def qs_run_circuit(h, sched):
+    _check(lib().qs_run_circuit(h, sched))
+
+
+def qs_run_circuit_timed(h, sched):
+    """Run a schedule; returns the device time of every op in milliseconds."""
+    out = np.zeros(max(qs_schedule_num_ops(sched), 1), dtype=np.float32)
+    _check(lib().qs_run_circuit_timed(h, sched, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out[:qs_schedule_num_ops(sched)]
+
+
+def qs_set_device(device):
+    _check(lib().qs_set_device(int(device)))
+
+
+def qs_schedule_upload_bytes(sched, dtype):
+    v = lib().qs_schedule_upload_bytes(sched, int(dtype))
+    if v < 0:
+        _check(v)
+    return int(v)

@@ -1,0 +1,209 @@
+"""CUDA path against the oracle, element by element, through the C ABI.
+
+Tolerances (absolute max |dpsi|): 1e-12 for complex128 and 2e-6 for complex64
+(single sweeps are checked far tighter).  Integer outputs (samples) must match
+bit for bit when both sides see the same amplitudes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1704_01127_gb300.qs as qs
+from inputs import random_state, random_unitary, random_diag, random_qubits, random_phase_poly
+from oracle import sim, schedule, circuit
+
+pytestmark = pytest.mark.gpu
+
+TOL = {qs.QS_C128: 1e-12, qs.QS_C64: 2e-6}
+SWEEP_TOL = {qs.QS_C128: 1e-14, qs.QS_C64: 3e-6}
+
+
+def f32_round(psi):
+    """The complex128 values a complex64 state holds after rounding."""
+    return psi.astype(np.complex64).astype(np.complex128)
+
+
+class State:
+    def __init__(self, n, dtype):
+        self.h = qs.qs_alloc(n, dtype)
+        self.n, self.dtype = n, dtype
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        qs.qs_free(self.h)
+
+
+def target_patterns(n, k):
+    """Low, high, mixed and unsorted target sets for a k-qubit cluster."""
+    pats = [list(range(k)), list(range(n - k, n)), list(reversed(range(k)))]
+    if n >= k + 6:
+        pats.append([0, 3, 5, n - 1, n - 2][:k])
+        pats.append(random_qubits(n, k, 1000 + n * 7 + k))
+        pats.append([5 + j for j in range(k)])
+    return pats
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("n", [5, 6, 9, 14, 17])
+def test_apply_cluster(dtype, k, n):
+    if k > n:
+        pytest.skip("k > n")
+    for t, qubits in enumerate(target_patterns(n, k)):
+        U = random_unitary(k, 10 * n + k + t)
+        psi = random_state(n, 7 * n + k + t)
+        if dtype == qs.QS_C64:
+            psi = f32_round(psi)
+        ref = psi.copy()
+        sim.apply_kq(ref, qubits, U)
+        with State(n, dtype) as s:
+            qs.qs_set_amplitudes(s.h, psi)
+            qs.qs_apply_cluster(s.h, qubits, U)
+            out = qs.qs_get_amplitudes(s.h)
+        assert np.max(np.abs(out - ref)) < SWEEP_TOL[dtype], (qubits,)
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_apply_cluster_n_equals_k(dtype):
+    for k in range(1, 6):
+        U = random_unitary(k, k)
+        psi = f32_round(random_state(k, k + 50))
+        ref = psi.copy()
+        sim.apply_kq(ref, list(range(k))[::-1], U)
+        with State(k, dtype) as s:
+            qs.qs_set_amplitudes(s.h, psi)
+            qs.qs_apply_cluster(s.h, list(range(k))[::-1], U)
+            assert np.max(np.abs(qs.qs_get_amplitudes(s.h) - ref)) < SWEEP_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+@pytest.mark.parametrize("k", [1, 3, 7, 12])
+def test_apply_diag(dtype, k):
+    n = 14
+    qubits = random_qubits(n, k, k)
+    d = random_diag(k, k + 1)
+    psi = f32_round(random_state(n, k + 2))
+    ref = psi.copy()
+    sim.apply_diag(ref, qubits, d)
+    with State(n, dtype) as s:
+        qs.qs_set_amplitudes(s.h, psi)
+        qs.qs_apply_diag(s.h, qubits, d)
+        assert np.max(np.abs(qs.qs_get_amplitudes(s.h) - ref)) < SWEEP_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+@pytest.mark.parametrize("n,n_edges", [(3, 2), (12, 0), (15, 20), (20, 60)])
+def test_apply_phase(dtype, n, n_edges):
+    coeff, edges = random_phase_poly(n, n_edges, n + n_edges)
+    psi = f32_round(random_state(n, n))
+    ref = psi.copy()
+    sim.apply_phase(ref, coeff, edges)
+    with State(n, dtype) as s:
+        qs.qs_set_amplitudes(s.h, psi)
+        qs.qs_apply_phase(s.h, coeff, edges)
+        assert np.max(np.abs(qs.qs_get_amplitudes(s.h) - ref)) < SWEEP_TOL[dtype]
+
+
+def run_lib(n, gates_arr, dtype, **sched_kw):
+    sc = qs.qs_schedule_build(n, gates_arr, **sched_kw)
+    try:
+        with State(n, dtype) as s:
+            qs.qs_init_basis(s.h, 0)
+            qs.qs_run_circuit(s.h, sc)
+            return qs.qs_get_amplitudes(s.h), qs.qs_stats(s.h), qs.qs_probabilities(s.h)
+    finally:
+        qs.qs_schedule_free(sc)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_config_4x4_depth10_plain_c128(seed):
+    """16 qubits, depth 10, complex128, gate by gate: full state and probabilities."""
+    n, g = qs.qs_supremacy_circuit(4, 4, 10, seed)
+    ref = sim.run_circuit(n, qs.gates_to_tuples(g))
+    psi, st, p = run_lib(n, g, qs.QS_C128, fuse=False)
+    assert np.max(np.abs(psi - ref)) <= 1e-12
+    np.testing.assert_allclose(p, sim.probabilities(ref), rtol=0, atol=1e-13)
+    assert abs(st[0] - 1) < 1e-13
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+@pytest.mark.parametrize("grid,depth,k_max", [((4, 4), 10, 5), ((4, 5), 25, 4), ((4, 5), 25, 5),
+                                              ((3, 6), 25, 3), ((2, 3), 12, 5)])
+def test_fused_circuit_matches_oracle(dtype, grid, depth, k_max):
+    n, g = qs.qs_supremacy_circuit(grid[0], grid[1], depth, 3)
+    ref = sim.run_circuit(n, qs.gates_to_tuples(g))
+    psi, st, p = run_lib(n, g, dtype, k_max=k_max)
+    assert np.max(np.abs(psi - ref)) <= TOL[dtype]
+    assert abs(st[0] - 1) < (1e-13 if dtype == qs.QS_C128 else 1e-5)
+
+
+def test_stats_match_oracle():
+    n, g = qs.qs_supremacy_circuit(4, 5, 25, 1)
+    ref = sim.run_circuit(n, qs.gates_to_tuples(g))
+    _, st, _ = run_lib(n, g, qs.QS_C128, k_max=5)
+    want = sim.stats(ref)
+    for a, b in zip(st, want):
+        assert abs(a - b) <= 1e-10 * max(1.0, abs(b))
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+@pytest.mark.parametrize("n", [2, 7, 10, 16, 21])
+def test_sampling_bit_exact(dtype, n):
+    """Same amplitudes on both sides -> the same outcomes, bit for bit."""
+    psi = f32_round(random_state(n, 40 + n)) if dtype == qs.QS_C64 else random_state(n, 40 + n)
+    m = 4096
+    with State(n, dtype) as s:
+        qs.qs_set_amplitudes(s.h, psi)
+        got = qs.qs_sample(s.h, 12345 + n, m)
+    want = sim.sample(psi, 12345 + n, m)
+    assert np.array_equal(got, want)
+
+
+def test_init_states():
+    for n in (1, 7, 15):
+        with State(n, qs.QS_C128) as s:
+            qs.qs_init_uniform(s.h)
+            psi = qs.qs_get_amplitudes(s.h)
+            np.testing.assert_allclose(psi.real, 2.0 ** (-n / 2), rtol=1e-15)
+            qs.qs_init_basis(s.h, (1 << n) - 1)
+            psi = qs.qs_get_amplitudes(s.h)
+            assert psi[-1] == 1 and np.count_nonzero(psi) == 1
+
+
+def test_errors_leave_gpu_usable():
+    with State(8, qs.QS_C128) as s:
+        for bad in ([0, 0], [8], [-1], list(range(6))):
+            with pytest.raises(qs.QSError) as e:
+                qs.qs_apply_cluster(s.h, bad, np.eye(1 << len(bad)))
+            assert e.value.code == qs.QS_EINVAL
+        with pytest.raises(qs.QSError):
+            qs.qs_init_basis(s.h, 256)
+        with pytest.raises(qs.QSError):
+            qs.qs_apply_phase(s.h, np.zeros(8), [(3, 3)])
+        qs.qs_init_basis(s.h, 3)
+        assert abs(qs.qs_norm(s.h) - 1) == 0
+    with pytest.raises(qs.QSError) as e:
+        qs.qs_alloc(40, qs.QS_C128)
+    assert e.value.code == qs.QS_EINVAL
+
+
+def test_wrap_torch_tensor():
+    torch = pytest.importorskip("torch")
+    n = 12
+    buf = torch.zeros(2 << n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = qs.qs_wrap(buf, n, qs.QS_C128, stream)
+    try:
+        qs.qs_init_uniform(h)
+        U = random_unitary(2, 3)
+        qs.qs_apply_cluster(h, [0, 11], U)
+        qs.qs_synchronize(h)
+        got = buf.cpu().numpy().view(np.complex128)
+    finally:
+        qs.qs_free(h)
+    ref = sim.uniform_state(n)
+    sim.apply_kq(ref, [0, 11], U)
+    assert np.max(np.abs(got - ref)) < 1e-15

@@ -1,0 +1,119 @@
+"""Host logic of the library against the oracle (CPU only, no GPU needed):
+the C ABI loads and exports every declared symbol; circuit generation and
+scheduling are bit-exact with the oracle; cluster unitaries agree to 1e-14."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1704_01127_gb300.qs as qs
+from oracle import circuit, schedule, sim
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "qs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qs_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = qs.lib()
+    names = header_functions()
+    assert len(names) >= 25
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(qs.exported_symbols())
+
+
+@pytest.mark.parametrize("grid,depth,removed,seed", [
+    ((4, 4), 10, (), 0), ((4, 4), 10, (), 1), ((5, 6), 25, (), 3), ((4, 8), 25, (), 0),
+    ((5, 7), 25, ((4, 6),), 2), ((3, 11), 40, (), 4), ((4, 5), 17, (), 9), ((6, 5), 24, (), 0)])
+def test_generator_bit_exact(grid, depth, removed, seed):
+    n_lib, g_lib = qs.qs_supremacy_circuit(grid[0], grid[1], depth, seed, removed=removed)
+    n_or, g_or = circuit.supremacy_circuit(grid[0], grid[1], depth, seed, removed=removed)
+    assert n_lib == n_or
+    assert qs.gates_to_tuples(g_lib) == g_or
+
+
+def test_generator_rejects_bad_arguments():
+    with pytest.raises(qs.QSError):
+        qs.qs_supremacy_circuit(0, 4, 10, 0)
+    with pytest.raises(qs.QSError):
+        qs.qs_supremacy_circuit(4, 4, 10, 0, removed=((9, 9),))
+    with pytest.raises(qs.QSError):
+        qs.qs_supremacy_circuit(7, 7, 4, 0)   # 49 qubits > QS_MAX_QUBITS
+
+
+def _lib_ops(n, gates, **kw):
+    h = qs.qs_schedule_build(n, gates, **kw)
+    try:
+        return [qs.qs_schedule_op(h, i) for i in range(qs.qs_schedule_num_ops(h))]
+    finally:
+        qs.qs_schedule_free(h)
+
+
+@pytest.mark.parametrize("grid,depth,seed,k_max", [
+    ((4, 4), 10, 0, 5), ((4, 4), 10, 1, 4), ((5, 6), 25, 0, 5), ((5, 6), 25, 2, 4),
+    ((4, 8), 25, 1, 5), ((3, 11), 40, 0, 3), ((4, 5), 30, 5, 2), ((6, 5), 24, 0, 5)])
+def test_schedule_bit_exact_with_oracle(grid, depth, seed, k_max):
+    n, g = qs.qs_supremacy_circuit(grid[0], grid[1], depth, seed)
+    tuples = qs.gates_to_tuples(g)
+    lib_ops = _lib_ops(n, g, k_max=k_max)
+    or_ops = schedule.schedule(n, tuples, k_max=k_max)
+    assert len(lib_ops) == len(or_ops)
+    for a, b in zip(lib_ops, or_ops):
+        assert a["kind"] == b["kind"]
+        assert a["gates"] == b["gates"]
+        if a["kind"] == "dense":
+            assert a["qubits"] == b["qubits"]
+            np.testing.assert_allclose(a["matrix"], b["matrix"], rtol=0, atol=1e-14)
+        else:
+            assert list(a["coeff"]) == list(b["coeff"])
+            assert a["edges"] == [tuple(e) for e in b["edges"]]
+
+
+def test_plain_schedule_one_op_per_gate():
+    n, g = qs.qs_supremacy_circuit(4, 4, 10, 0)
+    ops = _lib_ops(n, g, fuse=False)
+    assert [op["gates"] for op in ops] == [(i,) for i in range(len(g))]
+
+
+def test_schedule_counts_table_1_30_qubits():
+    n, g = qs.qs_supremacy_circuit(6, 5, 24, 0)
+    h = qs.qs_schedule_build(n, g, k_max=5, merge_phase=False)
+    try:
+        count = qs.qs_schedule_num_ops(h)
+    finally:
+        qs.qs_schedule_free(h)
+    assert count <= 1.15 * 36
+
+
+def test_schedule_rejects_bad_input():
+    n, g = qs.qs_supremacy_circuit(4, 4, 10, 0)
+    with pytest.raises(qs.QSError):
+        qs.qs_schedule_build(n, g, k_max=6)
+    bad = g.copy()
+    bad[3]["q0"] = 99
+    with pytest.raises(qs.QSError):
+        qs.qs_schedule_build(n, bad, k_max=5)
+
+
+def test_schedule_from_ops_sorts_qubits_and_permutes():
+    from inputs import random_unitary
+    U = random_unitary(3, 1)
+    h = qs.qs_schedule_from_ops(6, [(qs.QS_OP_DENSE, (4, 0, 2), U)])
+    try:
+        op = qs.qs_schedule_op(h, 0)
+    finally:
+        qs.qs_schedule_free(h)
+    assert op["qubits"] == (0, 2, 4)
+    # applying either form on a random state gives the same result (oracle)
+    from inputs import random_state
+    psi = random_state(6, 2)
+    a, b = psi.copy(), psi.copy()
+    sim.apply_kq(a, [4, 0, 2], U)
+    sim.apply_kq(b, list(op["qubits"]), op["matrix"])
+    np.testing.assert_allclose(a, b, atol=1e-15)
