@@ -120,6 +120,22 @@ int qs_stats(qs_state *s, double out[4]);
  * sequential across them).  out: m uint64 in host memory.  m >= 0. */
 int qs_sample(qs_state *s, uint64_t seed, int64_t m, uint64_t *out);
 
+/* qs_stats without any allocation.  The paper has no counterpart: this entry
+ * exists for callers that may not allocate device memory, for example code that
+ * runs while a framework's caching allocator owns the device memory, or code
+ * that cannot afford the device-wide synchronisation a cudaMalloc implies.
+ * dev_amp: 2^n amplitudes of the given dtype in device memory (16-byte
+ * aligned, interleaved re, im), read only; out: 4 doubles in host memory, as
+ * qs_stats.  The partial sums use a fixed 32,800-byte array compiled into the
+ * library (one per GPU that loads it, held until the process exits); the
+ * kernels use at most 1024 blocks, so every n in [1, QS_MAX_QUBITS] fits and
+ * anything else is rejected with QS_EINVAL.  The first call on a device looks
+ * up that array's device address; make that first call before any stream
+ * capture.  Calls share the array: calls whose kernels overlap on the GPU (on
+ * different streams) race and must be serialised by the caller.  Calls no
+ * cudaMalloc / cudaFree; synchronises `stream` before returning. */
+int qs_stats_static(const void *dev_amp, int n, int dtype, void *stream, double out[4]);
+
 /* Wait for all work queued on the state's stream. */
 int qs_synchronize(qs_state *s);
 

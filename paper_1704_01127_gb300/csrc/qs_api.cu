@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "qs_internal.h"
@@ -537,4 +538,77 @@ extern "C" int qs_synchronize(qs_state *s)
     if (!s) return qs_fail(QS_EINVAL, "qs_synchronize: null state");
     QS_CUDA(cudaStreamSynchronize((cudaStream_t)s->stream), "qs_synchronize");
     return QS_OK;
+}
+
+// --------------------------------------------------------------------------
+// Allocation-free statistics (no counterpart in the paper).
+//
+// For callers that must not allocate device memory: the partial sums live in a
+// file-scope device array instead of the state's scratch.  Every call shares
+// it, so calls whose kernels overlap on the GPU race on it.
+// --------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticStatsBlocks = 1024;   // partial sums per statistic
+// 4 statistics per block, plus 4 result slots: 4 * 1025 doubles = 32800 bytes.
+static __device__ __align__(256) double g_stats_scratch[4 * (kStaticStatsBlocks + 1)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double *g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_stats_scratch on the current device (looked up once per
+// device, with that device current).
+int static_scratch(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_stats_static: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return qs_fail(QS_EUNSUPPORTED, "qs_stats_static: device %d", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_stats_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "qs_stats_static: cudaGetSymbolAddress");
+        g_static_ptr[dev] = (double *)p;
+    }
+    *out = g_static_ptr[dev];
+    return QS_OK;
+}
+
+template <typename C>
+int stats_static_impl(const void *amp, int n, void *stream, double *out)
+{
+    double *scr;
+    int rc = static_scratch(&scr);
+    if (rc) return rc;
+    const uint64_t N = 1ULL << n;
+    const int block = 256;
+    int grid = (int)std::min<uint64_t>((N + block - 1) / block, (uint64_t)sm_count_dev() * 4);
+    grid = std::min(grid, kStaticStatsBlocks);
+    double *part = scr, *res = scr + 4 * kStaticStatsBlocks;
+    cudaStream_t st = (cudaStream_t)stream;
+    // every partial slot in [0, grid) and every result slot is written before it is read
+    k_stats_partial<C, 4><<<grid, block, 0, st>>>((const C *)amp, N, part);
+    k_stats_final<4><<<1, 32, 0, st>>>(part, grid, res);
+    QS_CUDA(cudaGetLastError(), "qs_stats_static launch");
+    QS_CUDA(cudaMemcpyAsync(out, res, sizeof(double) * 4, cudaMemcpyDeviceToHost, st), "qs_stats_static copy");
+    QS_CUDA(cudaStreamSynchronize(st), "qs_stats_static sync");
+    out[2] /= (double)N;
+    out[3] /= (double)N;
+    return QS_OK;
+}
+
+}  // namespace
+
+extern "C" int qs_stats_static(const void *dev_amp, int n, int dtype, void *stream, double out[4])
+{
+    if (!dev_amp || !out || ((uintptr_t)dev_amp & 15))
+        return qs_fail(QS_EINVAL, "qs_stats_static: null or misaligned pointer");
+    if (n < 1 || n > QS_MAX_QUBITS)
+        return qs_fail(QS_EINVAL, "qs_stats_static: n = %d outside [1, %d]", n, QS_MAX_QUBITS);
+    if (dtype != QS_C64 && dtype != QS_C128)
+        return qs_fail(QS_EINVAL, "qs_stats_static: dtype %d", dtype);
+    return dtype == QS_C128 ? stats_static_impl<double2>(dev_amp, n, stream, out)
+                            : stats_static_impl<float2>(dev_amp, n, stream, out);
 }

@@ -80,6 +80,7 @@ _SIGS = {
     "qs_run_circuit": ([_VP, _VP], ctypes.c_int),
     "qs_run_circuit_timed": ([_VP, _VP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "qs_set_device": ([ctypes.c_int], ctypes.c_int),
+    "qs_stats_static": ([_VP, ctypes.c_int, ctypes.c_int, _VP, _DP], ctypes.c_int),
     "qs_schedule_upload_bytes": ([_VP, ctypes.c_int], ctypes.c_int64),
 }
 
@@ -357,3 +358,13 @@ def qs_schedule_upload_bytes(sched, dtype):
     if v < 0:
         _check(v)
     return int(v)
+
+
+def qs_stats_static(dev_ptr, n, dtype, stream=None):
+    """Allocation-free statistics of 2^n amplitudes already in device memory
+    (int pointer or CUDA tensor): (sum p, entropy, mean N p, mean (N p)^2)."""
+    if hasattr(dev_ptr, "data_ptr"):
+        dev_ptr = dev_ptr.data_ptr()
+    out = np.zeros(4, dtype=np.float64)
+    _check(lib().qs_stats_static(_VP(dev_ptr), int(n), int(dtype), _stream_ptr(stream), _dp(out)))
+    return tuple(float(x) for x in out)
