@@ -63,6 +63,12 @@ void qs_free(qs_state *s);
  * qs_alloc / qs_wrap calls.  QS_ECUDA if the device does not exist. */
 int qs_set_device(int device);
 
+/* Which kernels apply 5-qubit dense clusters: QS_PATH_AUTO (tensor cores for
+ * complex64, CUDA cores otherwise), QS_PATH_CUDA_CORES, QS_PATH_TENSOR (complex64
+ * only; QS_EUNSUPPORTED at apply time otherwise). */
+enum { QS_PATH_AUTO = 0, QS_PATH_CUDA_CORES = 1, QS_PATH_TENSOR = 2 };
+int qs_set_path(qs_state *s, int path);
+
 int qs_num_qubits(const qs_state *s);
 int qs_dtype(const qs_state *s);
 void *qs_device_ptr(const qs_state *s);        /* device pointer to amplitude 0 */

@@ -367,6 +367,37 @@ int qs_state_scratch(qs_state *s, size_t bytes, void **out)
     return QS_OK;
 }
 
+int qs_state_status(qs_state *s, int **out)
+{
+    if (!s->status) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, 256);
+        if (e != cudaSuccess) return cuda_fail(e, "status word");
+        e = cudaMemsetAsync(p, 0, 256, (cudaStream_t)s->stream);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return cuda_fail(e, "status word");
+        }
+        s->status = (int *)p;
+    }
+    *out = s->status;
+    return QS_OK;
+}
+
+int qs_check_status(qs_state *s)
+{
+    if (!s->status) return QS_OK;
+    int v = 0;
+    cudaStream_t st = (cudaStream_t)s->stream;
+    QS_CUDA(cudaMemcpyAsync(&v, s->status, sizeof(int), cudaMemcpyDeviceToHost, st), "status read");
+    QS_CUDA(cudaStreamSynchronize(st), "status read");
+    if (v) {
+        cudaMemsetAsync(s->status, 0, sizeof(int), st);
+        return qs_fail(QS_ETIMEOUT, "a kernel's bounded wait ran out (status %d)", v);
+    }
+    return QS_OK;
+}
+
 // ------------------------------------------------------------------- C ABI
 
 extern "C" const char *qs_last_error(void) { return g_err; }
@@ -402,7 +433,15 @@ extern "C" void qs_free(qs_state *s)
     if (s->owned && s->amp) cudaFree(s->amp);
     if (s->scratch) cudaFree(s->scratch);
     if (s->pinned) cudaFreeHost(s->pinned);
+    if (s->status) cudaFree(s->status);
     delete s;
+}
+
+extern "C" int qs_set_path(qs_state *s, int path)
+{
+    if (!s || path < QS_PATH_AUTO || path > QS_PATH_TENSOR) return qs_fail(QS_EINVAL, "qs_set_path");
+    s->path = path;
+    return QS_OK;
 }
 
 extern "C" int qs_num_qubits(const qs_state *s) { return s ? s->n : 0; }
@@ -468,6 +507,7 @@ extern "C" int qs_set_amplitudes(qs_state *s, const double *host)
 extern "C" int qs_get_amplitudes(qs_state *s, double *host)
 {
     if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_get_amplitudes: null argument");
+    if (int rc = qs_check_status(s)) return rc;
     uint64_t N = 1ULL << s->n;
     cudaStream_t st = (cudaStream_t)s->stream;
     if (s->dtype == QS_C128) {
@@ -485,12 +525,14 @@ extern "C" int qs_get_amplitudes(qs_state *s, double *host)
 extern "C" int qs_norm(qs_state *s, double *out)
 {
     if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_norm: null argument");
+    if (int rc = qs_check_status(s)) return rc;
     return s->dtype == QS_C128 ? stats_impl<double2>(s, out, 1) : stats_impl<float2>(s, out, 1);
 }
 
 extern "C" int qs_stats(qs_state *s, double out[4])
 {
     if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_stats: null argument");
+    if (int rc = qs_check_status(s)) return rc;
     return s->dtype == QS_C128 ? stats_impl<double2>(s, out, 4) : stats_impl<float2>(s, out, 4);
 }
 
@@ -537,7 +579,7 @@ extern "C" int qs_synchronize(qs_state *s)
 {
     if (!s) return qs_fail(QS_EINVAL, "qs_synchronize: null state");
     QS_CUDA(cudaStreamSynchronize((cudaStream_t)s->stream), "qs_synchronize");
-    return QS_OK;
+    return qs_check_status(s);
 }
 
 // --------------------------------------------------------------------------

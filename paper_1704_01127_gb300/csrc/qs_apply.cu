@@ -206,8 +206,14 @@ int launch_dense_r(qs_state *s, const int *q, int k, const void *U)
 
 }  // namespace
 
-int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix)
+int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix,
+                    const void *dev_tc)
 {
+    if (k == 5 && s->path != QS_PATH_CUDA_CORES) {
+        if (s->dtype == QS_C64 && dev_tc) return qs_launch_dense5_tc(s, sorted_qubits, dev_tc);
+        if (s->path == QS_PATH_TENSOR)
+            return qs_fail(QS_EUNSUPPORTED, "tensor-core path: complex64 5-qubit clusters only");
+    }
     return s->dtype == QS_C128 ? launch_dense_r<double>(s, sorted_qubits, k, dev_matrix)
                                : launch_dense_r<float>(s, sorted_qubits, k, dev_matrix);
 }
@@ -291,6 +297,13 @@ std::vector<uint8_t> to_real(const std::vector<double> &v, int dtype)
     return out;
 }
 
+// Tensor-core operands follow the plain matrix (8 KB for complex64, 256-byte aligned).
+const void *tc_pack(const qs_op_host &op, int dtype, const uint8_t *data)
+{
+    if (op.k != 5 || dtype != QS_C64) return nullptr;
+    return data + 8192;
+}
+
 int check_state(qs_state *s, const char *who)
 {
     if (!s || !s->amp) return qs_fail(QS_EINVAL, "%s: null state", who);
@@ -343,6 +356,12 @@ std::vector<uint8_t> schedule_blob(const qs_schedule *sc, int dtype, std::vector
             std::memcpy(part.data() + 64, tab.data(), tab.size());
         } else {
             part = to_real(op.matrix, dtype);
+            if (op.k == 5 && dtype == QS_C64) {
+                std::vector<uint8_t> tc = qs_pack_tc_c64(op.matrix);
+                size_t at = (part.size() + 255) & ~(size_t)255;
+                part.resize(at + tc.size());
+                std::memcpy(part.data() + at, tc.data(), tc.size());
+            }
         }
         size_t at = (blob.size() + 255) & ~(size_t)255;
         blob.resize(at + part.size());
@@ -389,9 +408,15 @@ extern "C" int qs_apply_cluster(qs_state *s, const int *qubits, int k, const dou
     std::vector<double> M;
     sort_targets(qubits, k, U, true, q, M);
     std::vector<uint8_t> packed = to_real(M, s->dtype);
+    const bool tc = k == 5 && s->dtype == QS_C64;
+    if (tc) {
+        std::vector<uint8_t> p = qs_pack_tc_c64(M);
+        packed.resize(8192 + p.size());
+        std::memcpy(packed.data() + 8192, p.data(), p.size());
+    }
     void *dU;
     if ((rc = stage(s, packed.data(), packed.size(), &dU))) return rc;
-    return qs_launch_dense(s, q, k, dU);
+    return qs_launch_dense(s, q, k, dU, tc ? (const uint8_t *)dU + 8192 : nullptr);
 }
 
 extern "C" int qs_apply_diag(qs_state *s, const int *qubits, int k, const double *d)
@@ -444,7 +469,7 @@ extern "C" int qs_run_circuit(qs_state *s, const qs_schedule *sc)
         const qs_op_host &op = sc->ops[i];
         const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
         if (op.kind == QS_OP_DENSE) {
-            rc = qs_launch_dense(s, op.qubits, op.k, data);
+            rc = qs_launch_dense(s, op.qubits, op.k, data, tc_pack(op, s->dtype, data));
         } else if (op.kind == QS_OP_DIAG) {
             rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
         } else {
@@ -472,7 +497,7 @@ extern "C" int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *o
     for (size_t i = 0; i < nops && !rc; i++) {
         const qs_op_host &op = sc->ops[i];
         const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
-        if (op.kind == QS_OP_DENSE) rc = qs_launch_dense(s, op.qubits, op.k, data);
+        if (op.kind == QS_OP_DENSE) rc = qs_launch_dense(s, op.qubits, op.k, data, tc_pack(op, s->dtype, data));
         else if (op.kind == QS_OP_DIAG) rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
         else rc = qs_launch_phase(s, data, d.n_act[i]);
         cudaEventRecord(ev[i + 1], st);

@@ -23,6 +23,8 @@ struct qs_state {
     size_t scratch_bytes = 0;
     void *pinned = nullptr;       // small pinned host buffer for results
     size_t pinned_bytes = 0;
+    int *status = nullptr;        // device word set by kernels whose bounded waits ran out
+    int path = 0;                 // QS_PATH_*
 };
 
 // One op of a schedule, host side.
@@ -65,7 +67,9 @@ struct qs_phase_term {
 };
 
 // Launchers (qs_apply.cu).  All validate nothing: callers check arguments.
-int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix);
+// dev_tc: tensor-core operand pack of a 5-qubit cluster (qs_tc.cu) or null.
+int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix,
+                    const void *dev_tc);
 int qs_launch_diag(qs_state *s, const int *qubits, int k, const void *dev_table);
 int qs_launch_phase(qs_state *s, const void *dev_phase, int n_act);
 
@@ -75,3 +79,12 @@ std::vector<uint8_t> qs_pack_phase(int n, const std::vector<int32_t> &coeff,
 
 // Device scratch of at least `bytes` on the state (qs_api.cu).
 int qs_state_scratch(qs_state *s, size_t bytes, void **out);
+// Device status word of the state (allocated and zeroed on first use), and a
+// check that returns QS_ETIMEOUT (and clears the word) if a kernel set it.
+int qs_state_status(qs_state *s, int **out);
+int qs_check_status(qs_state *s);
+
+// Tensor-core 5-qubit sweep (qs_tc.cu).
+std::vector<uint8_t> qs_pack_tc_c64(const std::vector<double> &sorted_matrix);
+size_t qs_tc_pack_bytes(int dtype);
+int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack);

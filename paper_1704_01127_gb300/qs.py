@@ -16,6 +16,7 @@ QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = 0, -1, -2,
 QS_C64, QS_C128 = 0, 1
 QS_MAX_K = 5
 QS_OP_DENSE, QS_OP_PHASE, QS_OP_DIAG = 0, 1, 2
+QS_PATH_AUTO, QS_PATH_CUDA_CORES, QS_PATH_TENSOR = 0, 1, 2
 GATE_KIND = {"h": 0, "t": 1, "x_1_2": 2, "y_1_2": 3, "cz": 4, "x": 5, "tdg": 6,
              "x_1_2dg": 7, "y_1_2dg": 8}
 GATE_NAME = {v: k for k, v in GATE_KIND.items()}
@@ -80,6 +81,7 @@ _SIGS = {
     "qs_run_circuit": ([_VP, _VP], ctypes.c_int),
     "qs_run_circuit_timed": ([_VP, _VP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "qs_set_device": ([ctypes.c_int], ctypes.c_int),
+    "qs_set_path": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_stats_static": ([_VP, ctypes.c_int, ctypes.c_int, _VP, _DP], ctypes.c_int),
     "qs_schedule_upload_bytes": ([_VP, ctypes.c_int], ctypes.c_int64),
 }
@@ -368,3 +370,7 @@ def qs_stats_static(dev_ptr, n, dtype, stream=None):
     out = np.zeros(4, dtype=np.float64)
     _check(lib().qs_stats_static(_VP(dev_ptr), int(n), int(dtype), _stream_ptr(stream), _dp(out)))
     return tuple(float(x) for x in out)
+
+
+def qs_set_path(h, path):
+    _check(lib().qs_set_path(h, int(path)))

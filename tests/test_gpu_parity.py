@@ -207,3 +207,49 @@ def test_wrap_torch_tensor():
     ref = sim.uniform_state(n)
     sim.apply_kq(ref, [0, 11], U)
     assert np.max(np.abs(got - ref)) < 1e-15
+
+
+# ------------------------------------------------ tensor-core 5-qubit sweep (c64)
+
+@pytest.mark.parametrize("n", [5, 8, 11, 12, 13, 16, 19])
+def test_tc_cluster_c64_matches_oracle(n):
+    """Tensor-core path (tf32 head/tail split, FP32 accumulation) on every target
+    pattern, from a single group (n = 5) through ragged and full 128-group tiles."""
+    for t, qubits in enumerate(target_patterns(n, 5)):
+        U = random_unitary(5, 300 + 10 * n + t)
+        psi = f32_round(random_state(n, 400 + n + t))
+        ref = psi.copy()
+        sim.apply_kq(ref, qubits, U)
+        out = {}
+        for path in (qs.QS_PATH_TENSOR, qs.QS_PATH_CUDA_CORES):
+            with State(n, qs.QS_C64) as s:
+                qs.qs_set_path(s.h, path)
+                qs.qs_set_amplitudes(s.h, psi)
+                qs.qs_apply_cluster(s.h, qubits, U)
+                out[path] = qs.qs_get_amplitudes(s.h)
+        scale = np.max(np.abs(psi))
+        assert np.max(np.abs(out[qs.QS_PATH_TENSOR] - ref)) < 2e-6 * max(scale, 1e-3) * 8, qubits
+        assert np.max(np.abs(out[qs.QS_PATH_CUDA_CORES] - ref)) < SWEEP_TOL[qs.QS_C64]
+
+
+def test_tc_fused_circuit_c64():
+    n, g = qs.qs_supremacy_circuit(4, 5, 25, 7)
+    ref = sim.run_circuit(n, qs.gates_to_tuples(g))
+    sc = qs.qs_schedule_build(n, g, k_max=5)
+    try:
+        with State(n, qs.QS_C64) as s:
+            qs.qs_set_path(s.h, qs.QS_PATH_TENSOR)
+            qs.qs_init_basis(s.h, 0)
+            qs.qs_run_circuit(s.h, sc)
+            psi = qs.qs_get_amplitudes(s.h)
+    finally:
+        qs.qs_schedule_free(sc)
+    assert np.max(np.abs(psi - ref)) <= 2e-6
+
+
+def test_tensor_path_rejects_c128():
+    with State(8, qs.QS_C128) as s:
+        qs.qs_set_path(s.h, qs.QS_PATH_TENSOR)
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_apply_cluster(s.h, [0, 1, 2, 3, 4], random_unitary(5, 0))
+        assert e.value.code == qs.QS_EUNSUPPORTED
