@@ -63,9 +63,14 @@ void qs_free(qs_state *s);
  * qs_alloc / qs_wrap calls.  QS_ECUDA if the device does not exist. */
 int qs_set_device(int device);
 
-/* Which kernels apply 5-qubit dense clusters: QS_PATH_AUTO (tensor cores for
- * complex64, CUDA cores otherwise), QS_PATH_CUDA_CORES, QS_PATH_TENSOR (complex64
- * only; QS_EUNSUPPORTED at apply time otherwise). */
+/* Which kernels apply dense clusters.  The tensor-core sweep handles 5-qubit
+ * clusters (smaller ones embedded as U (x) 1 on extra qubits; n >= 5):
+ * complex64 by a tf32 head/tail split with FP32 accumulation, complex128 by
+ * exact 8-bit integer digit planes on the bf16 path rebuilt in integer
+ * arithmetic.  QS_PATH_AUTO: tensor cores for complex64 5-qubit clusters and
+ * for complex128 clusters of 2..5 qubits, CUDA cores otherwise;
+ * QS_PATH_TENSOR: tensor cores for every dense cluster (n >= 5);
+ * QS_PATH_CUDA_CORES: the FP32 / FP64 CUDA-core kernel for every cluster. */
 enum { QS_PATH_AUTO = 0, QS_PATH_CUDA_CORES = 1, QS_PATH_TENSOR = 2 };
 int qs_set_path(qs_state *s, int path);
 

@@ -77,12 +77,14 @@ k_dense(typename cplx<R>::t *__restrict__ psi, uint64_t n_groups, Targets t,
         C v[D];
 #pragma unroll
         for (int x = 0; x < D; x++) v[x] = p[member_offset<K>(x, t)];
-#pragma unroll
+        // rows of U one at a time (kept rolled so v[] stays in registers)
+#pragma unroll 1
         for (int l = 0; l < D; l++) {
             R ar = 0, ai = 0;
+            const C *row = Us + l * D;
 #pragma unroll
             for (int x = 0; x < D; x++) {
-                C m = Us[l * D + x];
+                C m = row[x];
                 ar = fma(v[x].x, m.x, ar);
                 ai = fma(v[x].y, m.x, ai);
                 ar = fma(-v[x].y, m.y, ar);
@@ -140,32 +142,61 @@ __device__ __forceinline__ C rotate8(C a, int m)
     return o;
 }
 
-// Product of T-type phases and CZ signs (Sec. 2, Sec. 3.5): the exponent
-// m(i) = sum_q c_q i_q + 4 sum_{(a,b)} i_a i_b mod 8 is evaluated with popcounts
-// on the index bits; CZ-only ops cost no floating-point work.
+// Product of T-type phases and CZ signs (Sec. 2, Sec. 3.5): amplitude i gets
+// e^{i pi m(i)/4}, m(i) = sum_q c_q i_q + 4 sum_a i_a popc(i & P_a) mod 8, with
+// P_a the CZ partners b > a of qubit a.  The index splits into low bits l
+// (below L) and high bits h.  The low part m_lo(l) (the c_q and partner pairs
+// inside the low bits) is a table built once per CTA in shared memory; every
+// chunk of 2^L amplitudes shares h, so m_hi(h) and the mask M_h of low qubits
+// whose partner set meets h an odd number of times are computed once per
+// chunk:  m(i) = m_lo(l) + m_hi(h) + 4 popc(l & M_h).  CZ-only ops cost no
+// floating-point work.
+constexpr int kPhaseLowBits = 14;
+
 template <typename R>
-__global__ void k_phase(typename cplx<R>::t *__restrict__ psi, uint64_t N,
-                        const qs_phase_dev *__restrict__ ph, int n_act)
+__global__ void __launch_bounds__(256)
+k_phase(typename cplx<R>::t *__restrict__ psi, int n, const qs_phase_dev *__restrict__ ph, int n_act)
 {
     using C = typename cplx<R>::t;
-    __shared__ uint64_t cm[3];
+    __shared__ uint8_t tab[1 << kPhaseLowBits];
     __shared__ uint64_t part[64];
     __shared__ int act[64];
-    if (threadIdx.x < 3) cm[threadIdx.x] = ph->cmask[threadIdx.x];
+    const int L = n < kPhaseLowBits ? n : kPhaseLowBits;
+    const uint64_t lowmask = (1ULL << L) - 1;
+    const uint64_t c0 = ph->cmask[0], c1 = ph->cmask[1], c2 = ph->cmask[2];
     const qs_phase_term *terms = reinterpret_cast<const qs_phase_term *>(ph + 1);
     for (int i = threadIdx.x; i < n_act; i += blockDim.x) {
         part[i] = terms[i].partners;
         act[i] = terms[i].a;
     }
     __syncthreads();
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        int m = __popcll(i & cm[0]) + 2 * __popcll(i & cm[1]) + 4 * __popcll(i & cm[2]);
+    for (int l = threadIdx.x; l < (1 << L); l += blockDim.x) {
+        const uint64_t x = (uint64_t)l;
+        int m = __popcll(x & c0) + 2 * __popcll(x & c1) + 4 * __popcll(x & c2);
         int par = 0;
         for (int t = 0; t < n_act; t++)
-            if ((i >> act[t]) & 1) par ^= __popcll(i & part[t]);
-        m = (m + 4 * (par & 1)) & 7;
-        if (m) psi[i] = rotate8<C, R>(psi[i], m);
+            if (act[t] < L && ((x >> act[t]) & 1)) par ^= __popcll(x & part[t] & lowmask);
+        tab[l] = (uint8_t)((m + 4 * (par & 1)) & 7);
+    }
+    __syncthreads();
+    const uint64_t n_chunks = 1ULL << (n - L);
+    for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint64_t h = ch << L;
+        int mh = __popcll(h & c0) + 2 * __popcll(h & c1) + 4 * __popcll(h & c2);
+        int parh = 0;
+        uint64_t Mh = 0;
+        for (int t = 0; t < n_act; t++) {
+            const int a = act[t];
+            const int odd = __popcll(h & part[t]) & 1;
+            if (a >= L) parh ^= (int)((h >> a) & 1) & odd;
+            else Mh |= (uint64_t)odd << a;
+        }
+        mh = (mh + 4 * parh) & 7;
+        C *base = psi + h;
+        for (int l = threadIdx.x; l < (1 << L); l += blockDim.x) {
+            const int m = (tab[l] + mh + 4 * __popcll((uint64_t)l & Mh)) & 7;
+            if (m) base[l] = rotate8<C, R>(base[l], m);
+        }
     }
 }
 
@@ -209,11 +240,7 @@ int launch_dense_r(qs_state *s, const int *q, int k, const void *U)
 int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix,
                     const void *dev_tc)
 {
-    if (k == 5 && s->path != QS_PATH_CUDA_CORES) {
-        if (s->dtype == QS_C64 && dev_tc) return qs_launch_dense5_tc(s, sorted_qubits, dev_tc);
-        if (s->path == QS_PATH_TENSOR)
-            return qs_fail(QS_EUNSUPPORTED, "tensor-core path: complex64 5-qubit clusters only");
-    }
+    if (k == 5 && dev_tc) return qs_launch_dense5_tc(s, sorted_qubits, dev_tc);
     return s->dtype == QS_C128 ? launch_dense_r<double>(s, sorted_qubits, k, dev_matrix)
                                : launch_dense_r<float>(s, sorted_qubits, k, dev_matrix);
 }
@@ -234,14 +261,15 @@ int qs_launch_diag(qs_state *s, const int *dev_qubits, int k, const void *dev_ta
 
 int qs_launch_phase(qs_state *s, const void *dev_phase, int n_act)
 {
-    uint64_t N = 1ULL << s->n;
+    const int L = s->n < kPhaseLowBits ? s->n : kPhaseLowBits;
+    const uint64_t chunks = 1ULL << (s->n - L);
     const int block = 256;
-    int grid = grid_for(N, block, 8);
+    int grid = (int)std::min<uint64_t>(chunks, (uint64_t)sm_count() * 8);
     cudaStream_t st = (cudaStream_t)s->stream;
     if (s->dtype == QS_C128)
-        k_phase<double><<<grid, block, 0, st>>>((double2 *)s->amp, N, (const qs_phase_dev *)dev_phase, n_act);
+        k_phase<double><<<grid, block, 0, st>>>((double2 *)s->amp, s->n, (const qs_phase_dev *)dev_phase, n_act);
     else
-        k_phase<float><<<grid, block, 0, st>>>((float2 *)s->amp, N, (const qs_phase_dev *)dev_phase, n_act);
+        k_phase<float><<<grid, block, 0, st>>>((float2 *)s->amp, s->n, (const qs_phase_dev *)dev_phase, n_act);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "k_phase launch: %s", cudaGetErrorString(e));
 }
@@ -297,12 +325,6 @@ std::vector<uint8_t> to_real(const std::vector<double> &v, int dtype)
     return out;
 }
 
-// Tensor-core operands follow the plain matrix (8 KB for complex64, 256-byte aligned).
-const void *tc_pack(const qs_op_host &op, int dtype, const uint8_t *data)
-{
-    if (op.k != 5 || dtype != QS_C64) return nullptr;
-    return data + 8192;
-}
 
 int check_state(qs_state *s, const char *who)
 {
@@ -337,13 +359,65 @@ int check_qubits(qs_state *s, const int *qubits, int k, int kmax, const char *wh
     return QS_OK;
 }
 
+// Which dense clusters go to the tensor cores.  complex64: 5-qubit clusters
+// (the FP32 CUDA-core kernel keeps up with HBM below that).  complex128: every
+// cluster of 2 or more qubits, embedded in 5 qubits when smaller (native FP64
+// runs at 1/58 of the FP32 rate, so even a 2-qubit FP64 sweep is ALU-bound).
+bool tc_wanted(int dtype, int k, int n)
+{
+    if (n < 5) return false;
+    return dtype == QS_C64 ? k == 5 : k >= 2;
+}
+
+// U (x) 1: a k-qubit cluster (sorted qubits q, sorted matrix M) as a 5-qubit
+// one on q plus the lowest qubits not in q; output sorted as well.
+void embed5(const int *q, int k, const std::vector<double> &M, int n, std::array<int, 5> &q5,
+            std::vector<double> &M5)
+{
+    uint64_t used = 0;
+    for (int j = 0; j < k; j++) used |= 1ULL << q[j];
+    uint64_t all = used;
+    for (int b = 0; b < n && __builtin_popcountll(all) < 5; b++) all |= 1ULL << b;
+    int pos[5], j5 = 0;
+    for (int b = 0; b < n; b++)
+        if ((all >> b) & 1) q5[j5++] = b;
+    // position of each original target within q5
+    for (int j = 0; j < k; j++)
+        for (int i = 0; i < 5; i++)
+            if (q5[i] == q[j]) pos[j] = i;
+    uint32_t extra = 0;
+    for (int i = 0; i < 5; i++)
+        if (!((used >> q5[i]) & 1)) extra |= 1u << i;
+    const int d = 1 << k;
+    M5.assign(2 * 32 * 32, 0.0);
+    for (int r5 = 0; r5 < 32; r5++)
+        for (int c5 = 0; c5 < 32; c5++) {
+            if ((r5 & extra) != (c5 & extra)) continue;
+            int r = 0, c = 0;
+            for (int j = 0; j < k; j++) {
+                r |= ((r5 >> pos[j]) & 1) << j;
+                c |= ((c5 >> pos[j]) & 1) << j;
+            }
+            M5[2 * (r5 * 32 + c5)] = M[2 * (r * d + c)];
+            M5[2 * (r5 * 32 + c5) + 1] = M[2 * (r * d + c) + 1];
+        }
+}
+
+std::vector<uint8_t> tc_pack_for(int dtype, const std::vector<double> &M5)
+{
+    return dtype == QS_C64 ? qs_pack_tc_c64(M5) : qs_pack_tc_c128(M5);
+}
+
 // Device image of a schedule for one dtype: every op's data, 256-byte aligned.
 std::vector<uint8_t> schedule_blob(const qs_schedule *sc, int dtype, std::vector<size_t> &offset,
-                                   std::vector<int> &n_act)
+                                   std::vector<int> &n_act, std::vector<size_t> &tc_off,
+                                   std::vector<std::array<int, 5>> &tc_q)
 {
     std::vector<uint8_t> blob;
     offset.assign(sc->ops.size(), 0);
     n_act.assign(sc->ops.size(), 0);
+    tc_off.assign(sc->ops.size(), 0);
+    tc_q.assign(sc->ops.size(), std::array<int, 5>{{0, 0, 0, 0, 0}});
     for (size_t i = 0; i < sc->ops.size(); i++) {
         const qs_op_host &op = sc->ops[i];
         std::vector<uint8_t> part;
@@ -356,11 +430,19 @@ std::vector<uint8_t> schedule_blob(const qs_schedule *sc, int dtype, std::vector
             std::memcpy(part.data() + 64, tab.data(), tab.size());
         } else {
             part = to_real(op.matrix, dtype);
-            if (op.k == 5 && dtype == QS_C64) {
-                std::vector<uint8_t> tc = qs_pack_tc_c64(op.matrix);
+            if (tc_wanted(dtype, op.k, sc->n)) {
+                std::vector<double> M5;
+                if (op.k == 5) {
+                    for (int j = 0; j < 5; j++) tc_q[i][j] = op.qubits[j];
+                    M5 = op.matrix;
+                } else {
+                    embed5(op.qubits, op.k, op.matrix, sc->n, tc_q[i], M5);
+                }
+                std::vector<uint8_t> tc = tc_pack_for(dtype, M5);
                 size_t at = (part.size() + 255) & ~(size_t)255;
                 part.resize(at + tc.size());
                 std::memcpy(part.data() + at, tc.data(), tc.size());
+                tc_off[i] = at;
             }
         }
         size_t at = (blob.size() + 255) & ~(size_t)255;
@@ -383,7 +465,7 @@ int ensure_dev_schedule(qs_state *s, const qs_schedule *csc)
         cudaFree(d.pool);
         d.pool = nullptr;
     }
-    std::vector<uint8_t> blob = schedule_blob(sc, s->dtype, d.offset, d.n_act);
+    std::vector<uint8_t> blob = schedule_blob(sc, s->dtype, d.offset, d.n_act, d.tc_off, d.tc_q);
     cudaError_t e = cudaMalloc(&d.pool, blob.size());
     if (e != cudaSuccess) {
         d.pool = nullptr;
@@ -394,6 +476,13 @@ int ensure_dev_schedule(qs_state *s, const qs_schedule *csc)
     d.bytes = blob.size();
     d.device = dev;
     return QS_OK;
+}
+
+int launch_op_dense(qs_state *s, const qs_dev_sched &d, size_t i, const qs_op_host &op, const uint8_t *data)
+{
+    if (d.tc_off[i] && s->path != QS_PATH_CUDA_CORES)
+        return qs_launch_dense5_tc(s, d.tc_q[i].data(), data + d.tc_off[i]);
+    return qs_launch_dense(s, op.qubits, op.k, data, nullptr);
 }
 
 }  // namespace
@@ -407,16 +496,26 @@ extern "C" int qs_apply_cluster(qs_state *s, const int *qubits, int k, const dou
     int q[QS_MAX_K];
     std::vector<double> M;
     sort_targets(qubits, k, U, true, q, M);
-    std::vector<uint8_t> packed = to_real(M, s->dtype);
-    const bool tc = k == 5 && s->dtype == QS_C64;
+    const bool tc = s->path == QS_PATH_TENSOR ? s->n >= 5
+                                              : s->path == QS_PATH_AUTO && tc_wanted(s->dtype, k, s->n);
     if (tc) {
-        std::vector<uint8_t> p = qs_pack_tc_c64(M);
-        packed.resize(8192 + p.size());
-        std::memcpy(packed.data() + 8192, p.data(), p.size());
+        std::array<int, 5> q5;
+        std::vector<double> M5;
+        if (k == 5) {
+            for (int j = 0; j < 5; j++) q5[j] = q[j];
+            M5 = M;
+        } else {
+            embed5(q, k, M, s->n, q5, M5);
+        }
+        std::vector<uint8_t> p = tc_pack_for(s->dtype, M5);
+        void *dp;
+        if ((rc = stage(s, p.data(), p.size(), &dp))) return rc;
+        return qs_launch_dense5_tc(s, q5.data(), dp);
     }
+    std::vector<uint8_t> packed = to_real(M, s->dtype);
     void *dU;
     if ((rc = stage(s, packed.data(), packed.size(), &dU))) return rc;
-    return qs_launch_dense(s, q, k, dU, tc ? (const uint8_t *)dU + 8192 : nullptr);
+    return qs_launch_dense(s, q, k, dU, nullptr);
 }
 
 extern "C" int qs_apply_diag(qs_state *s, const int *qubits, int k, const double *d)
@@ -469,7 +568,7 @@ extern "C" int qs_run_circuit(qs_state *s, const qs_schedule *sc)
         const qs_op_host &op = sc->ops[i];
         const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
         if (op.kind == QS_OP_DENSE) {
-            rc = qs_launch_dense(s, op.qubits, op.k, data, tc_pack(op, s->dtype, data));
+            rc = launch_op_dense(s, d, i, op, data);
         } else if (op.kind == QS_OP_DIAG) {
             rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
         } else {
@@ -497,7 +596,7 @@ extern "C" int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *o
     for (size_t i = 0; i < nops && !rc; i++) {
         const qs_op_host &op = sc->ops[i];
         const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
-        if (op.kind == QS_OP_DENSE) rc = qs_launch_dense(s, op.qubits, op.k, data, tc_pack(op, s->dtype, data));
+        if (op.kind == QS_OP_DENSE) rc = launch_op_dense(s, d, i, op, data);
         else if (op.kind == QS_OP_DIAG) rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
         else rc = qs_launch_phase(s, data, d.n_act[i]);
         cudaEventRecord(ev[i + 1], st);
@@ -514,9 +613,10 @@ extern "C" int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *o
 extern "C" int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype)
 {
     if (!sc || (dtype != QS_C64 && dtype != QS_C128)) return qs_fail(QS_EINVAL, "qs_schedule_upload_bytes");
-    std::vector<size_t> off;
+    std::vector<size_t> off, to;
     std::vector<int> na;
-    return (int64_t)schedule_blob(sc, dtype, off, na).size();
+    std::vector<std::array<int, 5>> tq;
+    return (int64_t)schedule_blob(sc, dtype, off, na, to, tq).size();
 }
 
 extern "C" int qs_set_device(int device)

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cstddef>
+#include <array>
 #include <vector>
 #include <utility>
 
@@ -45,6 +46,8 @@ struct qs_dev_sched {
     size_t bytes = 0;
     std::vector<size_t> offset;          // byte offset of op i's data in pool
     std::vector<int> n_act;              // phase ops: number of CZ partner terms
+    std::vector<size_t> tc_off;          // dense ops: offset of the tensor-core pack in op data (0: none)
+    std::vector<std::array<int, 5>> tc_q;  // dense ops: the 5 qubits the tensor-core sweep uses
 };
 
 struct qs_schedule {
@@ -86,5 +89,6 @@ int qs_check_status(qs_state *s);
 
 // Tensor-core 5-qubit sweep (qs_tc.cu).
 std::vector<uint8_t> qs_pack_tc_c64(const std::vector<double> &sorted_matrix);
+std::vector<uint8_t> qs_pack_tc_c128(const std::vector<double> &sorted_matrix);
 size_t qs_tc_pack_bytes(int dtype);
 int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack);

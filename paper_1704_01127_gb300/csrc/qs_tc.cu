@@ -19,6 +19,7 @@
 // apart (leading byte offset), 8-row groups 2048 B apart (stride byte offset).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -47,12 +48,12 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 
 // shared-memory matrix descriptor (tcgen05): start >> 4, LBO >> 4, SBO >> 4,
 // version 1 at bit 46, base offset 0, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo = kSBO)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
     d |= (uint64_t)((kLBO >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
@@ -81,6 +82,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
@@ -131,6 +141,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
         : "r"(taddr));
 #pragma unroll
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+// 8 consecutive 32-bit columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld()
 {
@@ -213,18 +233,25 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const f
 
     const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
     uint32_t parity = 0;
-    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const uint64_t g = tile * kRows + tid;
-        const bool valid = g < n_groups;
-        float2 *p = psi + (valid ? base5(g, t) : 0);
-        // gather + split: members 2c and 2c+1 fill K columns 4c..4c+3
+    // software pipeline: the next tile's amplitudes are loaded into registers
+    // while the tensor cores work on the current one
+    float2 v[32];
+    uint64_t tile = blockIdx.x;
+    bool valid = false;
+    float2 *p = psi;
+    auto load_tile = [&](uint64_t tl, float2 *vv, bool &val, float2 *&pp) {
+        const uint64_t g = tl * kRows + tid;
+        val = tl < n_tiles && g < n_groups;
+        pp = psi + (val ? base5(g, t) : 0);
+#pragma unroll
+        for (int x = 0; x < 32; x++) vv[x] = val ? pp[off5(x, t)] : make_float2(0.f, 0.f);
+    };
+    load_tile(tile, v, valid, p);
+    for (; tile < n_tiles; tile += gridDim.x) {
+        // split: members 2c and 2c+1 fill K columns 4c..4c+3
 #pragma unroll
         for (int c = 0; c < 16; c++) {
-            float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-            if (valid) {
-                v0 = p[off5(2 * c, t)];
-                v1 = p[off5(2 * c + 1, t)];
-            }
+            const float2 v0 = v[2 * c], v1 = v[2 * c + 1];
             float4 h = make_float4(tf32_head(v0.x), tf32_head(v0.y), tf32_head(v1.x), tf32_head(v1.y));
             float4 tl = make_float4(tf32_round(v0.x - h.x), tf32_round(v0.y - h.y), tf32_round(v1.x - h.z),
                                     tf32_round(v1.y - h.w));
@@ -245,6 +272,9 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const f
             }
             mma_commit(mbar_a);
         }
+        float2 *const p_cur = p;
+        const bool valid_cur = valid;
+        load_tile(tile + gridDim.x, v, valid, p);
         bool ok = false;
         for (long it = 0; it < kWaitLimit; it++)
             if (mbar_try_wait(mbar_a, parity)) {
@@ -263,14 +293,16 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const f
         }
         parity ^= 1;
         tc_fence_after();
-        float r[kN];
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-        for (int c = 0; c < kN / 16; c++) tmem_ld16(lane_addr + c * 16, r + c * 16);
-        tmem_wait_ld();
-        if (valid) {
+        for (int c = 0; c < kN / 16; c++) {
+            float r[16];
+            tmem_ld16(lane_addr + c * 16, r);
+            tmem_wait_ld();
+            if (valid_cur) {
 #pragma unroll
-            for (int l = 0; l < 32; l++) p[off5(l, t)] = make_float2(r[2 * l], r[2 * l + 1]);
+                for (int l = 0; l < 8; l++) p_cur[off5(8 * c + l, t)] = make_float2(r[2 * l], r[2 * l + 1]);
+            }
         }
         tc_fence_before();
         __syncthreads();
@@ -280,7 +312,254 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const f
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-bool g_attr_set[64] = {false};
+
+// ----------------------------------------------------------------------------
+// complex128: exact integer slices on the bf16 tensor path.
+//
+// Each row r (group) is scaled by its largest exponent E_r and each column n of
+// B^T by its largest exponent G_n; a value m 2^{e-1075} becomes the fixed-point
+// integer F = round(m 2^{e-E-7}) (half to even), |F| <= 2^46, so
+// F = sum_{s<6} d_s 2^{8(5-s)}
+// with balanced digits d_s in [-128, 127] (exact in bf16).  With A_i, B_j the
+// digit planes and T = sum_{d<=6} D_d 2^{8(5-d)},
+//   sum_k a_rk b_kn ~ 2^{E_r + G_n - 2096} T[r][n],  D_d = sum_{i+j=d} (A_i B_j^T),
+// and the planes with i + j = d <= 6 are summed in accumulator D_d (TMEM; the
+// dropped planes, d >= 7, weigh about 2^-51 of the result).  Every product of
+// digits is an integer of magnitude <= 2^14 and a 64-term sum <= 2^20, so
+// D_0..D_3 (at most four products) are exact integers of magnitude <= 2^22 in
+// FP32; D_4..D_6 carry weight <= 2^-32 and are combined in FP32.  The FP64
+// result is rebuilt with integer arithmetic only.
+// ----------------------------------------------------------------------------
+constexpr int kSlices = 6;                                   // digit planes of A (the state)
+constexpr int kSlicesB = 7;                                  // digit planes of B (the unitary)
+constexpr int kDiags = 7;                                    // accumulators D_0 .. D_6
+constexpr uint32_t kSBO16 = 1024;                            // 8 K-chunks x 128 B (16-bit elements)
+constexpr size_t kPlaneA = (size_t)kRows * kK * 2;           // 16 KB per A digit plane
+constexpr size_t kPlaneB = (size_t)kN * kK * 2;              // 8 KB per B digit plane
+constexpr size_t kSmemC128 = kSlices * kPlaneA + kSlicesB * kPlaneB + 256;   // + column exponents
+constexpr int kTmemCols128 = 512;
+// D fp32, A/B bf16 (format 1), K-major, N = 64, M = 128
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                               ((uint32_t)(kRows >> 4) << 24);
+
+// byte offset of 16-bit element (row, k) in a K-major no-swizzle tile with 64 K
+__host__ __device__ __forceinline__ uint32_t cm_off16(int row, int k)
+{
+    return (uint32_t)((((row >> 3) * (kK / 8)) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Fixed point of a double relative to biased exponent E (|F| <= 2^46, rounded
+// to nearest), plus the digit bias, as an unsigned 64-bit integer.
+__device__ __forceinline__ uint64_t fixed48(double a, int E)
+{
+    const uint64_t bits = (uint64_t)__double_as_longlong(a);
+    const int e = (int)((bits >> 52) & 0x7FF);
+    const int shift = E + 7 - e;
+    uint64_t F = 0;
+    if (e != 0 && shift < 60) {
+        const uint64_t m = (bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+        // round half to even: the structured amplitudes of early circuit layers
+        // hit exact ties often, and rounding ties up would bias the norm
+        F = (m + (1ULL << (shift - 1)) - 1 + ((m >> shift) & 1)) >> shift;
+        if (bits >> 63) F = 0 - F;
+    }
+    return F + 0x808080808080ULL;
+}
+
+// bf16 bits of (byte - 128) for byte in [0, 255]: 2^23 + byte - (2^23 + 128) is
+// exact in fp32 and has at most 8 significant bits.
+__device__ __forceinline__ uint32_t digit_bf16(uint32_t byte)
+{
+    return __float_as_uint(__uint_as_float(0x4B000000u | byte) - 8388736.0f) >> 16;
+}
+
+// exact int from an fp32 integer of magnitude <= 2^22
+__device__ __forceinline__ int exact_int(float x)
+{
+    return __float_as_int(x + 12582912.0f) - 0x4B400000;
+}
+
+// T * 2^X as a double (T signed, |T| < 2^62), integer arithmetic only
+__device__ __forceinline__ double ldexp_int(long long T, int X)
+{
+    if (T == 0) return 0.0;
+    const uint64_t sign = T < 0 ? (1ULL << 63) : 0;
+    uint64_t A = T < 0 ? (uint64_t)(-T) : (uint64_t)T;
+    const int lz = __clzll((long long)A);
+    A <<= lz;                                   // leading one at bit 63
+    uint64_t mant = A >> 11;                    // 53 bits
+    const uint64_t rest = A & 0x7FF;
+    if (rest > 0x400 || (rest == 0x400 && (mant & 1))) mant++;
+    int ex = 63 - lz + X + 1023;
+    if (mant >> 53) {                           // rounding carried into bit 53
+        mant >>= 1;
+        ex++;
+    }
+    if (ex <= 0) return 0.0;
+    return __longlong_as_double((long long)(sign | ((uint64_t)ex << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
+}
+
+// 256 threads: thread t owns row (t & 127) and half h = t >> 7 of that row's
+// 32 amplitudes (members 16h .. 16h+15, K columns 32h .. 32h+31); warp w reads
+// TMEM lanes 32 (w & 3) .. +31, the output columns of its half.
+__global__ void __launch_bounds__(256, 1)
+k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const uint8_t *__restrict__ bpack,
+                 int *__restrict__ status)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *A = smem;                                         // kSlices planes
+    uint8_t *B = smem + kSlices * kPlaneA;                     // kSlices planes
+    int *Gcol = reinterpret_cast<int *>(B + kSlicesB * kPlaneB);
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int rowexp[2][kRows];
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (kRows - 1), half = tid >> 7;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(bpack);
+        uint4 *dst = reinterpret_cast<uint4 *>(B);
+        for (int i = tid; i < (int)((kSlicesB * kPlaneB + 256) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(&tmem_base_s), kTmemCols128);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar), 1);
+        fence_mbar_init();
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+    const uint32_t mbar_a = smem_u32(&mbar);
+    const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+
+    const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
+    uint32_t parity = 0;
+    // software pipeline: the next tile's amplitudes are loaded into registers
+    // while the tensor cores and the epilogue work on the current one
+    double2 v[16];
+    uint64_t tile = blockIdx.x;
+    bool valid = false;
+    double2 *p = psi;
+    auto load_tile = [&](uint64_t tl, double2 *vv, bool &val, double2 *&pp) {
+        const uint64_t g = tl * kRows + row;
+        val = tl < n_tiles && g < n_groups;
+        pp = psi + (val ? base5(g, t) : 0);
+#pragma unroll
+        for (int x = 0; x < 16; x++) vv[x] = val ? pp[off5(16 * half + x, t)] : make_double2(0.0, 0.0);
+    };
+    load_tile(tile, v, valid, p);
+    for (; tile < n_tiles; tile += gridDim.x) {
+        int emax = 0;
+#pragma unroll
+        for (int x = 0; x < 16; x++) {
+            emax = max(emax, (int)((__double_as_longlong(v[x].x) >> 52) & 0x7FF));
+            emax = max(emax, (int)((__double_as_longlong(v[x].y) >> 52) & 0x7FF));
+        }
+        rowexp[half][row] = emax;
+        __syncthreads();
+        const int E = max(rowexp[0][row], rowexp[1][row]);
+        // digits: 4 chunks of 8 K-columns (4 members) per slice
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            uint64_t G[8];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                G[2 * j] = fixed48(v[4 * c + j].x, E);
+                G[2 * j + 1] = fixed48(v[4 * c + j].y, E);
+            }
+            const int k0 = 32 * half + 8 * c;
+#pragma unroll
+            for (int sl = 0; sl < kSlices; sl++) {
+                const int sh = 8 * (5 - sl);
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    uint32_t lo = digit_bf16((uint32_t)(G[2 * j] >> sh) & 0xFF);
+                    uint32_t hi = digit_bf16((uint32_t)(G[2 * j + 1] >> sh) & 0xFF);
+                    w[j] = lo | (hi << 16);
+                }
+                *reinterpret_cast<uint4 *>(A + sl * kPlaneA + cm_off16(row, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int d = 0; d < kDiags; d++) {
+                bool first = true;
+#pragma unroll
+                for (int i = 0; i <= d; i++) {
+                    const int j = d - i;
+                    if (i >= kSlices || j >= kSlicesB) continue;
+#pragma unroll
+                    for (int ks = 0; ks < kK / 16; ks++) {
+                        const uint32_t koff = ks * 2 * kLBO;   // 16 bf16 = two core matrices along K
+                        mma_bf16(tmem + 64 * d, smem_desc(a0 + i * kPlaneA + koff, kSBO16),
+                                 smem_desc(b0 + j * kPlaneB + koff, kSBO16), kIdescBf16, first ? 0u : 1u);
+                        first = false;
+                    }
+                }
+            }
+            mma_commit(mbar_a);
+        }
+        double2 *const p_cur = p;
+        const bool valid_cur = valid;
+        load_tile(tile + gridDim.x, v, valid, p);
+        bool ok = false;
+        for (long it = 0; it < kWaitLimit; it++)
+            if (mbar_try_wait(mbar_a, parity)) {
+                ok = true;
+                break;
+            }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(status, 1);
+                for (long it = 0; it < kWaitLimit; it++)
+                    if (mbar_try_wait(mbar_a, parity)) break;
+            }
+            break;
+        }
+        parity ^= 1;
+        tc_fence_after();
+        const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+#pragma unroll 1
+        for (int c = 0; c < 4; c++) {
+            const int col0 = 32 * half + 8 * c;
+            float D[kDiags][8];
+#pragma unroll
+            for (int d = 0; d < kDiags; d++) tmem_ld8(lane_addr + 64 * d + col0, D[d]);
+            tmem_wait_ld();
+            double out[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                long long U = ((long long)exact_int(D[0][q]) << 24) + ((long long)exact_int(D[1][q]) << 16) +
+                              ((long long)exact_int(D[2][q]) << 8) + (long long)exact_int(D[3][q]);
+                // D_4 + D_5 / 256 + D_6 / 65536
+                float L = fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]);
+                long long T = (U << 16) + (long long)__float2ll_rn(L * 256.0f);
+                out[q] = ldexp_int(T, E + Gcol[col0 + q] - 2096);
+            }
+            if (valid_cur) {
+#pragma unroll
+                for (int l = 0; l < 4; l++) p_cur[off5(16 * half + 4 * c + l, t)] = make_double2(out[2 * l], out[2 * l + 1]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols128);
+}
+
+bool g_attr_set[2][64] = {{false}};
 
 }  // namespace
 
@@ -316,30 +595,92 @@ std::vector<uint8_t> qs_pack_tc_c64(const std::vector<double> &M)
     return out;
 }
 
-size_t qs_tc_pack_bytes(int dtype) { return dtype == QS_C64 ? 2 * kBBytesF32 : 0; }
+// Host: digit planes of the real-form matrix for the complex128 path.  Per
+// column n of B^T the largest biased exponent G_n; a value becomes
+// F' = round(m 2^{e-G_n+1}), |F'| <= 2^54, = sum_{j<7} e_j 2^{8(6-j)} with
+// balanced digits, i.e. the same scale as the state's digits (weight
+// 2^{8(5-j)} of 2^{G_n-1068}) plus one extra plane, so the unitary is carried
+// to about 2^-55; bf16 planes in the canonical layout, then the 64 exponents.
+std::vector<uint8_t> qs_pack_tc_c128(const std::vector<double> &M)
+{
+    std::vector<uint8_t> out(kSlicesB * kPlaneB + 256, 0);
+    double bt[kN][kK];
+    for (int l = 0; l < 32; l++)
+        for (int x = 0; x < 32; x++) {
+            double re = M[2 * (l * 32 + x)], im = M[2 * (l * 32 + x) + 1];
+            bt[2 * l][2 * x] = re;
+            bt[2 * l][2 * x + 1] = -im;
+            bt[2 * l + 1][2 * x] = im;
+            bt[2 * l + 1][2 * x + 1] = re;
+        }
+    int *Gcol = reinterpret_cast<int *>(out.data() + kSlicesB * kPlaneB);
+    for (int n = 0; n < kN; n++) {
+        int G = 0;
+        for (int k = 0; k < kK; k++) {
+            uint64_t b;
+            std::memcpy(&b, &bt[n][k], 8);
+            G = std::max(G, (int)((b >> 52) & 0x7FF));
+        }
+        Gcol[n] = G;
+        for (int k = 0; k < kK; k++) {
+            uint64_t b;
+            std::memcpy(&b, &bt[n][k], 8);
+            int e = (int)((b >> 52) & 0x7FF), shift = G - 1 - e;
+            uint64_t F = 0;
+            if (e != 0 && shift < 60) {
+                uint64_t m = (b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+                F = shift < 0    ? (m << -shift)
+                    : shift == 0 ? m
+                                 : (m + (1ULL << (shift - 1)) - 1 + ((m >> shift) & 1)) >> shift;   // half to even
+                if (b >> 63) F = 0 - F;
+            }
+            uint64_t Gb = F + 0x80808080808080ULL;
+            for (int sl = 0; sl < kSlicesB; sl++) {
+                int dig = (int)((Gb >> (8 * (6 - sl))) & 0xFF) - 128;
+                float f = (float)dig;
+                uint32_t u;
+                std::memcpy(&u, &f, 4);
+                uint16_t h = (uint16_t)(u >> 16);
+                std::memcpy(out.data() + sl * kPlaneB + cm_off16(n, k), &h, 2);
+            }
+        }
+    }
+    return out;
+}
+
+size_t qs_tc_pack_bytes(int dtype) { return dtype == QS_C64 ? 2 * kBBytesF32 : kSlicesB * kPlaneB + 256; }
 
 int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack)
 {
-    if (s->dtype != QS_C64) return qs_fail(QS_EUNSUPPORTED, "tensor-core sweep: complex64 only");
+    const bool c64 = s->dtype == QS_C64;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (dev >= 0 && dev < 64 && !g_attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_dense5_tc_c64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSmemF32);
+    if (dev < 0 || dev >= 64) return qs_fail(QS_EUNSUPPORTED, "device %d", dev);
+    if (!g_attr_set[c64][dev]) {
+        cudaError_t e = c64 ? cudaFuncSetAttribute(k_dense5_tc_c64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kSmemF32)
+                            : cudaFuncSetAttribute(k_dense5_tc_c128, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kSmemC128);
         if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
-        g_attr_set[dev] = true;
+        g_attr_set[c64][dev] = true;
     }
     Targets5 t;
     for (int j = 0; j < 5; j++) t.q[j] = sorted_qubits[j];
     const uint64_t groups = 1ULL << (s->n - 5);
     const uint64_t tiles = (groups + kRows - 1) / kRows;
-    int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms * 2);
     int *status;
     int rc = qs_state_status(s, &status);
     if (rc) return rc;
-    k_dense5_tc_c64<<<grid, kRows, kSmemF32, (cudaStream_t)s->stream>>>(
-        (float2 *)s->amp, groups, t, (const float *)dev_pack, status);
+    if (c64) {
+        int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms * 2);
+        k_dense5_tc_c64<<<grid, kRows, kSmemF32, (cudaStream_t)s->stream>>>(
+            (float2 *)s->amp, groups, t, (const float *)dev_pack, status);
+    } else {
+        int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms);
+        k_dense5_tc_c128<<<grid, 2 * kRows, kSmemC128, (cudaStream_t)s->stream>>>(
+            (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
+    }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "tc launch: %s", cudaGetErrorString(e));
 }
