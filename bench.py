@@ -32,6 +32,9 @@ WORKLOADS = {
     "5x6_d25_c64": (5, 6, (), 25, "c64", 5),
     "4x8_d25_c64": (4, 8, (), 25, "c64", 5),
     "4x4_d10_c128": (4, 4, (), 10, "c128", 5),
+    # small cases (256 MB states, still larger than L2) for profiler captures
+    "4x6_d25_c128": (4, 6, (), 25, "c128", 5),
+    "5x5_d25_c64": (5, 5, (), 25, "c64", 5),
 }
 
 

@@ -121,7 +121,15 @@ __global__ void k_diag(typename cplx<R>::t *__restrict__ psi, uint64_t N, int k,
 }
 
 // Multiply by e^{i pi m / 4}: an odd m first takes one factor
-// e^{i pi/4} = (1 + i)/sqrt(2), the rest is a quarter turn (no arithmetic).
+// e^{i pi/4} = (1 + i)/sqrt(2); the remaining quarter turn i^{m >> 1} only swaps
+// and negates, done on the bit patterns (sign-bit flips) so complex128 spends
+// no FP64 instruction on it.
+__device__ __forceinline__ float flip(float x, bool f) { return __int_as_float(__float_as_int(x) ^ (f ? 0x80000000 : 0)); }
+__device__ __forceinline__ double flip(double x, bool f)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (f ? (long long)0x8000000000000000ULL : 0LL));
+}
+
 template <typename C, typename R>
 __device__ __forceinline__ C rotate8(C a, int m)
 {
@@ -132,13 +140,11 @@ __device__ __forceinline__ C rotate8(C a, int m)
         b.y = (a.x + a.y) * r;
         a = b;
     }
+    const int q = (m >> 1) & 3;                  // i^q: 0 (x, y), 1 (-y, x), 2 (-x, -y), 3 (y, -x)
+    const bool sw = q & 1;
     C o;
-    switch ((m >> 1) & 3) {
-    case 0: o = a; break;
-    case 1: o.x = -a.y; o.y = a.x; break;
-    case 2: o.x = -a.x; o.y = -a.y; break;
-    default: o.x = a.y; o.y = -a.x; break;
-    }
+    o.x = flip(sw ? a.y : a.x, q == 1 || q == 2);
+    o.y = flip(sw ? a.x : a.y, q >= 2);
     return o;
 }
 

@@ -328,7 +328,8 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const f
 // digits is an integer of magnitude <= 2^14 and a 64-term sum <= 2^20, so
 // D_0..D_3 (at most four products) are exact integers of magnitude <= 2^22 in
 // FP32; D_4..D_6 carry weight <= 2^-32 and are combined in FP32.  The FP64
-// result is rebuilt with integer arithmetic only.
+// result is one int64 -> double conversion with the scale added to the
+// exponent field.
 // ----------------------------------------------------------------------------
 constexpr int kSlices = 6;                                   // digit planes of A (the state)
 constexpr int kSlicesB = 7;                                  // digit planes of B (the unitary)
@@ -366,11 +367,19 @@ __device__ __forceinline__ uint64_t fixed48(double a, int E)
     return F + 0x808080808080ULL;
 }
 
-// bf16 bits of (byte - 128) for byte in [0, 255]: 2^23 + byte - (2^23 + 128) is
-// exact in fp32 and has at most 8 significant bits.
-__device__ __forceinline__ uint32_t digit_bf16(uint32_t byte)
+// Digit byte b of a 32-bit word, as the fp32 value (byte - 128): one byte
+// permute builds 0x4B0000uu (= 2^23 + byte), one add subtracts 2^23 + 128; the
+// result is exact and has at most 8 significant bits, so its upper 16 bits are
+// the bf16 encoding.
+template <int b>
+__device__ __forceinline__ float digit_f32(uint32_t word)
 {
-    return __float_as_uint(__uint_as_float(0x4B000000u | byte) - 8388736.0f) >> 16;
+    return __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540u | b)) - 8388736.0f;
+}
+// bf16 pair (lo, hi) from two exact fp32 digits
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
 }
 
 // exact int from an fp32 integer of magnitude <= 2^22
@@ -379,43 +388,33 @@ __device__ __forceinline__ int exact_int(float x)
     return __float_as_int(x + 12582912.0f) - 0x4B400000;
 }
 
-// T * 2^X as a double (T signed, |T| < 2^62), integer arithmetic only
-__device__ __forceinline__ double ldexp_int(long long T, int X)
+// T * 2^X as a double (|T| < 2^62): one int64 -> double conversion (rounded
+// to nearest), then X added to the exponent field (no FP64 arithmetic)
+__device__ __forceinline__ double scale_int(long long T, int X)
 {
     if (T == 0) return 0.0;
-    const uint64_t sign = T < 0 ? (1ULL << 63) : 0;
-    uint64_t A = T < 0 ? (uint64_t)(-T) : (uint64_t)T;
-    const int lz = __clzll((long long)A);
-    A <<= lz;                                   // leading one at bit 63
-    uint64_t mant = A >> 11;                    // 53 bits
-    const uint64_t rest = A & 0x7FF;
-    if (rest > 0x400 || (rest == 0x400 && (mant & 1))) mant++;
-    int ex = 63 - lz + X + 1023;
-    if (mant >> 53) {                           // rounding carried into bit 53
-        mant >>= 1;
-        ex++;
-    }
-    if (ex <= 0) return 0.0;
-    return __longlong_as_double((long long)(sign | ((uint64_t)ex << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
+    const long long b = __double_as_longlong(__ll2double_rn(T)) + ((long long)X << 52);
+    return __longlong_as_double(b);
 }
 
-// 256 threads: thread t owns row (t & 127) and half h = t >> 7 of that row's
-// 32 amplitudes (members 16h .. 16h+15, K columns 32h .. 32h+31); warp w reads
-// TMEM lanes 32 (w & 3) .. +31, the output columns of its half.
-__global__ void __launch_bounds__(256, 1)
+// 512 threads: thread t owns row (t & 127) and quarter h = t >> 7 of that row's
+// 32 amplitudes (members 8h .. 8h+7, K columns 16h .. 16h+15); warp w reads
+// TMEM lanes 32 (w & 3) .. +31 and the output columns of its quarter.
+constexpr int kTpr128 = 4;                                   // threads per row
+__global__ void __launch_bounds__(kRows * kTpr128, 1)
 k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const uint8_t *__restrict__ bpack,
                  int *__restrict__ status)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *A = smem;                                         // kSlices planes
-    uint8_t *B = smem + kSlices * kPlaneA;                     // kSlices planes
+    uint8_t *B = smem + kSlices * kPlaneA;                     // kSlicesB planes
     int *Gcol = reinterpret_cast<int *>(B + kSlicesB * kPlaneB);
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base_s;
-    __shared__ int rowexp[2][kRows];
+    __shared__ int rowexp[kTpr128][kRows];
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = tid & (kRows - 1), half = tid >> 7;
+    const int row = tid & (kRows - 1), part = tid >> 7;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(bpack);
         uint4 *dst = reinterpret_cast<uint4 *>(B);
@@ -441,7 +440,7 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
     uint32_t parity = 0;
     // software pipeline: the next tile's amplitudes are loaded into registers
     // while the tensor cores and the epilogue work on the current one
-    double2 v[16];
+    double2 v[8];
     uint64_t tile = blockIdx.x;
     bool valid = false;
     double2 *p = psi;
@@ -450,41 +449,47 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
         val = tl < n_tiles && g < n_groups;
         pp = psi + (val ? base5(g, t) : 0);
 #pragma unroll
-        for (int x = 0; x < 16; x++) vv[x] = val ? pp[off5(16 * half + x, t)] : make_double2(0.0, 0.0);
+        for (int x = 0; x < 8; x++) vv[x] = val ? pp[off5(8 * part + x, t)] : make_double2(0.0, 0.0);
     };
     load_tile(tile, v, valid, p);
     for (; tile < n_tiles; tile += gridDim.x) {
         int emax = 0;
 #pragma unroll
-        for (int x = 0; x < 16; x++) {
+        for (int x = 0; x < 8; x++) {
             emax = max(emax, (int)((__double_as_longlong(v[x].x) >> 52) & 0x7FF));
             emax = max(emax, (int)((__double_as_longlong(v[x].y) >> 52) & 0x7FF));
         }
-        rowexp[half][row] = emax;
+        rowexp[part][row] = emax;
         __syncthreads();
-        const int E = max(rowexp[0][row], rowexp[1][row]);
-        // digits: 4 chunks of 8 K-columns (4 members) per slice
+        const int E = max(max(rowexp[0][row], rowexp[1][row]), max(rowexp[2][row], rowexp[3][row]));
+        // digits: 2 chunks of 8 K-columns (4 members) per slice; digit s of a
+        // value is byte 5 - s of its biased fixed-point integer G
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            uint64_t G[8];
+        for (int c = 0; c < 2; c++) {
+            uint32_t glo[8], ghi[8];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                G[2 * j] = fixed48(v[4 * c + j].x, E);
-                G[2 * j + 1] = fixed48(v[4 * c + j].y, E);
+                const uint64_t g0 = fixed48(v[4 * c + j].x, E), g1 = fixed48(v[4 * c + j].y, E);
+                glo[2 * j] = (uint32_t)g0;
+                ghi[2 * j] = (uint32_t)(g0 >> 32);
+                glo[2 * j + 1] = (uint32_t)g1;
+                ghi[2 * j + 1] = (uint32_t)(g1 >> 32);
             }
-            const int k0 = 32 * half + 8 * c;
-#pragma unroll
-            for (int sl = 0; sl < kSlices; sl++) {
-                const int sh = 8 * (5 - sl);
-                uint32_t w[4];
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    uint32_t lo = digit_bf16((uint32_t)(G[2 * j] >> sh) & 0xFF);
-                    uint32_t hi = digit_bf16((uint32_t)(G[2 * j + 1] >> sh) & 0xFF);
-                    w[j] = lo | (hi << 16);
-                }
-                *reinterpret_cast<uint4 *>(A + sl * kPlaneA + cm_off16(row, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
-            }
+            uint8_t *dst = A + cm_off16(row, 16 * part + 8 * c);
+            uint4 w;
+#define QS_DIGIT_PLANE(SL, WORDS, BYTE)                                                        \
+    w.x = pack_bf16(digit_f32<BYTE>(WORDS[0]), digit_f32<BYTE>(WORDS[1]));                   \
+    w.y = pack_bf16(digit_f32<BYTE>(WORDS[2]), digit_f32<BYTE>(WORDS[3]));                   \
+    w.z = pack_bf16(digit_f32<BYTE>(WORDS[4]), digit_f32<BYTE>(WORDS[5]));                   \
+    w.w = pack_bf16(digit_f32<BYTE>(WORDS[6]), digit_f32<BYTE>(WORDS[7]));                   \
+    *reinterpret_cast<uint4 *>(dst + (SL) * kPlaneA) = w;
+            QS_DIGIT_PLANE(0, ghi, 1)      // bits 40-47
+            QS_DIGIT_PLANE(1, ghi, 0)      // bits 32-39
+            QS_DIGIT_PLANE(2, glo, 3)      // bits 24-31
+            QS_DIGIT_PLANE(3, glo, 2)      // bits 16-23
+            QS_DIGIT_PLANE(4, glo, 1)      // bits 8-15
+            QS_DIGIT_PLANE(5, glo, 0)      // bits 0-7
+#undef QS_DIGIT_PLANE
         }
         fence_proxy_async();
         tc_fence_before();
@@ -530,8 +535,8 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
         tc_fence_after();
         const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
-        for (int c = 0; c < 4; c++) {
-            const int col0 = 32 * half + 8 * c;
+        for (int c = 0; c < 2; c++) {
+            const int col0 = 16 * part + 8 * c;
             float D[kDiags][8];
 #pragma unroll
             for (int d = 0; d < kDiags; d++) tmem_ld8(lane_addr + 64 * d + col0, D[d]);
@@ -541,14 +546,14 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
             for (int q = 0; q < 8; q++) {
                 long long U = ((long long)exact_int(D[0][q]) << 24) + ((long long)exact_int(D[1][q]) << 16) +
                               ((long long)exact_int(D[2][q]) << 8) + (long long)exact_int(D[3][q]);
-                // D_4 + D_5 / 256 + D_6 / 65536
+                // D_4 + D_5 / 256 + D_6 / 65536; 256 L < 2^31
                 float L = fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]);
-                long long T = (U << 16) + (long long)__float2ll_rn(L * 256.0f);
-                out[q] = ldexp_int(T, E + Gcol[col0 + q] - 2096);
+                long long T = (U << 16) + (long long)__float2int_rn(L * 256.0f);
+                out[q] = scale_int(T, E + Gcol[col0 + q] - 2096);
             }
             if (valid_cur) {
 #pragma unroll
-                for (int l = 0; l < 4; l++) p_cur[off5(16 * half + 4 * c + l, t)] = make_double2(out[2 * l], out[2 * l + 1]);
+                for (int l = 0; l < 4; l++) p_cur[off5(8 * part + 4 * c + l, t)] = make_double2(out[2 * l], out[2 * l + 1]);
             }
         }
         tc_fence_before();
@@ -678,7 +683,7 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
             (float2 *)s->amp, groups, t, (const float *)dev_pack, status);
     } else {
         int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms);
-        k_dense5_tc_c128<<<grid, 2 * kRows, kSmemC128, (cudaStream_t)s->stream>>>(
+        k_dense5_tc_c128<<<grid, kTpr128 * kRows, kSmemC128, (cudaStream_t)s->stream>>>(
             (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
     }
     cudaError_t e = cudaGetLastError();

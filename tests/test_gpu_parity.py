@@ -286,3 +286,19 @@ def test_tc_c128_zero_and_tiny_rows():
         out = qs.qs_get_amplitudes(s.h)
     assert np.max(np.abs(out - ref)) < 1e-15
     assert np.all(out[: 1 << 9] == 0)
+
+
+def test_entropy_table_log_accuracy():
+    """The table-driven logarithm of the entropy reduction against libm on
+    probabilities spread over many binades (closed form: -sum p ln p)."""
+    n = 14
+    g = np.random.Generator(np.random.PCG64(5))
+    mag = np.exp(g.uniform(-60, 0, 1 << n))
+    psi = (mag * np.exp(1j * g.uniform(0, 6.3, 1 << n))).astype(np.complex128)
+    psi /= np.sqrt(np.sum(np.abs(psi) ** 2))
+    p = np.abs(psi) ** 2
+    want = -np.sum(p[p > 0] * np.log(p[p > 0]))
+    with State(n, qs.QS_C128) as s:
+        qs.qs_set_amplitudes(s.h, psi)
+        got = qs.qs_stats(s.h)[1]
+    assert abs(got - want) <= 1e-13 * max(1.0, abs(want))
