@@ -287,6 +287,83 @@ def run_ours(args):
     return line
 
 
+# ------------------------------------------------------- batched workload
+
+def run_batch(args):
+    """512 independent circuits (seeds 0..511; grids 4x4 / 4x5 / 3x7, depths
+    8..40), complex64, one persistent launch replayed from a CUDA graph, against
+    a loop of single-circuit launches of the same schedules."""
+    import torch
+    from paper_1704_01127_gb300 import build as _build
+    _build.build()
+    import paper_1704_01127_gb300.qs as qs
+    world, rank, local, dist = dist_setup(args)
+    qs.qs_set_device(local)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    n_circ = 512
+    circs = []
+    for s in range(n_circ):
+        r, c, d = qs.qs_batch_circuit_params(s)
+        circs.append(qs.qs_supremacy_circuit(r, c, d, s))
+    k_max, C, T, tune_ms = qs.qs_batch_autotune(circs, qs.QS_C64, stream)
+    scheds = [qs.qs_schedule_build(n, g, k_max=k_max) for (n, g) in circs]
+    b = qs.qs_batch_create(scheds, qs.QS_C64, stream)
+    qs.qs_batch_set_config(b, C, T)
+    for _ in range(args.warmup):
+        qs.qs_batch_run_graph(b)
+    torch.cuda.synchronize()
+    barrier(dist)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            qs.qs_batch_run_graph(b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = max_over_ranks(dist, e0.elapsed_time(e1) / 1e3)
+    st = qs.qs_batch_stats(b, n_circ)
+    qs.qs_batch_free(b)
+    # loop of single-circuit launches (default kernel paths), same schedules
+    states = {}
+    for (n, _) in circs:
+        if n not in states:
+            states[n] = qs.qs_alloc(n, qs.QS_C64, stream)
+    def loop():
+        for (n, _), sc in zip(circs, scheds):
+            qs.qs_init_basis(states[n], 0)
+            qs.qs_run_circuit(states[n], sc)
+    loop()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    loop()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_s = e0.elapsed_time(e1) / 1e3
+    for h in states.values():
+        qs.qs_free(h)
+    for sc in scheds:
+        qs.qs_schedule_free(sc)
+    if rank != 0:
+        return None
+    per_launch = elapsed / args.steps
+    return {
+        "metric": METRIC, "value": per_launch / n_circ, "unit": "s/circuit", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "512 circuits (seeds 0..511), grids 4x4/4x5/3x7, 8..40 CZ cycles, c64, "
+                               "one persistent launch per step from a CUDA graph",
+                   "autotuned": {"k_max": k_max, "cluster_ctas": C, "threads": T, "tune_ms": tune_ms},
+                   "l2": "states total %.0f MB; inputs re-initialised every launch" % (
+                       sum(8 << n for (n, _) in circs) / 1e6)},
+        "circuits_per_s": n_circ / per_launch, "loop_circuits_per_s": n_circ / loop_s,
+        "speedup_vs_loop": loop_s / per_launch,
+        "mean_m2": float(st[:, 3].mean()), "max_norm_drift": float(abs(st[:, 0] - 1).max()),
+        "gpu_launches": args.steps, "clocks": clk.summary(),
+    }
+
+
 # ------------------------------------------------------------ oracle (CPU) leg
 
 def cpu_baseline(args, n_steps):
@@ -346,7 +423,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="5x6_d25_c128")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch512_c64"], default="5x6_d25_c128")
     ap.add_argument("--plain", action="store_true", help="gate-by-gate form instead of fused")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison run")
     ap.add_argument("--no-e2e", action="store_true")
@@ -355,7 +432,12 @@ def main():
     if args.warmup < 3:
         print("note: warmup raised to 3", file=sys.stderr)
         args.warmup = 3
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload == "batch512_c64":
+        line = run_batch(args)
+    else:
+        line = run_ours(args)
     if line is not None:
         print(json.dumps(line))
 

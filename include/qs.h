@@ -246,6 +246,46 @@ int qs_run_circuit(qs_state *s, const qs_schedule *sc);
  * milliseconds to op_ms[i] (host, qs_schedule_num_ops entries). */
 int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *op_ms);
 
+/* ------------------------------------------------------------------------
+ * Batched simulation of many small circuits (one persistent launch).
+ * ---------------------------------------------------------------------- */
+typedef struct qs_batch qs_batch;   /* opaque, owned by the library */
+
+/* Grid and depth of the batched workload's circuit `seed` (this library's
+ * reading of "grids uniform over 4x4, 4x5, 3x7, depth uniform over 8..40"):
+ * r = SplitMix64 output 0 of (seed ^ 0x6A09E667F3BCC909); grid = r mod 3 in
+ * that order, cz_cycles = 8 + (r >> 32) mod 33.  The circuit itself is
+ * qs_supremacy_circuit(rows, cols, none removed, cz_cycles, seed). */
+int qs_batch_circuit_params(uint64_t seed, int *rows, int *cols, int *cz_cycles);
+
+/* One state per schedule (1..26 qubits, dense and phase ops), all in one
+ * device allocation, plus the packed op list.  Each run starts every state at
+ * |0...0> and applies its schedule; a cluster of CTAs owns one circuit at a
+ * time (ops in order, a cluster barrier between ops), circuits sorted by
+ * descending cost.  stream: cudaStream_t (non-NULL for graph replay). */
+int qs_batch_create(int n_circuits, const qs_schedule *const *schedules, int dtype, void *stream,
+                    qs_batch **out);
+void qs_batch_free(qs_batch *b);
+/* Launch configuration: CTAs per cluster in {1, 2, 4, 8}, threads in {128, 256, 512}. */
+int qs_batch_set_config(qs_batch *b, int cluster_ctas, int threads);
+int qs_batch_get_config(const qs_batch *b, int *cluster_ctas, int *threads);
+/* One persistent launch of the whole batch on the batch's stream. */
+int qs_batch_run(qs_batch *b);
+/* The same launch, captured once into a CUDA graph (re-captured when the
+ * configuration changes) and replayed. */
+int qs_batch_run_graph(qs_batch *b);
+/* Per circuit i: out[4i..4i+3] as qs_stats (FP64); synchronises the stream. */
+int qs_batch_stats(qs_batch *b, double *out);
+/* State i as complex128 in host memory (2^n_i amplitudes). */
+int qs_batch_get_amplitudes(qs_batch *b, int i, double *host_c128);
+/* Time all launch configurations; keep and report the fastest (ms per launch). */
+int qs_batch_tune(qs_batch *b, int *cluster_ctas, int *threads, float *ms);
+/* Autotuner of the batched path: for k_max in {3, 4, 5}, schedule every circuit
+ * (qs_schedule_build, fused, phase merge), build the batch, tune its launch
+ * configuration; report the fastest (k_max, cluster_ctas, threads, ms). */
+int qs_batch_autotune(int n_circuits, const int *n_qubits, const qs_gate *const *gates, const int *n_gates,
+                      int dtype, void *stream, int *k_max, int *cluster_ctas, int *threads, float *ms);
+
 #ifdef __cplusplus
 }
 #endif

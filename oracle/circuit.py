@@ -106,3 +106,16 @@ def from_text(text):
     n = int(rows[0][0])
     gates = [(int(r[0]), r[1], tuple(int(x) for x in r[2:])) for r in rows[1:]]
     return n, gates
+
+
+BATCH_GRIDS = ((4, 4), (4, 5), (3, 7))
+
+
+def batch_circuit_params(seed):
+    """Grid and CZ-cycle count of circuit `seed` of the batched workload (grids
+    uniform over 4x4, 4x5, 3x7; depths uniform over 8..40).  Reading: r is output
+    0 of SplitMix64 seeded with seed XOR 0x6A09E667F3BCC909; the grid is r mod 3
+    in the order above and the depth 8 + ((r >> 32) mod 33)."""
+    r = splitmix64(seed ^ 0x6A09E667F3BCC909, 0)
+    rows, cols = BATCH_GRIDS[r % 3]
+    return rows, cols, 8 + ((r >> 32) % 33)

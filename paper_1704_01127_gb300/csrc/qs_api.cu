@@ -9,6 +9,7 @@
 #include <mutex>
 #include <vector>
 
+#include "qs_device.cuh"
 #include "qs_internal.h"
 
 namespace {
@@ -71,16 +72,7 @@ __global__ void k_set_one(C *psi, uint64_t x)
     psi[x] = o;
 }
 
-// p = fl(fl(re^2) + fl(im^2)) in FP64 (no contraction into an FMA).
-__device__ __forceinline__ double prob(double2 a)
-{
-    return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
-}
-__device__ __forceinline__ double prob(float2 a)
-{
-    double x = a.x, y = a.y;
-    return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
-}
+using qsd::prob;
 
 template <typename C>
 __global__ void k_probs(const C *__restrict__ psi, uint64_t first, uint64_t count, double *__restrict__ p)
@@ -90,42 +82,9 @@ __global__ void k_probs(const C *__restrict__ psi, uint64_t first, uint64_t coun
         p[i] = prob(psi[first + i]);
 }
 
-// Natural logarithm of a positive normal double, table-driven (P. T. P. Tang,
-// "Table-driven implementation of the logarithm function in IEEE floating-point
-// arithmetic", ACM TOMS 16(4), 1990): p = 2^e m, m in [1, 2); c_j is the centre
-// of the mantissa interval [1 + j/128, 1 + (j+1)/128) picked by the top seven
-// mantissa bits, r = m / c_j - 1 (|r| <= 1/256) and
-//   ln p = e ln 2 + ln c_j + ln(1 + r),  ln(1 + r) = r - r^2/2 + ... - r^6/6,
-// truncation error below r^7/7 < 2^-58.  ln c_j and 1/c_j come from the CUDA
-// math library once per block (shared-memory table).
-struct LogTable {
-    double inv[128], ln[128];
-};
-
-__device__ __forceinline__ void log_table_init(LogTable &t)
-{
-    for (int j = threadIdx.x; j < 128; j += blockDim.x) {
-        const double c = 1.0 + (j + 0.5) / 128.0;
-        t.inv[j] = 1.0 / c;
-        t.ln[j] = log(c);
-    }
-}
-
-__device__ __forceinline__ double log_tab(const LogTable &t, double p)
-{
-    const long long bits = __double_as_longlong(p);
-    const int e = (int)(bits >> 52) - 1023;
-    const int j = (int)((bits >> 45) & 127);
-    const double m = __longlong_as_double((bits & 0xFFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
-    const double r = fma(m, t.inv[j], -1.0);
-    double q = -1.0 / 6.0;
-    q = fma(q, r, 0.2);
-    q = fma(q, r, -0.25);
-    q = fma(q, r, 1.0 / 3.0);
-    q = fma(q, r, -0.5);
-    q = fma(q, r, 1.0);
-    return fma((double)e, 0.69314718055994530942, t.ln[j] + q * r);
-}
+using qsd::LogTable;
+using qsd::log_table_init;
+using qsd::log_tab;
 
 // Per-block FP64 partial sums of (p, -p ln p, N p, (N p)^2); NSTAT = 1 or 4.
 template <typename C, int NSTAT>

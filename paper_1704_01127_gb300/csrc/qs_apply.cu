@@ -6,17 +6,16 @@
 #include <cstring>
 #include <vector>
 
+#include "qs_device.cuh"
 #include "qs_internal.h"
 
 namespace {
 
-template <typename R> struct cplx;
-template <> struct cplx<double> { using t = double2; };
-template <> struct cplx<float> { using t = float2; };
-
-struct Targets {
-    int q[QS_MAX_K];   // ascending
-};
+using qsd::cplx;
+using qsd::Targets;
+using qsd::group_base;
+using qsd::member_offset;
+using qsd::rotate8;
 
 int g_sms = 0;
 int sm_count()
@@ -28,29 +27,6 @@ int sm_count()
         if (g_sms <= 0) g_sms = 1;
     }
     return g_sms;
-}
-
-// Insert a zero bit at each (ascending) target position: group id -> index of
-// the group's x = 0 member (Sec. 3.2: the c bits fill the non-target positions).
-template <int K>
-__device__ __forceinline__ uint64_t group_base(uint64_t g, const Targets &t)
-{
-#pragma unroll
-    for (int j = 0; j < K; j++) {
-        uint64_t lo = g & ((1ULL << t.q[j]) - 1);
-        g = ((g ^ lo) << 1) | lo;
-    }
-    return g;
-}
-
-template <int K>
-__device__ __forceinline__ uint64_t member_offset(int x, const Targets &t)
-{
-    uint64_t o = 0;
-#pragma unroll
-    for (int j = 0; j < K; j++)
-        if ((x >> j) & 1) o |= 1ULL << t.q[j];
-    return o;
 }
 
 // Dense k-qubit cluster: one thread per group c, the 2^K amplitudes gathered at
@@ -72,30 +48,8 @@ k_dense(typename cplx<R>::t *__restrict__ psi, uint64_t n_groups, Targets t,
         Us[i] = reinterpret_cast<const C *>(Ug)[i];
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += stride) {
-        C *p = psi + group_base<K>(g, t);
-        C v[D];
-#pragma unroll
-        for (int x = 0; x < D; x++) v[x] = p[member_offset<K>(x, t)];
-        // rows of U one at a time (kept rolled so v[] stays in registers)
-#pragma unroll 1
-        for (int l = 0; l < D; l++) {
-            R ar = 0, ai = 0;
-            const C *row = Us + l * D;
-#pragma unroll
-            for (int x = 0; x < D; x++) {
-                C m = row[x];
-                ar = fma(v[x].x, m.x, ar);
-                ai = fma(v[x].y, m.x, ai);
-                ar = fma(-v[x].y, m.y, ar);
-                ai = fma(v[x].x, m.y, ai);
-            }
-            C o;
-            o.x = ar;
-            o.y = ai;
-            p[member_offset<K>(l, t)] = o;
-        }
-    }
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += stride)
+        qsd::dense_group<R, K, false>(psi + group_base<K>(g, t), t, Us);
 }
 
 // Table diagonal on up to QS_MAX_DIAG_K qubits: psi_i *= d[x(i)].
@@ -120,34 +74,6 @@ __global__ void k_diag(typename cplx<R>::t *__restrict__ psi, uint64_t N, int k,
     }
 }
 
-// Multiply by e^{i pi m / 4}: an odd m first takes one factor
-// e^{i pi/4} = (1 + i)/sqrt(2); the remaining quarter turn i^{m >> 1} only swaps
-// and negates, done on the bit patterns (sign-bit flips) so complex128 spends
-// no FP64 instruction on it.
-__device__ __forceinline__ float flip(float x, bool f) { return __int_as_float(__float_as_int(x) ^ (f ? 0x80000000 : 0)); }
-__device__ __forceinline__ double flip(double x, bool f)
-{
-    return __longlong_as_double(__double_as_longlong(x) ^ (f ? (long long)0x8000000000000000ULL : 0LL));
-}
-
-template <typename C, typename R>
-__device__ __forceinline__ C rotate8(C a, int m)
-{
-    if (m & 1) {
-        const R r = (R)0.70710678118654752440;
-        C b;
-        b.x = (a.x - a.y) * r;
-        b.y = (a.x + a.y) * r;
-        a = b;
-    }
-    const int q = (m >> 1) & 3;                  // i^q: 0 (x, y), 1 (-y, x), 2 (-x, -y), 3 (y, -x)
-    const bool sw = q & 1;
-    C o;
-    o.x = flip(sw ? a.y : a.x, q == 1 || q == 2);
-    o.y = flip(sw ? a.x : a.y, q >= 2);
-    return o;
-}
-
 // Product of T-type phases and CZ signs (Sec. 2, Sec. 3.5): amplitude i gets
 // e^{i pi m(i)/4}, m(i) = sum_q c_q i_q + 4 sum_a i_a popc(i & P_a) mod 8, with
 // P_a the CZ partners b > a of qubit a.  The index splits into low bits l
@@ -168,7 +94,6 @@ k_phase(typename cplx<R>::t *__restrict__ psi, int n, const qs_phase_dev *__rest
     __shared__ uint64_t part[64];
     __shared__ int act[64];
     const int L = n < kPhaseLowBits ? n : kPhaseLowBits;
-    const uint64_t lowmask = (1ULL << L) - 1;
     const uint64_t c0 = ph->cmask[0], c1 = ph->cmask[1], c2 = ph->cmask[2];
     const qs_phase_term *terms = reinterpret_cast<const qs_phase_term *>(ph + 1);
     for (int i = threadIdx.x; i < n_act; i += blockDim.x) {
@@ -176,28 +101,14 @@ k_phase(typename cplx<R>::t *__restrict__ psi, int n, const qs_phase_dev *__rest
         act[i] = terms[i].a;
     }
     __syncthreads();
-    for (int l = threadIdx.x; l < (1 << L); l += blockDim.x) {
-        const uint64_t x = (uint64_t)l;
-        int m = __popcll(x & c0) + 2 * __popcll(x & c1) + 4 * __popcll(x & c2);
-        int par = 0;
-        for (int t = 0; t < n_act; t++)
-            if (act[t] < L && ((x >> act[t]) & 1)) par ^= __popcll(x & part[t] & lowmask);
-        tab[l] = (uint8_t)((m + 4 * (par & 1)) & 7);
-    }
+    const uint64_t cm[3] = {c0, c1, c2};
+    for (int l = threadIdx.x; l < (1 << L); l += blockDim.x) tab[l] = qsd::phase_low((uint64_t)l, cm, act, part, n_act, L);
     __syncthreads();
     const uint64_t n_chunks = 1ULL << (n - L);
     for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
         const uint64_t h = ch << L;
-        int mh = __popcll(h & c0) + 2 * __popcll(h & c1) + 4 * __popcll(h & c2);
-        int parh = 0;
-        uint64_t Mh = 0;
-        for (int t = 0; t < n_act; t++) {
-            const int a = act[t];
-            const int odd = __popcll(h & part[t]) & 1;
-            if (a >= L) parh ^= (int)((h >> a) & 1) & odd;
-            else Mh |= (uint64_t)odd << a;
-        }
-        mh = (mh + 4 * parh) & 7;
+        uint64_t Mh;
+        const int mh = qsd::phase_high(h, cm, act, part, n_act, L, Mh);
         C *base = psi + h;
         for (int l = threadIdx.x; l < (1 << L); l += blockDim.x) {
             const int m = (tab[l] + mh + 4 * __popcll((uint64_t)l & Mh)) & 7;

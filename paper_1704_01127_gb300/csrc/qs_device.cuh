@@ -1,0 +1,193 @@
+// Device building blocks shared by the single-state kernels (qs_apply.cu) and
+// the batched persistent kernel (qs_batch.cu), so both run the same arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "qs_internal.h"
+
+namespace qsd {
+
+template <typename R> struct cplx;
+template <> struct cplx<double> { using t = double2; };
+template <> struct cplx<float> { using t = float2; };
+
+struct Targets {
+    int q[QS_MAX_K];   // ascending
+};
+
+// Insert a zero bit at each (ascending) target position: group id -> index of
+// the group's x = 0 member (Sec. 3.2: the c bits fill the non-target positions).
+template <int K>
+__device__ __forceinline__ uint64_t group_base(uint64_t g, const Targets &t)
+{
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        uint64_t lo = g & ((1ULL << t.q[j]) - 1);
+        g = ((g ^ lo) << 1) | lo;
+    }
+    return g;
+}
+
+template <int K>
+__device__ __forceinline__ uint64_t member_offset(int x, const Targets &t)
+{
+    uint64_t o = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++)
+        if ((x >> j) & 1) o |= 1ULL << t.q[j];
+    return o;
+}
+
+template <bool CG, typename C>
+__device__ __forceinline__ C ld(const C *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// One group of a dense k-qubit cluster (Sec. 3.2): the 2^K amplitudes at
+// strides 2^{q_j} are gathered into registers, v <- U v, and scattered back.
+// Each complex multiply-accumulate is the pair of real FMA updates of
+// Eqs. (2)-(3): acc += (v_R m_R, v_I m_R) then acc += (-v_I m_I, v_R m_I).
+// CG: loads bypass L1 (the batched kernel shares states between the CTAs of a
+// cluster).
+template <typename R, int K, bool CG>
+__device__ __forceinline__ void dense_group(typename cplx<R>::t *p, const Targets &t,
+                                            const typename cplx<R>::t *Us)
+{
+    using C = typename cplx<R>::t;
+    constexpr int D = 1 << K;
+    C v[D];
+#pragma unroll
+    for (int x = 0; x < D; x++) v[x] = ld<CG>(p + member_offset<K>(x, t));
+    // rows of U one at a time (kept rolled so v[] stays in registers)
+#pragma unroll 1
+    for (int l = 0; l < D; l++) {
+        R ar = 0, ai = 0;
+        const C *row = Us + l * D;
+#pragma unroll
+        for (int x = 0; x < D; x++) {
+            C m = row[x];
+            ar = fma(v[x].x, m.x, ar);
+            ai = fma(v[x].y, m.x, ai);
+            ar = fma(-v[x].y, m.y, ar);
+            ai = fma(v[x].x, m.y, ai);
+        }
+        C o;
+        o.x = ar;
+        o.y = ai;
+        p[member_offset<K>(l, t)] = o;
+    }
+}
+
+// Multiply by e^{i pi m / 4}: an odd m first takes one factor
+// e^{i pi/4} = (1 + i)/sqrt(2); the remaining quarter turn i^{m >> 1} only swaps
+// and negates, done on the bit patterns (sign-bit flips) so complex128 spends
+// no FP64 instruction on it.
+__device__ __forceinline__ float flip(float x, bool f) { return __int_as_float(__float_as_int(x) ^ (f ? 0x80000000 : 0)); }
+__device__ __forceinline__ double flip(double x, bool f)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (f ? (long long)0x8000000000000000ULL : 0LL));
+}
+
+template <typename C, typename R>
+__device__ __forceinline__ C rotate8(C a, int m)
+{
+    if (m & 1) {
+        const R r = (R)0.70710678118654752440;
+        C b;
+        b.x = (a.x - a.y) * r;
+        b.y = (a.x + a.y) * r;
+        a = b;
+    }
+    const int q = (m >> 1) & 3;                  // i^q: 0 (x, y), 1 (-y, x), 2 (-x, -y), 3 (y, -x)
+    const bool sw = q & 1;
+    C o;
+    o.x = flip(sw ? a.y : a.x, q == 1 || q == 2);
+    o.y = flip(sw ? a.x : a.y, q >= 2);
+    return o;
+}
+
+// Phase products (Sec. 2, Sec. 3.5): amplitude i gets e^{i pi m(i)/4},
+// m(i) = sum_q c_q i_q + 4 sum_a i_a popc(i & P_a) mod 8, with P_a the CZ
+// partners b > a of qubit a.  With i = h | l (l: the low L bits) this is
+// m_lo(l) + m_hi(h) + 4 popc(l & M_h): m_lo is a table over the low bits,
+// m_hi and the mask M_h (low qubits whose partner set meets h an odd number of
+// times) are fixed for a chunk of 2^L amplitudes.
+__device__ __forceinline__ uint8_t phase_low(uint64_t x, const uint64_t *cm, const int *act,
+                                             const uint64_t *part, int n_act, int L)
+{
+    const uint64_t lowmask = (1ULL << L) - 1;
+    int m = __popcll(x & cm[0]) + 2 * __popcll(x & cm[1]) + 4 * __popcll(x & cm[2]);
+    int par = 0;
+    for (int t = 0; t < n_act; t++)
+        if (act[t] < L && ((x >> act[t]) & 1)) par ^= __popcll(x & part[t] & lowmask);
+    return (uint8_t)((m + 4 * (par & 1)) & 7);
+}
+
+__device__ __forceinline__ int phase_high(uint64_t h, const uint64_t *cm, const int *act, const uint64_t *part,
+                                          int n_act, int L, uint64_t &Mh)
+{
+    int mh = __popcll(h & cm[0]) + 2 * __popcll(h & cm[1]) + 4 * __popcll(h & cm[2]);
+    int parh = 0;
+    Mh = 0;
+    for (int t = 0; t < n_act; t++) {
+        const int a = act[t];
+        const int odd = __popcll(h & part[t]) & 1;
+        if (a >= L) parh ^= (int)((h >> a) & 1) & odd;
+        else Mh |= (uint64_t)odd << a;
+    }
+    return (mh + 4 * parh) & 7;
+}
+
+// p = fl(fl(re^2) + fl(im^2)) in FP64 (no contraction into an FMA).
+__device__ __forceinline__ double prob(double2 a)
+{
+    return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
+}
+__device__ __forceinline__ double prob(float2 a)
+{
+    double x = a.x, y = a.y;
+    return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
+}
+
+// Natural logarithm of a positive normal double, table-driven (P. T. P. Tang,
+// "Table-driven implementation of the logarithm function in IEEE floating-point
+// arithmetic", ACM TOMS 16(4), 1990): p = 2^e m, m in [1, 2); c_j is the centre
+// of the mantissa interval [1 + j/128, 1 + (j+1)/128) picked by the top seven
+// mantissa bits, r = m / c_j - 1 (|r| <= 1/256) and
+//   ln p = e ln 2 + ln c_j + ln(1 + r),  ln(1 + r) = r - r^2/2 + ... - r^6/6,
+// truncation error below r^7/7 < 2^-58.  ln c_j and 1/c_j come from the CUDA
+// math library once per block (shared-memory table).
+struct LogTable {
+    double inv[128], ln[128];
+};
+
+__device__ __forceinline__ void log_table_init(LogTable &t)
+{
+    for (int j = threadIdx.x; j < 128; j += blockDim.x) {
+        const double c = 1.0 + (j + 0.5) / 128.0;
+        t.inv[j] = 1.0 / c;
+        t.ln[j] = log(c);
+    }
+}
+
+__device__ __forceinline__ double log_tab(const LogTable &t, double p)
+{
+    const long long bits = __double_as_longlong(p);
+    const int e = (int)(bits >> 52) - 1023;
+    const int j = (int)((bits >> 45) & 127);
+    const double m = __longlong_as_double((bits & 0xFFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    const double r = fma(m, t.inv[j], -1.0);
+    double q = -1.0 / 6.0;
+    q = fma(q, r, 0.2);
+    q = fma(q, r, -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    q = fma(q, r, 1.0);
+    return fma((double)e, 0.69314718055994530942, t.ln[j] + q * r);
+}
+
+}  // namespace qsd

@@ -83,6 +83,18 @@ _SIGS = {
     "qs_set_device": ([ctypes.c_int], ctypes.c_int),
     "qs_set_path": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_stats_static": ([_VP, ctypes.c_int, ctypes.c_int, _VP, _DP], ctypes.c_int),
+    "qs_batch_circuit_params": ([ctypes.c_uint64, _IP, _IP, _IP], ctypes.c_int),
+    "qs_batch_create": ([ctypes.c_int, ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qs_batch_free": ([_VP], None),
+    "qs_batch_set_config": ([_VP, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "qs_batch_get_config": ([_VP, _IP, _IP], ctypes.c_int),
+    "qs_batch_run": ([_VP], ctypes.c_int),
+    "qs_batch_run_graph": ([_VP], ctypes.c_int),
+    "qs_batch_stats": ([_VP, _DP], ctypes.c_int),
+    "qs_batch_get_amplitudes": ([_VP, ctypes.c_int, _DP], ctypes.c_int),
+    "qs_batch_tune": ([_VP, _IP, _IP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "qs_batch_autotune": ([ctypes.c_int, _IP, ctypes.POINTER(_VP), _IP, ctypes.c_int, _VP, _IP, _IP, _IP,
+                           ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "qs_schedule_upload_bytes": ([_VP, ctypes.c_int], ctypes.c_int64),
 }
 
@@ -374,3 +386,71 @@ def qs_stats_static(dev_ptr, n, dtype, stream=None):
 
 def qs_set_path(h, path):
     _check(lib().qs_set_path(h, int(path)))
+
+
+# ------------------------------------------------------------------- batches
+
+def qs_batch_circuit_params(seed):
+    r, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().qs_batch_circuit_params(ctypes.c_uint64(int(seed)), ctypes.byref(r), ctypes.byref(c),
+                                         ctypes.byref(d)))
+    return r.value, c.value, d.value
+
+
+def qs_batch_create(schedules, dtype=QS_C64, stream=None):
+    arr = (_VP * len(schedules))(*[s.value if isinstance(s, _VP) else s for s in schedules])
+    h = _VP()
+    _check(lib().qs_batch_create(len(schedules), arr, int(dtype), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def qs_batch_free(b):
+    lib().qs_batch_free(b)
+
+
+def qs_batch_set_config(b, cluster_ctas, threads):
+    _check(lib().qs_batch_set_config(b, int(cluster_ctas), int(threads)))
+
+
+def qs_batch_get_config(b):
+    c, t = ctypes.c_int(), ctypes.c_int()
+    _check(lib().qs_batch_get_config(b, ctypes.byref(c), ctypes.byref(t)))
+    return c.value, t.value
+
+
+def qs_batch_run(b):
+    _check(lib().qs_batch_run(b))
+
+
+def qs_batch_run_graph(b):
+    _check(lib().qs_batch_run_graph(b))
+
+
+def qs_batch_stats(b, n_circuits):
+    out = np.zeros(4 * n_circuits, dtype=np.float64)
+    _check(lib().qs_batch_stats(b, _dp(out)))
+    return out.reshape(n_circuits, 4)
+
+
+def qs_batch_get_amplitudes(b, i, n):
+    out = np.empty(1 << n, dtype=np.complex128)
+    _check(lib().qs_batch_get_amplitudes(b, int(i), _dp(out.view(np.float64))))
+    return out
+
+
+def qs_batch_tune(b):
+    c, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(lib().qs_batch_tune(b, ctypes.byref(c), ctypes.byref(t), ctypes.byref(ms)))
+    return c.value, t.value, ms.value
+
+
+def qs_batch_autotune(circuits, dtype=QS_C64, stream=None):
+    """circuits: list of (n, gates) -> (k_max, cluster_ctas, threads, ms)."""
+    gates = [np.ascontiguousarray(g, dtype=GATE_DTYPE) for (_, g) in circuits]
+    nq = np.ascontiguousarray([n for (n, _) in circuits], dtype=np.int32)
+    ng = np.ascontiguousarray([g.size for g in gates], dtype=np.int32)
+    ptrs = (_VP * len(gates))(*[g.ctypes.data for g in gates])
+    km, c, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(lib().qs_batch_autotune(len(gates), _ip(nq), ptrs, _ip(ng), int(dtype), _stream_ptr(stream),
+                                   ctypes.byref(km), ctypes.byref(c), ctypes.byref(t), ctypes.byref(ms)))
+    return km.value, c.value, t.value, ms.value

@@ -117,3 +117,15 @@ def test_schedule_from_ops_sorts_qubits_and_permutes():
     sim.apply_kq(a, [4, 0, 2], U)
     sim.apply_kq(b, list(op["qubits"]), op["matrix"])
     np.testing.assert_allclose(a, b, atol=1e-15)
+
+
+def test_batch_circuit_params_match_oracle_and_are_uniform():
+    grids, depths = {}, []
+    for seed in range(512):
+        lib = qs.qs_batch_circuit_params(seed)
+        assert lib == circuit.batch_circuit_params(seed)
+        grids[lib[:2]] = grids.get(lib[:2], 0) + 1
+        depths.append(lib[2])
+    assert set(grids) == {(4, 4), (4, 5), (3, 7)}
+    assert all(120 < v < 220 for v in grids.values())
+    assert min(depths) == 8 and max(depths) == 40
