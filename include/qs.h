@@ -286,6 +286,64 @@ int qs_batch_tune(qs_batch *b, int *cluster_ctas, int *threads, float *ms);
 int qs_batch_autotune(int n_circuits, const int *n_qubits, const qs_gate *const *gates, const int *n_gates,
                       int dtype, void *stream, int *k_max, int *cluster_ctas, int *threads, float *ms);
 
+/* ------------------------------------------------------------------------
+ * Cost models and planning (Sec. 3.3: the best cluster size depends on the
+ * machine; Sec. 3.6: the scheduler packs gates into clusters of k <= k_max).
+ * ---------------------------------------------------------------------- */
+#define QS_NFEAT 12
+/* Op features, in this order: n/32, dtype (1 = complex128), diagonal (phase)
+ * op, k/5, tensor-core path, lowest target/n, highest target/n, targets below
+ * bit 5 (/5), targets below bit 3 (/3), log2(state bytes)/40, phase CZ terms/n,
+ * phase has odd (T-type) coefficients.  Predictions are times in ms. */
+int qs_op_features(int n, int dtype, int kind, int k, const int *qubits, int path, int n_act, int odd,
+                   double out[QS_NFEAT]);
+/* max(2 bytes(state) / hbm_gbs, flops / peak) + 5 us, peaks FP32 70 TFLOP/s and
+ * FP64 1.2 TFLOP/s for CUDA-core sweeps; tensor-core sweeps counted as HBM-bound. */
+double qs_cost_analytic_ms(const double features[QS_NFEAT], double hbm_gbs);
+
+/* Timing harness: `count` random ops (85% dense with k uniform in 1..5, targets
+ * uniform, kernel path CUDA cores or tensor cores; 15% phase ops), n uniform in
+ * [n_min, n_max] (5..33), each run once to upload and once timed with CUDA
+ * events on a state the harness allocates; ops whose analytic estimate exceeds
+ * max_ms are redrawn.  features: count x QS_NFEAT; ms: count. */
+int qs_cost_sample(int n_min, int n_max, int dtype, int count, uint64_t seed, double max_ms, double *features,
+                   double *ms);
+
+/* The MLP: QS_NFEAT inputs, two tanh layers of 64, one linear output; FP64
+ * parameters W1[F][64], b1[64], W2[64][64], b2[64], w3[64], b3 in one array,
+ * trained on the GPU (forward, backward and Adam kernels of this library). */
+typedef struct qs_mlp qs_mlp;
+int qs_mlp_create(uint64_t seed, qs_mlp **out);       /* Glorot-uniform weights */
+void qs_mlp_free(qs_mlp *m);
+int qs_mlp_num_params(void);
+int qs_mlp_get_params(const qs_mlp *m, double *out);
+int qs_mlp_set_params(qs_mlp *m, const double *in);
+/* X: B x QS_NFEAT (host), out: B */
+int qs_mlp_forward(qs_mlp *m, const double *X, int B, double *out);
+/* Gradient of mean (out - Y)^2 with respect to the parameters (host output). */
+int qs_mlp_gradient(qs_mlp *m, const double *X, const double *Y, int B, double *grad, double *loss);
+/* Full-batch Adam (beta 0.9 / 0.999), `epochs` steps at learning rate lr. */
+int qs_mlp_train(qs_mlp *m, const double *X, const double *Y, int B, int epochs, double lr, double *loss);
+
+enum { QS_COST_AUTO = 0, QS_COST_ANALYTIC = 1, QS_COST_MLP = 2 };
+typedef struct qs_cost_model qs_cost_model;
+int qs_cost_model_create(double hbm_gbs, qs_cost_model **out);   /* analytic until fitted */
+void qs_cost_model_free(qs_cost_model *c);
+/* Fit the MLP on log-time of the timings (features standardised; every fifth
+ * sample by a seeded hash held out).  report: training loss, held-out median
+ * |log error| of the MLP and of the analytic model, and whether the MLP will be
+ * used (1: it beat the analytic model). */
+int qs_cost_model_fit(qs_cost_model *c, const double *features, const double *ms, int count, int epochs,
+                      uint64_t seed, double report[4]);
+/* Predicted ms.  QS_COST_AUTO: the MLP where it was chosen by the fit and the
+ * features lie inside the training range, the analytic model elsewhere. */
+int qs_cost_model_predict(const qs_cost_model *c, const double *features, int count, int which, double *ms);
+/* Plan a circuit: for k_max in 2..5 build the schedule, choose each dense op's
+ * kernel path (CUDA or tensor cores) by predicted time, keep the k_max with the
+ * smallest predicted total.  The schedule records the chosen paths. */
+int qs_plan_circuit(int n, const qs_gate *gates, int n_gates, int dtype, const qs_cost_model *c, int which,
+                    qs_schedule **out, int *k_max, double *predicted_ms);
+
 #ifdef __cplusplus
 }
 #endif

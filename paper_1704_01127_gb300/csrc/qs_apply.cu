@@ -154,6 +154,15 @@ int launch_dense_r(qs_state *s, const int *q, int k, const void *U)
 
 }  // namespace
 
+// complex64: 5-qubit clusters (the FP32 CUDA-core kernel keeps up with HBM
+// below that); complex128: every cluster of 2 or more qubits (native FP64 runs
+// at 1/58 of the FP32 rate).  Tensor-core sweeps need n >= 5.
+bool qs_tc_wanted(int dtype, int k, int n)
+{
+    if (n < 5) return false;
+    return dtype == QS_C64 ? k == 5 : k >= 2;
+}
+
 int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix,
                     const void *dev_tc)
 {
@@ -280,11 +289,7 @@ int check_qubits(qs_state *s, const int *qubits, int k, int kmax, const char *wh
 // (the FP32 CUDA-core kernel keeps up with HBM below that).  complex128: every
 // cluster of 2 or more qubits, embedded in 5 qubits when smaller (native FP64
 // runs at 1/58 of the FP32 rate, so even a 2-qubit FP64 sweep is ALU-bound).
-bool tc_wanted(int dtype, int k, int n)
-{
-    if (n < 5) return false;
-    return dtype == QS_C64 ? k == 5 : k >= 2;
-}
+bool tc_wanted(int dtype, int k, int n) { return qs_tc_wanted(dtype, k, n); }
 
 // U (x) 1: a k-qubit cluster (sorted qubits q, sorted matrix M) as a 5-qubit
 // one on q plus the lowest qubits not in q; output sorted as well.
@@ -347,7 +352,7 @@ std::vector<uint8_t> schedule_blob(const qs_schedule *sc, int dtype, std::vector
             std::memcpy(part.data() + 64, tab.data(), tab.size());
         } else {
             part = to_real(op.matrix, dtype);
-            if (tc_wanted(dtype, op.k, sc->n)) {
+            if (sc->n >= 5) {   // tensor-core operands for every dense op (any path may run it)
                 std::vector<double> M5;
                 if (op.k == 5) {
                     for (int j = 0; j < 5; j++) tc_q[i][j] = op.qubits[j];
@@ -395,9 +400,14 @@ int ensure_dev_schedule(qs_state *s, const qs_schedule *csc)
     return QS_OK;
 }
 
+// Kernel path of a dense op: the state's setting if not AUTO, else the op's
+// planned path if any, else the default policy.
 int launch_op_dense(qs_state *s, const qs_dev_sched &d, size_t i, const qs_op_host &op, const uint8_t *data)
 {
-    if (d.tc_off[i] && s->path != QS_PATH_CUDA_CORES)
+    int path = s->path != QS_PATH_AUTO ? s->path
+               : op.path != QS_PATH_AUTO ? op.path
+               : (tc_wanted(s->dtype, op.k, s->n) ? QS_PATH_TENSOR : QS_PATH_CUDA_CORES);
+    if (path == QS_PATH_TENSOR && d.tc_off[i])
         return qs_launch_dense5_tc(s, d.tc_q[i].data(), data + d.tc_off[i]);
     return qs_launch_dense(s, op.qubits, op.k, data, nullptr);
 }

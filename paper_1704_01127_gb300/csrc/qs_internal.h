@@ -37,6 +37,7 @@ struct qs_op_host {
     std::vector<double> matrix;          // dense: 2^{2k} complex interleaved; diag: 2^k
     std::vector<int32_t> coeff;          // phase: n values mod 8
     std::vector<std::pair<int, int>> edges;   // phase: CZ pairs
+    int path = 0;                        // dense: QS_PATH_* chosen by a planner (0: default policy)
 };
 
 // Device copy of a schedule's op data for one amplitude type.
@@ -75,6 +76,9 @@ int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *de
                     const void *dev_tc);
 int qs_launch_diag(qs_state *s, const int *qubits, int k, const void *dev_table);
 int qs_launch_phase(qs_state *s, const void *dev_phase, int n_act);
+
+// Default kernel-path policy for a dense cluster (qs_apply.cu).
+bool qs_tc_wanted(int dtype, int k, int n);
 
 // Pack a phase op into its device layout (qs_circuit.cpp).
 std::vector<uint8_t> qs_pack_phase(int n, const std::vector<int32_t> &coeff,

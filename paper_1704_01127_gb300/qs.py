@@ -84,6 +84,25 @@ _SIGS = {
     "qs_set_path": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_stats_static": ([_VP, ctypes.c_int, ctypes.c_int, _VP, _DP], ctypes.c_int),
     "qs_batch_circuit_params": ([ctypes.c_uint64, _IP, _IP, _IP], ctypes.c_int),
+    "qs_op_features": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP, ctypes.c_int, ctypes.c_int,
+                        ctypes.c_int, _DP], ctypes.c_int),
+    "qs_cost_analytic_ms": ([_DP, ctypes.c_double], ctypes.c_double),
+    "qs_cost_sample": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_double,
+                        _DP, _DP], ctypes.c_int),
+    "qs_mlp_create": ([ctypes.c_uint64, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qs_mlp_free": ([_VP], None),
+    "qs_mlp_num_params": ([], ctypes.c_int),
+    "qs_mlp_get_params": ([_VP, _DP], ctypes.c_int),
+    "qs_mlp_set_params": ([_VP, _DP], ctypes.c_int),
+    "qs_mlp_forward": ([_VP, _DP, ctypes.c_int, _DP], ctypes.c_int),
+    "qs_mlp_gradient": ([_VP, _DP, _DP, ctypes.c_int, _DP, _DP], ctypes.c_int),
+    "qs_mlp_train": ([_VP, _DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double, _DP], ctypes.c_int),
+    "qs_cost_model_create": ([ctypes.c_double, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qs_cost_model_free": ([_VP], None),
+    "qs_cost_model_fit": ([_VP, _DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _DP], ctypes.c_int),
+    "qs_cost_model_predict": ([_VP, _DP, ctypes.c_int, ctypes.c_int, _DP], ctypes.c_int),
+    "qs_plan_circuit": ([ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(_VP), _IP,
+                         _DP], ctypes.c_int),
     "qs_batch_create": ([ctypes.c_int, ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "qs_batch_free": ([_VP], None),
     "qs_batch_set_config": ([_VP, ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -454,3 +473,119 @@ def qs_batch_autotune(circuits, dtype=QS_C64, stream=None):
     _check(lib().qs_batch_autotune(len(gates), _ip(nq), ptrs, _ip(ng), int(dtype), _stream_ptr(stream),
                                    ctypes.byref(km), ctypes.byref(c), ctypes.byref(t), ctypes.byref(ms)))
     return km.value, c.value, t.value, ms.value
+
+
+# ---------------------------------------------------------------- cost models
+
+QS_NFEAT = 12
+QS_COST_AUTO, QS_COST_ANALYTIC, QS_COST_MLP = 0, 1, 2
+
+
+def qs_op_features(n, dtype, kind, k=0, qubits=(), path=0, n_act=0, odd=0):
+    q = np.zeros(5, dtype=np.int32)
+    q[:len(qubits)] = qubits
+    out = np.zeros(QS_NFEAT, dtype=np.float64)
+    _check(lib().qs_op_features(int(n), int(dtype), int(kind), int(k), _ip(q), int(path), int(n_act), int(odd),
+                                _dp(out)))
+    return out
+
+
+def qs_cost_analytic_ms(features, hbm_gbs=6696.8):
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    return float(lib().qs_cost_analytic_ms(_dp(f), float(hbm_gbs)))
+
+
+def qs_cost_sample(n_min, n_max, dtype, count, seed, max_ms=200.0):
+    feats = np.zeros((int(count), QS_NFEAT), dtype=np.float64)
+    ms = np.zeros(int(count), dtype=np.float64)
+    _check(lib().qs_cost_sample(int(n_min), int(n_max), int(dtype), int(count), ctypes.c_uint64(int(seed)),
+                                float(max_ms), _dp(feats), _dp(ms)))
+    return feats, ms
+
+
+def qs_mlp_create(seed=0):
+    h = _VP()
+    _check(lib().qs_mlp_create(ctypes.c_uint64(int(seed)), ctypes.byref(h)))
+    return h
+
+
+def qs_mlp_free(h):
+    lib().qs_mlp_free(h)
+
+
+def qs_mlp_num_params():
+    return int(lib().qs_mlp_num_params())
+
+
+def qs_mlp_get_params(h):
+    out = np.zeros(qs_mlp_num_params(), dtype=np.float64)
+    _check(lib().qs_mlp_get_params(h, _dp(out)))
+    return out
+
+
+def qs_mlp_set_params(h, w):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    assert w.size == qs_mlp_num_params()
+    _check(lib().qs_mlp_set_params(h, _dp(w)))
+
+
+def qs_mlp_forward(h, X):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros(X.shape[0], dtype=np.float64)
+    _check(lib().qs_mlp_forward(h, _dp(X), int(X.shape[0]), _dp(out)))
+    return out
+
+
+def qs_mlp_gradient(h, X, Y):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    g = np.zeros(qs_mlp_num_params(), dtype=np.float64)
+    loss = ctypes.c_double()
+    _check(lib().qs_mlp_gradient(h, _dp(X), _dp(Y), int(X.shape[0]), _dp(g), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def qs_mlp_train(h, X, Y, epochs, lr=3e-3):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    loss = ctypes.c_double()
+    _check(lib().qs_mlp_train(h, _dp(X), _dp(Y), int(X.shape[0]), int(epochs), float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def qs_cost_model_create(hbm_gbs=6696.8):
+    h = _VP()
+    _check(lib().qs_cost_model_create(float(hbm_gbs), ctypes.byref(h)))
+    return h
+
+
+def qs_cost_model_free(h):
+    lib().qs_cost_model_free(h)
+
+
+def qs_cost_model_fit(h, features, ms, epochs=1500, seed=0):
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    t = np.ascontiguousarray(ms, dtype=np.float64)
+    rep = np.zeros(4, dtype=np.float64)
+    _check(lib().qs_cost_model_fit(h, _dp(f), _dp(t), int(t.size), int(epochs), ctypes.c_uint64(int(seed)),
+                                   _dp(rep)))
+    return {"train_loss": rep[0], "mlp_holdout_median_abs_log_err": rep[1],
+            "analytic_holdout_median_abs_log_err": rep[2], "use_mlp": bool(rep[3])}
+
+
+def qs_cost_model_predict(h, features, which=QS_COST_AUTO):
+    f = np.ascontiguousarray(features, dtype=np.float64).reshape(-1, QS_NFEAT)
+    out = np.zeros(f.shape[0], dtype=np.float64)
+    _check(lib().qs_cost_model_predict(h, _dp(f), int(f.shape[0]), int(which), _dp(out)))
+    return out
+
+
+def qs_plan_circuit(n, gates, dtype, model, which=QS_COST_AUTO):
+    """(schedule, k_max, predicted_ms)."""
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    h = _VP()
+    km = ctypes.c_int()
+    t = ctypes.c_double()
+    _check(lib().qs_plan_circuit(int(n), g.ctypes.data_as(_VP), int(g.size), int(dtype), model, int(which),
+                                 ctypes.byref(h), ctypes.byref(km), ctypes.byref(t)))
+    return h, km.value, t.value
