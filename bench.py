@@ -364,6 +364,68 @@ def run_batch(args):
     }
 
 
+# ------------------------------------------------------- learned scheduling
+
+def run_learned(args):
+    """Harness timings of random clusters -> MLP fitted on the GPU -> circuits
+    planned with the analytic model and with the learned model (auto fallback),
+    both measured; grids 4x7 / 5x6 / 3x11, 30 CZ cycles, complex64 and complex128."""
+    import numpy as np
+    import torch
+    from paper_1704_01127_gb300 import build as _build
+    _build.build()
+    import paper_1704_01127_gb300.qs as qs
+    world, rank, local, dist = dist_setup(args)
+    qs.qs_set_device(local)
+    torch.cuda.set_device(local)
+    hbm_gbs, _, _ = load_peaks()
+    t0 = time.perf_counter()
+    F, T = [], []
+    # (n range, samples, ms cap): cheap sizes in bulk, large ones sparsely
+    plan = [((18, 26), 7500, 400.0), ((27, 30), 2000, 400.0), ((31, 33), 500, 400.0)]
+    for dt in (qs.QS_C64, qs.QS_C128):
+        for (lo, hi), cnt, cap in plan:
+            f, t = qs.qs_cost_sample(lo, hi, dt, cnt, seed=1000 * dt + lo, max_ms=cap)
+            F.append(f)
+            T.append(t)
+    F, T = np.concatenate(F), np.concatenate(T)
+    harness_s = time.perf_counter() - t0
+    cm = qs.qs_cost_model_create(hbm_gbs)
+    t1 = time.perf_counter()
+    rep = qs.qs_cost_model_fit(cm, F, T, epochs=2000, seed=7)
+    fit_s = time.perf_counter() - t1
+    rows = []
+    for (r, c) in ((4, 7), (5, 6), (3, 11)):
+        for dt in (qs.QS_C64, qs.QS_C128):
+            n, g = qs.qs_supremacy_circuit(r, c, 30, 0)
+            h = qs.qs_alloc(n, dt)
+            res = {"grid": "%dx%d" % (r, c), "qubits": n, "dtype": "c128" if dt else "c64"}
+            for name, which in (("analytic", qs.QS_COST_ANALYTIC), ("learned", qs.QS_COST_AUTO)):
+                sc, km, pred = qs.qs_plan_circuit(n, g, dt, cm, which)
+                times = []
+                for rep_i in range(2):
+                    qs.qs_init_basis(h, 0)
+                    ms = qs.qs_run_circuit_timed(h, sc)
+                    times.append(float(ms.sum()))
+                paths = [qs.qs_schedule_op(sc, i) for i in range(qs.qs_schedule_num_ops(sc))]
+                res[name] = {"k_max": km, "predicted_s": pred / 1e3, "measured_s": min(times) / 1e3,
+                             "ops": len(paths)}
+                qs.qs_schedule_free(sc)
+            res["gain"] = res["analytic"]["measured_s"] / res["learned"]["measured_s"]
+            qs.qs_free(h)
+            rows.append(res)
+    qs.qs_cost_model_free(cm)
+    if rank != 0:
+        return None
+    geo = float(np.exp(np.mean([np.log(r["gain"]) for r in rows])))
+    return {"metric": METRIC, "value": sum(r["learned"]["measured_s"] for r in rows) / len(rows), "unit": "s/circuit",
+            "n_gpus": world, "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
+            "config": {"workload": "learned scheduling: 4x7, 5x6, 3x11 grids, 30 CZ cycles, c64 and c128"},
+            "harness": {"timings": int(T.size), "seconds": harness_s}, "fit": dict(rep, seconds=fit_s),
+            "circuits": rows, "geomean_gain_learned_vs_analytic": geo}
+
+
 # ------------------------------------------------------------ oracle (CPU) leg
 
 def cpu_baseline(args, n_steps):
@@ -423,7 +485,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch512_c64"], default="5x6_d25_c128")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch512_c64", "learned"], default="5x6_d25_c128")
     ap.add_argument("--plain", action="store_true", help="gate-by-gate form instead of fused")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison run")
     ap.add_argument("--no-e2e", action="store_true")
@@ -436,6 +498,8 @@ def main():
         line = run_reference(args)
     elif args.workload == "batch512_c64":
         line = run_batch(args)
+    elif args.workload == "learned":
+        line = run_learned(args)
     else:
         line = run_ours(args)
     if line is not None:
