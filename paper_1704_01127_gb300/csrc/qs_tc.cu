@@ -152,6 +152,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
 #pragma unroll
     for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
 }
+// 4 consecutive 32-bit columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v)
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 4; i++) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_wait_ld()
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -397,21 +407,26 @@ __device__ __forceinline__ double scale_int(long long T, int X)
     return __longlong_as_double(b);
 }
 
-// 512 threads: thread t owns row (t & 127) and quarter h = t >> 7 of that row's
-// 32 amplitudes (members 8h .. 8h+7, K columns 16h .. 16h+15); warp w reads
-// TMEM lanes 32 (w & 3) .. +31 and the output columns of its quarter.
-constexpr int kTpr128 = 4;                                   // threads per row
-__global__ void __launch_bounds__(kRows * kTpr128, 1)
+// TPR threads per row: thread t owns row (t & 127) and part h = t >> 7 of that
+// row's 32 amplitudes (members h*MPT .. +MPT-1, K columns 2*MPT*h ..); warp w
+// reads TMEM lanes 32 (w & 3) .. +31 and the output columns of part w >> 2.
+// With TPR = 8 a CTA has 32 warps, enough to hide the load latency.
+template <int TPR>
+__global__ void __launch_bounds__(kRows * TPR, 1)
 k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const uint8_t *__restrict__ bpack,
                  int *__restrict__ status)
 {
+    constexpr int MPT = 32 / TPR;            // members per thread
+    constexpr int CH = MPT / 4;              // 8-column chunks per thread (4 members each)
+    constexpr int COLS = kN / TPR;           // output columns per thread
+    constexpr int EC = TPR >= 8 ? 4 : 8;     // epilogue chunk (columns), sized to the register budget
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *A = smem;                                         // kSlices planes
     uint8_t *B = smem + kSlices * kPlaneA;                     // kSlicesB planes
     int *Gcol = reinterpret_cast<int *>(B + kSlicesB * kPlaneB);
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base_s;
-    __shared__ int rowexp[kTpr128][kRows];
+    __shared__ int rowexp[TPR][kRows];
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int row = tid & (kRows - 1), part = tid >> 7;
@@ -440,7 +455,7 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
     uint32_t parity = 0;
     // software pipeline: the next tile's amplitudes are loaded into registers
     // while the tensor cores and the epilogue work on the current one
-    double2 v[8];
+    double2 v[MPT];
     uint64_t tile = blockIdx.x;
     bool valid = false;
     double2 *p = psi;
@@ -449,23 +464,26 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
         val = tl < n_tiles && g < n_groups;
         pp = psi + (val ? base5(g, t) : 0);
 #pragma unroll
-        for (int x = 0; x < 8; x++) vv[x] = val ? pp[off5(8 * part + x, t)] : make_double2(0.0, 0.0);
+        for (int x = 0; x < MPT; x++) vv[x] = val ? pp[off5(MPT * part + x, t)] : make_double2(0.0, 0.0);
     };
     load_tile(tile, v, valid, p);
     for (; tile < n_tiles; tile += gridDim.x) {
-        int emax = 0;
+        // largest exponent field of the row (bits 20..30 of the high words)
+        uint32_t emax = 0;
 #pragma unroll
-        for (int x = 0; x < 8; x++) {
-            emax = max(emax, (int)((__double_as_longlong(v[x].x) >> 52) & 0x7FF));
-            emax = max(emax, (int)((__double_as_longlong(v[x].y) >> 52) & 0x7FF));
+        for (int x = 0; x < MPT; x++) {
+            emax = max(emax, (uint32_t)__double2hiint(v[x].x) & 0x7FF00000u);
+            emax = max(emax, (uint32_t)__double2hiint(v[x].y) & 0x7FF00000u);
         }
-        rowexp[part][row] = emax;
+        rowexp[part][row] = (int)(emax >> 20);
         __syncthreads();
-        const int E = max(max(rowexp[0][row], rowexp[1][row]), max(rowexp[2][row], rowexp[3][row]));
-        // digits: 2 chunks of 8 K-columns (4 members) per slice; digit s of a
+        int E = 0;
+#pragma unroll
+        for (int h = 0; h < TPR; h++) E = max(E, rowexp[h][row]);
+        // digits: CH chunks of 8 K-columns (4 members) per slice; digit s of a
         // value is byte 5 - s of its biased fixed-point integer G
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
+        for (int c = 0; c < CH; c++) {
             uint32_t glo[8], ghi[8];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -475,7 +493,7 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
                 glo[2 * j + 1] = (uint32_t)g1;
                 ghi[2 * j + 1] = (uint32_t)(g1 >> 32);
             }
-            uint8_t *dst = A + cm_off16(row, 16 * part + 8 * c);
+            uint8_t *dst = A + cm_off16(row, 2 * MPT * part + 8 * c);
             uint4 w;
 #define QS_DIGIT_PLANE(SL, WORDS, BYTE)                                                        \
     w.x = pack_bf16(digit_f32<BYTE>(WORDS[0]), digit_f32<BYTE>(WORDS[1]));                   \
@@ -535,25 +553,29 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
         tc_fence_after();
         const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
-        for (int c = 0; c < 2; c++) {
-            const int col0 = 16 * part + 8 * c;
-            float D[kDiags][8];
+        for (int c = 0; c < COLS / EC; c++) {
+            const int col0 = COLS * part + EC * c;
+            float D[kDiags][EC];
 #pragma unroll
-            for (int d = 0; d < kDiags; d++) tmem_ld8(lane_addr + 64 * d + col0, D[d]);
+            for (int d = 0; d < kDiags; d++) {
+                if constexpr (EC == 8) tmem_ld8(lane_addr + 64 * d + col0, D[d]);
+                else tmem_ld4(lane_addr + 64 * d + col0, D[d]);
+            }
             tmem_wait_ld();
-            double out[8];
+            double out[EC];
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                long long U = ((long long)exact_int(D[0][q]) << 24) + ((long long)exact_int(D[1][q]) << 16) +
-                              ((long long)exact_int(D[2][q]) << 8) + (long long)exact_int(D[3][q]);
+            for (int q = 0; q < EC; q++) {
+                const long long U = (long long)exact_int(D[0][q]) * 16777216LL + (long long)exact_int(D[1][q]) * 65536LL +
+                                    (long long)exact_int(D[2][q]) * 256LL + (long long)exact_int(D[3][q]);
                 // D_4 + D_5 / 256 + D_6 / 65536; 256 L < 2^31
-                float L = fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]);
-                long long T = (U << 16) + (long long)__float2int_rn(L * 256.0f);
+                const float L = fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]);
+                const long long T = U * 65536LL + (long long)__float2int_rn(L * 256.0f);
                 out[q] = scale_int(T, E + Gcol[col0 + q] - 2096);
             }
             if (valid_cur) {
 #pragma unroll
-                for (int l = 0; l < 4; l++) p_cur[off5(8 * part + 4 * c + l, t)] = make_double2(out[2 * l], out[2 * l + 1]);
+                for (int l = 0; l < EC / 2; l++)
+                    p_cur[off5(col0 / 2 + l, t)] = make_double2(out[2 * l], out[2 * l + 1]);
             }
         }
         tc_fence_before();
@@ -564,6 +586,7 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
     if (warp == 0) tmem_dealloc(tmem, kTmemCols128);
 }
 
+constexpr int kTpr128 = 4;   // threads per row of the complex128 kernel (512 per CTA; 8 measured slower)
 bool g_attr_set[2][64] = {{false}};
 
 }  // namespace
@@ -665,7 +688,7 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
     if (!g_attr_set[c64][dev]) {
         cudaError_t e = c64 ? cudaFuncSetAttribute(k_dense5_tc_c64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)kSmemF32)
-                            : cudaFuncSetAttribute(k_dense5_tc_c128, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            : cudaFuncSetAttribute(k_dense5_tc_c128<kTpr128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)kSmemC128);
         if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
         g_attr_set[c64][dev] = true;
@@ -683,7 +706,7 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
             (float2 *)s->amp, groups, t, (const float *)dev_pack, status);
     } else {
         int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms);
-        k_dense5_tc_c128<<<grid, kTpr128 * kRows, kSmemC128, (cudaStream_t)s->stream>>>(
+        k_dense5_tc_c128<kTpr128><<<grid, kTpr128 * kRows, kSmemC128, (cudaStream_t)s->stream>>>(
             (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
     }
     cudaError_t e = cudaGetLastError();
