@@ -586,7 +586,225 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
     if (warp == 0) tmem_dealloc(tmem, kTmemCols128);
 }
 
+
+// ----------------------------------------------------------------------------
+// complex128, warp-specialised: the same arithmetic as k_dense5_tc_c128 with
+// the per-tile work split between two groups that run concurrently.
+//   splitters (warps 0..15, 4 threads per row): gather tile t+1 and cut it into
+//     digit planes as soon as the tensor cores are done reading tile t's planes;
+//     thread 0 issues the MMAs of a tile once its planes are written and the
+//     epilogue group has released the accumulators;
+//   epilogue (warps 16..23, 2 threads per row, 32 output columns each): wait for
+//     tile t's MMAs, rebuild and store FP64 results, release the accumulators.
+// Hand-offs: mbar_mma (tcgen05.commit, one arrival per tile) and mbar_free (256
+// epilogue arrivals per tile); the splitters meet at named barrier 1, whose
+// OR-reduced variant makes every timeout decision uniform across the group.
+// Every wait is bounded; a timeout sets the status word and all threads leave
+// their loops, so the final barrier and the TMEM release are always reached.
+// ----------------------------------------------------------------------------
+constexpr int kSplitThreads = 512;
+constexpr int kEpiThreads = 256;
+
+__device__ __forceinline__ void bar_split() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+__device__ __forceinline__ bool bar_split_or(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, 1, 512, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity)
+{
+    for (long it = 0; it < kWaitLimit; it++)
+        if (mbar_try_wait(mbar, parity)) return true;
+    return false;
+}
+
+__global__ void __launch_bounds__(kSplitThreads + kEpiThreads, 1)
+k_dense5_tc_c128_ws(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const uint8_t *__restrict__ bpack,
+                    int *__restrict__ status)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *A = smem;
+    uint8_t *B = smem + kSlices * kPlaneA;
+    int *Gcol = reinterpret_cast<int *>(B + kSlicesB * kPlaneB);
+    __shared__ __align__(8) uint64_t mbar_mma, mbar_free;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int rowexp[4][kRows];
+    __shared__ int rowE[2][kRows];
+    __shared__ volatile int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(bpack);
+        uint4 *dst = reinterpret_cast<uint4 *>(B);
+        for (int i = tid; i < (int)((kSlicesB * kPlaneB + 256) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(&tmem_base_s), kTmemCols128);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar_mma), 1);
+        mbar_init(smem_u32(&mbar_free), kEpiThreads);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+    const uint32_t mma_a = smem_u32(&mbar_mma), free_a = smem_u32(&mbar_free);
+    const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
+
+    if (tid < kSplitThreads) {
+        // ------------------------------------------------------------ splitters
+        const int row = tid & (kRows - 1), part = tid >> 7;
+        const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+        double2 v[8];
+        auto load_tile = [&](uint64_t tl) {
+            const uint64_t g = tl * kRows + row;
+            const bool val = tl < n_tiles && g < n_groups;
+            const double2 *pp = psi + (val ? base5(g, t) : 0);
+#pragma unroll
+            for (int x = 0; x < 8; x++) v[x] = val ? pp[off5(8 * part + x, t)] : make_double2(0.0, 0.0);
+        };
+        load_tile(blockIdx.x);
+        int it = 0;
+        for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, it++) {
+            // tile it-1's MMAs must have finished reading the planes
+            const bool ok = it == 0 || mbar_wait_bounded(mma_a, (it - 1) & 1);
+            if (bar_split_or(!ok || abort_flag)) {
+                if (tid == 0) atomicExch(status, 1);
+                break;
+            }
+            uint32_t emax = 0;
+#pragma unroll
+            for (int x = 0; x < 8; x++) {
+                emax = max(emax, (uint32_t)__double2hiint(v[x].x) & 0x7FF00000u);
+                emax = max(emax, (uint32_t)__double2hiint(v[x].y) & 0x7FF00000u);
+            }
+            rowexp[part][row] = (int)(emax >> 20);
+            bar_split();
+            const int E = max(max(rowexp[0][row], rowexp[1][row]), max(rowexp[2][row], rowexp[3][row]));
+            if (part == 0) rowE[it & 1][row] = E;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                uint32_t glo[8], ghi[8];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const uint64_t g0 = fixed48(v[4 * c + j].x, E), g1 = fixed48(v[4 * c + j].y, E);
+                    glo[2 * j] = (uint32_t)g0;
+                    ghi[2 * j] = (uint32_t)(g0 >> 32);
+                    glo[2 * j + 1] = (uint32_t)g1;
+                    ghi[2 * j + 1] = (uint32_t)(g1 >> 32);
+                }
+                uint8_t *dst = A + cm_off16(row, 16 * part + 8 * c);
+                uint4 w;
+#define QS_DIGIT_PLANE(SL, WORDS, BYTE)                                                        \
+    w.x = pack_bf16(digit_f32<BYTE>(WORDS[0]), digit_f32<BYTE>(WORDS[1]));                   \
+    w.y = pack_bf16(digit_f32<BYTE>(WORDS[2]), digit_f32<BYTE>(WORDS[3]));                   \
+    w.z = pack_bf16(digit_f32<BYTE>(WORDS[4]), digit_f32<BYTE>(WORDS[5]));                   \
+    w.w = pack_bf16(digit_f32<BYTE>(WORDS[6]), digit_f32<BYTE>(WORDS[7]));                   \
+    *reinterpret_cast<uint4 *>(dst + (SL) * kPlaneA) = w;
+                QS_DIGIT_PLANE(0, ghi, 1)
+                QS_DIGIT_PLANE(1, ghi, 0)
+                QS_DIGIT_PLANE(2, glo, 3)
+                QS_DIGIT_PLANE(3, glo, 2)
+                QS_DIGIT_PLANE(4, glo, 1)
+                QS_DIGIT_PLANE(5, glo, 0)
+#undef QS_DIGIT_PLANE
+            }
+            fence_proxy_async();
+            bar_split();
+            if (tid == 0) {
+                // the epilogue must have released tile it-1's accumulators
+                if (it > 0 && !mbar_wait_bounded(free_a, (it - 1) & 1)) {
+                    atomicExch(status, 1);
+                    abort_flag = 1;
+                } else {
+                    tc_fence_after();
+#pragma unroll
+                    for (int d = 0; d < kDiags; d++) {
+                        bool first = true;
+#pragma unroll
+                        for (int i = 0; i <= d; i++) {
+                            const int j = d - i;
+                            if (i >= kSlices || j >= kSlicesB) continue;
+#pragma unroll
+                            for (int ks = 0; ks < kK / 16; ks++) {
+                                const uint32_t koff = ks * 2 * kLBO;
+                                mma_bf16(tmem + 64 * d, smem_desc(a0 + i * kPlaneA + koff, kSBO16),
+                                         smem_desc(b0 + j * kPlaneB + koff, kSBO16), kIdescBf16, first ? 0u : 1u);
+                                first = false;
+                            }
+                        }
+                    }
+                    mma_commit(mma_a);
+                }
+            }
+            load_tile(tile + gridDim.x);
+        }
+        // leave only after the last MMAs are complete (they read this CTA's planes)
+        if (tid == 0 && it > 0 && !abort_flag) mbar_wait_bounded(mma_a, (it - 1) & 1);
+    } else {
+        // ------------------------------------------------------------- epilogue
+        const int ew = warp - kSplitThreads / 32;                 // 0..7
+        const int row = 32 * (warp & 3) + (tid & 31), half = ew >> 2;
+        const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        int it = 0;
+        for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, it++) {
+            if (!mbar_wait_bounded(mma_a, it & 1) || abort_flag) {
+                atomicExch(status, 1);
+                abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int E = rowE[it & 1][row];
+            const uint64_t g = tile * kRows + row;
+            const bool valid = g < n_groups;
+            double2 *p = psi + (valid ? base5(g, t) : 0);
+#pragma unroll 1
+            for (int c = 0; c < 8; c++) {
+                const int col0 = 32 * half + 4 * c;
+                float D[kDiags][4];
+#pragma unroll
+                for (int d = 0; d < kDiags; d++) tmem_ld4(lane_addr + 64 * d + col0, D[d]);
+                tmem_wait_ld();
+                double out[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const long long U = (long long)exact_int(D[0][q]) * 16777216LL +
+                                        (long long)exact_int(D[1][q]) * 65536LL +
+                                        (long long)exact_int(D[2][q]) * 256LL + (long long)exact_int(D[3][q]);
+                    const float L = fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]);
+                    const long long T = U * 65536LL + (long long)__float2int_rn(L * 256.0f);
+                    out[q] = scale_int(T, E + Gcol[col0 + q] - 2096);
+                }
+                if (valid) {
+                    p[off5(col0 / 2, t)] = make_double2(out[0], out[1]);
+                    p[off5(col0 / 2 + 1, t)] = make_double2(out[2], out[3]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(free_a);
+        }
+    }
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols128);
+}
+
 constexpr int kTpr128 = 4;   // threads per row of the complex128 kernel (512 per CTA; 8 measured slower)
+constexpr bool kC128WarpSpecialised = true;
 bool g_attr_set[2][64] = {{false}};
 
 }  // namespace
@@ -690,6 +908,8 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
                                                    (int)kSmemF32)
                             : cudaFuncSetAttribute(k_dense5_tc_c128<kTpr128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)kSmemC128);
+        if (e == cudaSuccess && !c64)
+            e = cudaFuncSetAttribute(k_dense5_tc_c128_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemC128);
         if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
         g_attr_set[c64][dev] = true;
     }
@@ -706,8 +926,12 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
             (float2 *)s->amp, groups, t, (const float *)dev_pack, status);
     } else {
         int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms);
-        k_dense5_tc_c128<kTpr128><<<grid, kTpr128 * kRows, kSmemC128, (cudaStream_t)s->stream>>>(
-            (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
+        if (kC128WarpSpecialised)
+            k_dense5_tc_c128_ws<<<grid, kSplitThreads + kEpiThreads, kSmemC128, (cudaStream_t)s->stream>>>(
+                (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
+        else
+            k_dense5_tc_c128<kTpr128><<<grid, kTpr128 * kRows, kSmemC128, (cudaStream_t)s->stream>>>(
+                (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "tc launch: %s", cudaGetErrorString(e));
