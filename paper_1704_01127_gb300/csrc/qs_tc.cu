@@ -353,6 +353,42 @@ constexpr int kTmemCols128 = 512;
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
                                ((uint32_t)(kRows >> 4) << 24);
 
+// instruction descriptor of a bf16 MMA with M = 128 and N = 64 * planes
+__host__ __device__ constexpr uint32_t idesc_bf16_planes(int planes)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 * planes >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+
+// The MMAs of one complex128 tile.  Digit planes of B are contiguous 8 KB
+// blocks, i.e. exactly 8 row groups (one SBO stride each) apart, and the
+// accumulators D_d are contiguous 64-column blocks of TMEM, so one MMA with
+// N = 64 * m and B starting at plane j computes A_i B_j .. A_i B_{j+m-1} into
+// D_{i+j} .. D_{i+j+m-1} at once (m <= 4, N <= 256).  Products with i = 0 come
+// first and initialise D_0..D_6; all others accumulate.  Descriptors differ
+// only in their start-address field (address >> 4, below 2^14), so each is a
+// precomputed base plus an offset.
+__device__ __forceinline__ void issue_c128_mmas(uint32_t tmem, uint32_t a0, uint32_t b0)
+{
+    const uint64_t da = smem_desc(a0, kSBO16), db = smem_desc(b0, kSBO16);
+#pragma unroll
+    for (int i = 0; i < kSlices; i++) {
+#pragma unroll
+        for (int j = 0; j + i < kDiags && j < kSlicesB; j += 4) {
+            int m = 4;
+            if (j + m > kSlicesB) m = kSlicesB - j;
+            if (i + j + m > kDiags) m = kDiags - i - j;
+#pragma unroll
+            for (int ks = 0; ks < kK / 16; ks++) {
+                const uint32_t koff = ks * 2 * kLBO;   // 16 bf16 = two core matrices along K
+                const uint64_t adesc = da + ((uint64_t)(i * kPlaneA + koff) >> 4);
+                const uint64_t bdesc = db + ((uint64_t)(j * kPlaneB + koff) >> 4);
+                const uint32_t acc = (i == 0 && ks == 0) ? 0u : 1u;
+                mma_bf16(tmem + 64 * (i + j), adesc, bdesc, idesc_bf16_planes(m), acc);
+            }
+        }
+    }
+}
+
 // byte offset of 16-bit element (row, k) in a K-major no-swizzle tile with 64 K
 __host__ __device__ __forceinline__ uint32_t cm_off16(int row, int k)
 {
@@ -514,22 +550,7 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
         __syncthreads();
         tc_fence_after();
         if (tid == 0) {
-#pragma unroll
-            for (int d = 0; d < kDiags; d++) {
-                bool first = true;
-#pragma unroll
-                for (int i = 0; i <= d; i++) {
-                    const int j = d - i;
-                    if (i >= kSlices || j >= kSlicesB) continue;
-#pragma unroll
-                    for (int ks = 0; ks < kK / 16; ks++) {
-                        const uint32_t koff = ks * 2 * kLBO;   // 16 bf16 = two core matrices along K
-                        mma_bf16(tmem + 64 * d, smem_desc(a0 + i * kPlaneA + koff, kSBO16),
-                                 smem_desc(b0 + j * kPlaneB + koff, kSBO16), kIdescBf16, first ? 0u : 1u);
-                        first = false;
-                    }
-                }
-            }
+            issue_c128_mmas(tmem, a0, b0);
             mma_commit(mbar_a);
         }
         double2 *const p_cur = p;
@@ -594,16 +615,16 @@ k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const
 //     digit planes as soon as the tensor cores are done reading tile t's planes;
 //     thread 0 issues the MMAs of a tile once its planes are written and the
 //     epilogue group has released the accumulators;
-//   epilogue (warps 16..23, 2 threads per row, 32 output columns each): wait for
+//   epilogue (warps 16..31, 4 threads per row, 16 output columns each): wait for
 //     tile t's MMAs, rebuild and store FP64 results, release the accumulators.
-// Hand-offs: mbar_mma (tcgen05.commit, one arrival per tile) and mbar_free (256
-// epilogue arrivals per tile); the splitters meet at named barrier 1, whose
+// Hand-offs: mbar_mma (tcgen05.commit, one arrival per tile) and mbar_free (one
+// arrival per epilogue thread per tile); the splitters meet at named barrier 1, whose
 // OR-reduced variant makes every timeout decision uniform across the group.
 // Every wait is bounded; a timeout sets the status word and all threads leave
 // their loops, so the final barrier and the TMEM release are always reached.
 // ----------------------------------------------------------------------------
 constexpr int kSplitThreads = 512;
-constexpr int kEpiThreads = 256;
+constexpr int kEpiThreads = 512;
 
 __device__ __forceinline__ void bar_split() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 __device__ __forceinline__ bool bar_split_or(bool v)
@@ -733,22 +754,7 @@ k_dense5_tc_c128_ws(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, co
                     abort_flag = 1;
                 } else {
                     tc_fence_after();
-#pragma unroll
-                    for (int d = 0; d < kDiags; d++) {
-                        bool first = true;
-#pragma unroll
-                        for (int i = 0; i <= d; i++) {
-                            const int j = d - i;
-                            if (i >= kSlices || j >= kSlicesB) continue;
-#pragma unroll
-                            for (int ks = 0; ks < kK / 16; ks++) {
-                                const uint32_t koff = ks * 2 * kLBO;
-                                mma_bf16(tmem + 64 * d, smem_desc(a0 + i * kPlaneA + koff, kSBO16),
-                                         smem_desc(b0 + j * kPlaneB + koff, kSBO16), kIdescBf16, first ? 0u : 1u);
-                                first = false;
-                            }
-                        }
-                    }
+                    issue_c128_mmas(tmem, a0, b0);
                     mma_commit(mma_a);
                 }
             }
@@ -758,7 +764,9 @@ k_dense5_tc_c128_ws(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, co
         if (tid == 0 && it > 0 && !abort_flag) mbar_wait_bounded(mma_a, (it - 1) & 1);
     } else {
         // ------------------------------------------------------------- epilogue
-        const int ew = warp - kSplitThreads / 32;                 // 0..7
+        const int ew = warp - kSplitThreads / 32;                 // 0 .. kEpiThreads/32 - 1
+        constexpr int kEpiParts = kEpiThreads / kRows;            // threads per row
+        constexpr int kEpiCols = kN / kEpiParts;                  // output columns per thread
         const int row = 32 * (warp & 3) + (tid & 31), half = ew >> 2;
         const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         int it = 0;
@@ -774,8 +782,8 @@ k_dense5_tc_c128_ws(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, co
             const bool valid = g < n_groups;
             double2 *p = psi + (valid ? base5(g, t) : 0);
 #pragma unroll 1
-            for (int c = 0; c < 8; c++) {
-                const int col0 = 32 * half + 4 * c;
+            for (int c = 0; c < kEpiCols / 4; c++) {
+                const int col0 = kEpiCols * half + 4 * c;
                 float D[kDiags][4];
 #pragma unroll
                 for (int d = 0; d < kDiags; d++) tmem_ld4(lane_addr + 64 * d + col0, D[d]);
