@@ -47,6 +47,25 @@ def load_peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+def measured_traffic(kernel, n):
+    """DRAM bytes (read + write) per launch from the committed ncu record of
+    `kernel`, scaled from the captured state size to 2^n amplitudes; None when
+    there is no record or the kernel's source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") != kernel:
+            continue
+        src = os.path.join(ROOT, f["source"])
+        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != f["sha256"]:
+            return None
+        return int(f["dram_bytes"]) * 2 ** (n - int(f["n"]))
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -202,18 +221,26 @@ def run_ours(args):
     achieved_gbs = sweep_bytes / (dom_ms * 1e-3) / 1e9
     kind, k = dom_key
     flops = (1 << n) * (8 * (1 << k) - 2) if kind == "dense" else 0
-    if dtype == qs.QS_C128 and kind == "dense":
+    # kernel path of the default policy: tensor cores for complex64 5-qubit and
+    # complex128 2..5-qubit clusters, CUDA cores otherwise
+    tensor = kind == "dense" and n >= 5 and ((dtype == qs.QS_C64 and k == 5) or (dtype == qs.QS_C128 and k >= 2))
+    if kind == "dense" and dtype == qs.QS_C128 and not tensor:
         # native FP64: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock
         fp64_peak = 152 * 2 * 2 * sm_max_mhz * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": flops / (dom_ms * 1e-3) / 1e12, "peak": fp64_peak,
                 "unit": "TFLOP/s", "peak_source": "derived FP64 (152 SM x 2 FMA/clk x 2 x %.0f MHz)" % sm_max_mhz}
+        kname = "k_dense<double,%d>" % k
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
                 "peak_source": peak_src}
+        kname = ("k_dense5_tc_c128_ws" if dtype == qs.QS_C128 else "k_dense5_tc_c64") if tensor else (
+            "k_dense<%s,%d>" % ("double" if dtype == qs.QS_C128 else "float", k) if kind == "dense"
+            else "k_phase<%s>" % ("double" if dtype == qs.QS_C128 else "float"))
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["kernel"] = "%s k=%d" % (kind, k) if kind == "dense" else kind
+    roof["traffic"] = measured_traffic(kname, n)
+    roof["kernel"] = kname
     roof["kernel_ms"] = dom_ms
+    roof["algorithmic_bytes"] = sweep_bytes
     roof["effective_hbm_gbs"] = achieved_gbs
     roof["hbm_frac"] = achieved_gbs / hbm_gbs
 

@@ -86,7 +86,9 @@ using qsd::LogTable;
 using qsd::log_table_init;
 using qsd::log_tab;
 
-// Per-block FP64 partial sums of (p, -p ln p, N p, (N p)^2); NSTAT = 1 or 4.
+// Per-block FP64 partial sums of (p, -p ln p, p, p^2); NSTAT = 1 or 4.  The
+// mean of N p equals the sum of p, and the mean of (N p)^2 is N sum p^2, so
+// the moments cost one FMA per amplitude; the host applies the factor N.
 template <typename C, int NSTAT>
 __global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *__restrict__ part)
 {
@@ -98,7 +100,6 @@ __global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *_
     double acc[NSTAT];
 #pragma unroll
     for (int j = 0; j < NSTAT; j++) acc[j] = 0;
-    const double Nd = (double)N;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         double p = prob(psi[i]);
@@ -106,11 +107,10 @@ __global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *_
         if (NSTAT == 4) {
             // p below the normal range contributes less than 1e-305
             if (p >= 2.2250738585072014e-308) acc[1] -= p * log_tab(lt, p);
-            double np = Nd * p;
-            acc[2] += np;
-            acc[3] += np * np;
+            acc[3] = fma(p, p, acc[3]);
         }
     }
+    if (NSTAT == 4) acc[2] = acc[0];
     __shared__ double red[NSTAT][32];
 #pragma unroll
     for (int j = 0; j < NSTAT; j++) {
@@ -277,10 +277,7 @@ int stats_impl(qs_state *s, double *out, int nstat)
     QS_CUDA(cudaGetLastError(), "stats launch");
     QS_CUDA(cudaMemcpyAsync(out, res, sizeof(double) * nstat, cudaMemcpyDeviceToHost, st), "stats copy");
     QS_CUDA(cudaStreamSynchronize(st), "stats sync");
-    if (nstat == 4) {
-        out[2] /= (double)N;
-        out[3] /= (double)N;
-    }
+    if (nstat == 4) out[3] *= (double)N;   // mean of (N p)^2 = N sum p^2
     return QS_OK;
 }
 
@@ -638,8 +635,7 @@ int stats_static_impl(const void *amp, int n, void *stream, double *out)
     QS_CUDA(cudaGetLastError(), "qs_stats_static launch");
     QS_CUDA(cudaMemcpyAsync(out, res, sizeof(double) * 4, cudaMemcpyDeviceToHost, st), "qs_stats_static copy");
     QS_CUDA(cudaStreamSynchronize(st), "qs_stats_static sync");
-    out[2] /= (double)N;
-    out[3] /= (double)N;
+    out[3] *= (double)N;   // mean of (N p)^2 = N sum p^2
     return QS_OK;
 }
 

@@ -138,6 +138,7 @@ k_batch_stats(const BatchCirc *__restrict__ circ, const typename cplx<R>::t *__r
 {
     __shared__ qsd::LogTable lt;
     __shared__ double red[4][8];
+    static_assert(sizeof(qsd::LogTable) + sizeof(red) < 48 * 1024, "static shared memory");
     qsd::log_table_init(lt);
     __syncthreads();
     const BatchCirc cc = circ[blockIdx.x];
@@ -148,8 +149,7 @@ k_batch_stats(const BatchCirc *__restrict__ circ, const typename cplx<R>::t *__r
         const double p = qsd::prob(amp[cc.amp_off + i]);
         a[0] += p;
         if (p >= 2.2250738585072014e-308) a[1] -= p * qsd::log_tab(lt, p);
-        a[2] += Nd * p;
-        a[3] += (Nd * p) * (Nd * p);
+        a[3] = fma(p, p, a[3]);
     }
 #pragma unroll
     for (int j = 0; j < 4; j++) {
@@ -159,9 +159,11 @@ k_batch_stats(const BatchCirc *__restrict__ circ, const typename cplx<R>::t *__r
     }
     __syncthreads();
     if (threadIdx.x < 4) {
+        // sum p, entropy, mean of N p (= sum p), mean of (N p)^2 (= N sum p^2)
+        const int src = threadIdx.x == 2 ? 0 : threadIdx.x;
         double v = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[threadIdx.x][w];
-        out[4 * blockIdx.x + threadIdx.x] = threadIdx.x >= 2 ? v / Nd : v;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[src][w];
+        out[4 * blockIdx.x + threadIdx.x] = threadIdx.x == 3 ? v * Nd : v;
     }
 }
 

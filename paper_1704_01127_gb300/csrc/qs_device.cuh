@@ -156,19 +156,20 @@ __device__ __forceinline__ double prob(float2 a)
 // Natural logarithm of a positive normal double, table-driven (P. T. P. Tang,
 // "Table-driven implementation of the logarithm function in IEEE floating-point
 // arithmetic", ACM TOMS 16(4), 1990): p = 2^e m, m in [1, 2); c_j is the centre
-// of the mantissa interval [1 + j/128, 1 + (j+1)/128) picked by the top seven
-// mantissa bits, r = m / c_j - 1 (|r| <= 1/256) and
-//   ln p = e ln 2 + ln c_j + ln(1 + r),  ln(1 + r) = r - r^2/2 + ... - r^6/6,
-// truncation error below r^7/7 < 2^-58.  ln c_j and 1/c_j come from the CUDA
-// math library once per block (shared-memory table).
+// of the mantissa interval [1 + j/1024, 1 + (j+1)/1024) picked by the top ten
+// mantissa bits, r = m / c_j - 1 (|r| <= 2^-11) and
+//   ln p = e ln 2 + ln c_j + ln(1 + r),  ln(1 + r) = r - r^2/2 + r^3/3 - r^4/4,
+// truncation error below r^5/5 < 2^-57.  ln c_j and 1/c_j come from the CUDA
+// math library once per block (shared-memory table, 16 KB).
+constexpr int kLogBits = 10;
 struct LogTable {
-    double inv[128], ln[128];
+    double inv[1 << kLogBits], ln[1 << kLogBits];
 };
 
 __device__ __forceinline__ void log_table_init(LogTable &t)
 {
-    for (int j = threadIdx.x; j < 128; j += blockDim.x) {
-        const double c = 1.0 + (j + 0.5) / 128.0;
+    for (int j = threadIdx.x; j < (1 << kLogBits); j += blockDim.x) {
+        const double c = 1.0 + (j + 0.5) / (double)(1 << kLogBits);
         t.inv[j] = 1.0 / c;
         t.ln[j] = log(c);
     }
@@ -178,16 +179,14 @@ __device__ __forceinline__ double log_tab(const LogTable &t, double p)
 {
     const long long bits = __double_as_longlong(p);
     const int e = (int)(bits >> 52) - 1023;
-    const int j = (int)((bits >> 45) & 127);
+    const int j = (int)((bits >> (52 - kLogBits)) & ((1 << kLogBits) - 1));
     const double m = __longlong_as_double((bits & 0xFFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
     const double r = fma(m, t.inv[j], -1.0);
-    double q = -1.0 / 6.0;
-    q = fma(q, r, 0.2);
-    q = fma(q, r, -0.25);
+    double q = -0.25;
     q = fma(q, r, 1.0 / 3.0);
     q = fma(q, r, -0.5);
     q = fma(q, r, 1.0);
-    return fma((double)e, 0.69314718055994530942, t.ln[j] + q * r);
+    return fma((double)e, 0.69314718055994530942, fma(q, r, t.ln[j]));
 }
 
 }  // namespace qsd

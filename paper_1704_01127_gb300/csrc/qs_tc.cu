@@ -349,9 +349,6 @@ constexpr size_t kPlaneA = (size_t)kRows * kK * 2;           // 16 KB per A digi
 constexpr size_t kPlaneB = (size_t)kN * kK * 2;              // 8 KB per B digit plane
 constexpr size_t kSmemC128 = kSlices * kPlaneA + kSlicesB * kPlaneB + 256;   // + column exponents
 constexpr int kTmemCols128 = 512;
-// D fp32, A/B bf16 (format 1), K-major, N = 64, M = 128
-constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                               ((uint32_t)(kRows >> 4) << 24);
 
 // instruction descriptor of a bf16 MMA with M = 128 and N = 64 * planes
 __host__ __device__ constexpr uint32_t idesc_bf16_planes(int planes)
