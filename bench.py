@@ -123,7 +123,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup(args=None, backend=None):
+    """Rank / world from the torchrun environment; a process group (NCCL on GPU
+    boxes, gloo otherwise) when more than one rank runs.  Ranks are replicas:
+    each simulates its own circuits, and the group only carries the timing."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -131,8 +134,12 @@ def dist_setup(args):
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
     return world, rank, local, dist
 
 
@@ -142,12 +149,19 @@ def barrier(dist):
 
 
 def max_over_ranks(dist, x):
+    """The largest x over all ranks (the job's elapsed time)."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_seconds_per_circuit(elapsed_max, circuits_per_rank, world):
+    """Whole-job wall time divided by the circuits all ranks simulated."""
+    return elapsed_max / (circuits_per_rank * world)
 
 
 # ------------------------------------------------------------------ our arm
@@ -212,7 +226,7 @@ def run_ours(args):
     barrier(dist)
     dev_s = ev0.elapsed_time(ev1) / 1e3
     elapsed = max_over_ranks(dist, max(dev_s, wall))
-    per_circuit = elapsed / (args.steps * world)
+    per_circuit = job_seconds_per_circuit(elapsed, args.steps, world)
 
     # dominant kernel: the (kind, k) class with the most device time
     dom_key = max(kernel_ms, key=lambda kk: sum(kernel_ms[kk]))
