@@ -11,8 +11,10 @@
 // complex64: every real is split into a tf32 head and a tf32 tail,
 // a ~ a_h + a_t (a_h: a with its low 13 mantissa bits cleared, a_t: the rest
 // rounded to the nearest tf32, so the split is unbiased), and
-// D = A_h B_h + A_h B_t + A_t B_h accumulates in FP32 in tensor memory
-// (tcgen05.mma kind::tf32, M = 128, N = 64, K = 8 per instruction).
+// D = A_h B_h + (A_h B_t + A_t B_h) accumulates in FP32 in tensor memory, the
+// head product and the correction in separate accumulators added once with
+// round-to-nearest (tcgen05.mma kind::tf32, M = 128, N = 64, K = 8 per
+// instruction).
 //
 // Operands sit in shared memory in the canonical K-major layout without
 // swizzle: 8-row x 16-byte core matrices, core matrices adjacent along K 128 B
@@ -32,7 +34,7 @@ constexpr int kK = 64;              // reals per group (MMA K)
 constexpr int kN = 64;              // output reals per group (MMA N)
 constexpr uint32_t kLBO = 128;      // bytes between K-adjacent core matrices
 constexpr uint32_t kSBO = 2048;     // bytes between 8-row groups (16 core matrices)
-constexpr int kTmemCols = 64;
+constexpr int kTmemCols = 128;     // complex64: head product and correction terms
 constexpr long kWaitLimit = 1L << 24;   // bounded mbarrier polling
 
 // byte offset of fp32 element (row, k) in a K-major no-swizzle tile with 64 K
@@ -206,7 +208,7 @@ constexpr size_t kBBytesF32 = (size_t)kN * kK * 4;         // 16 KB
 constexpr size_t kSmemF32 = 2 * kTileBytesF32 + 2 * kBBytesF32;
 
 // One CTA of 128 threads; thread r owns row r (group) of each tile.  Tiles are
-// taken in a grid-stride loop; warp 0 holds 64 TMEM columns for the CTA.
+// taken in a grid-stride loop; warp 0 holds 128 TMEM columns for the CTA.
 __global__ void __launch_bounds__(128, 2)
 k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const float *__restrict__ bpack,
                 int *__restrict__ status)
@@ -276,9 +278,12 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const f
 #pragma unroll
             for (int ks = 0; ks < kK / 8; ks++) {
                 const uint32_t koff = ks * 2 * kLBO;   // 8 tf32 = two core matrices along K
+                // head product and the two correction products in separate
+                // accumulators: the tensor core's FP32 accumulation rounds
+                // toward zero, so fewer steps on the large sum mean less drift
                 mma_tf32(tmem, smem_desc(a_h + koff), smem_desc(b_h + koff), kIdescTf32, ks > 0);
-                mma_tf32(tmem, smem_desc(a_h + koff), smem_desc(b_t + koff), kIdescTf32, 1);
-                mma_tf32(tmem, smem_desc(a_t + koff), smem_desc(b_h + koff), kIdescTf32, 1);
+                mma_tf32(tmem + kN, smem_desc(a_h + koff), smem_desc(b_t + koff), kIdescTf32, ks > 0);
+                mma_tf32(tmem + kN, smem_desc(a_t + koff), smem_desc(b_h + koff), kIdescTf32, 1);
             }
             mma_commit(mbar_a);
         }
@@ -306,12 +311,14 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const f
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
         for (int c = 0; c < kN / 16; c++) {
-            float r[16];
+            float r[16], q[16];
             tmem_ld16(lane_addr + c * 16, r);
+            tmem_ld16(lane_addr + kN + c * 16, q);
             tmem_wait_ld();
             if (valid_cur) {
 #pragma unroll
-                for (int l = 0; l < 8; l++) p_cur[off5(8 * c + l, t)] = make_float2(r[2 * l], r[2 * l + 1]);
+                for (int l = 0; l < 8; l++)
+                    p_cur[off5(8 * c + l, t)] = make_float2(r[2 * l] + q[2 * l], r[2 * l + 1] + q[2 * l + 1]);
             }
         }
         tc_fence_before();
