@@ -90,6 +90,9 @@ int qs_init_uniform(qs_state *s);
  * state, rounding to the state's dtype; and back (widening for QS_C64). */
 int qs_set_amplitudes(qs_state *s, const double *host_c128);
 int qs_get_amplitudes(qs_state *s, double *host_c128);
+/* Amplitudes at `count` indices (each < 2^n) as complex128 (host memory; out:
+ * 2*count doubles), for spot checks of states too large to copy whole. */
+int qs_get_amplitudes_at(qs_state *s, const uint64_t *indices, int64_t count, double *out);
 
 /* Apply a dense k-qubit gate in place (Sec. 3.2): for every assignment c of the
  * n-k other bits, the 2^k amplitudes whose target bits spell x (x_j = bit

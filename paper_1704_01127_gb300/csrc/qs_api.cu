@@ -521,6 +521,30 @@ extern "C" int qs_get_amplitudes(qs_state *s, double *host)
     return QS_OK;
 }
 
+extern "C" int qs_get_amplitudes_at(qs_state *s, const uint64_t *idx, int64_t count, double *out)
+{
+    if (!s || !s->amp || count < 0 || (count > 0 && (!idx || !out)))
+        return qs_fail(QS_EINVAL, "qs_get_amplitudes_at: bad arguments");
+    if (int rc = qs_check_status(s)) return rc;
+    const uint64_t N = 1ULL << s->n;
+    cudaStream_t st = (cudaStream_t)s->stream;
+    for (int64_t j = 0; j < count; j++) {
+        if (idx[j] >= N) return qs_fail(QS_EINVAL, "qs_get_amplitudes_at: index %lld out of range", (long long)j);
+        if (s->dtype == QS_C128) {
+            QS_CUDA(cudaMemcpyAsync(out + 2 * j, (double2 *)s->amp + idx[j], 16, cudaMemcpyDeviceToHost, st),
+                    "qs_get_amplitudes_at");
+        } else {
+            float f[2];
+            QS_CUDA(cudaMemcpyAsync(f, (float2 *)s->amp + idx[j], 8, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes_at");
+            QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes_at");
+            out[2 * j] = f[0];
+            out[2 * j + 1] = f[1];
+        }
+    }
+    QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes_at");
+    return QS_OK;
+}
+
 extern "C" int qs_norm(qs_state *s, double *out)
 {
     if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_norm: null argument");

@@ -59,6 +59,7 @@ _SIGS = {
     "qs_init_uniform": ([_VP], ctypes.c_int),
     "qs_set_amplitudes": ([_VP, _DP], ctypes.c_int),
     "qs_get_amplitudes": ([_VP, _DP], ctypes.c_int),
+    "qs_get_amplitudes_at": ([_VP, _U64P, ctypes.c_int64, _DP], ctypes.c_int),
     "qs_apply_cluster": ([_VP, _IP, ctypes.c_int, _DP], ctypes.c_int),
     "qs_apply_diag": ([_VP, _IP, ctypes.c_int, _DP], ctypes.c_int),
     "qs_apply_phase": ([_VP, _IP, ctypes.c_int, _IP], ctypes.c_int),
@@ -217,6 +218,13 @@ def qs_set_amplitudes(h, psi):
 def qs_get_amplitudes(h):
     out = np.empty(1 << qs_num_qubits(h), dtype=np.complex128)
     _check(lib().qs_get_amplitudes(h, _dp(out.view(np.float64))))
+    return out
+
+
+def qs_get_amplitudes_at(h, indices):
+    idx = np.ascontiguousarray(indices, dtype=np.uint64)
+    out = np.empty(idx.size, dtype=np.complex128)
+    _check(lib().qs_get_amplitudes_at(h, idx.ctypes.data_as(_U64P), int(idx.size), _dp(out.view(np.float64))))
     return out
 
 
