@@ -247,7 +247,7 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
                 "peak_source": peak_src}
-        kname = ("k_dense5_tc_c128_ws" if dtype == qs.QS_C128 else "k_dense5_tc_c64") if tensor else (
+        kname = ("k_dense5_tc_c128_pipe" if dtype == qs.QS_C128 else "k_dense5_tc_c64") if tensor else (
             "k_dense<%s,%d>" % ("double" if dtype == qs.QS_C128 else "float", k) if kind == "dense"
             else "k_phase<%s>" % ("double" if dtype == qs.QS_C128 else "float"))
     roof["frac"] = roof["achieved"] / roof["peak"]

@@ -144,16 +144,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 #pragma unroll
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
-// 8 consecutive 32-bit columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
-{
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
-}
 // 4 consecutive 32-bit columns of this thread's TMEM lane
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v)
 {
@@ -357,42 +347,6 @@ constexpr size_t kPlaneB = (size_t)kN * kK * 2;              // 8 KB per B digit
 constexpr size_t kSmemC128 = kSlices * kPlaneA + kSlicesB * kPlaneB + 256;   // + column exponents
 constexpr int kTmemCols128 = 512;
 
-// instruction descriptor of a bf16 MMA with M = 128 and N = 64 * planes
-__host__ __device__ constexpr uint32_t idesc_bf16_planes(int planes)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 * planes >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
-}
-
-// The MMAs of one complex128 tile.  Digit planes of B are contiguous 8 KB
-// blocks, i.e. exactly 8 row groups (one SBO stride each) apart, and the
-// accumulators D_d are contiguous 64-column blocks of TMEM, so one MMA with
-// N = 64 * m and B starting at plane j computes A_i B_j .. A_i B_{j+m-1} into
-// D_{i+j} .. D_{i+j+m-1} at once (m <= 4, N <= 256).  Products with i = 0 come
-// first and initialise D_0..D_6; all others accumulate.  Descriptors differ
-// only in their start-address field (address >> 4, below 2^14), so each is a
-// precomputed base plus an offset.
-__device__ __forceinline__ void issue_c128_mmas(uint32_t tmem, uint32_t a0, uint32_t b0)
-{
-    const uint64_t da = smem_desc(a0, kSBO16), db = smem_desc(b0, kSBO16);
-#pragma unroll
-    for (int i = 0; i < kSlices; i++) {
-#pragma unroll
-        for (int j = 0; j + i < kDiags && j < kSlicesB; j += 4) {
-            int m = 4;
-            if (j + m > kSlicesB) m = kSlicesB - j;
-            if (i + j + m > kDiags) m = kDiags - i - j;
-#pragma unroll
-            for (int ks = 0; ks < kK / 16; ks++) {
-                const uint32_t koff = ks * 2 * kLBO;   // 16 bf16 = two core matrices along K
-                const uint64_t adesc = da + ((uint64_t)(i * kPlaneA + koff) >> 4);
-                const uint64_t bdesc = db + ((uint64_t)(j * kPlaneB + koff) >> 4);
-                const uint32_t acc = (i == 0 && ks == 0) ? 0u : 1u;
-                mma_bf16(tmem + 64 * (i + j), adesc, bdesc, idesc_bf16_planes(m), acc);
-            }
-        }
-    }
-}
-
 // byte offset of 16-bit element (row, k) in a K-major no-swizzle tile with 64 K
 __host__ __device__ __forceinline__ uint32_t cm_off16(int row, int k)
 {
@@ -438,195 +392,6 @@ __device__ __forceinline__ int exact_int(float x)
     return __float_as_int(x + 12582912.0f) - 0x4B400000;
 }
 
-// T * 2^X as a double (|T| < 2^62): one int64 -> double conversion (rounded
-// to nearest), then X added to the exponent field (no FP64 arithmetic)
-__device__ __forceinline__ double scale_int(long long T, int X)
-{
-    if (T == 0) return 0.0;
-    const long long b = __double_as_longlong(__ll2double_rn(T)) + ((long long)X << 52);
-    return __longlong_as_double(b);
-}
-
-// TPR threads per row: thread t owns row (t & 127) and part h = t >> 7 of that
-// row's 32 amplitudes (members h*MPT .. +MPT-1, K columns 2*MPT*h ..); warp w
-// reads TMEM lanes 32 (w & 3) .. +31 and the output columns of part w >> 2.
-// With TPR = 8 a CTA has 32 warps, enough to hide the load latency.
-template <int TPR>
-__global__ void __launch_bounds__(kRows * TPR, 1)
-k_dense5_tc_c128(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const uint8_t *__restrict__ bpack,
-                 int *__restrict__ status)
-{
-    constexpr int MPT = 32 / TPR;            // members per thread
-    constexpr int CH = MPT / 4;              // 8-column chunks per thread (4 members each)
-    constexpr int COLS = kN / TPR;           // output columns per thread
-    constexpr int EC = TPR >= 8 ? 4 : 8;     // epilogue chunk (columns), sized to the register budget
-    extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *A = smem;                                         // kSlices planes
-    uint8_t *B = smem + kSlices * kPlaneA;                     // kSlicesB planes
-    int *Gcol = reinterpret_cast<int *>(B + kSlicesB * kPlaneB);
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t tmem_base_s;
-    __shared__ int rowexp[TPR][kRows];
-
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = tid & (kRows - 1), part = tid >> 7;
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(bpack);
-        uint4 *dst = reinterpret_cast<uint4 *>(B);
-        for (int i = tid; i < (int)((kSlicesB * kPlaneB + 256) / 16); i += blockDim.x) dst[i] = src[i];
-    }
-    if (warp == 0) {
-        tmem_alloc(smem_u32(&tmem_base_s), kTmemCols128);
-        tmem_relinquish();
-    }
-    if (tid == 0) {
-        mbar_init(smem_u32(&mbar), 1);
-        fence_mbar_init();
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_base_s;
-    const uint32_t mbar_a = smem_u32(&mbar);
-    const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
-
-    const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
-    uint32_t parity = 0;
-    // software pipeline: the next tile's amplitudes are loaded into registers
-    // while the tensor cores and the epilogue work on the current one
-    double2 v[MPT];
-    uint64_t tile = blockIdx.x;
-    bool valid = false;
-    double2 *p = psi;
-    auto load_tile = [&](uint64_t tl, double2 *vv, bool &val, double2 *&pp) {
-        const uint64_t g = tl * kRows + row;
-        val = tl < n_tiles && g < n_groups;
-        pp = psi + (val ? base5(g, t) : 0);
-#pragma unroll
-        for (int x = 0; x < MPT; x++) vv[x] = val ? pp[off5(MPT * part + x, t)] : make_double2(0.0, 0.0);
-    };
-    load_tile(tile, v, valid, p);
-    for (; tile < n_tiles; tile += gridDim.x) {
-        // largest exponent field of the row (bits 20..30 of the high words)
-        uint32_t emax = 0;
-#pragma unroll
-        for (int x = 0; x < MPT; x++) {
-            emax = max(emax, (uint32_t)__double2hiint(v[x].x) & 0x7FF00000u);
-            emax = max(emax, (uint32_t)__double2hiint(v[x].y) & 0x7FF00000u);
-        }
-        rowexp[part][row] = (int)(emax >> 20);
-        __syncthreads();
-        int E = 0;
-#pragma unroll
-        for (int h = 0; h < TPR; h++) E = max(E, rowexp[h][row]);
-        // digits: CH chunks of 8 K-columns (4 members) per slice; digit s of a
-        // value is byte 5 - s of its biased fixed-point integer G
-#pragma unroll
-        for (int c = 0; c < CH; c++) {
-            uint32_t glo[8], ghi[8];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const uint64_t g0 = fixed48(v[4 * c + j].x, E), g1 = fixed48(v[4 * c + j].y, E);
-                glo[2 * j] = (uint32_t)g0;
-                ghi[2 * j] = (uint32_t)(g0 >> 32);
-                glo[2 * j + 1] = (uint32_t)g1;
-                ghi[2 * j + 1] = (uint32_t)(g1 >> 32);
-            }
-            uint8_t *dst = A + cm_off16(row, 2 * MPT * part + 8 * c);
-            uint4 w;
-#define QS_DIGIT_PLANE(SL, WORDS, BYTE)                                                        \
-    w.x = pack_bf16(digit_f32<BYTE>(WORDS[0]), digit_f32<BYTE>(WORDS[1]));                   \
-    w.y = pack_bf16(digit_f32<BYTE>(WORDS[2]), digit_f32<BYTE>(WORDS[3]));                   \
-    w.z = pack_bf16(digit_f32<BYTE>(WORDS[4]), digit_f32<BYTE>(WORDS[5]));                   \
-    w.w = pack_bf16(digit_f32<BYTE>(WORDS[6]), digit_f32<BYTE>(WORDS[7]));                   \
-    *reinterpret_cast<uint4 *>(dst + (SL) * kPlaneA) = w;
-            QS_DIGIT_PLANE(0, ghi, 1)      // bits 40-47
-            QS_DIGIT_PLANE(1, ghi, 0)      // bits 32-39
-            QS_DIGIT_PLANE(2, glo, 3)      // bits 24-31
-            QS_DIGIT_PLANE(3, glo, 2)      // bits 16-23
-            QS_DIGIT_PLANE(4, glo, 1)      // bits 8-15
-            QS_DIGIT_PLANE(5, glo, 0)      // bits 0-7
-#undef QS_DIGIT_PLANE
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {
-            issue_c128_mmas(tmem, a0, b0);
-            mma_commit(mbar_a);
-        }
-        double2 *const p_cur = p;
-        const bool valid_cur = valid;
-        load_tile(tile + gridDim.x, v, valid, p);
-        bool ok = false;
-        for (long it = 0; it < kWaitLimit; it++)
-            if (mbar_try_wait(mbar_a, parity)) {
-                ok = true;
-                break;
-            }
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicExch(status, 1);
-                for (long it = 0; it < kWaitLimit; it++)
-                    if (mbar_try_wait(mbar_a, parity)) break;
-            }
-            break;
-        }
-        parity ^= 1;
-        tc_fence_after();
-        const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-#pragma unroll 1
-        for (int c = 0; c < COLS / EC; c++) {
-            const int col0 = COLS * part + EC * c;
-            float D[kDiags][EC];
-#pragma unroll
-            for (int d = 0; d < kDiags; d++) {
-                if constexpr (EC == 8) tmem_ld8(lane_addr + 64 * d + col0, D[d]);
-                else tmem_ld4(lane_addr + 64 * d + col0, D[d]);
-            }
-            tmem_wait_ld();
-            double out[EC];
-#pragma unroll
-            for (int q = 0; q < EC; q++) {
-                const long long U = (long long)exact_int(D[0][q]) * 16777216LL + (long long)exact_int(D[1][q]) * 65536LL +
-                                    (long long)exact_int(D[2][q]) * 256LL + (long long)exact_int(D[3][q]);
-                // D_4 + D_5 / 256 + D_6 / 65536; 256 L < 2^31
-                const float L = fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]);
-                const long long T = U * 65536LL + (long long)__float2int_rn(L * 256.0f);
-                out[q] = scale_int(T, E + Gcol[col0 + q] - 2096);
-            }
-            if (valid_cur) {
-#pragma unroll
-                for (int l = 0; l < EC / 2; l++)
-                    p_cur[off5(col0 / 2 + l, t)] = make_double2(out[2 * l], out[2 * l + 1]);
-            }
-        }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-    }
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kTmemCols128);
-}
-
-
-// ----------------------------------------------------------------------------
-// complex128, warp-specialised: the same arithmetic as k_dense5_tc_c128 with
-// the per-tile work split between two groups that run concurrently.
-//   splitters (warps 0..15, 4 threads per row): gather tile t+1 and cut it into
-//     digit planes as soon as the tensor cores are done reading tile t's planes;
-//     thread 0 issues the MMAs of a tile once its planes are written and the
-//     epilogue group has released the accumulators;
-//   epilogue (warps 16..31, 4 threads per row, 16 output columns each): wait for
-//     tile t's MMAs, rebuild and store FP64 results, release the accumulators.
-// Hand-offs: mbar_mma (tcgen05.commit, one arrival per tile) and mbar_free (one
-// arrival per epilogue thread per tile); the splitters meet at named barrier 1, whose
-// OR-reduced variant makes every timeout decision uniform across the group.
-// Every wait is bounded; a timeout sets the status word and all threads leave
-// their loops, so the final barrier and the TMEM release are always reached.
-// ----------------------------------------------------------------------------
 constexpr int kSplitThreads = 512;
 constexpr int kEpiThreads = 512;
 
@@ -653,33 +418,99 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
     return false;
 }
 
+// ----------------------------------------------------------------------------
+// complex128 kernel: one CTA of 1024 threads per SM, two warp-specialised groups.
+//   splitters (warps 0..15, 4 threads per row, 8 amplitudes each): copy tile
+//     t+1 into a 64 KB stage with cp.async while tile t is processed; find the
+//     row exponents and the fixed-point values of tile t while the MMAs of
+//     tile t-1 still read the digit planes, then write the planes; thread 0
+//     issues the MMAs;
+//   epilogue (warps 16..31, 4 threads per row, 8 columns of each half): rebuild
+//     FP64 results from the accumulators and store them.
+// The output columns come in two halves of 32, so that the tensor cores work
+// on one half while the epilogue reads the other.
+//   TMEM: half h holds D_0..D_6 for its 32 columns at columns 256 h + 32 d.
+//   B:    4 KB blocks (half h, plane j) at (7 h + j) * 4 KB, so for A plane i
+//         one MMA with N = 32 (7 - i) reads B planes 0..6-i of half h and
+//         writes D_i..D_6 of that half (24 MMAs per half, 48 per tile).
+// Hand-offs per tile: mbar_mma[h] (tcgen05.commit after half h's MMAs; half 1's
+// also releases the A planes), mbar_free[h] (one arrival per epilogue thread
+// when half h's accumulators are read).  All waits are bounded.
+// ----------------------------------------------------------------------------
+constexpr int kHalfN = 32;
+constexpr uint32_t kBlockB = (uint32_t)kHalfN * kK * 2;   // 4 KB: one plane of one half
+
+__host__ __device__ constexpr uint32_t idesc_bf16_n(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void issue_c128_half(uint32_t tmem, uint32_t a0, uint32_t b0, int h)
+{
+    const uint64_t da = smem_desc(a0, kSBO16), db = smem_desc(b0 + h * kSlicesB * kBlockB, kSBO16);
+#pragma unroll
+    for (int i = 0; i < kSlices; i++) {
+#pragma unroll
+        for (int ks = 0; ks < kK / 16; ks++) {
+            const uint32_t koff = ks * 2 * kLBO;
+            mma_bf16(tmem + 256 * h + kHalfN * i, da + ((uint64_t)(i * kPlaneA + koff) >> 4),
+                     db + ((uint64_t)koff >> 4), idesc_bf16_n(kHalfN * (kDiags - i)), (i == 0 && ks == 0) ? 0u : 1u);
+        }
+    }
+}
+
+// 16-byte asynchronous global -> shared copy (zero fill when bytes = 0)
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *gptr, uint32_t bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gptr), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr size_t kStageC128 = (size_t)kSplitThreads * 8 * 16;   // raw next tile: 64 KB
+constexpr size_t kSmemC128Pipe = kSmemC128 + kStageC128;
+
 __global__ void __launch_bounds__(kSplitThreads + kEpiThreads, 1)
-k_dense5_tc_c128_ws(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const uint8_t *__restrict__ bpack,
-                    int *__restrict__ status)
+k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const uint8_t *__restrict__ bpack,
+                      int *__restrict__ status)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *A = smem;
     uint8_t *B = smem + kSlices * kPlaneA;
-    int *Gcol = reinterpret_cast<int *>(B + kSlicesB * kPlaneB);
-    __shared__ __align__(8) uint64_t mbar_mma, mbar_free;
+    uint4 *stage = reinterpret_cast<uint4 *>(smem + kSmemC128);   // [8][512] x 16 B
+    __shared__ __align__(8) uint64_t mbar_mma[2], mbar_free[2];
+    __shared__ uint64_t moff[32];         // offset of member x within a group
     __shared__ uint32_t tmem_base_s;
     __shared__ int rowexp[4][kRows];
-    __shared__ int rowE[2][kRows];
+    // exponent-field terms, added modulo 2^32 (only the sum must fit):
+    __shared__ uint32_t rowX[2][kRows];   // (E_r - 2096) << 20 of the last two tiles
+    __shared__ uint32_t colX[kN];         // G_n << 20
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     {
+        // plane-major pack (plane j = halves 0, 1) -> half-major blocks
         const uint4 *src = reinterpret_cast<const uint4 *>(bpack);
         uint4 *dst = reinterpret_cast<uint4 *>(B);
-        for (int i = tid; i < (int)((kSlicesB * kPlaneB + 256) / 16); i += blockDim.x) dst[i] = src[i];
+        constexpr int kPerBlock = (int)(kBlockB / 16);
+        for (int i = tid; i < kSlicesB * 2 * kPerBlock; i += blockDim.x) {
+            const int blk = i / kPerBlock, w = i - blk * kPerBlock;   // source block 2 j + h
+            const int j = blk >> 1, h = blk & 1;
+            dst[(h * kSlicesB + j) * kPerBlock + w] = src[i];
+        }
+        const int *G = reinterpret_cast<const int *>(bpack + kSlicesB * kPlaneB);
+        if (tid < kN) colX[tid] = (uint32_t)G[tid] << 20;
+        if (tid < 32) moff[tid] = off5(tid, t);
     }
     if (warp == 0) {
         tmem_alloc(smem_u32(&tmem_base_s), kTmemCols128);
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(smem_u32(&mbar_mma), 1);
-        mbar_init(smem_u32(&mbar_free), kEpiThreads);
+        for (int h = 0; h < 2; h++) {
+            mbar_init(smem_u32(&mbar_mma[h]), 1);
+            mbar_init(smem_u32(&mbar_free[h]), kEpiThreads);
+        }
         fence_mbar_init();
         abort_flag = 0;
     }
@@ -688,29 +519,33 @@ k_dense5_tc_c128_ws(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, co
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
-    const uint32_t mma_a = smem_u32(&mbar_mma), free_a = smem_u32(&mbar_free);
     const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
 
     if (tid < kSplitThreads) {
         // ------------------------------------------------------------ splitters
         const int row = tid & (kRows - 1), part = tid >> 7;
         const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
-        double2 v[8];
-        auto load_tile = [&](uint64_t tl) {
+        const uint32_t stage_a = smem_u32(stage) + 16u * tid;
+        // this thread's 8 amplitudes of tile tl into its own stage slots
+        // (slot x at x * 512 + tid): asynchronous, a whole iteration ahead
+        auto prefetch = [&](uint64_t tl) {
             const uint64_t g = tl * kRows + row;
             const bool val = tl < n_tiles && g < n_groups;
             const double2 *pp = psi + (val ? base5(g, t) : 0);
 #pragma unroll
-            for (int x = 0; x < 8; x++) v[x] = val ? pp[off5(8 * part + x, t)] : make_double2(0.0, 0.0);
+            for (int x = 0; x < 8; x++)
+                cp_async16(stage_a + 16u * kSplitThreads * x, val ? pp + moff[8 * part + x] : psi, val ? 16u : 0u);
+            cp_async_commit();
         };
-        load_tile(blockIdx.x);
+        prefetch(blockIdx.x);
         int it = 0;
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, it++) {
-            // tile it-1's MMAs must have finished reading the planes
-            const bool ok = it == 0 || mbar_wait_bounded(mma_a, (it - 1) & 1);
-            if (bar_split_or(!ok || abort_flag)) {
-                if (tid == 0) atomicExch(status, 1);
-                break;
+            cp_async_wait_all();
+            double2 v[8];
+#pragma unroll
+            for (int x = 0; x < 8; x++) {
+                const uint4 w = stage[kSplitThreads * x + tid];
+                v[x] = make_double2(__hiloint2double((int)w.y, (int)w.x), __hiloint2double((int)w.w, (int)w.z));
             }
             uint32_t emax = 0;
 #pragma unroll
@@ -718,22 +553,35 @@ k_dense5_tc_c128_ws(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, co
                 emax = max(emax, (uint32_t)__double2hiint(v[x].x) & 0x7FF00000u);
                 emax = max(emax, (uint32_t)__double2hiint(v[x].y) & 0x7FF00000u);
             }
+            // emax depends on every slot read above, so the shared loads are
+            // complete before the next tile's copies may overwrite the slots
+            asm volatile("" ::"r"(emax) : "memory");
+            prefetch(tile + gridDim.x);
             rowexp[part][row] = (int)(emax >> 20);
             bar_split();
             const int E = max(max(rowexp[0][row], rowexp[1][row]), max(rowexp[2][row], rowexp[3][row]));
-            if (part == 0) rowE[it & 1][row] = E;
+            // the epilogue of tile it-2 has released both halves (thread 0 waited
+            // for it before issuing tile it-1), so slot it & 1 is free
+            if (part == 0) rowX[it & 1][row] = (uint32_t)(E - 2096) << 20;
+            uint32_t glo[16], ghi[16];
+#pragma unroll
+            for (int x = 0; x < 8; x++) {
+                const uint64_t g0 = fixed48(v[x].x, E), g1 = fixed48(v[x].y, E);
+                glo[2 * x] = (uint32_t)g0;
+                ghi[2 * x] = (uint32_t)(g0 >> 32);
+                glo[2 * x + 1] = (uint32_t)g1;
+                ghi[2 * x + 1] = (uint32_t)(g1 >> 32);
+            }
+            // tile it-1's MMAs (both halves) must have finished reading the planes
+            const bool ok = it == 0 || mbar_wait_bounded(smem_u32(&mbar_mma[1]), (it - 1) & 1);
+            if (bar_split_or(!ok || abort_flag)) {
+                if (tid == 0) atomicExch(status, 1);
+                break;
+            }
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                uint32_t glo[8], ghi[8];
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const uint64_t g0 = fixed48(v[4 * c + j].x, E), g1 = fixed48(v[4 * c + j].y, E);
-                    glo[2 * j] = (uint32_t)g0;
-                    ghi[2 * j] = (uint32_t)(g0 >> 32);
-                    glo[2 * j + 1] = (uint32_t)g1;
-                    ghi[2 * j + 1] = (uint32_t)(g1 >> 32);
-                }
                 uint8_t *dst = A + cm_off16(row, 16 * part + 8 * c);
+                const uint32_t *wl = glo + 8 * c, *wh = ghi + 8 * c;
                 uint4 w;
 #define QS_DIGIT_PLANE(SL, WORDS, BYTE)                                                        \
     w.x = pack_bf16(digit_f32<BYTE>(WORDS[0]), digit_f32<BYTE>(WORDS[1]));                   \
@@ -741,82 +589,91 @@ k_dense5_tc_c128_ws(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, co
     w.z = pack_bf16(digit_f32<BYTE>(WORDS[4]), digit_f32<BYTE>(WORDS[5]));                   \
     w.w = pack_bf16(digit_f32<BYTE>(WORDS[6]), digit_f32<BYTE>(WORDS[7]));                   \
     *reinterpret_cast<uint4 *>(dst + (SL) * kPlaneA) = w;
-                QS_DIGIT_PLANE(0, ghi, 1)
-                QS_DIGIT_PLANE(1, ghi, 0)
-                QS_DIGIT_PLANE(2, glo, 3)
-                QS_DIGIT_PLANE(3, glo, 2)
-                QS_DIGIT_PLANE(4, glo, 1)
-                QS_DIGIT_PLANE(5, glo, 0)
+                QS_DIGIT_PLANE(0, wh, 1)
+                QS_DIGIT_PLANE(1, wh, 0)
+                QS_DIGIT_PLANE(2, wl, 3)
+                QS_DIGIT_PLANE(3, wl, 2)
+                QS_DIGIT_PLANE(4, wl, 1)
+                QS_DIGIT_PLANE(5, wl, 0)
 #undef QS_DIGIT_PLANE
             }
             fence_proxy_async();
             bar_split();
             if (tid == 0) {
-                // the epilogue must have released tile it-1's accumulators
-                if (it > 0 && !mbar_wait_bounded(free_a, (it - 1) & 1)) {
-                    atomicExch(status, 1);
-                    abort_flag = 1;
-                } else {
+                // half h of tile it-1 must have been read out before half h of tile it
+                for (int h = 0; h < 2; h++) {
+                    if (it > 0 && !mbar_wait_bounded(smem_u32(&mbar_free[h]), (it - 1) & 1)) {
+                        atomicExch(status, 1);
+                        abort_flag = 1;
+                        break;
+                    }
                     tc_fence_after();
-                    issue_c128_mmas(tmem, a0, b0);
-                    mma_commit(mma_a);
+                    issue_c128_half(tmem, a0, b0, h);
+                    mma_commit(smem_u32(&mbar_mma[h]));
                 }
             }
-            load_tile(tile + gridDim.x);
         }
+        cp_async_wait_all();
         // leave only after the last MMAs are complete (they read this CTA's planes)
-        if (tid == 0 && it > 0 && !abort_flag) mbar_wait_bounded(mma_a, (it - 1) & 1);
+        if (tid == 0 && it > 0 && !abort_flag) mbar_wait_bounded(smem_u32(&mbar_mma[1]), (it - 1) & 1);
     } else {
         // ------------------------------------------------------------- epilogue
-        const int ew = warp - kSplitThreads / 32;                 // 0 .. kEpiThreads/32 - 1
-        constexpr int kEpiParts = kEpiThreads / kRows;            // threads per row
-        constexpr int kEpiCols = kN / kEpiParts;                  // output columns per thread
-        const int row = 32 * (warp & 3) + (tid & 31), half = ew >> 2;
+        const int ew = warp - kSplitThreads / 32;                 // 0 .. 15
+        const int row = 32 * (warp & 3) + (tid & 31), q8 = ew >> 2;   // columns 8 q8 .. +7 of each half
         const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         int it = 0;
-        for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, it++) {
-            if (!mbar_wait_bounded(mma_a, it & 1) || abort_flag) {
-                atomicExch(status, 1);
-                abort_flag = 1;
-                break;
-            }
-            tc_fence_after();
-            const int E = rowE[it & 1][row];
+        bool failed = false;
+        for (uint64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x, it++) {
             const uint64_t g = tile * kRows + row;
             const bool valid = g < n_groups;
             double2 *p = psi + (valid ? base5(g, t) : 0);
+            for (int h = 0; h < 2; h++) {
+                if (!mbar_wait_bounded(smem_u32(&mbar_mma[h]), it & 1) || abort_flag) {
+                    atomicExch(status, 1);
+                    abort_flag = 1;
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t Xr = rowX[it & 1][row];
 #pragma unroll 1
-            for (int c = 0; c < kEpiCols / 4; c++) {
-                const int col0 = kEpiCols * half + 4 * c;
-                float D[kDiags][4];
+                for (int c = 0; c < 2; c++) {
+                    const int col = 8 * q8 + 4 * c;            // column within the half
+                    float D[kDiags][4];
 #pragma unroll
-                for (int d = 0; d < kDiags; d++) tmem_ld4(lane_addr + 64 * d + col0, D[d]);
-                tmem_wait_ld();
-                double out[4];
+                    for (int d = 0; d < kDiags; d++) tmem_ld4(lane_addr + 256 * h + kHalfN * d + col, D[d]);
+                    tmem_wait_ld();
+                    double out[4];
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const long long U = (long long)exact_int(D[0][q]) * 16777216LL +
-                                        (long long)exact_int(D[1][q]) * 65536LL +
-                                        (long long)exact_int(D[2][q]) * 256LL + (long long)exact_int(D[3][q]);
-                    const float L = fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]);
-                    const long long T = U * 65536LL + (long long)__float2int_rn(L * 256.0f);
-                    out[q] = scale_int(T, E + Gcol[col0 + q] - 2096);
+                    for (int q = 0; q < 4; q++) {
+                        // T = P 2^32 + Q 2^16 + r with P = D_0 2^8 + D_1 and
+                        // Q = D_2 2^8 + D_3 exact in 32 bits (|D_d| <= 2^22)
+                        const int P = exact_int(D[0][q]) * 256 + exact_int(D[1][q]);
+                        const int Q = exact_int(D[2][q]) * 256 + exact_int(D[3][q]);
+                        const float L = fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]);
+                        const long long T = ((long long)P << 32) + ((long long)Q << 16) +
+                                            (long long)__float2int_rn(L * 256.0f);
+                        const double dv = __ll2double_rn(T);
+                        const uint32_t hi = (uint32_t)__double2hiint(dv);
+                        // T = 0 gives +0.0 (hi = 0); otherwise add the scale to the exponent
+                        out[q] = __hiloint2double((int)(hi == 0 ? 0u : hi + Xr + colX[kHalfN * h + col + q]),
+                                                  __double2loint(dv));
+                    }
+                    if (valid) {
+                        const int m0 = (kHalfN * h + col) >> 1;
+                        p[moff[m0]] = make_double2(out[0], out[1]);
+                        p[moff[m0 + 1]] = make_double2(out[2], out[3]);
+                    }
                 }
-                if (valid) {
-                    p[off5(col0 / 2, t)] = make_double2(out[0], out[1]);
-                    p[off5(col0 / 2 + 1, t)] = make_double2(out[2], out[3]);
-                }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&mbar_free[h]));
             }
-            tc_fence_before();
-            mbar_arrive(free_a);
         }
     }
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, kTmemCols128);
 }
 
-constexpr int kTpr128 = 4;   // threads per row of the complex128 kernel (512 per CTA; 8 measured slower)
-constexpr bool kC128WarpSpecialised = true;
 bool g_attr_set[2][64] = {{false}};
 
 }  // namespace
@@ -918,10 +775,8 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
     if (!g_attr_set[c64][dev]) {
         cudaError_t e = c64 ? cudaFuncSetAttribute(k_dense5_tc_c64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)kSmemF32)
-                            : cudaFuncSetAttribute(k_dense5_tc_c128<kTpr128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)kSmemC128);
-        if (e == cudaSuccess && !c64)
-            e = cudaFuncSetAttribute(k_dense5_tc_c128_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemC128);
+                            : cudaFuncSetAttribute(k_dense5_tc_c128_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kSmemC128Pipe);
         if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
         g_attr_set[c64][dev] = true;
     }
@@ -938,12 +793,8 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
             (float2 *)s->amp, groups, t, (const float *)dev_pack, status);
     } else {
         int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms);
-        if (kC128WarpSpecialised)
-            k_dense5_tc_c128_ws<<<grid, kSplitThreads + kEpiThreads, kSmemC128, (cudaStream_t)s->stream>>>(
-                (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
-        else
-            k_dense5_tc_c128<kTpr128><<<grid, kTpr128 * kRows, kSmemC128, (cudaStream_t)s->stream>>>(
-                (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
+        k_dense5_tc_c128_pipe<<<grid, kSplitThreads + kEpiThreads, kSmemC128Pipe, (cudaStream_t)s->stream>>>(
+            (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "tc launch: %s", cudaGetErrorString(e));
