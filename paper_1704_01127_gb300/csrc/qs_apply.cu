@@ -292,14 +292,16 @@ int check_qubits(qs_state *s, const int *qubits, int k, int kmax, const char *wh
 bool tc_wanted(int dtype, int k, int n) { return qs_tc_wanted(dtype, k, n); }
 
 // U (x) 1: a k-qubit cluster (sorted qubits q, sorted matrix M) as a 5-qubit
-// one on q plus the lowest qubits not in q; output sorted as well.
+// one on q plus the highest qubits not in q; output sorted as well.
 void embed5(const int *q, int k, const std::vector<double> &M, int n, std::array<int, 5> &q5,
             std::vector<double> &M5)
 {
     uint64_t used = 0;
     for (int j = 0; j < k; j++) used |= 1ULL << q[j];
+    // pad with the highest free qubits: low qubits as targets would make the
+    // tile gather touch one amplitude per group instead of runs of groups
     uint64_t all = used;
-    for (int b = 0; b < n && __builtin_popcountll(all) < 5; b++) all |= 1ULL << b;
+    for (int b = n - 1; b >= 0 && __builtin_popcountll(all) < 5; b--) all |= 1ULL << b;
     int pos[5], j5 = 0;
     for (int b = 0; b < n; b++)
         if ((all >> b) & 1) q5[j5++] = b;

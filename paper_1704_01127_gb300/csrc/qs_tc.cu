@@ -87,7 +87,7 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate)
 {
     asm volatile(
@@ -321,13 +321,13 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const f
 
 
 // ----------------------------------------------------------------------------
-// complex128: exact integer slices on the bf16 tensor path.
+// complex128: exact integer slices on the fp16 tensor path.
 //
 // Each row r (group) is scaled by its largest exponent E_r and each column n of
 // B^T by its largest exponent G_n; a value m 2^{e-1075} becomes the fixed-point
 // integer F = round(m 2^{e-E-7}) (half to even), |F| <= 2^46, so
 // F = sum_{s<6} d_s 2^{8(5-s)}
-// with balanced digits d_s in [-128, 127] (exact in bf16).  With A_i, B_j the
+// with balanced digits d_s in [-128, 127] (exact in fp16).  With A_i, B_j the
 // digit planes and T = sum_{d<=6} D_d 2^{8(5-d)},
 //   sum_k a_rk b_kn ~ 2^{E_r + G_n - 2096} T[r][n],  D_d = sum_{i+j=d} (A_i B_j^T),
 // and the planes with i + j = d <= 6 are summed in accumulator D_d (TMEM; the
@@ -371,19 +371,16 @@ __device__ __forceinline__ uint64_t fixed48(double a, int E)
     return F + 0x808080808080ULL;
 }
 
-// Digit byte b of a 32-bit word, as the fp32 value (byte - 128): one byte
-// permute builds 0x4B0000uu (= 2^23 + byte), one add subtracts 2^23 + 128; the
-// result is exact and has at most 8 significant bits, so its upper 16 bits are
-// the bf16 encoding.
-template <int b>
-__device__ __forceinline__ float digit_f32(uint32_t word)
+// Digit planes in fp16: a byte b becomes the fp16 value 1024 + b when the
+// byte 0x64 is put above it, and one f16x2 add of -1152 gives two balanced
+// digits b - 128 (exact).  Bytes (k, k') of two words w0, w1 (the real and
+// imaginary parts of one amplitude) are first gathered into one word.
+__device__ __forceinline__ uint32_t f16x2_digits(uint32_t pairs, uint32_t sel)
 {
-    return __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540u | b)) - 8388736.0f;
-}
-// bf16 pair (lo, hi) from two exact fp32 digits
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
-{
-    return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+    uint32_t r;
+    const uint32_t w = __byte_perm(pairs, 0x64646464u, sel);
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(w), "r"(0xE480E480u));
+    return r;
 }
 
 // exact int from an fp32 integer of magnitude <= 2^22
@@ -440,9 +437,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 constexpr int kHalfN = 32;
 constexpr uint32_t kBlockB = (uint32_t)kHalfN * kK * 2;   // 4 KB: one plane of one half
 
-__host__ __device__ constexpr uint32_t idesc_bf16_n(int n)
+// instruction descriptor: D fp32, A and B fp16 (format 0), both K-major,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t idesc_f16_n(int n)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 }
 
 __device__ __forceinline__ void issue_c128_half(uint32_t tmem, uint32_t a0, uint32_t b0, int h)
@@ -453,8 +452,8 @@ __device__ __forceinline__ void issue_c128_half(uint32_t tmem, uint32_t a0, uint
 #pragma unroll
         for (int ks = 0; ks < kK / 16; ks++) {
             const uint32_t koff = ks * 2 * kLBO;
-            mma_bf16(tmem + 256 * h + kHalfN * i, da + ((uint64_t)(i * kPlaneA + koff) >> 4),
-                     db + ((uint64_t)koff >> 4), idesc_bf16_n(kHalfN * (kDiags - i)), (i == 0 && ks == 0) ? 0u : 1u);
+            mma_f16(tmem + 256 * h + kHalfN * i, da + ((uint64_t)(i * kPlaneA + koff) >> 4),
+                     db + ((uint64_t)koff >> 4), idesc_f16_n(kHalfN * (kDiags - i)), (i == 0 && ks == 0) ? 0u : 1u);
         }
     }
 }
@@ -581,21 +580,23 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, 
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 uint8_t *dst = A + cm_off16(row, 16 * part + 8 * c);
-                const uint32_t *wl = glo + 8 * c, *wh = ghi + 8 * c;
-                uint4 w;
-#define QS_DIGIT_PLANE(SL, WORDS, BYTE)                                                        \
-    w.x = pack_bf16(digit_f32<BYTE>(WORDS[0]), digit_f32<BYTE>(WORDS[1]));                   \
-    w.y = pack_bf16(digit_f32<BYTE>(WORDS[2]), digit_f32<BYTE>(WORDS[3]));                   \
-    w.z = pack_bf16(digit_f32<BYTE>(WORDS[4]), digit_f32<BYTE>(WORDS[5]));                   \
-    w.w = pack_bf16(digit_f32<BYTE>(WORDS[6]), digit_f32<BYTE>(WORDS[7]));                   \
-    *reinterpret_cast<uint4 *>(dst + (SL) * kPlaneA) = w;
-                QS_DIGIT_PLANE(0, wh, 1)
-                QS_DIGIT_PLANE(1, wh, 0)
-                QS_DIGIT_PLANE(2, wl, 3)
-                QS_DIGIT_PLANE(3, wl, 2)
-                QS_DIGIT_PLANE(4, wl, 1)
-                QS_DIGIT_PLANE(5, wl, 0)
-#undef QS_DIGIT_PLANE
+                uint32_t pl[6][4];                     // [plane][member of the chunk]
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int x = 4 * c + j;           // words 2x (re), 2x+1 (im)
+                    const uint32_t yh = __byte_perm(ghi[2 * x], ghi[2 * x + 1], 0x5410u);
+                    const uint32_t y23 = __byte_perm(glo[2 * x], glo[2 * x + 1], 0x7632u);
+                    const uint32_t y01 = __byte_perm(glo[2 * x], glo[2 * x + 1], 0x5410u);
+                    pl[0][j] = f16x2_digits(yh, 0x4341u);    // byte 5 of F
+                    pl[1][j] = f16x2_digits(yh, 0x4240u);    // byte 4
+                    pl[2][j] = f16x2_digits(y23, 0x4341u);   // byte 3
+                    pl[3][j] = f16x2_digits(y23, 0x4240u);   // byte 2
+                    pl[4][j] = f16x2_digits(y01, 0x4341u);   // byte 1
+                    pl[5][j] = f16x2_digits(y01, 0x4240u);   // byte 0
+                }
+#pragma unroll
+                for (int sl = 0; sl < kSlices; sl++)
+                    *reinterpret_cast<uint4 *>(dst + sl * kPlaneA) = make_uint4(pl[sl][0], pl[sl][1], pl[sl][2], pl[sl][3]);
             }
             fence_proxy_async();
             bar_split();
@@ -715,7 +716,19 @@ std::vector<uint8_t> qs_pack_tc_c64(const std::vector<double> &M)
 // F' = round(m 2^{e-G_n+1}), |F'| <= 2^54, = sum_{j<7} e_j 2^{8(6-j)} with
 // balanced digits, i.e. the same scale as the state's digits (weight
 // 2^{8(5-j)} of 2^{G_n-1068}) plus one extra plane, so the unitary is carried
-// to about 2^-55; bf16 planes in the canonical layout, then the 64 exponents.
+// to about 2^-55; fp16 planes in the canonical layout, then the 64 exponents.
+// fp16 encoding of an integer |d| <= 2048 (exact): the fp32 encoding with the
+// exponent rebased from 127 to 15 and the mantissa cut to 10 bits
+static uint16_t f16_of_small_int(int d)
+{
+    if (d == 0) return 0;
+    float f = (float)d;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t sign = (u >> 16) & 0x8000u, ex = ((u >> 23) & 0xFFu) - 127u + 15u;
+    return (uint16_t)(sign | (ex << 10) | ((u >> 13) & 0x3FFu));
+}
+
 std::vector<uint8_t> qs_pack_tc_c128(const std::vector<double> &M)
 {
     std::vector<uint8_t> out(kSlicesB * kPlaneB + 256, 0);
@@ -752,10 +765,7 @@ std::vector<uint8_t> qs_pack_tc_c128(const std::vector<double> &M)
             uint64_t Gb = F + 0x80808080808080ULL;
             for (int sl = 0; sl < kSlicesB; sl++) {
                 int dig = (int)((Gb >> (8 * (6 - sl))) & 0xFF) - 128;
-                float f = (float)dig;
-                uint32_t u;
-                std::memcpy(&u, &f, 4);
-                uint16_t h = (uint16_t)(u >> 16);
+                uint16_t h = f16_of_small_int(dig);
                 std::memcpy(out.data() + sl * kPlaneB + cm_off16(n, k), &h, 2);
             }
         }
