@@ -197,7 +197,12 @@ typedef struct {
     int32_t k_max;        /* 2..QS_MAX_K when fuse != 0 */
     int32_t fuse;         /* 0: one op per gate (plain form); 1: greedy clusters */
     int32_t merge_phase;  /* 1: merge neighbouring all-diagonal ops into one phase op */
-    int32_t reserved;
+    int32_t drop_final_diagonal;  /* 1: leave out the trailing all-diagonal ops.  They
+                                   * change phases only, not |amplitude|^2, so the
+                                   * output distribution, its statistics and samples
+                                   * are those of the full circuit (Sec. 3.6 skips the
+                                   * last CZ layer this way); amplitudes differ by
+                                   * those phases.  0: keep every gate. */
 } qs_sched_opts;
 
 /* Build a schedule for an n-qubit gate list.  With fuse, gates are packed into
@@ -205,6 +210,7 @@ typedef struct {
  * qubit set S, S grown from a seed gate while |S| <= k_max, the largest cluster
  * taken first), an all-diagonal cluster becomes a phase op, and every dense
  * cluster's unitary is the FP64 product of its gates in ascending qubit order.
+ * With drop_final_diagonal the trailing phase ops are left out (see the field).
  * Errors: QS_EINVAL (bad gate, opts). */
 int qs_schedule_build(int n, const qs_gate *gates, int n_gates, const qs_sched_opts *opts,
                       qs_schedule **out);

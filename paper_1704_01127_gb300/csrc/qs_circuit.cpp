@@ -398,6 +398,10 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
         }
         sc->ops.push_back(std::move(op));
     }
+    // trailing diagonal ops multiply every amplitude by a unit-modulus phase:
+    // the output distribution does not see them (Sec. 3.6)
+    if (opts->drop_final_diagonal)
+        while (!sc->ops.empty() && sc->ops.back().kind == QS_OP_PHASE) sc->ops.pop_back();
     *out = sc;
     return QS_OK;
 }

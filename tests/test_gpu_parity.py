@@ -123,6 +123,27 @@ def run_lib(n, gates_arr, dtype, path=qs.QS_PATH_AUTO, **sched_kw):
         qs.qs_schedule_free(sc)
 
 
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_drop_final_diagonal_keeps_the_distribution(dtype):
+    """Leaving out the trailing diagonal ops (Sec. 3.6) changes phases only:
+    moduli, probabilities and statistics are the full circuit's (oracle)."""
+    n, g = qs.qs_supremacy_circuit(4, 5, 25, 3)
+    ref = sim.run_circuit(n, qs.gates_to_tuples(g))
+    sc = qs.qs_schedule_build(n, g, k_max=5)
+    try:
+        last = qs.qs_schedule_op(sc, qs.qs_schedule_num_ops(sc) - 1)["kind"]
+    finally:
+        qs.qs_schedule_free(sc)
+    assert last == "phase"
+    psi, st, p = run_lib(n, g, dtype, k_max=5, drop_final_diagonal=True)
+    assert np.max(np.abs(np.abs(psi) - np.abs(ref))) <= TOL[dtype]
+    assert np.max(np.abs(psi - ref)) > 1e-3           # the phases did change
+    np.testing.assert_allclose(p, sim.probabilities(ref), rtol=0, atol=1e-13 if dtype == qs.QS_C128 else 1e-7)
+    want = sim.stats(ref)
+    for a, b in zip(st, want):
+        assert abs(a - b) <= (1e-10 if dtype == qs.QS_C128 else 1e-4) * max(1.0, abs(b))
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_config_4x4_depth10_plain_c128(seed):
     """16 qubits, depth 10, complex128, gate by gate: full state and probabilities."""

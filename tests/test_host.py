@@ -75,6 +75,22 @@ def test_schedule_bit_exact_with_oracle(grid, depth, seed, k_max):
             assert a["edges"] == [tuple(e) for e in b["edges"]]
 
 
+@pytest.mark.parametrize("grid,depth,seed", [((5, 6), 25, 1), ((4, 8), 25, 1), ((4, 4), 10, 0), ((3, 11), 40, 2)])
+def test_drop_final_diagonal_leaves_out_only_the_trailing_phase_ops(grid, depth, seed):
+    """Sec. 3.6: the last layer of diagonal gates does not change |psi|^2, so
+    the option removes exactly the trailing phase ops and nothing else."""
+    n, g = qs.qs_supremacy_circuit(grid[0], grid[1], depth, seed)
+    full = _lib_ops(n, g, k_max=5)
+    cut = _lib_ops(n, g, k_max=5, drop_final_diagonal=True)
+    keep = len(full)
+    while keep and full[keep - 1]["kind"] == "phase":
+        keep -= 1
+    assert len(cut) == keep and cut[-1]["kind"] == "dense"
+    assert [op["gates"] for op in cut] == [op["gates"] for op in full[:keep]]
+    dropped = [gi for op in full[keep:] for gi in op["gates"]]
+    assert all(qs.GATE_NAME[int(g[gi]["kind"])] in ("cz", "t", "tdg") for gi in dropped)
+
+
 def test_plain_schedule_one_op_per_gate():
     n, g = qs.qs_supremacy_circuit(4, 4, 10, 0)
     ops = _lib_ops(n, g, fuse=False)
