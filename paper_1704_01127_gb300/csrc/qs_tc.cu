@@ -391,16 +391,18 @@ __device__ __forceinline__ int exact_int(float x)
 
 constexpr int kSplitThreads = 512;
 constexpr int kEpiThreads = 512;
+constexpr int kSplitParts = kSplitThreads / kRows;   // splitter threads per row
+constexpr int kMPT = 32 / kSplitParts;               // amplitudes per splitter thread
 
-__device__ __forceinline__ void bar_split() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+__device__ __forceinline__ void bar_split() { asm volatile("bar.sync 1, %0;" ::"r"(kSplitThreads) : "memory"); }
 __device__ __forceinline__ bool bar_split_or(bool v)
 {
     uint32_t r;
     asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, 1, 512, q;\n\t"
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, 1, %2, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(r)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "r"(kSplitThreads)
         : "memory");
     return r != 0;
 }
@@ -416,14 +418,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 }
 
 // ----------------------------------------------------------------------------
-// complex128 kernel: one CTA of 1024 threads per SM, two warp-specialised groups.
-//   splitters (warps 0..15, 4 threads per row, 8 amplitudes each): copy tile
-//     t+1 into a 64 KB stage with cp.async while tile t is processed; find the
-//     row exponents and the fixed-point values of tile t while the MMAs of
-//     tile t-1 still read the digit planes, then write the planes; thread 0
-//     issues the MMAs;
-//   epilogue (warps 16..31, 4 threads per row, 8 columns of each half): rebuild
-//     FP64 results from the accumulators and store them.
+// complex128 kernel: one CTA per SM, two warp-specialised groups (as built:
+// 512 + 512 threads; 512 + 256 measured within 1%, slower with low targets).
+//   splitters (kSplitThreads / 128 threads per row, kMPT amplitudes each):
+//     copy tile t+1 into a 64 KB stage with cp.async while tile t is
+//     processed; find the row exponents and the fixed-point values of tile t
+//     while the MMAs of tile t-1 still read the digit planes, then write the
+//     planes; thread 0 issues the MMAs;
+//   epilogue (kEpiThreads / 128 threads per row, kEpiCols columns of each
+//     half): rebuild FP64 results from the accumulators and store them.
 // The output columns come in two halves of 32, so that the tensor cores work
 // on one half while the epilogue reads the other.
 //   TMEM: half h holds D_0..D_6 for its 32 columns at columns 256 h + 32 d.
@@ -435,6 +438,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 // when half h's accumulators are read).  All waits are bounded.
 // ----------------------------------------------------------------------------
 constexpr int kHalfN = 32;
+constexpr int kEpiCols = kHalfN * kRows / kEpiThreads;    // columns of each half per epilogue thread
 constexpr uint32_t kBlockB = (uint32_t)kHalfN * kK * 2;   // 4 KB: one plane of one half
 
 // instruction descriptor: D fp32, A and B fp16 (format 0), both K-major,
@@ -466,7 +470,7 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *gptr, uin
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-constexpr size_t kStageC128 = (size_t)kSplitThreads * 8 * 16;   // raw next tile: 64 KB
+constexpr size_t kStageC128 = (size_t)kSplitThreads * kMPT * 16;   // raw next tile: 64 KB
 constexpr size_t kSmemC128Pipe = kSmemC128 + kStageC128;
 
 __global__ void __launch_bounds__(kSplitThreads + kEpiThreads, 1)
@@ -480,7 +484,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, 
     __shared__ __align__(8) uint64_t mbar_mma[2], mbar_free[2];
     __shared__ uint64_t moff[32];         // offset of member x within a group
     __shared__ uint32_t tmem_base_s;
-    __shared__ int rowexp[4][kRows];
+    __shared__ int rowexp[kSplitParts][kRows];
     // exponent-field terms, added modulo 2^32 (only the sum must fit):
     __shared__ uint32_t rowX[2][kRows];   // (E_r - 2096) << 20 of the last two tiles
     __shared__ uint32_t colX[kN];         // G_n << 20
@@ -525,30 +529,30 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, 
         const int row = tid & (kRows - 1), part = tid >> 7;
         const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
         const uint32_t stage_a = smem_u32(stage) + 16u * tid;
-        // this thread's 8 amplitudes of tile tl into its own stage slots
-        // (slot x at x * 512 + tid): asynchronous, a whole iteration ahead
+        // this thread's kMPT amplitudes of tile tl into its own stage slots
+        // (slot x at x * kSplitThreads + tid): asynchronous, a whole iteration ahead
         auto prefetch = [&](uint64_t tl) {
             const uint64_t g = tl * kRows + row;
             const bool val = tl < n_tiles && g < n_groups;
             const double2 *pp = psi + (val ? base5(g, t) : 0);
 #pragma unroll
-            for (int x = 0; x < 8; x++)
-                cp_async16(stage_a + 16u * kSplitThreads * x, val ? pp + moff[8 * part + x] : psi, val ? 16u : 0u);
+            for (int x = 0; x < kMPT; x++)
+                cp_async16(stage_a + 16u * kSplitThreads * x, val ? pp + moff[kMPT * part + x] : psi, val ? 16u : 0u);
             cp_async_commit();
         };
         prefetch(blockIdx.x);
         int it = 0;
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, it++) {
             cp_async_wait_all();
-            double2 v[8];
+            double2 v[kMPT];
 #pragma unroll
-            for (int x = 0; x < 8; x++) {
+            for (int x = 0; x < kMPT; x++) {
                 const uint4 w = stage[kSplitThreads * x + tid];
                 v[x] = make_double2(__hiloint2double((int)w.y, (int)w.x), __hiloint2double((int)w.w, (int)w.z));
             }
             uint32_t emax = 0;
 #pragma unroll
-            for (int x = 0; x < 8; x++) {
+            for (int x = 0; x < kMPT; x++) {
                 emax = max(emax, (uint32_t)__double2hiint(v[x].x) & 0x7FF00000u);
                 emax = max(emax, (uint32_t)__double2hiint(v[x].y) & 0x7FF00000u);
             }
@@ -558,13 +562,15 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, 
             prefetch(tile + gridDim.x);
             rowexp[part][row] = (int)(emax >> 20);
             bar_split();
-            const int E = max(max(rowexp[0][row], rowexp[1][row]), max(rowexp[2][row], rowexp[3][row]));
+            int E = rowexp[0][row];
+#pragma unroll
+            for (int q = 1; q < kSplitParts; q++) E = max(E, rowexp[q][row]);
             // the epilogue of tile it-2 has released both halves (thread 0 waited
             // for it before issuing tile it-1), so slot it & 1 is free
             if (part == 0) rowX[it & 1][row] = (uint32_t)(E - 2096) << 20;
-            uint32_t glo[16], ghi[16];
+            uint32_t glo[2 * kMPT], ghi[2 * kMPT];
 #pragma unroll
-            for (int x = 0; x < 8; x++) {
+            for (int x = 0; x < kMPT; x++) {
                 const uint64_t g0 = fixed48(v[x].x, E), g1 = fixed48(v[x].y, E);
                 glo[2 * x] = (uint32_t)g0;
                 ghi[2 * x] = (uint32_t)(g0 >> 32);
@@ -578,8 +584,8 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, 
                 break;
             }
 #pragma unroll
-            for (int c = 0; c < 2; c++) {
-                uint8_t *dst = A + cm_off16(row, 16 * part + 8 * c);
+            for (int c = 0; c < kMPT / 4; c++) {
+                uint8_t *dst = A + cm_off16(row, 2 * kMPT * part + 8 * c);
                 uint32_t pl[6][4];                     // [plane][member of the chunk]
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
@@ -620,7 +626,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, 
     } else {
         // ------------------------------------------------------------- epilogue
         const int ew = warp - kSplitThreads / 32;                 // 0 .. 15
-        const int row = 32 * (warp & 3) + (tid & 31), q8 = ew >> 2;   // columns 8 q8 .. +7 of each half
+        const int row = 32 * (warp & 3) + (tid & 31), cq = ew >> 2;   // columns kEpiCols cq .. of each half
         const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         int it = 0;
         bool failed = false;
@@ -638,8 +644,8 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, 
                 tc_fence_after();
                 const uint32_t Xr = rowX[it & 1][row];
 #pragma unroll 1
-                for (int c = 0; c < 2; c++) {
-                    const int col = 8 * q8 + 4 * c;            // column within the half
+                for (int c = 0; c < kEpiCols / 4; c++) {
+                    const int col = kEpiCols * cq + 4 * c;     // column within the half
                     float D[kDiags][4];
 #pragma unroll
                     for (int d = 0; d < kDiags; d++) tmem_ld4(lane_addr + 256 * h + kHalfN * d + col, D[d]);
