@@ -82,35 +82,72 @@ __global__ void k_probs(const C *__restrict__ psi, uint64_t first, uint64_t coun
         p[i] = prob(psi[first + i]);
 }
 
-using qsd::LogTable;
-using qsd::log_table_init;
-using qsd::log_tab;
+using qsd::ff;
+using qsd::ff_add;
+using qsd::ff_from_double;
+using qsd::ff_mul;
+using qsd::ff_p_ln_p;
+using qsd::ff_sqr_f;
+using qsd::FFLogTable;
+using qsd::ff_log_table_init;
 
 // Per-block FP64 partial sums of (p, -p ln p, p, p^2); NSTAT = 1 or 4.  The
 // mean of N p equals the sum of p, and the mean of (N p)^2 is N sum p^2, so
 // the moments cost one FMA per amplitude; the host applies the factor N.
+// complex128: p, sum p and sum p^2 in FP64; the entropy term in float-float
+// (table-driven log, ff_p_ln_p), which keeps the FP64 pipe -- 1/64 of the FP32
+// rate on this GPU -- to four operations per amplitude.  complex64: p is
+// exact in float-float (x^2 and y^2 with their FMA rounding errors) and every
+// sum is float-float.  p outside [2^-79, 2^100] (where the low half of p's
+// float-float form would leave the normal float range; about never met by
+// normalised states of these sizes) takes FP64 p ln p from the math library;
+// p below the
+// normal double range contributes less than 1e-305 and is left out.
 template <typename C, int NSTAT>
 __global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *__restrict__ part)
 {
-    __shared__ LogTable lt;
+    constexpr bool c128 = sizeof(C) == 16;
+    __shared__ FFLogTable lt;
     if (NSTAT == 4) {
-        log_table_init(lt);
+        ff_log_table_init(lt);
         __syncthreads();
     }
-    double acc[NSTAT];
-#pragma unroll
-    for (int j = 0; j < NSTAT; j++) acc[j] = 0;
+    double d0 = 0, d3 = 0, dent = 0;
+    ff f0{0.f, 0.f}, f3{0.f, 0.f}, fent{0.f, 0.f};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        double p = prob(psi[i]);
-        acc[0] += p;
-        if (NSTAT == 4) {
-            // p below the normal range contributes less than 1e-305
-            if (p >= 2.2250738585072014e-308) acc[1] -= p * log_tab(lt, p);
-            acc[3] = fma(p, p, acc[3]);
+        const C a = psi[i];
+        if constexpr (c128) {
+            const double p = fma((double)a.x, (double)a.x, (double)a.y * (double)a.y);
+            d0 += p;
+            if (NSTAT == 4) {
+                d3 = fma(p, p, d3);
+                if (p >= 0x1p-79 && p <= 0x1p100)
+                    fent = ff_add(fent, ff_p_ln_p(lt, ff_from_double(p)));
+                else if (p >= 2.2250738585072014e-308)
+                    dent += p * log(p);
+            }
+        } else {
+            const ff p = ff_add(ff_sqr_f((float)a.x), ff_sqr_f((float)a.y));
+            f0 = ff_add(f0, p);
+            if (NSTAT == 4) {
+                f3 = ff_add(f3, ff_mul(p, p));
+                if (p.hi >= 0x1p-79f && p.hi <= 0x1p100f) {
+                    fent = ff_add(fent, ff_p_ln_p(lt, p));
+                } else if (p.hi > 0.f) {
+                    const double pd = (double)p.hi + (double)p.lo;
+                    if (pd >= 2.2250738585072014e-308) dent += pd * log(pd);
+                }
+            }
         }
     }
-    if (NSTAT == 4) acc[2] = acc[0];
+    double acc[NSTAT];
+    acc[0] = d0 + ((double)f0.hi + (double)f0.lo);
+    if (NSTAT == 4) {
+        acc[NSTAT > 1 ? 1 : 0] = -(dent + ((double)fent.hi + (double)fent.lo));
+        acc[NSTAT > 2 ? 2 : 0] = acc[0];
+        acc[NSTAT > 3 ? 3 : 0] = d3 + ((double)f3.hi + (double)f3.lo);
+    }
     __shared__ double red[NSTAT][32];
 #pragma unroll
     for (int j = 0; j < NSTAT; j++) {

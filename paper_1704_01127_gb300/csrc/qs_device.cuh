@@ -189,4 +189,98 @@ __device__ __forceinline__ double log_tab(const LogTable &t, double p)
     return fma((double)e, 0.69314718055994530942, fma(q, r, t.ln[j]));
 }
 
+// ---------------------------------------------------------------------------
+// Float-float ("double-float") arithmetic: a value is hi + lo with |lo| at most
+// half an ulp of hi, about 48 significant bits.  Error-free transforms after
+// Knuth (two-sum), Dekker (fast two-sum) and the FMA product error; GB300's
+// FP32 pipe is ~64x its FP64 pipe, so 10-20 FP32 operations per emulated
+// operation still run far faster than FP64.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return ff{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b)   // |a| >= |b| or a = 0
+{
+    const float s = __fadd_rn(a, b);
+    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = ff_two_sum(a.hi, b.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return ff_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_add_f(ff a, float b)
+{
+    ff s = ff_two_sum(a.hi, b);
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return ff_fast_two_sum(p, e);
+}
+// x^2 exactly as hi + lo (the FMA gives the rounding error of the product)
+__device__ __forceinline__ ff ff_sqr_f(float x)
+{
+    const float p = __fmul_rn(x, x);
+    return ff{p, fmaf(x, x, -p)};
+}
+// The top 48 bits of a double d with |d| in [2^-126, 2^128), by bit
+// manipulation only: hi = its top 24 significant bits, lo = the next 24
+// (0 when they fall below the normal float range).  Relative error < 2^-47.
+__device__ __forceinline__ ff ff_from_double(double d)
+{
+    const uint32_t hw = (uint32_t)__double2hiint(d), lw = (uint32_t)__double2loint(d);
+    const int E = (int)((hw >> 20) & 0x7FFu) - 1023;
+    const uint32_t sign = hw & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((uint32_t)(E + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+    const float scale = __uint_as_float((uint32_t)max(E - 47 + 127, 0) << 23);   // 2^(E-47) or 0
+    const float lo = __uint2float_rn((lw >> 5) & 0xFFFFFFu) * scale;
+    return ff{hi, sign ? -lo : lo};
+}
+
+// p ln p for p in [2^-79, 2^100] in float-float, table-driven after Tang
+// (ACM TOMS 16(4), 1990): p = 2^e m, c_j the centre of the mantissa interval
+// picked by the top ten bits, r = m / c_j - 1 (|r| < 2^-10), and
+//   ln p = e ln 2 + ln c_j + r + c,  c = -r^2/2 + r^3/3 - r^4/4 (in FP32),
+// with e ln 2, ln c_j and 1/c_j as float-float table entries.  Absolute error
+// of ln p about 2^-46, so each term carries a relative error near 2^-47.
+constexpr int kFFLogBits = 10;
+struct FFLogTable {
+    ff inv[1 << kFFLogBits], ln[1 << kFFLogBits];
+    ff eln2[255];   // e ln 2 for e = -127 .. 127
+};
+__device__ __forceinline__ void ff_log_table_init(FFLogTable &t)
+{
+    for (int j = threadIdx.x; j < (1 << kFFLogBits); j += blockDim.x) {
+        const double c = 1.0 + (j + 0.5) / (double)(1 << kFFLogBits);
+        t.inv[j] = ff_from_double(1.0 / c);
+        t.ln[j] = ff_from_double(log(c));
+    }
+    for (int e = threadIdx.x; e < 255; e += blockDim.x)
+        t.eln2[e] = e == 127 ? ff{0.0f, 0.0f} : ff_from_double((double)(e - 127) * 0.69314718055994530942);
+}
+__device__ __forceinline__ ff ff_p_ln_p(const FFLogTable &t, ff p)
+{
+    const uint32_t b = __float_as_uint(p.hi);
+    const int e = (int)((b >> 23) & 0xFFu) - 127;
+    const int j = (int)((b >> (23 - kFFLogBits)) & ((1u << kFFLogBits) - 1));
+    // m = p 2^-e: the exponent of hi replaced, lo scaled by the same power of two
+    const ff m = ff{__uint_as_float((b & 0x807FFFFFu) | (127u << 23)), p.lo * __uint_as_float((uint32_t)(127 - e) << 23)};
+    ff r = ff_mul(m, t.inv[j]);
+    r = ff_two_sum(__fsub_rn(r.hi, 1.0f), r.lo);            // hi - 1 is exact (hi within 2^-10 of 1)
+    const float x = r.hi;
+    const float c = x * x * fmaf(x, fmaf(x, -0.25f, 0.33333334f), -0.5f);
+    const ff lnp = ff_add(ff_add(t.eln2[e + 127], t.ln[j]), ff_add_f(r, c));
+    return ff_mul(p, lnp);
+}
+
 }  // namespace qsd
