@@ -76,10 +76,17 @@ int qs_set_path(qs_state *s, int path);
 
 int qs_num_qubits(const qs_state *s);
 int qs_dtype(const qs_state *s);
-void *qs_device_ptr(const qs_state *s);        /* device pointer to amplitude 0 */
+/* Device pointer to amplitude 0, holding the whole state: zeros the library
+ * has not written yet (see qs_init_basis) are written first, on the state's
+ * stream.  NULL for a null state or when that write fails. */
+void *qs_device_ptr(const qs_state *s);
 int qs_set_stream(qs_state *s, void *stream);
 
-/* |x>: amplitude x = 1, all others 0 (Sec. 2).  QS_EINVAL if x >= 2^n. */
+/* |x>: amplitude x = 1, all others 0 (Sec. 2).  QS_EINVAL if x >= 2^n.
+ * Only amplitude x is written now.  Tensor-core cluster sweeps then work on the
+ * indices the circuit so far can reach (targets of the clusters applied since,
+ * other bits as in x) and give the same result as on the zero-filled state;
+ * every other call writes the remaining zeros first. */
 int qs_init_basis(qs_state *s, uint64_t x);
 
 /* (2^{-n/2}, ..., 2^{-n/2}): the state after the H layer of cycle 0, which a

@@ -39,18 +39,6 @@ size_t amp_bytes(int dtype) { return dtype == QS_C128 ? 16 : 8; }
 
 // ------------------------------------------------------------------ kernels
 
-template <typename C>
-__global__ void k_fill_zero(C *psi, uint64_t N)
-{
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        C z;
-        z.x = 0;
-        z.y = 0;
-        psi[i] = z;
-    }
-}
-
 template <typename C, typename R>
 __global__ void k_fill_uniform(C *psi, uint64_t N, R a)
 {
@@ -58,6 +46,20 @@ __global__ void k_fill_uniform(C *psi, uint64_t N, R a)
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         C z;
         z.x = a;
+        z.y = 0;
+        psi[i] = z;
+    }
+}
+
+// zeros at every index outside the support {i : (i & ~free) == fix}
+template <typename C>
+__global__ void k_fill_outside(C *psi, uint64_t N, uint64_t free, uint64_t fix)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        if ((i & ~free) == fix) continue;
+        C z;
+        z.x = 0;
         z.y = 0;
         psi[i] = z;
     }
@@ -482,7 +484,13 @@ extern "C" int qs_set_path(qs_state *s, int path)
 
 extern "C" int qs_num_qubits(const qs_state *s) { return s ? s->n : 0; }
 extern "C" int qs_dtype(const qs_state *s) { return s ? s->dtype : -1; }
-extern "C" void *qs_device_ptr(const qs_state *s) { return s ? s->amp : nullptr; }
+// the caller reads the buffer directly: the zeros outside the support first
+extern "C" void *qs_device_ptr(const qs_state *s)
+{
+    if (!s) return nullptr;
+    if (qs_materialize(const_cast<qs_state *>(s))) return nullptr;
+    return s->amp;
+}
 extern "C" int qs_set_stream(qs_state *s, void *stream)
 {
     if (!s) return qs_fail(QS_EINVAL, "qs_set_stream: null state");
@@ -490,21 +498,38 @@ extern "C" int qs_set_stream(qs_state *s, void *stream)
     return QS_OK;
 }
 
+// |x>: one amplitude written, the support set to {x}; the zeros elsewhere are
+// written by the first call that needs them (qs_materialize), and sweeps on
+// the tensor cores never need them (Sec. 3.6 starts from a known state too).
 extern "C" int qs_init_basis(qs_state *s, uint64_t x)
 {
     if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_basis: null state");
     if (x >> s->n) return qs_fail(QS_EINVAL, "qs_init_basis: index out of range");
-    uint64_t N = 1ULL << s->n;
+    cudaStream_t st = (cudaStream_t)s->stream;
+    if (s->dtype == QS_C128)
+        k_set_one<double2><<<1, 1, 0, st>>>((double2 *)s->amp, x);
+    else
+        k_set_one<float2><<<1, 1, 0, st>>>((float2 *)s->amp, x);
+    QS_CUDA(cudaGetLastError(), "qs_init_basis");
+    s->sup_free = 0;
+    s->sup_fix = x;
+    return QS_OK;
+}
+
+int qs_materialize(qs_state *s)
+{
+    if (qs_support_full(s)) return QS_OK;
+    const uint64_t N = 1ULL << s->n, all = qs_index_mask(s->n);
+    const uint64_t fr = s->sup_free & all, fx = s->sup_fix & ~fr & all;
     int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count_dev() * 8);
     cudaStream_t st = (cudaStream_t)s->stream;
-    if (s->dtype == QS_C128) {
-        k_fill_zero<double2><<<grid, 256, 0, st>>>((double2 *)s->amp, N);
-        k_set_one<double2><<<1, 1, 0, st>>>((double2 *)s->amp, x);
-    } else {
-        k_fill_zero<float2><<<grid, 256, 0, st>>>((float2 *)s->amp, N);
-        k_set_one<float2><<<1, 1, 0, st>>>((float2 *)s->amp, x);
-    }
-    QS_CUDA(cudaGetLastError(), "qs_init_basis");
+    if (s->dtype == QS_C128)
+        k_fill_outside<double2><<<grid, 256, 0, st>>>((double2 *)s->amp, N, fr, fx);
+    else
+        k_fill_outside<float2><<<grid, 256, 0, st>>>((float2 *)s->amp, N, fr, fx);
+    QS_CUDA(cudaGetLastError(), "fill outside the support");
+    s->sup_free = ~0ULL;
+    s->sup_fix = 0;
     return QS_OK;
 }
 
@@ -521,6 +546,8 @@ extern "C" int qs_init_uniform(qs_state *s)
     else
         k_fill_uniform<float2, float><<<grid, 256, 0, st>>>((float2 *)s->amp, N, (float)a);
     QS_CUDA(cudaGetLastError(), "qs_init_uniform");
+    s->sup_free = ~0ULL;
+    s->sup_fix = 0;
     return QS_OK;
 }
 
@@ -537,6 +564,8 @@ extern "C" int qs_set_amplitudes(qs_state *s, const double *host)
         QS_CUDA(cudaMemcpyAsync(s->amp, f.data(), 8 * N, cudaMemcpyHostToDevice, st), "qs_set_amplitudes");
     }
     QS_CUDA(cudaStreamSynchronize(st), "qs_set_amplitudes sync");
+    s->sup_free = ~0ULL;
+    s->sup_fix = 0;
     return QS_OK;
 }
 
@@ -544,6 +573,7 @@ extern "C" int qs_get_amplitudes(qs_state *s, double *host)
 {
     if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_get_amplitudes: null argument");
     if (int rc = qs_check_status(s)) return rc;
+    if (int rc = qs_materialize(s)) return rc;
     uint64_t N = 1ULL << s->n;
     cudaStream_t st = (cudaStream_t)s->stream;
     if (s->dtype == QS_C128) {
@@ -563,6 +593,7 @@ extern "C" int qs_get_amplitudes_at(qs_state *s, const uint64_t *idx, int64_t co
     if (!s || !s->amp || count < 0 || (count > 0 && (!idx || !out)))
         return qs_fail(QS_EINVAL, "qs_get_amplitudes_at: bad arguments");
     if (int rc = qs_check_status(s)) return rc;
+    if (int rc = qs_materialize(s)) return rc;
     const uint64_t N = 1ULL << s->n;
     cudaStream_t st = (cudaStream_t)s->stream;
     for (int64_t j = 0; j < count; j++) {
@@ -586,6 +617,7 @@ extern "C" int qs_norm(qs_state *s, double *out)
 {
     if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_norm: null argument");
     if (int rc = qs_check_status(s)) return rc;
+    if (int rc = qs_materialize(s)) return rc;
     return s->dtype == QS_C128 ? stats_impl<double2>(s, out, 1) : stats_impl<float2>(s, out, 1);
 }
 
@@ -593,12 +625,14 @@ extern "C" int qs_stats(qs_state *s, double out[4])
 {
     if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_stats: null argument");
     if (int rc = qs_check_status(s)) return rc;
+    if (int rc = qs_materialize(s)) return rc;
     return s->dtype == QS_C128 ? stats_impl<double2>(s, out, 4) : stats_impl<float2>(s, out, 4);
 }
 
 extern "C" int qs_probabilities(qs_state *s, double *out, int out_on_device)
 {
     if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_probabilities: null argument");
+    if (int rc = qs_materialize(s)) return rc;
     const uint64_t N = 1ULL << s->n;
     cudaStream_t st = (cudaStream_t)s->stream;
     const int sms = sm_count_dev();
@@ -632,6 +666,7 @@ extern "C" int qs_probabilities(qs_state *s, double *out, int out_on_device)
 extern "C" int qs_sample(qs_state *s, uint64_t seed, int64_t m, uint64_t *out)
 {
     if (!s || !s->amp || m < 0 || (m > 0 && !out)) return qs_fail(QS_EINVAL, "qs_sample: bad arguments");
+    if (int rc = qs_materialize(s)) return rc;
     return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out) : sample_impl<float2>(s, seed, m, out);
 }
 

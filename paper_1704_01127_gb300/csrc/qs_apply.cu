@@ -166,13 +166,17 @@ bool qs_tc_wanted(int dtype, int k, int n)
 int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix,
                     const void *dev_tc)
 {
-    if (k == 5 && dev_tc) return qs_launch_dense5_tc(s, sorted_qubits, dev_tc);
+    if (k == 5 && dev_tc) return qs_launch_dense5_tc(s, sorted_qubits, dev_tc, ~0ULL);
+    int rc = qs_materialize(s);   // the CUDA-core sweeps read every amplitude
+    if (rc) return rc;
     return s->dtype == QS_C128 ? launch_dense_r<double>(s, sorted_qubits, k, dev_matrix)
                                : launch_dense_r<float>(s, sorted_qubits, k, dev_matrix);
 }
 
 int qs_launch_diag(qs_state *s, const int *dev_qubits, int k, const void *dev_table)
 {
+    int rc = qs_materialize(s);
+    if (rc) return rc;
     uint64_t N = 1ULL << s->n;
     const int block = 256;
     int grid = grid_for(N, block, 8);
@@ -187,6 +191,8 @@ int qs_launch_diag(qs_state *s, const int *dev_qubits, int k, const void *dev_ta
 
 int qs_launch_phase(qs_state *s, const void *dev_phase, int n_act)
 {
+    int rc = qs_materialize(s);
+    if (rc) return rc;
     const int L = s->n < kPhaseLowBits ? s->n : kPhaseLowBits;
     const uint64_t chunks = 1ULL << (s->n - L);
     const int block = 256;
@@ -409,8 +415,11 @@ int launch_op_dense(qs_state *s, const qs_dev_sched &d, size_t i, const qs_op_ho
     int path = s->path != QS_PATH_AUTO ? s->path
                : op.path != QS_PATH_AUTO ? op.path
                : (tc_wanted(s->dtype, op.k, s->n) ? QS_PATH_TENSOR : QS_PATH_CUDA_CORES);
-    if (path == QS_PATH_TENSOR && d.tc_off[i])
-        return qs_launch_dense5_tc(s, d.tc_q[i].data(), data + d.tc_off[i]);
+    if (path == QS_PATH_TENSOR && d.tc_off[i]) {
+        uint64_t grow = 0;
+        for (int j = 0; j < op.k; j++) grow |= 1ULL << op.qubits[j];
+        return qs_launch_dense5_tc(s, d.tc_q[i].data(), data + d.tc_off[i], grow);
+    }
     return qs_launch_dense(s, op.qubits, op.k, data, nullptr);
 }
 
@@ -439,7 +448,9 @@ extern "C" int qs_apply_cluster(qs_state *s, const int *qubits, int k, const dou
         std::vector<uint8_t> p = tc_pack_for(s->dtype, M5);
         void *dp;
         if ((rc = stage(s, p.data(), p.size(), &dp))) return rc;
-        return qs_launch_dense5_tc(s, q5.data(), dp);
+        uint64_t grow = 0;
+        for (int j = 0; j < k; j++) grow |= 1ULL << q[j];
+        return qs_launch_dense5_tc(s, q5.data(), dp, grow);
     }
     std::vector<uint8_t> packed = to_real(M, s->dtype);
     void *dU;

@@ -250,9 +250,10 @@ __device__ __forceinline__ ff ff_from_double(double d)
 // p ln p for p in [2^-79, 2^100] in float-float, table-driven after Tang
 // (ACM TOMS 16(4), 1990): p = 2^e m, c_j the centre of the mantissa interval
 // picked by the top ten bits, r = m / c_j - 1 (|r| < 2^-10), and
-//   ln p = e ln 2 + ln c_j + r + c,  c = -r^2/2 + r^3/3 - r^4/4 (in FP32),
-// with e ln 2, ln c_j and 1/c_j as float-float table entries.  Absolute error
-// of ln p about 2^-46, so each term carries a relative error near 2^-47.
+//   ln p = e ln 2 + ln c_j + r - r^2/2 + r^3/3 - r^4/4,
+// with e ln 2, ln c_j and 1/c_j as float-float table entries.  The error of
+// ln p is about 2^-48 of |e ln 2| + |ln c_j| plus 2^-55 (float-float
+// rounding), so each term p ln p carries a relative error near 2^-47.
 constexpr int kFFLogBits = 10;
 struct FFLogTable {
     ff inv[1 << kFFLogBits], ln[1 << kFFLogBits];
@@ -277,9 +278,13 @@ __device__ __forceinline__ ff ff_p_ln_p(const FFLogTable &t, ff p)
     const ff m = ff{__uint_as_float((b & 0x807FFFFFu) | (127u << 23)), p.lo * __uint_as_float((uint32_t)(127 - e) << 23)};
     ff r = ff_mul(m, t.inv[j]);
     r = ff_two_sum(__fsub_rn(r.hi, 1.0f), r.lo);            // hi - 1 is exact (hi within 2^-10 of 1)
+    // ln(1 + r) = r - r^2/2 + r^3/3 - r^4/4: -x^2/2 (x = r.hi) exactly as
+    // float-float, the rest (below 2^-32) in FP32, -x r.lo for the cross term
     const float x = r.hi;
-    const float c = x * x * fmaf(x, fmaf(x, -0.25f, 0.33333334f), -0.5f);
-    const ff lnp = ff_add(ff_add(t.eln2[e + 127], t.ln[j]), ff_add_f(r, c));
+    const ff sq = ff_sqr_f(x);
+    const ff half = ff{-0.5f * sq.hi, -0.5f * sq.lo};
+    const float tail = fmaf(x * x * x, fmaf(x, -0.25f, 0.33333334f), -x * r.lo);
+    const ff lnp = ff_add(ff_add(t.eln2[e + 127], t.ln[j]), ff_add(ff_add_f(r, tail), half));
     return ff_mul(p, lnp);
 }
 

@@ -26,7 +26,24 @@ struct qs_state {
     size_t pinned_bytes = 0;
     int *status = nullptr;        // device word set by kernels whose bounded waits ran out
     int path = 0;                 // QS_PATH_*
+    // Support: amplitudes may be nonzero only at indices i with
+    // (i & ~sup_free) == sup_fix.  After qs_init_basis the support is one index
+    // and memory outside the support is left unwritten; the tensor-core sweeps
+    // work on the support only (their result is the same as on the
+    // zero-filled state), and every other call first writes the zeros
+    // (qs_materialize).  Full support: sup_free = ~0.
+    uint64_t sup_free = ~0ULL;
+    uint64_t sup_fix = 0;
 };
+
+inline uint64_t qs_index_mask(int n) { return n >= 64 ? ~0ULL : ((1ULL << n) - 1); }
+inline bool qs_support_full(const qs_state *s)
+{
+    const uint64_t a = qs_index_mask(s->n);
+    return (s->sup_free & a) == a;
+}
+// Write zeros outside the support and make it full (no-op when full).
+int qs_materialize(qs_state *s);
 
 // One op of a schedule, host side.
 struct qs_op_host {
@@ -95,4 +112,7 @@ int qs_check_status(qs_state *s);
 std::vector<uint8_t> qs_pack_tc_c64(const std::vector<double> &sorted_matrix);
 std::vector<uint8_t> qs_pack_tc_c128(const std::vector<double> &sorted_matrix);
 size_t qs_tc_pack_bytes(int dtype);
-int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack);
+// 5-qubit tensor-core sweep over the state's support; grow = the qubits that
+// join the support (the cluster's own targets; an embedded cluster's padding
+// qubits stay fixed).
+int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack, uint64_t grow);

@@ -170,21 +170,40 @@ __device__ __forceinline__ float tf32_round(float x)
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-struct Targets5 {
+// Where the members of a group sit for one 5-qubit sweep over the state's
+// support (the indices that may hold nonzero amplitudes): group g's x = 0
+// member is g with zeros inserted at the positions of zmask (the five targets
+// and the support's fixed bits) and the fixed bits' values OR-ed in; member x
+// adds the target bits of x.  Bit x of mmask is set when member x lies in the
+// support before the sweep; the others are zero and are not read.  With the
+// full support (full = 1): zeros at the targets only, fix = 0, every member
+// read.  No arrays: an indexed parameter array would be copied to local memory.
+struct TileLayout {
     int q[5];
+    int full;
+    uint32_t mmask;
+    uint64_t fix;
+    uint64_t zmask;
 };
 
-__device__ __forceinline__ uint64_t base5(uint64_t g, const Targets5 &t)
+__device__ __forceinline__ uint64_t tile_base(uint64_t g, const TileLayout &t)
 {
+    if (t.full) {
 #pragma unroll
-    for (int j = 0; j < 5; j++) {
-        uint64_t lo = g & ((1ULL << t.q[j]) - 1);
+        for (int j = 0; j < 5; j++) {
+            const uint64_t lo = g & ((1ULL << t.q[j]) - 1);
+            g = ((g ^ lo) << 1) | lo;
+        }
+        return g;
+    }
+    for (uint64_t z = t.zmask; z; z &= z - 1) {
+        const uint64_t lo = g & ((z & (0 - z)) - 1);      // bits below the lowest zero position
         g = ((g ^ lo) << 1) | lo;
     }
-    return g;
+    return g | t.fix;
 }
 
-__device__ __forceinline__ uint64_t off5(int x, const Targets5 &t)
+__device__ __forceinline__ uint64_t off5(int x, const TileLayout &t)
 {
     uint64_t o = 0;
 #pragma unroll
@@ -200,7 +219,7 @@ constexpr size_t kSmemF32 = 2 * kTileBytesF32 + 2 * kBBytesF32;
 // One CTA of 128 threads; thread r owns row r (group) of each tile.  Tiles are
 // taken in a grid-stride loop; warp 0 holds 128 TMEM columns for the CTA.
 __global__ void __launch_bounds__(128, 2)
-k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const float *__restrict__ bpack,
+k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const float *__restrict__ bpack,
                 int *__restrict__ status)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -244,9 +263,9 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const f
     auto load_tile = [&](uint64_t tl, float2 *vv, bool &val, float2 *&pp) {
         const uint64_t g = tl * kRows + tid;
         val = tl < n_tiles && g < n_groups;
-        pp = psi + (val ? base5(g, t) : 0);
+        pp = psi + (val ? tile_base(g, t) : 0);
 #pragma unroll
-        for (int x = 0; x < 32; x++) vv[x] = val ? pp[off5(x, t)] : make_float2(0.f, 0.f);
+        for (int x = 0; x < 32; x++) vv[x] = val && ((t.mmask >> x) & 1) ? pp[off5(x, t)] : make_float2(0.f, 0.f);
     };
     load_tile(tile, v, valid, p);
     for (; tile < n_tiles; tile += gridDim.x) {
@@ -474,7 +493,7 @@ constexpr size_t kStageC128 = (size_t)kSplitThreads * kMPT * 16;   // raw next t
 constexpr size_t kSmemC128Pipe = kSmemC128 + kStageC128;
 
 __global__ void __launch_bounds__(kSplitThreads + kEpiThreads, 1)
-k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, const uint8_t *__restrict__ bpack,
+k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const uint8_t *__restrict__ bpack,
                       int *__restrict__ status)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -534,10 +553,12 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, 
         auto prefetch = [&](uint64_t tl) {
             const uint64_t g = tl * kRows + row;
             const bool val = tl < n_tiles && g < n_groups;
-            const double2 *pp = psi + (val ? base5(g, t) : 0);
+            const double2 *pp = psi + (val ? tile_base(g, t) : 0);
 #pragma unroll
-            for (int x = 0; x < kMPT; x++)
-                cp_async16(stage_a + 16u * kSplitThreads * x, val ? pp + moff[kMPT * part + x] : psi, val ? 16u : 0u);
+            for (int x = 0; x < kMPT; x++) {
+                const bool vx = val && ((t.mmask >> (kMPT * part + x)) & 1);   // members outside the support are zero
+                cp_async16(stage_a + 16u * kSplitThreads * x, vx ? pp + moff[kMPT * part + x] : psi, vx ? 16u : 0u);
+            }
             cp_async_commit();
         };
         prefetch(blockIdx.x);
@@ -633,7 +654,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, Targets5 t, 
         for (uint64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x, it++) {
             const uint64_t g = tile * kRows + row;
             const bool valid = g < n_groups;
-            double2 *p = psi + (valid ? base5(g, t) : 0);
+            double2 *p = psi + (valid ? tile_base(g, t) : 0);
             for (int h = 0; h < 2; h++) {
                 if (!mbar_wait_bounded(smem_u32(&mbar_mma[h]), it & 1) || abort_flag) {
                     atomicExch(status, 1);
@@ -781,7 +802,7 @@ std::vector<uint8_t> qs_pack_tc_c128(const std::vector<double> &M)
 
 size_t qs_tc_pack_bytes(int dtype) { return dtype == QS_C64 ? 2 * kBBytesF32 : kSlicesB * kPlaneB + 256; }
 
-int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack)
+int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack, uint64_t grow)
 {
     const bool c64 = s->dtype == QS_C64;
     int dev = 0, sms = 0;
@@ -796,9 +817,28 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
         if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
         g_attr_set[c64][dev] = true;
     }
-    Targets5 t;
-    for (int j = 0; j < 5; j++) t.q[j] = sorted_qubits[j];
-    const uint64_t groups = 1ULL << (s->n - 5);
+    // the sweep covers the support after it: the support's free bits plus the
+    // targets; groups enumerate the free bits that are not targets
+    const uint64_t all = qs_index_mask(s->n);
+    const uint64_t fr = s->sup_free & all, fx = s->sup_fix & ~fr & all;
+    TileLayout t;
+    uint64_t tm = 0;
+    for (int j = 0; j < 5; j++) {
+        t.q[j] = sorted_qubits[j];
+        tm |= 1ULL << t.q[j];
+    }
+    t.mmask = 0;
+    for (int x = 0; x < 32; x++) {
+        bool in = true;
+        for (int j = 0; j < 5; j++)
+            if (!((fr >> t.q[j]) & 1) && (uint64_t)((x >> j) & 1) != ((fx >> t.q[j]) & 1)) in = false;
+        if (in) t.mmask |= 1u << x;
+    }
+    const uint64_t G = fr & ~tm;
+    t.zmask = all & ~G;
+    t.fix = fx & ~tm;
+    t.full = fr == all;
+    const uint64_t groups = 1ULL << __builtin_popcountll(G);
     const uint64_t tiles = (groups + kRows - 1) / kRows;
     int *status;
     int rc = qs_state_status(s, &status);
@@ -812,6 +852,11 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
         k_dense5_tc_c128_pipe<<<grid, kSplitThreads + kEpiThreads, kSmemC128Pipe, (cudaStream_t)s->stream>>>(
             (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
     }
+    // amplitudes on the padding targets of an embedded cluster keep their
+    // fixed values (U (x) 1 leaves zero inputs zero), so only the cluster's own
+    // qubits join the support
+    s->sup_free = (fr | (grow & tm)) == all ? ~0ULL : (fr | (grow & tm));
+    s->sup_fix = fx & ~(grow & tm);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "tc launch: %s", cudaGetErrorString(e));
 }

@@ -123,6 +123,89 @@ def run_lib(n, gates_arr, dtype, path=qs.QS_PATH_AUTO, **sched_kw):
         qs.qs_schedule_free(sc)
 
 
+def _run_from(n, g, dtype, x, lazy):
+    """Run the fused schedule from |x>: lazily (qs_init_basis) or from the
+    fully written basis vector (qs_set_amplitudes)."""
+    sc = qs.qs_schedule_build(n, g, k_max=5)
+    try:
+        with State(n, dtype) as s:
+            if lazy:
+                qs.qs_init_basis(s.h, x)
+            else:
+                e = np.zeros(1 << n, dtype=np.complex128)
+                e[x] = 1
+                qs.qs_set_amplitudes(s.h, e)
+            qs.qs_run_circuit(s.h, sc)
+            return qs.qs_get_amplitudes(s.h)
+    finally:
+        qs.qs_schedule_free(sc)
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+@pytest.mark.parametrize("grid,x", [((4, 5), 0), ((4, 5), 0xB5A3), ((3, 7), 0x155555), ((4, 4), 7)])
+def test_basis_start_on_the_support_is_bit_exact(dtype, grid, x):
+    """Sweeps on the support after qs_init_basis give bit for bit the result of
+    the same sweeps on the zero-filled basis vector, and match the oracle."""
+    n, g = qs.qs_supremacy_circuit(grid[0], grid[1], 25, 2)
+    x &= (1 << n) - 1
+    lazy = _run_from(n, g, dtype, x, True)
+    full = _run_from(n, g, dtype, x, False)
+    assert np.array_equal(lazy, full)
+    if dtype == qs.QS_C128:
+        want = sim.run_circuit(n, qs.gates_to_tuples(g), psi=sim.basis_state(n, x))
+        assert np.max(np.abs(lazy - want)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_basis_start_mixed_paths_match_oracle(dtype):
+    """Tensor-core clusters on a growing support, then a CUDA-core cluster and a
+    phase op (both write the zeros first), then tensor-core clusters again."""
+    n = 14
+    ops = [((0, 1, 2, 3, 4), qs.QS_PATH_TENSOR), ((7, 9, 10, 11, 13), qs.QS_PATH_TENSOR),
+           ((3, 12), qs.QS_PATH_TENSOR), ((2, 5, 6), qs.QS_PATH_CUDA_CORES),
+           ((0, 6, 8, 12, 13), qs.QS_PATH_TENSOR), ((1, 4, 5, 9), qs.QS_PATH_TENSOR)]
+    x = 0x2A5
+    ref = np.zeros(1 << n, dtype=np.complex128)
+    ref[x] = 1
+    with State(n, dtype) as s:
+        qs.qs_init_basis(s.h, x)
+        for j, (qq, path) in enumerate(ops):
+            U = random_unitary(len(qq), 90 + j)
+            qs.qs_set_path(s.h, path)
+            qs.qs_apply_cluster(s.h, qq, U)
+            sim.apply_kq(ref, qq, U)
+            if j == 3:
+                coeff, edges = random_phase_poly(n, 10, 77)
+                qs.qs_apply_phase(s.h, coeff, edges)
+                sim.apply_phase(ref, coeff, edges)
+        got = qs.qs_get_amplitudes(s.h)
+    assert np.max(np.abs(got - ref)) <= 4 * SWEEP_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_basis_start_every_reader_sees_the_zeros(dtype):
+    n, x = 16, 0x9C3
+    N = 1 << n
+    e = np.zeros(N, dtype=np.complex128)
+    e[x] = 1
+    with State(n, dtype) as s:
+        qs.qs_init_basis(s.h, x)
+        st = qs.qs_stats(s.h)
+        # entropy -1 ln 1: the float-float logarithm leaves an error of ~1e-18
+        assert st[0] == 1 and abs(st[1]) <= 1e-14 and st[3] == N
+    with State(n, dtype) as s:
+        qs.qs_init_basis(s.h, x)
+        assert np.array_equal(qs.qs_probabilities(s.h), np.abs(e) ** 2)
+    with State(n, dtype) as s:
+        qs.qs_init_basis(s.h, x)
+        assert np.all(qs.qs_sample(s.h, 5, 64) == x)
+    with State(n, dtype) as s:
+        qs.qs_init_basis(s.h, x)
+        got = qs.qs_get_amplitudes_at(s.h, np.array([x, 0, N - 1], dtype=np.uint64))
+        assert np.array_equal(got, np.array([1, 0, 0], dtype=np.complex128))
+        assert np.array_equal(qs.qs_get_amplitudes(s.h), e)
+
+
 @pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
 def test_drop_final_diagonal_keeps_the_distribution(dtype):
     """Leaving out the trailing diagonal ops (Sec. 3.6) changes phases only:
