@@ -105,13 +105,21 @@ using qsd::ff_log_table_init;
 // normalised states of these sizes) takes FP64 p ln p from the math library;
 // p below the
 // normal double range contributes less than 1e-305 and is left out.
+// The float-float log tables, built once per device (k_fflog_init) and copied
+// into shared memory by every block of the statistics kernel.
+__device__ __align__(16) FFLogTable g_fflog;
+
+__global__ void k_fflog_init() { ff_log_table_init(g_fflog); }
+
 template <typename C, int NSTAT>
 __global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *__restrict__ part)
 {
     constexpr bool c128 = sizeof(C) == 16;
-    __shared__ FFLogTable lt;
+    __shared__ __align__(16) FFLogTable lt;
     if (NSTAT == 4) {
-        ff_log_table_init(lt);
+        const uint2 *src = reinterpret_cast<const uint2 *>(&g_fflog);
+        uint2 *dst = reinterpret_cast<uint2 *>(&lt);
+        for (int i = threadIdx.x; i < (int)(sizeof(FFLogTable) / sizeof(uint2)); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
     }
     double d0 = 0, d3 = 0, dent = 0;
@@ -185,6 +193,24 @@ __global__ void k_stats_final(const double *__restrict__ part, int nblocks, doub
         for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (threadIdx.x == 0) out[j] = v;
     }
+}
+
+std::mutex g_fflog_mu;
+bool g_fflog_ready[64] = {false};
+
+// Build the log tables on the current device once (one block, then a wait).
+int ensure_fflog(cudaStream_t st)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return qs_fail(QS_EUNSUPPORTED, "statistics: no usable device");
+    std::lock_guard<std::mutex> lock(g_fflog_mu);
+    if (g_fflog_ready[dev]) return QS_OK;
+    k_fflog_init<<<1, 1024, 0, st>>>();
+    QS_CUDA(cudaGetLastError(), "log table launch");
+    QS_CUDA(cudaStreamSynchronize(st), "log table");
+    g_fflog_ready[dev] = true;
+    return QS_OK;
 }
 
 // ------------------------------------------------------------------ sampling
@@ -306,6 +332,7 @@ int stats_impl(qs_state *s, double *out, int nstat)
     if (rc) return rc;
     double *part = (double *)scr, *res = part + (size_t)grid * 4;
     cudaStream_t st = (cudaStream_t)s->stream;
+    if (nstat == 4 && (rc = ensure_fflog(st))) return rc;
     if (nstat == 1) {
         k_stats_partial<C, 1><<<grid, block, 0, st>>>((const C *)s->amp, N, part);
         k_stats_final<1><<<1, 32, 0, st>>>(part, grid, res);
@@ -725,6 +752,7 @@ int stats_static_impl(const void *amp, int n, void *stream, double *out)
     grid = std::min(grid, kStaticStatsBlocks);
     double *part = scr, *res = scr + 4 * kStaticStatsBlocks;
     cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure_fflog(st))) return rc;
     // every partial slot in [0, grid) and every result slot is written before it is read
     k_stats_partial<C, 4><<<grid, block, 0, st>>>((const C *)amp, N, part);
     k_stats_final<4><<<1, 32, 0, st>>>(part, grid, res);
