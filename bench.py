@@ -191,7 +191,7 @@ def run_ours(args):
     launches = [0]
 
     def on_tensor_cores(kind, k):
-        return kind == "dense" and n >= 5 and ((dtype == qs.QS_C64 and k == 5) or (dtype == qs.QS_C128 and k >= 2))
+        return kind == "dense" and n >= 5 and ((dtype == qs.QS_C64 and k >= 4) or (dtype == qs.QS_C128 and k >= 2))
 
     def one_step(seed, record):
         nq, gates = qs.qs_supremacy_circuit(rows, cols, cycles, seed, removed=removed)       # a1
@@ -254,7 +254,7 @@ def run_ours(args):
     flops = (1 << n) * (8 * (1 << k) - 2) if kind == "dense" else 0
     # kernel path of the default policy: tensor cores for complex64 5-qubit and
     # complex128 2..5-qubit clusters, CUDA cores otherwise
-    tensor = kind == "dense" and n >= 5 and ((dtype == qs.QS_C64 and k == 5) or (dtype == qs.QS_C128 and k >= 2))
+    tensor = kind == "dense" and n >= 5 and ((dtype == qs.QS_C64 and k >= 4) or (dtype == qs.QS_C128 and k >= 2))
     if kind == "dense" and dtype == qs.QS_C128 and not tensor:
         # native FP64: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock
         fp64_peak = 152 * 2 * 2 * sm_max_mhz * 1e6 / 1e12

@@ -66,9 +66,9 @@ int qs_set_device(int device);
 /* Which kernels apply dense clusters.  The tensor-core sweep handles 5-qubit
  * clusters (smaller ones embedded as U (x) 1 on extra qubits; n >= 5):
  * complex64 by a tf32 head/tail split with FP32 accumulation, complex128 by
- * exact 8-bit integer digit planes on the bf16 path rebuilt in integer
- * arithmetic.  QS_PATH_AUTO: tensor cores for complex64 5-qubit clusters and
- * for complex128 clusters of 2..5 qubits, CUDA cores otherwise;
+ * exact 8-bit integer digit planes on the fp16 path rebuilt in integer
+ * arithmetic.  QS_PATH_AUTO: tensor cores for complex64 clusters of 4 and 5
+ * qubits and for complex128 clusters of 2..5 qubits, CUDA cores otherwise;
  * QS_PATH_TENSOR: tensor cores for every dense cluster (n >= 5);
  * QS_PATH_CUDA_CORES: the FP32 / FP64 CUDA-core kernel for every cluster. */
 enum { QS_PATH_AUTO = 0, QS_PATH_CUDA_CORES = 1, QS_PATH_TENSOR = 2 };

@@ -154,13 +154,15 @@ int launch_dense_r(qs_state *s, const int *q, int k, const void *U)
 
 }  // namespace
 
-// complex64: 5-qubit clusters (the FP32 CUDA-core kernel keeps up with HBM
-// below that); complex128: every cluster of 2 or more qubits (native FP64 runs
-// at 1/58 of the FP32 rate).  Tensor-core sweeps need n >= 5.
+// complex64: clusters of 4 and 5 qubits (a 4-qubit cluster embedded in 5 on
+// the tensor cores measured 11.3 ms at 32 qubits against 16.1 ms for the FP32
+// CUDA-core sweep, which is FMA-bound there); complex128: every cluster of 2 or
+// more qubits (native FP64 runs at 1/58 of the FP32 rate).  Tensor-core sweeps
+// need n >= 5.
 bool qs_tc_wanted(int dtype, int k, int n)
 {
     if (n < 5) return false;
-    return dtype == QS_C64 ? k == 5 : k >= 2;
+    return dtype == QS_C64 ? k >= 4 : k >= 2;
 }
 
 int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix,
@@ -291,10 +293,9 @@ int check_qubits(qs_state *s, const int *qubits, int k, int kmax, const char *wh
     return QS_OK;
 }
 
-// Which dense clusters go to the tensor cores.  complex64: 5-qubit clusters
-// (the FP32 CUDA-core kernel keeps up with HBM below that).  complex128: every
-// cluster of 2 or more qubits, embedded in 5 qubits when smaller (native FP64
-// runs at 1/58 of the FP32 rate, so even a 2-qubit FP64 sweep is ALU-bound).
+// Which dense clusters go to the tensor cores (qs_tc_wanted): complex64 clusters
+// of 4 and 5 qubits, complex128 clusters of 2 or more; smaller ones are
+// embedded in 5 qubits.
 bool tc_wanted(int dtype, int k, int n) { return qs_tc_wanted(dtype, k, n); }
 
 // U (x) 1: a k-qubit cluster (sorted qubits q, sorted matrix M) as a 5-qubit

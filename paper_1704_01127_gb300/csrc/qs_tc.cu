@@ -184,6 +184,7 @@ struct TileLayout {
     uint32_t mmask;
     uint64_t fix;
     uint64_t zmask;
+    int pairs;   // complex64: qubit 0 is a target and the buffer 16-byte aligned
 };
 
 __device__ __forceinline__ uint64_t tile_base(uint64_t g, const TileLayout &t)
@@ -264,8 +265,19 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const
         const uint64_t g = tl * kRows + tid;
         val = tl < n_tiles && g < n_groups;
         pp = psi + (val ? tile_base(g, t) : 0);
+        if (t.pairs) {
+            // members 2i and 2i+1 differ in qubit 0: one 16-byte load each
+            // (a member outside the support is read but replaced by zero)
 #pragma unroll
-        for (int x = 0; x < 32; x++) vv[x] = val && ((t.mmask >> x) & 1) ? pp[off5(x, t)] : make_float2(0.f, 0.f);
+            for (int x = 0; x < 32; x += 2) {
+                const float4 w = val ? *reinterpret_cast<const float4 *>(pp + off5(x, t)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                vv[x] = ((t.mmask >> x) & 1) ? make_float2(w.x, w.y) : make_float2(0.f, 0.f);
+                vv[x + 1] = ((t.mmask >> (x + 1)) & 1) ? make_float2(w.z, w.w) : make_float2(0.f, 0.f);
+            }
+        } else {
+#pragma unroll
+            for (int x = 0; x < 32; x++) vv[x] = val && ((t.mmask >> x) & 1) ? pp[off5(x, t)] : make_float2(0.f, 0.f);
+        }
     };
     load_tile(tile, v, valid, p);
     for (; tile < n_tiles; tile += gridDim.x) {
@@ -324,7 +336,13 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const
             tmem_ld16(lane_addr + c * 16, r);
             tmem_ld16(lane_addr + kN + c * 16, q);
             tmem_wait_ld();
-            if (valid_cur) {
+            if (valid_cur && t.pairs) {
+#pragma unroll
+                for (int l = 0; l < 8; l += 2)
+                    *reinterpret_cast<float4 *>(p_cur + off5(8 * c + l, t)) =
+                        make_float4(r[2 * l] + q[2 * l], r[2 * l + 1] + q[2 * l + 1], r[2 * l + 2] + q[2 * l + 2],
+                                    r[2 * l + 3] + q[2 * l + 3]);
+            } else if (valid_cur) {
 #pragma unroll
                 for (int l = 0; l < 8; l++)
                     p_cur[off5(8 * c + l, t)] = make_float2(r[2 * l] + q[2 * l], r[2 * l + 1] + q[2 * l + 1]);
@@ -838,6 +856,7 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
     t.zmask = all & ~G;
     t.fix = fx & ~tm;
     t.full = fr == all;
+    t.pairs = c64 && t.q[0] == 0 && ((uintptr_t)s->amp & 15) == 0;
     const uint64_t groups = 1ULL << __builtin_popcountll(G);
     const uint64_t tiles = (groups + kRows - 1) / kRows;
     int *status;

@@ -319,6 +319,34 @@ def test_wrap_torch_tensor():
     assert np.max(np.abs(got - ref)) < 1e-15
 
 
+def test_tc_c64_qubit0_paired():
+    """complex64 tensor-core sweeps with qubit 0 as a target move amplitude
+    pairs with 16-byte accesses (qs_wrap only adopts 16-byte aligned buffers):
+    a 5-qubit and an embedded 4-qubit cluster on a wrapped buffer match the
+    oracle, and a buffer 8 bytes off the boundary is refused."""
+    torch = pytest.importorskip("torch")
+    n = 13
+    buf = torch.zeros((2 << n) + 2, dtype=torch.float32, device="cuda")
+    psi0 = f32_round(random_state(n, 71))
+    buf[: 2 << n] = torch.from_numpy(psi0.view(np.float64).astype(np.float32)).cuda()
+    stream = torch.cuda.current_stream()
+    with pytest.raises(qs.QSError) as e:
+        qs.qs_wrap(buf.data_ptr() + 8, n, qs.QS_C64, stream)
+    assert e.value.code == qs.QS_EINVAL
+    h = qs.qs_wrap(buf.data_ptr(), n, qs.QS_C64, stream)
+    ref = psi0.copy()
+    try:
+        qs.qs_set_path(h, qs.QS_PATH_TENSOR)
+        for j, qq in enumerate([(0, 1, 2, 7, 11), (0, 4, 9, 12), (3, 0, 6, 10, 8)]):
+            U = random_unitary(len(qq), 80 + j)
+            qs.qs_apply_cluster(h, list(qq), U)
+            sim.apply_kq(ref, list(qq), U)
+        got = qs.qs_get_amplitudes(h)
+    finally:
+        qs.qs_free(h)
+    assert np.max(np.abs(got - ref)) <= 3 * SWEEP_TOL[qs.QS_C64]
+
+
 # ------------------------------------------------ tensor-core 5-qubit sweep (c64)
 
 @pytest.mark.parametrize("n", [5, 8, 11, 12, 13, 16, 19])
