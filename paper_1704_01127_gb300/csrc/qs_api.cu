@@ -327,7 +327,7 @@ int stats_impl(qs_state *s, double *out, int nstat)
     uint64_t N = 1ULL << s->n;
     const int block = 256;
     int grid = (int)std::min<uint64_t>((N + block - 1) / block, (uint64_t)sm_count_dev() * 4);
-    void *scr;
+    void *scr = nullptr;
     int rc = qs_state_scratch(s, sizeof(double) * (size_t)(grid + 1) * 4, &scr);
     if (rc) return rc;
     double *part = (double *)scr, *res = part + (size_t)grid * 4;
@@ -354,7 +354,7 @@ int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out)
     const uint64_t B = std::min<uint64_t>(N, 1024), nb = N / B;
     const uint64_t G = std::min<uint64_t>(nb, 1024), ns = nb / G;
     size_t bytes = sizeof(double) * (2 * nb + 2 * ns) + sizeof(uint64_t) * (size_t)std::max<int64_t>(m, 1);
-    void *scr;
+    void *scr = nullptr;
     int rc = qs_state_scratch(s, bytes, &scr);
     if (rc) return rc;
     double *S = (double *)scr, *R = S + nb, *T = R + nb, *Q = T + ns;
@@ -677,7 +677,7 @@ extern "C" int qs_probabilities(qs_state *s, double *out, int out_on_device)
     }
     // host output: chunks of at most 2^25 values through the scratch buffer
     const uint64_t chunk = std::min<uint64_t>(N, 1ULL << 25);
-    void *scr;
+    void *scr = nullptr;
     int rc = qs_state_scratch(s, sizeof(double) * chunk, &scr);
     if (rc) return rc;
     for (uint64_t first = 0; first < N; first += chunk) {

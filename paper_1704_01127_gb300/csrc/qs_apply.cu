@@ -270,7 +270,7 @@ int check_state(qs_state *s, const char *who)
 // runs after earlier kernels on the stream have finished reading the slot).
 int stage(qs_state *s, const void *host, size_t bytes, void **dev)
 {
-    void *p;
+    void *p = nullptr;
     int rc = qs_state_scratch(s, bytes, &p);
     if (rc) return rc;
     cudaError_t e = cudaMemcpyAsync(p, host, bytes, cudaMemcpyHostToDevice, (cudaStream_t)s->stream);
@@ -447,14 +447,14 @@ extern "C" int qs_apply_cluster(qs_state *s, const int *qubits, int k, const dou
             embed5(q, k, M, s->n, q5, M5);
         }
         std::vector<uint8_t> p = tc_pack_for(s->dtype, M5);
-        void *dp;
+        void *dp = nullptr;
         if ((rc = stage(s, p.data(), p.size(), &dp))) return rc;
         uint64_t grow = 0;
         for (int j = 0; j < k; j++) grow |= 1ULL << q[j];
         return qs_launch_dense5_tc(s, q5.data(), dp, grow);
     }
     std::vector<uint8_t> packed = to_real(M, s->dtype);
-    void *dU;
+    void *dU = nullptr;
     if ((rc = stage(s, packed.data(), packed.size(), &dU))) return rc;
     return qs_launch_dense(s, q, k, dU, nullptr);
 }
@@ -472,7 +472,7 @@ extern "C" int qs_apply_diag(qs_state *s, const int *qubits, int k, const double
     std::vector<uint8_t> blob(64 + tab.size());
     std::memcpy(blob.data(), q, sizeof(int) * k);
     std::memcpy(blob.data() + 64, tab.data(), tab.size());
-    void *dev;
+    void *dev = nullptr;
     if ((rc = stage(s, blob.data(), blob.size(), &dev))) return rc;
     return qs_launch_diag(s, (const int *)dev, k, (const uint8_t *)dev + 64);
 }
@@ -493,7 +493,7 @@ extern "C" int qs_apply_phase(qs_state *s, const int *coeff, int n_edges, const 
     }
     int n_act;
     std::vector<uint8_t> blob = qs_pack_phase(s->n, c, e, &n_act);
-    void *dev;
+    void *dev = nullptr;
     if ((rc = stage(s, blob.data(), blob.size(), &dev))) return rc;
     return qs_launch_phase(s, dev, n_act);
 }

@@ -216,8 +216,7 @@ int launch_batch(qs_batch *b, int C, int block)
                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<float>, block, 0);
     if (e != cudaSuccess || occ < 1) occ = 1;
     int clusters = std::max(1, std::min(b->n_circ, sms * occ / C));
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(clusters * C);
     cfg.blockDim = dim3(block);
     cfg.stream = (cudaStream_t)b->stream;

@@ -419,7 +419,8 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
     for (int i = 0; i < n_ops; i++) {
         int k = ks[i];
         bool dense = kinds[i] == QS_OP_DENSE;
-        if ((!dense && kinds[i] != QS_OP_DIAG) || k < 1 || k > (dense ? QS_MAX_K : QS_MAX_K) || k > n) {
+        // both kinds take at most QS_MAX_K qubits here (QS_MAX_K slots per op)
+        if ((!dense && kinds[i] != QS_OP_DIAG) || k < 1 || k > QS_MAX_K || k > n) {
             delete sc;
             return qs_fail(QS_EINVAL, "qs_schedule_from_ops: bad op %d", i);
         }
@@ -435,7 +436,8 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
             }
             seen |= 1ULL << q[j];
         }
-        std::sort(perm, perm + k, [&](int a, int b) { return q[a] < q[b]; });
+        for (int a = 1; a < k; a++)   // insertion sort of at most five positions
+            for (int b = a; b > 0 && q[perm[b]] < q[perm[b - 1]]; b--) std::swap(perm[b], perm[b - 1]);
         const int d = 1 << k;
         int64_t need = dense ? 2LL * d * d : 2LL * d;
         if (offsets[i] < 0 || offsets[i] + need > pool_len) {
