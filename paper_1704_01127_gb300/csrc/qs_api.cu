@@ -93,24 +93,26 @@ using qsd::ff_sqr_f;
 using qsd::FFLogTable;
 using qsd::ff_log_table_init;
 
-// Per-block FP64 partial sums of (p, -p ln p, p, p^2); NSTAT = 1 or 4.  The
-// mean of N p equals the sum of p, and the mean of (N p)^2 is N sum p^2, so
-// the moments cost one FMA per amplitude; the host applies the factor N.
-// complex128: p, sum p and sum p^2 in FP64; the entropy term in float-float
-// (table-driven log, ff_p_ln_p), which keeps the FP64 pipe -- 1/64 of the FP32
-// rate on this GPU -- to four operations per amplitude.  complex64: p is
-// exact in float-float (x^2 and y^2 with their FMA rounding errors) and every
-// sum is float-float.  p outside [2^-79, 2^100] (where the low half of p's
-// float-float form would leave the normal float range; about never met by
-// normalised states of these sizes) takes FP64 p ln p from the math library;
-// p below the
-// normal double range contributes less than 1e-305 and is left out.
 // The float-float log tables, built once per device (k_fflog_init) and copied
 // into shared memory by every block of the statistics kernel.
 __device__ __align__(16) FFLogTable g_fflog;
 
 __global__ void k_fflog_init() { ff_log_table_init(g_fflog); }
 
+// Per-block FP64 partial sums of (p, -p ln p, p, p^2); NSTAT = 1 or 4.  The
+// mean of N p equals the sum of p, and the mean of (N p)^2 is N sum p^2, so
+// the moments cost one product per amplitude; the host applies the factor N.
+// Everything runs in float-float on the FP32 pipe (GB300's FP64 pipe runs at
+// 1/64 of its rate): complex128 amplitudes are split into float-float by bit
+// manipulation (48 of their 53 bits), complex64 ones give p exactly (x^2 and
+// y^2 with their FMA rounding errors).  p, p^2 and p ln p (table-driven log,
+// ff_p_ln_p) are summed per thread in float-float; the rounding errors of
+// those sums are random, about 2^-48 of the partial sum per step, so the
+// total norm of a 30-qubit state carries an error near 1e-15.  p below 2^-79
+// (where the low half of p's float-float form would leave the normal float
+// range) takes p ln p from the FP64 math library, and complex128 amplitudes of
+// 2^30 or more (unnormalised input) are summed in FP64 throughout; p below the
+// normal double range contributes less than 1e-305 and is left out.
 template <typename C, int NSTAT>
 __global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *__restrict__ part)
 {
@@ -128,14 +130,31 @@ __global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *_
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         const C a = psi[i];
         if constexpr (c128) {
-            const double p = fma((double)a.x, (double)a.x, (double)a.y * (double)a.y);
-            d0 += p;
-            if (NSTAT == 4) {
-                d3 = fma(p, p, d3);
-                if (p >= 0x1p-79 && p <= 0x1p100)
-                    fent = ff_add(fent, ff_p_ln_p(lt, ff_from_double(p)));
-                else if (p >= 2.2250738585072014e-308)
+            const double ax = fabs((double)a.x), ay = fabs((double)a.y);
+            if (ax < 0x1p30 && ay < 0x1p30) {
+                // x and y as float-float (values below 2^-60 add less than 2^-120
+                // to p and count as zero), p and its sums in float-float
+                const ff x = ax >= 0x1p-60 ? ff_from_double((double)a.x) : ff{0.f, 0.f};
+                const ff y = ay >= 0x1p-60 ? ff_from_double((double)a.y) : ff{0.f, 0.f};
+                const ff p = ff_add(ff_mul(x, x), ff_mul(y, y));
+                f0 = ff_add(f0, p);
+                if (NSTAT == 4) {
+                    f3 = ff_add(f3, ff_mul(p, p));
+                    if (p.hi >= 0x1p-79f) {
+                        fent = ff_add(fent, ff_p_ln_p(lt, p));
+                    } else if (p.hi > 0.f) {
+                        const double pd = (double)p.hi + (double)p.lo;
+                        if (pd >= 2.2250738585072014e-308) dent += pd * log(pd);
+                    }
+                }
+            } else {
+                // an amplitude of 2^30 or more (unnormalised input): FP64 throughout
+                const double p = fma((double)a.x, (double)a.x, (double)a.y * (double)a.y);
+                d0 += p;
+                if (NSTAT == 4) {
+                    d3 = fma(p, p, d3);
                     dent += p * log(p);
+                }
             }
         } else {
             const ff p = ff_add(ff_sqr_f((float)a.x), ff_sqr_f((float)a.y));
