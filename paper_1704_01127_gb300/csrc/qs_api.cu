@@ -130,12 +130,16 @@ __global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *_
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         const C a = psi[i];
         if constexpr (c128) {
-            const double ax = fabs((double)a.x), ay = fabs((double)a.y);
-            if (ax < 0x1p30 && ay < 0x1p30) {
+            // magnitude tests on the exponent fields (integer compares; FP64
+            // compares would run on the FP64 pipe): field < 1053 is |v| < 2^30,
+            // field >= 963 is |v| >= 2^-60
+            const uint32_t ex = ((uint32_t)__double2hiint((double)a.x) >> 20) & 0x7FFu;
+            const uint32_t ey = ((uint32_t)__double2hiint((double)a.y) >> 20) & 0x7FFu;
+            if (ex < 1053u && ey < 1053u) {
                 // x and y as float-float (values below 2^-60 add less than 2^-120
                 // to p and count as zero), p and its sums in float-float
-                const ff x = ax >= 0x1p-60 ? ff_from_double((double)a.x) : ff{0.f, 0.f};
-                const ff y = ay >= 0x1p-60 ? ff_from_double((double)a.y) : ff{0.f, 0.f};
+                const ff x = ex >= 963u ? ff_from_double((double)a.x) : ff{0.f, 0.f};
+                const ff y = ey >= 963u ? ff_from_double((double)a.y) : ff{0.f, 0.f};
                 const ff p = ff_add(ff_mul(x, x), ff_mul(y, y));
                 f0 = ff_add(f0, p);
                 if (NSTAT == 4) {
