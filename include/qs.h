@@ -83,10 +83,11 @@ void *qs_device_ptr(const qs_state *s);
 int qs_set_stream(qs_state *s, void *stream);
 
 /* |x>: amplitude x = 1, all others 0 (Sec. 2).  QS_EINVAL if x >= 2^n.
- * Only amplitude x is written now.  Tensor-core cluster sweeps then work on the
- * indices the circuit so far can reach (targets of the clusters applied since,
- * other bits as in x) and give the same result as on the zero-filled state;
- * every other call writes the remaining zeros first. */
+ * On a state from qs_alloc only amplitude x is written now.  Tensor-core
+ * cluster sweeps then work on the indices the circuit so far can reach
+ * (targets of the clusters applied since, other bits as in x) and give the same
+ * result as on the zero-filled state; every other call writes the remaining
+ * zeros first.  A state on the caller's buffer (qs_wrap) is written in full. */
 int qs_init_basis(qs_state *s, uint64_t x);
 
 /* (2^{-n/2}, ..., 2^{-n/2}): the state after the H layer of cycle 0, which a

@@ -551,6 +551,7 @@ extern "C" int qs_set_stream(qs_state *s, void *stream)
 // |x>: one amplitude written, the support set to {x}; the zeros elsewhere are
 // written by the first call that needs them (qs_materialize), and sweeps on
 // the tensor cores never need them (Sec. 3.6 starts from a known state too).
+// States on a caller's buffer (qs_wrap) get their zeros at once.
 extern "C" int qs_init_basis(qs_state *s, uint64_t x)
 {
     if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_basis: null state");
@@ -563,7 +564,9 @@ extern "C" int qs_init_basis(qs_state *s, uint64_t x)
     QS_CUDA(cudaGetLastError(), "qs_init_basis");
     s->sup_free = 0;
     s->sup_fix = x;
-    return QS_OK;
+    // a wrapped buffer can be read by its owner without a library call: its
+    // zeros are written now
+    return s->owned ? QS_OK : qs_materialize(s);
 }
 
 int qs_materialize(qs_state *s)

@@ -300,6 +300,24 @@ def test_errors_leave_gpu_usable():
     assert e.value.code == qs.QS_EINVAL
 
 
+def test_wrapped_buffer_basis_start_is_written_in_full():
+    """The caller can read a wrapped buffer directly, so qs_init_basis writes
+    every amplitude of it at once (no deferred zeros)."""
+    torch = pytest.importorskip("torch")
+    n = 12
+    buf = torch.ones(2 << n, dtype=torch.float64, device="cuda")
+    h = qs.qs_wrap(buf, n, qs.QS_C128, torch.cuda.current_stream())
+    try:
+        qs.qs_init_basis(h, 37)
+        qs.qs_synchronize(h)
+        got = buf.cpu().numpy().view(np.complex128)
+    finally:
+        qs.qs_free(h)
+    want = np.zeros(1 << n, dtype=np.complex128)
+    want[37] = 1
+    assert np.array_equal(got, want)
+
+
 def test_wrap_torch_tensor():
     torch = pytest.importorskip("torch")
     n = 12
