@@ -74,6 +74,23 @@ int qs_set_device(int device);
 enum { QS_PATH_AUTO = 0, QS_PATH_CUDA_CORES = 1, QS_PATH_TENSOR = 2 };
 int qs_set_path(qs_state *s, int path);
 
+/* Phase folding in qs_run_circuit (on by default).  A phase op (merged CZ / T
+ * run, Sec. 2) that directly follows a dense op run by the tensor-core sweep
+ * is applied inside that sweep, saving its own HBM sweep.  The phase terms on
+ * the sweep's five qubits are multiplied into the cluster matrix (FP64, before
+ * packing).  A CZ with one end off those qubits acts on each group as a Z on
+ * the other end or not, and one with both ends off as a phase of the whole
+ * group (the specialisation Sec. 3.5 makes for CZ on global qubits); these and
+ * the coefficients off the sweep's qubits become a power of i per group and a
+ * sign per member, applied to the sweep's outputs.  The fold is taken only
+ * where every coefficient off the sweep's qubits is even (a power of i;
+ * CZ-only layers always qualify); other phase ops run as their own sweep.
+ * on = 0 turns folding off.  Results agree with the unfolded run to rounding;
+ * bit for bit (up to the sign of zeros) when no phase term lies on the
+ * sweep's qubits, as the matrix is then unchanged.  QS_EINVAL for a null
+ * state. */
+int qs_set_phase_fold(qs_state *s, int on);
+
 int qs_num_qubits(const qs_state *s);
 int qs_dtype(const qs_state *s);
 /* Device pointer to amplitude 0, holding the whole state: zeros the library
@@ -225,8 +242,14 @@ int qs_schedule_build(int n, const qs_gate *gates, int n_gates, const qs_sched_o
 
 /* A schedule from explicit ops (the caller's own clustering): op i is dense
  * (kinds[i] = QS_OP_DENSE: ks[i] qubits in qubits[5i..5i+ks[i]), unitary at
- * pool[offsets[i]], 2^k x 2^k complex128 interleaved) or a table diagonal
- * (QS_OP_DIAG, 2^k complex128 at pool[offsets[i]]). */
+ * pool[offsets[i]], 2^k x 2^k complex128 interleaved), a table diagonal
+ * (QS_OP_DIAG, 2^k complex128 at pool[offsets[i]]) or a phase op (QS_OP_PHASE,
+ * Sec. 2: amplitude x times e^{i pi s(x) / 4}, s(x) = sum_q c_q x_q +
+ * 4 sum_pairs x_a x_b; ks[i] = number of CZ pairs, qubits[] unused; at
+ * pool[offsets[i]] the n coefficients c_q, then the 2 ks[i] qubits of the
+ * pairs, all integers stored as doubles; coefficients are taken mod 8).
+ * QS_EINVAL for a bad kind, qubit, pair, non-integer entry or a read past the
+ * pool. */
 int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const int *ks,
                          const int *qubits, const int64_t *offsets,
                          const double *pool, int64_t pool_len, qs_schedule **out);
@@ -260,7 +283,9 @@ int qs_run_circuit(qs_state *s, const qs_schedule *sc);
 
 /* As qs_run_circuit, recording a CUDA event before and after every op on the
  * state's stream; waits for the stream and writes op i's device time in
- * milliseconds to op_ms[i] (host, qs_schedule_num_ops entries). */
+ * milliseconds to op_ms[i] (host, qs_schedule_num_ops entries).  A phase op
+ * folded into the sweep before it (qs_set_phase_fold) launches nothing and
+ * gets op_ms[i] = -1; its time is part of the previous op's. */
 int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *op_ms);
 
 /* ------------------------------------------------------------------------

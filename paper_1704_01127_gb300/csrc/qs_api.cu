@@ -532,6 +532,13 @@ extern "C" int qs_set_path(qs_state *s, int path)
     return QS_OK;
 }
 
+extern "C" int qs_set_phase_fold(qs_state *s, int on)
+{
+    if (!s) return qs_fail(QS_EINVAL, "qs_set_phase_fold: null state");
+    s->fold_phase = on != 0;
+    return QS_OK;
+}
+
 extern "C" int qs_num_qubits(const qs_state *s) { return s ? s->n : 0; }
 extern "C" int qs_dtype(const qs_state *s) { return s ? s->dtype : -1; }
 // the caller reads the buffer directly: the zeros outside the support first

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -339,16 +340,91 @@ std::vector<uint8_t> tc_pack_for(int dtype, const std::vector<double> &M5)
     return dtype == QS_C64 ? qs_pack_tc_c64(M5) : qs_pack_tc_c128(M5);
 }
 
+// Fold of phase op ph into the tensor-core sweep on the sorted qubits q5 with
+// matrix M5 (qs_post_phase): M5f = D M5, D the diagonal of the phase terms on
+// q5 (coefficients and CZ pairs with both ends in q5, Sec. 2), and desc the
+// rest: CZ pairs with one or no end in q5 and the coefficients off q5, which
+// act on each group as a conditional Z on a target or a phase of the group
+// (Sec. 3.5).  False when a coefficient off q5 is odd (its factor is not a
+// power of i) or there are more CZ terms off q5 than the kernel holds.
+bool fold_phase(int n, const std::array<int, 5> &q5, const std::vector<double> &M5, const qs_op_host &ph,
+                std::vector<double> &M5f, std::vector<uint8_t> &desc)
+{
+    int pos[64];
+    std::fill(pos, pos + 64, -1);
+    for (int j = 0; j < 5; j++) pos[q5[j]] = j;
+    qs_post_phase hdr;
+    std::memset(&hdr, 0, sizeof(hdr));
+    int cq[5] = {0, 0, 0, 0, 0};        // coefficient of qubit q5[j]
+    for (int q = 0; q < n; q++) {
+        const int c = ((ph.coeff[q] % 8) + 8) % 8;
+        if (pos[q] >= 0) {
+            cq[pos[q]] = c;
+        } else {
+            if (c & 1) return false;
+            if (c & 2) hdr.c1 |= 1ULL << q;
+            if (c & 4) hdr.c2 |= 1ULL << q;
+        }
+    }
+    uint32_t inner[5] = {0, 0, 0, 0, 0};   // bit j' of inner[j]: CZ (q5[j], q5[j']), j < j', mod 2
+    std::vector<uint64_t> partners(n, 0);
+    for (const auto &e : ph.edges) {
+        const int a = std::min(e.first, e.second), b = std::max(e.first, e.second);
+        const int ja = pos[a], jb = pos[b];
+        if (ja >= 0 && jb >= 0) inner[ja] ^= 1u << jb;
+        else if (ja >= 0) hdr.tp[ja] ^= 1ULL << b;
+        else if (jb >= 0) hdr.tp[jb] ^= 1ULL << a;
+        else partners[a] ^= 1ULL << b;
+    }
+    std::vector<qs_phase_term> terms;
+    for (int a = 0; a < n; a++)
+        if (partners[a]) terms.push_back({partners[a], a, 0});
+    if ((int)terms.size() > QS_MAX_POST_TERMS) return false;
+    hdr.n_terms = (int32_t)terms.size();
+    // row m of M5 times w^{s(m)}, w = e^{i pi / 4}: exact for even s
+    const double r = std::sqrt(0.5);
+    const double wr[8] = {1, r, 0, -r, -1, -r, 0, r}, wi[8] = {0, r, 1, r, 0, -r, -1, -r};
+    M5f.assign(M5.size(), 0.0);
+    for (int m = 0; m < 32; m++) {
+        int sm = 0;
+        for (int j = 0; j < 5; j++)
+            if ((m >> j) & 1) sm += cq[j] + 4 * __builtin_popcount(inner[j] & (uint32_t)m);
+        sm &= 7;
+        for (int x = 0; x < 32; x++) {
+            const double a = M5[2 * (m * 32 + x)], b = M5[2 * (m * 32 + x) + 1];
+            M5f[2 * (m * 32 + x)] = a * wr[sm] - b * wi[sm];
+            M5f[2 * (m * 32 + x) + 1] = a * wi[sm] + b * wr[sm];
+        }
+    }
+    desc.resize(sizeof(hdr) + terms.size() * sizeof(qs_phase_term));
+    std::memcpy(desc.data(), &hdr, sizeof(hdr));
+    if (!terms.empty()) std::memcpy(desc.data() + sizeof(hdr), terms.data(), terms.size() * sizeof(qs_phase_term));
+    return true;
+}
+
+// Append bytes to an op's data at a 256-byte boundary; returns their offset.
+size_t append_aligned(std::vector<uint8_t> &part, const std::vector<uint8_t> &bytes)
+{
+    const size_t at = (part.size() + 255) & ~(size_t)255;
+    part.resize(at + bytes.size());
+    std::memcpy(part.data() + at, bytes.data(), bytes.size());
+    return at;
+}
+
 // Device image of a schedule for one dtype: every op's data, 256-byte aligned.
-std::vector<uint8_t> schedule_blob(const qs_schedule *sc, int dtype, std::vector<size_t> &offset,
-                                   std::vector<int> &n_act, std::vector<size_t> &tc_off,
-                                   std::vector<std::array<int, 5>> &tc_q)
+std::vector<uint8_t> schedule_blob(const qs_schedule *sc, int dtype, qs_dev_sched &d)
 {
     std::vector<uint8_t> blob;
-    offset.assign(sc->ops.size(), 0);
-    n_act.assign(sc->ops.size(), 0);
-    tc_off.assign(sc->ops.size(), 0);
-    tc_q.assign(sc->ops.size(), std::array<int, 5>{{0, 0, 0, 0, 0}});
+    const size_t nops = sc->ops.size();
+    std::vector<size_t> &offset = d.offset, &tc_off = d.tc_off;
+    std::vector<std::array<int, 5>> &tc_q = d.tc_q;
+    offset.assign(nops, 0);
+    d.n_act.assign(nops, 0);
+    tc_off.assign(nops, 0);
+    d.fold_off.assign(nops, 0);
+    d.post_off.assign(nops, 0);
+    tc_q.assign(nops, std::array<int, 5>{{0, 0, 0, 0, 0}});
+    std::vector<int> &n_act = d.n_act;
     for (size_t i = 0; i < sc->ops.size(); i++) {
         const qs_op_host &op = sc->ops[i];
         std::vector<uint8_t> part;
@@ -369,11 +445,15 @@ std::vector<uint8_t> schedule_blob(const qs_schedule *sc, int dtype, std::vector
                 } else {
                     embed5(op.qubits, op.k, op.matrix, sc->n, tc_q[i], M5);
                 }
-                std::vector<uint8_t> tc = tc_pack_for(dtype, M5);
-                size_t at = (part.size() + 255) & ~(size_t)255;
-                part.resize(at + tc.size());
-                std::memcpy(part.data() + at, tc.data(), tc.size());
-                tc_off[i] = at;
+                tc_off[i] = append_aligned(part, tc_pack_for(dtype, M5));
+                // a phase op right after it can run inside its sweep
+                std::vector<double> M5f;
+                std::vector<uint8_t> desc;
+                if (i + 1 < nops && sc->ops[i + 1].kind == QS_OP_PHASE &&
+                    fold_phase(sc->n, tc_q[i], M5, sc->ops[i + 1], M5f, desc)) {
+                    d.fold_off[i] = append_aligned(part, tc_pack_for(dtype, M5f));
+                    d.post_off[i] = append_aligned(part, desc);
+                }
             }
         }
         size_t at = (blob.size() + 255) & ~(size_t)255;
@@ -396,7 +476,7 @@ int ensure_dev_schedule(qs_state *s, const qs_schedule *csc)
         cudaFree(d.pool);
         d.pool = nullptr;
     }
-    std::vector<uint8_t> blob = schedule_blob(sc, s->dtype, d.offset, d.n_act, d.tc_off, d.tc_q);
+    std::vector<uint8_t> blob = schedule_blob(sc, s->dtype, d);
     cudaError_t e = cudaMalloc(&d.pool, blob.size());
     if (e != cudaSuccess) {
         d.pool = nullptr;
@@ -410,15 +490,22 @@ int ensure_dev_schedule(qs_state *s, const qs_schedule *csc)
 }
 
 // Kernel path of a dense op: the state's setting if not AUTO, else the op's
-// planned path if any, else the default policy.
-int launch_op_dense(qs_state *s, const qs_dev_sched &d, size_t i, const qs_op_host &op, const uint8_t *data)
+// planned path if any, else the default policy.  *folded: the phase op after
+// it ran inside its tensor-core sweep.
+int launch_op_dense(qs_state *s, const qs_dev_sched &d, size_t i, const qs_op_host &op, const uint8_t *data,
+                    bool *folded)
 {
+    *folded = false;
     int path = s->path != QS_PATH_AUTO ? s->path
                : op.path != QS_PATH_AUTO ? op.path
                : (tc_wanted(s->dtype, op.k, s->n) ? QS_PATH_TENSOR : QS_PATH_CUDA_CORES);
     if (path == QS_PATH_TENSOR && d.tc_off[i]) {
         uint64_t grow = 0;
         for (int j = 0; j < op.k; j++) grow |= 1ULL << op.qubits[j];
+        if (s->fold_phase && d.fold_off[i]) {
+            *folded = true;
+            return qs_launch_dense5_tc(s, d.tc_q[i].data(), data + d.fold_off[i], grow, data + d.post_off[i]);
+        }
         return qs_launch_dense5_tc(s, d.tc_q[i].data(), data + d.tc_off[i], grow);
     }
     return qs_launch_dense(s, op.qubits, op.k, data, nullptr);
@@ -509,7 +596,9 @@ extern "C" int qs_run_circuit(qs_state *s, const qs_schedule *sc)
         const qs_op_host &op = sc->ops[i];
         const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
         if (op.kind == QS_OP_DENSE) {
-            rc = launch_op_dense(s, d, i, op, data);
+            bool folded;
+            rc = launch_op_dense(s, d, i, op, data, &folded);
+            if (folded) i++;   // the phase op after it ran inside the sweep
         } else if (op.kind == QS_OP_DIAG) {
             rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
         } else {
@@ -531,21 +620,30 @@ extern "C" int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *o
     cudaStream_t st = (cudaStream_t)s->stream;
     size_t nops = sc->ops.size();
     std::vector<cudaEvent_t> ev(nops + 1);
+    std::vector<char> skipped(nops, 0);
     for (auto &e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) return qs_fail(QS_ECUDA, "event create");
     cudaEventRecord(ev[0], st);
     for (size_t i = 0; i < nops && !rc; i++) {
         const qs_op_host &op = sc->ops[i];
         const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
-        if (op.kind == QS_OP_DENSE) rc = launch_op_dense(s, d, i, op, data);
+        bool folded = false;
+        if (op.kind == QS_OP_DENSE) rc = launch_op_dense(s, d, i, op, data, &folded);
         else if (op.kind == QS_OP_DIAG) rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
         else rc = qs_launch_phase(s, data, d.n_act[i]);
         cudaEventRecord(ev[i + 1], st);
+        if (folded) {   // the phase op after it ran inside the sweep
+            skipped[++i] = 1;
+            cudaEventRecord(ev[i + 1], st);
+        }
     }
     if (!rc) {
         cudaError_t e = cudaEventSynchronize(ev[nops]);
         if (e != cudaSuccess) rc = qs_fail(QS_ECUDA, "qs_run_circuit_timed: %s", cudaGetErrorString(e));
-        for (size_t i = 0; i < nops && !rc; i++) cudaEventElapsedTime(&op_ms[i], ev[i], ev[i + 1]);
+        for (size_t i = 0; i < nops && !rc; i++) {
+            if (skipped[i]) op_ms[i] = -1.0f;
+            else cudaEventElapsedTime(&op_ms[i], ev[i], ev[i + 1]);
+        }
     }
     for (auto &e : ev) cudaEventDestroy(e);
     return rc;
@@ -554,10 +652,8 @@ extern "C" int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *o
 extern "C" int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype)
 {
     if (!sc || (dtype != QS_C64 && dtype != QS_C128)) return qs_fail(QS_EINVAL, "qs_schedule_upload_bytes");
-    std::vector<size_t> off, to;
-    std::vector<int> na;
-    std::vector<std::array<int, 5>> tq;
-    return (int64_t)schedule_blob(sc, dtype, off, na, to, tq).size();
+    qs_dev_sched tmp;
+    return (int64_t)schedule_blob(sc, dtype, tmp).size();
 }
 
 extern "C" int qs_set_device(int device)

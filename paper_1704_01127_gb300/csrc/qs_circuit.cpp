@@ -2,6 +2,7 @@
 // greedy gate clustering (Sec. 3.6, step 2), FP64 cluster unitaries in sorted
 // qubit order (Sec. 3.2) and diagonal phase ops (Sec. 3.5).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <set>
 #include <vector>
@@ -406,6 +407,42 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
     return QS_OK;
 }
 
+// A phase op from the pool (qs_schedule_from_ops): n coefficients, then
+// n_pairs CZ pairs, integers stored as doubles.
+static bool phase_from_pool(int n, int n_pairs, const double *pool, int64_t pool_len, int64_t at,
+                            qs_op_host &op)
+{
+    if (n_pairs < 0 || at < 0 || at > pool_len || pool_len - at < n + 2 * (int64_t)n_pairs) return false;
+    auto integer = [](double v, int lo, int hi, int &out) {
+        if (!(v >= lo && v <= hi) || v != std::floor(v)) return false;
+        out = (int)v;
+        return true;
+    };
+    const double *src = pool + at;
+    op.kind = QS_OP_PHASE;
+    op.coeff.assign(n, 0);
+    op.edges.clear();
+    uint64_t support = 0;
+    for (int q = 0; q < n; q++) {
+        int c;
+        if (!integer(src[q], -(1 << 30), 1 << 30, c)) return false;
+        op.coeff[q] = ((c % 8) + 8) % 8;
+        if (op.coeff[q]) support |= 1ULL << q;
+    }
+    for (int e = 0; e < n_pairs; e++) {
+        int a, b;
+        if (!integer(src[n + 2 * e], 0, n - 1, a) || !integer(src[n + 2 * e + 1], 0, n - 1, b) || a == b)
+            return false;
+        op.edges.push_back({a, b});
+        support |= (1ULL << a) | (1ULL << b);
+    }
+    op.k = __builtin_popcountll(support);
+    int j = 0;
+    for (int q = 0; q < n && j < QS_MAX_K; q++)
+        if ((support >> q) & 1) op.qubits[j++] = q;
+    return true;
+}
+
 extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const int *ks,
                                     const int *qubits, const int64_t *offsets,
                                     const double *pool, int64_t pool_len, qs_schedule **out)
@@ -418,6 +455,15 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
     sc->n = n;
     for (int i = 0; i < n_ops; i++) {
         int k = ks[i];
+        if (kinds[i] == QS_OP_PHASE) {
+            qs_op_host op;
+            if (!phase_from_pool(n, k, pool, pool_len, offsets[i], op)) {
+                delete sc;
+                return qs_fail(QS_EINVAL, "qs_schedule_from_ops: bad phase op %d", i);
+            }
+            sc->ops.push_back(std::move(op));
+            continue;
+        }
         bool dense = kinds[i] == QS_OP_DENSE;
         // both kinds take at most QS_MAX_K qubits here (QS_MAX_K slots per op)
         if ((!dense && kinds[i] != QS_OP_DIAG) || k < 1 || k > QS_MAX_K || k > n) {

@@ -26,6 +26,7 @@ struct qs_state {
     size_t pinned_bytes = 0;
     int *status = nullptr;        // device word set by kernels whose bounded waits ran out
     int path = 0;                 // QS_PATH_*
+    bool fold_phase = true;       // qs_set_phase_fold
     // Support: amplitudes may be nonzero only at indices i with
     // (i & ~sup_free) == sup_fix.  After qs_init_basis the support is one index
     // and memory outside the support is left unwritten; the tensor-core sweeps
@@ -66,6 +67,10 @@ struct qs_dev_sched {
     std::vector<int> n_act;              // phase ops: number of CZ partner terms
     std::vector<size_t> tc_off;          // dense ops: offset of the tensor-core pack in op data (0: none)
     std::vector<std::array<int, 5>> tc_q;  // dense ops: the 5 qubits the tensor-core sweep uses
+    // dense ops followed by a phase op that folds into their tensor-core sweep:
+    // offsets in op data of the pack of the folded matrix and of its
+    // qs_post_phase (0: no fold)
+    std::vector<size_t> fold_off, post_off;
 };
 
 struct qs_schedule {
@@ -86,6 +91,26 @@ struct qs_phase_term {
     int32_t a;
     int32_t pad;
 };
+
+// A phase op folded into the tensor-core sweep of the dense op before it
+// (device layout, in the schedule's op data).  For an index x = b + m spread
+// over the sweep's five qubits (b: the group's base, those bits zero; m: the
+// member, bit j on qubit j of the sweep), the phase factor not carried by the
+// folded matrix is i^e(b) (-1)^popc(m & flip(b)) with
+//   e(b) = popc(b & c1) + 2 popc(b & c2) + 2 sum_terms b_a popc(b & partners_a)  (mod 4)
+//   bit j of flip(b) = popc(b & tp[j]) mod 2
+// c1, c2: qubits off the sweep whose coefficient (mod 8) has bit 1 / bit 2 set
+// (bit 0 is clear there, else there is no fold); tp[j]: CZ partners of the
+// sweep's qubit j off the sweep; terms: CZ pairs with both ends off the sweep
+// (qs_phase_term, partners above a, pairs counted mod 2).
+struct qs_post_phase {
+    uint64_t c1, c2;
+    uint64_t tp[5];
+    int32_t n_terms;
+    int32_t pad;
+    // followed by n_terms qs_phase_term
+};
+constexpr int QS_MAX_POST_TERMS = 64;
 
 // Launchers (qs_apply.cu).  All validate nothing: callers check arguments.
 // dev_tc: tensor-core operand pack of a 5-qubit cluster (qs_tc.cu) or null.
@@ -115,4 +140,6 @@ size_t qs_tc_pack_bytes(int dtype);
 // 5-qubit tensor-core sweep over the state's support; grow = the qubits that
 // join the support (the cluster's own targets; an embedded cluster's padding
 // qubits stay fixed).
-int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack, uint64_t grow);
+// dev_post: a folded phase op (qs_post_phase, device) or null.
+int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack, uint64_t grow,
+                        const void *dev_post = nullptr);

@@ -213,15 +213,83 @@ __device__ __forceinline__ uint64_t off5(int x, const TileLayout &t)
     return o;
 }
 
+// A phase op folded into the sweep (qs_post_phase), copied to shared memory.
+struct PostSmem {
+    uint64_t c1, c2, tp[5];
+    uint64_t part[QS_MAX_POST_TERMS];
+    int a[QS_MAX_POST_TERMS];
+    int n;
+};
+
+__device__ __forceinline__ void post_load(PostSmem &ps, const qs_post_phase *g, int tid, int nthr)
+{
+    const qs_phase_term *terms = reinterpret_cast<const qs_phase_term *>(g + 1);
+    const int n = min(g->n_terms, QS_MAX_POST_TERMS);   // the host never packs more
+    if (tid == 0) {
+        ps.c1 = g->c1;
+        ps.c2 = g->c2;
+        for (int j = 0; j < 5; j++) ps.tp[j] = g->tp[j];
+        ps.n = n;
+    }
+    for (int i = tid; i < n; i += nthr) {
+        ps.part[i] = terms[i].partners;
+        ps.a[i] = terms[i].a;
+    }
+}
+
+// For the group with base index b: the exponent e of i (mod 4) and the mask of
+// members whose sign flips (CZ partners off the sweep), as qs_post_phase
+// defines them.
+__device__ __forceinline__ void post_row(const PostSmem &ps, uint64_t b, uint32_t &e, uint32_t &flip)
+{
+    uint32_t x = (uint32_t)__popcll(b & ps.c1) + 2u * (uint32_t)__popcll(b & ps.c2);
+    for (int i = 0; i < ps.n; i++)
+        if ((b >> ps.a[i]) & 1) x += 2u * (uint32_t)__popcll(b & ps.part[i]);
+    uint32_t f = 0;
+#pragma unroll
+    for (int j = 0; j < 5; j++) f |= ((uint32_t)__popcll(b & ps.tp[j]) & 1u) << j;
+    e = x & 3u;
+    flip = f;
+}
+
+// exponent of i for member m of a group with (e, flip)
+__device__ __forceinline__ uint32_t post_member(uint32_t e, uint32_t flip, int m)
+{
+    return (e + 2u * (uint32_t)__popc((uint32_t)m & flip)) & 3u;
+}
+
+// (re + i im) i^r
+__device__ __forceinline__ float2 rot_i(float2 v, uint32_t r)
+{
+    const float a = (r & 1u) ? v.y : v.x, b = (r & 1u) ? v.x : v.y;
+    return make_float2(((r + 1u) & 2u) ? -a : a, (r & 2u) ? -b : b);
+}
+
+// the same on the two words of each FP64 value: a swap and sign-bit flips
+__device__ __forceinline__ void rot_i_words(uint32_t &h0, uint32_t &l0, uint32_t &h1, uint32_t &l1, uint32_t r)
+{
+    if (r & 1u) {
+        const uint32_t th = h0, tl = l0;
+        h0 = h1;
+        l0 = l1;
+        h1 = th;
+        l1 = tl;
+    }
+    h0 ^= ((r + 1u) & 2u) ? 0x80000000u : 0u;
+    h1 ^= (r & 2u) ? 0x80000000u : 0u;
+}
+
 constexpr size_t kTileBytesF32 = (size_t)kRows * kK * 4;   // 32 KB
 constexpr size_t kBBytesF32 = (size_t)kN * kK * 4;         // 16 KB
 constexpr size_t kSmemF32 = 2 * kTileBytesF32 + 2 * kBBytesF32;
 
 // One CTA of 128 threads; thread r owns row r (group) of each tile.  Tiles are
 // taken in a grid-stride loop; warp 0 holds 128 TMEM columns for the CTA.
+// kPost: a phase op folded into the sweep is applied to the outputs.
+template <bool kPost>
 __global__ void __launch_bounds__(128, 2)
 k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const float *__restrict__ bpack,
-                int *__restrict__ status)
+                const qs_post_phase *__restrict__ post, int *__restrict__ status)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *A_h = smem;
@@ -230,6 +298,7 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const
     uint8_t *B_t = B_h + kBBytesF32;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base_s;
+    __shared__ PostSmem ps;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     {
@@ -237,6 +306,7 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const
         float4 *dst = reinterpret_cast<float4 *>(B_h);
         for (int i = tid; i < (int)(2 * kBBytesF32 / 16); i += blockDim.x) dst[i] = src[i];
     }
+    if constexpr (kPost) post_load(ps, post, tid, blockDim.x);
     if (warp == 0) {
         tmem_alloc(smem_u32(&tmem_base_s), kTmemCols);
         tmem_relinquish();
@@ -330,6 +400,14 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const
         parity ^= 1;
         tc_fence_after();
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        uint32_t pe = 0, pf = 0;
+        if constexpr (kPost) post_row(ps, (uint64_t)(p_cur - psi), pe, pf);
+        // output of member m: head + corrections, times the folded phase's factor
+        auto out_of = [&](const float *r, const float *q, int l, int m) {
+            float2 v = make_float2(r[2 * l] + q[2 * l], r[2 * l + 1] + q[2 * l + 1]);
+            if constexpr (kPost) v = rot_i(v, post_member(pe, pf, m));
+            return v;
+        };
 #pragma unroll
         for (int c = 0; c < kN / 16; c++) {
             float r[16], q[16];
@@ -338,14 +416,13 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const
             tmem_wait_ld();
             if (valid_cur && t.pairs) {
 #pragma unroll
-                for (int l = 0; l < 8; l += 2)
-                    *reinterpret_cast<float4 *>(p_cur + off5(8 * c + l, t)) =
-                        make_float4(r[2 * l] + q[2 * l], r[2 * l + 1] + q[2 * l + 1], r[2 * l + 2] + q[2 * l + 2],
-                                    r[2 * l + 3] + q[2 * l + 3]);
+                for (int l = 0; l < 8; l += 2) {
+                    const float2 v0 = out_of(r, q, l, 8 * c + l), v1 = out_of(r, q, l + 1, 8 * c + l + 1);
+                    *reinterpret_cast<float4 *>(p_cur + off5(8 * c + l, t)) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                }
             } else if (valid_cur) {
 #pragma unroll
-                for (int l = 0; l < 8; l++)
-                    p_cur[off5(8 * c + l, t)] = make_float2(r[2 * l] + q[2 * l], r[2 * l + 1] + q[2 * l + 1]);
+                for (int l = 0; l < 8; l++) p_cur[off5(8 * c + l, t)] = out_of(r, q, l, 8 * c + l);
             }
         }
         tc_fence_before();
@@ -510,9 +587,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr size_t kStageC128 = (size_t)kSplitThreads * kMPT * 16;   // raw next tile: 64 KB
 constexpr size_t kSmemC128Pipe = kSmemC128 + kStageC128;
 
+template <bool kPost>
 __global__ void __launch_bounds__(kSplitThreads + kEpiThreads, 1)
 k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const uint8_t *__restrict__ bpack,
-                      int *__restrict__ status)
+                      const qs_post_phase *__restrict__ post, int *__restrict__ status)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *A = smem;
@@ -526,6 +604,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     __shared__ uint32_t rowX[2][kRows];   // (E_r - 2096) << 20 of the last two tiles
     __shared__ uint32_t colX[kN];         // G_n << 20
     __shared__ volatile int abort_flag;
+    __shared__ PostSmem ps;               // a phase op folded into the sweep (kPost)
 
     const int tid = threadIdx.x, warp = tid >> 5;
     {
@@ -541,6 +620,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
         const int *G = reinterpret_cast<const int *>(bpack + kSlicesB * kPlaneB);
         if (tid < kN) colX[tid] = (uint32_t)G[tid] << 20;
         if (tid < 32) moff[tid] = off5(tid, t);
+        if constexpr (kPost) post_load(ps, post, tid, blockDim.x);
     }
     if (warp == 0) {
         tmem_alloc(smem_u32(&tmem_base_s), kTmemCols128);
@@ -673,6 +753,8 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             const uint64_t g = tile * kRows + row;
             const bool valid = g < n_groups;
             double2 *p = psi + (valid ? tile_base(g, t) : 0);
+            uint32_t pe = 0, pf = 0;
+            if constexpr (kPost) post_row(ps, (uint64_t)(p - psi), pe, pf);
             for (int h = 0; h < 2; h++) {
                 if (!mbar_wait_bounded(smem_u32(&mbar_mma[h]), it & 1) || abort_flag) {
                     atomicExch(status, 1);
@@ -689,7 +771,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
 #pragma unroll
                     for (int d = 0; d < kDiags; d++) tmem_ld4(lane_addr + 256 * h + kHalfN * d + col, D[d]);
                     tmem_wait_ld();
-                    double out[4];
+                    uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
                         // T = P 2^32 + Q 2^16 + r with P = D_0 2^8 + D_1 and
@@ -702,13 +784,19 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
                         const double dv = __ll2double_rn(T);
                         const uint32_t hi = (uint32_t)__double2hiint(dv);
                         // T = 0 gives +0.0 (hi = 0); otherwise add the scale to the exponent
-                        out[q] = __hiloint2double((int)(hi == 0 ? 0u : hi + Xr + colX[kHalfN * h + col + q]),
-                                                  __double2loint(dv));
+                        hw[q] = hi == 0 ? 0u : hi + Xr + colX[kHalfN * h + col + q];
+                        lw[q] = (uint32_t)__double2loint(dv);
+                    }
+                    const int m0 = (kHalfN * h + col) >> 1;   // columns 2m, 2m+1: re, im of member m
+                    if constexpr (kPost) {
+                        rot_i_words(hw[0], lw[0], hw[1], lw[1], post_member(pe, pf, m0));
+                        rot_i_words(hw[2], lw[2], hw[3], lw[3], post_member(pe, pf, m0 + 1));
                     }
                     if (valid) {
-                        const int m0 = (kHalfN * h + col) >> 1;
-                        p[moff[m0]] = make_double2(out[0], out[1]);
-                        p[moff[m0 + 1]] = make_double2(out[2], out[3]);
+                        p[moff[m0]] = make_double2(__hiloint2double((int)hw[0], (int)lw[0]),
+                                                   __hiloint2double((int)hw[1], (int)lw[1]));
+                        p[moff[m0 + 1]] = make_double2(__hiloint2double((int)hw[2], (int)lw[2]),
+                                                       __hiloint2double((int)hw[3], (int)lw[3]));
                     }
                 }
                 tc_fence_before();
@@ -720,7 +808,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     if (warp == 0) tmem_dealloc(tmem, kTmemCols128);
 }
 
-bool g_attr_set[2][64] = {{false}};
+bool g_attr_set[2][2][64] = {};   // [complex64][folded phase][device]
 
 }  // namespace
 
@@ -820,20 +908,22 @@ std::vector<uint8_t> qs_pack_tc_c128(const std::vector<double> &M)
 
 size_t qs_tc_pack_bytes(int dtype) { return dtype == QS_C64 ? 2 * kBBytesF32 : kSlicesB * kPlaneB + 256; }
 
-int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack, uint64_t grow)
+int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack, uint64_t grow,
+                        const void *dev_post)
 {
-    const bool c64 = s->dtype == QS_C64;
+    const bool c64 = s->dtype == QS_C64, fold = dev_post != nullptr;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (dev < 0 || dev >= 64) return qs_fail(QS_EUNSUPPORTED, "device %d", dev);
-    if (!g_attr_set[c64][dev]) {
-        cudaError_t e = c64 ? cudaFuncSetAttribute(k_dense5_tc_c64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)kSmemF32)
-                            : cudaFuncSetAttribute(k_dense5_tc_c128_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)kSmemC128Pipe);
+    if (!g_attr_set[c64][fold][dev]) {
+        const void *fn = c64 ? (fold ? (const void *)k_dense5_tc_c64<true> : (const void *)k_dense5_tc_c64<false>)
+                             : (fold ? (const void *)k_dense5_tc_c128_pipe<true>
+                                     : (const void *)k_dense5_tc_c128_pipe<false>);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(c64 ? kSmemF32 : kSmemC128Pipe));
         if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
-        g_attr_set[c64][dev] = true;
+        g_attr_set[c64][fold][dev] = true;
     }
     // the sweep covers the support after it: the support's free bits plus the
     // targets; groups enumerate the free bits that are not targets
@@ -862,14 +952,24 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
     int *status;
     int rc = qs_state_status(s, &status);
     if (rc) return rc;
+    const qs_post_phase *post = (const qs_post_phase *)dev_post;
+    cudaStream_t st = (cudaStream_t)s->stream;
     if (c64) {
         int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms * 2);
-        k_dense5_tc_c64<<<grid, kRows, kSmemF32, (cudaStream_t)s->stream>>>(
-            (float2 *)s->amp, groups, t, (const float *)dev_pack, status);
+        if (fold)
+            k_dense5_tc_c64<true><<<grid, kRows, kSmemF32, st>>>((float2 *)s->amp, groups, t,
+                                                                (const float *)dev_pack, post, status);
+        else
+            k_dense5_tc_c64<false><<<grid, kRows, kSmemF32, st>>>((float2 *)s->amp, groups, t,
+                                                                 (const float *)dev_pack, post, status);
     } else {
         int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms);
-        k_dense5_tc_c128_pipe<<<grid, kSplitThreads + kEpiThreads, kSmemC128Pipe, (cudaStream_t)s->stream>>>(
-            (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, status);
+        if (fold)
+            k_dense5_tc_c128_pipe<true><<<grid, kSplitThreads + kEpiThreads, kSmemC128Pipe, st>>>(
+                (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, post, status);
+        else
+            k_dense5_tc_c128_pipe<false><<<grid, kSplitThreads + kEpiThreads, kSmemC128Pipe, st>>>(
+                (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, post, status);
     }
     // amplitudes on the padding targets of an embedded cluster keep their
     // fixed values (U (x) 1 leaves zero inputs zero), so only the cluster's own

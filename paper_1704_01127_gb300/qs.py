@@ -83,6 +83,7 @@ _SIGS = {
     "qs_run_circuit_timed": ([_VP, _VP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "qs_set_device": ([ctypes.c_int], ctypes.c_int),
     "qs_set_path": ([_VP, ctypes.c_int], ctypes.c_int),
+    "qs_set_phase_fold": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_stats_static": ([_VP, ctypes.c_int, ctypes.c_int, _VP, _DP], ctypes.c_int),
     "qs_batch_circuit_params": ([ctypes.c_uint64, _IP, _IP, _IP], ctypes.c_int),
     "qs_op_features": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP, ctypes.c_int, ctypes.c_int,
@@ -323,12 +324,21 @@ def qs_schedule_build(n, gates, k_max=5, fuse=True, merge_phase=True, drop_final
 
 
 def qs_schedule_from_ops(n, ops):
-    """ops: list of (kind, qubits, complex matrix or diagonal)."""
+    """ops: list of (kind, qubits, complex matrix or diagonal), or for a phase
+    op (QS_OP_PHASE, CZ pairs, n coefficients)."""
     kinds, ks, qubits, offsets, pool = [], [], [], [], []
     at = 0
     for kind, qs, m in ops:
         kinds.append(kind)
         ks.append(len(qs))
+        if kind == QS_OP_PHASE:
+            qubits.extend([0] * QS_MAX_K)
+            flat = np.concatenate([np.asarray(m, dtype=np.float64).reshape(-1),
+                                   np.asarray(qs, dtype=np.float64).reshape(-1)])
+            offsets.append(at)
+            pool.append(flat)
+            at += flat.size
+            continue
         qubits.extend(list(qs) + [0] * (QS_MAX_K - len(qs)))
         flat = _c128(m).reshape(-1).view(np.float64)
         offsets.append(at)
@@ -384,7 +394,8 @@ def qs_run_circuit(h, sched):
 
 
 def qs_run_circuit_timed(h, sched):
-    """Run a schedule; returns the device time of every op in milliseconds."""
+    """Run a schedule; returns the device time of every op in milliseconds
+    (-1 for a phase op that ran inside the sweep before it)."""
     out = np.zeros(max(qs_schedule_num_ops(sched), 1), dtype=np.float32)
     _check(lib().qs_run_circuit_timed(h, sched, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
     return out[:qs_schedule_num_ops(sched)]
@@ -413,6 +424,10 @@ def qs_stats_static(dev_ptr, n, dtype, stream=None):
 
 def qs_set_path(h, path):
     _check(lib().qs_set_path(h, int(path)))
+
+
+def qs_set_phase_fold(h, on):
+    _check(lib().qs_set_phase_fold(h, 1 if on else 0))
 
 
 # ------------------------------------------------------------------- batches

@@ -135,6 +135,28 @@ def test_schedule_from_ops_sorts_qubits_and_permutes():
     np.testing.assert_allclose(a, b, atol=1e-15)
 
 
+def test_schedule_from_ops_phase_op():
+    """A phase op from explicit coefficients and CZ pairs (Sec. 2): stored mod 8
+    with its pairs and support; malformed ones are refused."""
+    n = 8
+    coeff = [0, 9, -1, 4, 0, 0, 2, 0]
+    pairs = [(0, 5), (5, 7), (0, 5)]
+    h = qs.qs_schedule_from_ops(n, [(qs.QS_OP_PHASE, pairs, coeff)])
+    try:
+        op = qs.qs_schedule_op(h, 0)
+    finally:
+        qs.qs_schedule_free(h)
+    assert op["kind"] == "phase"
+    assert list(op["coeff"]) == [0, 1, 7, 4, 0, 0, 2, 0]
+    assert [tuple(e) for e in op["edges"]] == pairs
+    assert op["support"] == 7          # qubits with a coefficient or in a pair: 0, 1, 2, 3, 5, 6, 7
+    for bad_pairs, bad_coeff in [([(2, 2)], [0] * n), ([(0, 8)], [0] * n), ([], [0.5] + [0] * (n - 1)),
+                                 ([], [0] * (n - 1))]:
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_schedule_from_ops(n, [(qs.QS_OP_PHASE, bad_pairs, bad_coeff)])
+        assert e.value.code == qs.QS_EINVAL
+
+
 def test_batch_circuit_params_match_oracle_and_are_uniform():
     grids, depths = {}, []
     for seed in range(512):
