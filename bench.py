@@ -184,6 +184,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     n, _ = qs.qs_supremacy_circuit(rows, cols, cycles, 0, removed=removed)
     h = qs.qs_alloc(n, dtype, stream)
+    qs.qs_set_phase_fold(h, not args.no_fold)
     state_bytes = amp_bytes << n
 
     kernel_ms = {}      # (kind, k) -> per-launch ms of full-state sweeps in the timed region
@@ -267,7 +268,7 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
                 "peak_source": peak_src}
-        kname = ("k_dense5_tc_c128_pipe" if dtype == qs.QS_C128 else "k_dense5_tc_c64") if tensor else (
+        kname = ("k_dense5_tc_c128_pipe<false>" if dtype == qs.QS_C128 else "k_dense5_tc_c64<false>") if tensor else (
             "k_dense<%s,%d>" % ("double" if dtype == qs.QS_C128 else "float", k) if kind == "dense"
             else "k_phase<%s>" % ("double" if dtype == qs.QS_C128 else "float"))
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -344,7 +345,8 @@ def run_ours(args):
         "config": {"workload": "%dx%d grid, %d qubits, %d CZ cycles, %s, %s" % (
             rows, cols, n, cycles, dt, "gate by gate" if args.plain else "fused k<=%d + phase diagonals" % k_max),
             "seeds": "rank*1000 + step", "l2": "state %.1f GiB > L2 129 MB (no flush needed)" % (state_bytes / 2**30),
-            "parallelism": "replicas" if world > 1 else "single GPU"},
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "phase_fold": not args.no_fold},
         "roofline": roof, "sweeps": sweeps, "plain": plain,
         "speedup_vs_plain": (plain["s_per_circuit"] / per_circuit) if plain else None,
         "porter_thomas": {"sum_p": stats[0], "entropy": stats[1], "m2": stats[3]},
@@ -556,6 +558,8 @@ def main():
     ap.add_argument("--plain", action="store_true", help="gate-by-gate form instead of fused")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison run")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fold", action="store_true",
+                    help="run every phase op as its own sweep (no folding into the tensor-core sweep before it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
