@@ -365,6 +365,37 @@ def test_tc_c64_qubit0_paired():
     assert np.max(np.abs(got - ref)) <= 3 * SWEEP_TOL[qs.QS_C64]
 
 
+@pytest.mark.parametrize("targets", [(0, 1, 2, 8, 9), (2, 3, 4, 10, 11), (0, 1, 2, 3, 4), (1, 9, 10, 13, 15),
+                                     (0, 5, 6, 10, 11), (3, 4, 5, 12, 13), (0, 4, 9, 12)])
+def test_tc_c64_low_targets(targets):
+    """complex64 tensor-core sweeps on low targets (a warp's rows far apart in
+    memory, member pairs on qubit 0): on a dense state they match the oracle;
+    from a basis state, the cluster on the one-amplitude support (layout with
+    fixed bits) and on the zero-filled state (full layout) agree bit for bit."""
+    n = 16
+    U = random_unitary(len(targets), sum(targets))
+    psi = f32_round(random_state(n, 5 + sum(targets)))
+    ref = psi.copy()
+    sim.apply_kq(ref, list(targets), U)
+    with State(n, qs.QS_C64) as s:
+        qs.qs_set_amplitudes(s.h, psi)
+        qs.qs_apply_cluster(s.h, list(targets), U)
+        got = qs.qs_get_amplitudes(s.h)
+    assert np.max(np.abs(got - ref)) <= SWEEP_TOL[qs.QS_C64]
+    x = 0x2D6B
+    e = np.zeros(1 << n, dtype=np.complex128)
+    e[x] = 1
+    with State(n, qs.QS_C64) as s:
+        qs.qs_init_basis(s.h, x)
+        qs.qs_apply_cluster(s.h, list(targets), U)
+        lazy = qs.qs_get_amplitudes(s.h)
+    with State(n, qs.QS_C64) as s:
+        qs.qs_set_amplitudes(s.h, e)
+        qs.qs_apply_cluster(s.h, list(targets), U)
+        full = qs.qs_get_amplitudes(s.h)
+    assert np.array_equal(lazy, full)
+
+
 # ------------------------------------------------ tensor-core 5-qubit sweep (c64)
 
 @pytest.mark.parametrize("n", [5, 8, 11, 12, 13, 16, 19])
