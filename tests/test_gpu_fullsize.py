@@ -10,12 +10,17 @@ amplitudes compared between precisions.
   (tolerance 2e-6); norm drift and Porter-Thomas moments of both.
 * 34 qubits (5x7 minus a corner), complex64 only (128 GiB): norm drift and
   Porter-Thomas moments; circuit + inverse returns |0...0> within 1e-4.
+* 32 qubits, complex64, uniform state (every p = 2^-32 exactly, so every CDF
+  sum is exact and outcome j is floor(u_j 2^32), the rule the oracle is pinned
+  to): 4096 samples bit for bit.  Above 30 qubits the super-block prefixes no
+  longer fit the draw kernel's shared memory and are searched in device memory.
 """
 import numpy as np
 import pytest
 
 import paper_1704_01127_gb300.qs as qs
 from oracle import circuit as ocircuit
+from oracle import sim
 
 pytestmark = pytest.mark.gpu
 
@@ -84,3 +89,15 @@ def test_34_qubits_c64_norm_pt_and_inverse():
         assert abs(abs(a0) ** 2 - 1) < 1e-4
     finally:
         qs.qs_free(h)
+
+
+def test_sampling_32_qubits_uniform_c64():
+    n, m, seed = 32, 4096, 2024
+    h = qs.qs_alloc(n, qs.QS_C64)
+    try:
+        qs.qs_init_uniform(h)
+        got = qs.qs_sample(h, seed, m)
+    finally:
+        qs.qs_free(h)
+    want = np.array([(sim.splitmix64(seed, j) >> 11) >> (53 - n) for j in range(m)], dtype=np.uint64)
+    assert np.array_equal(got, want)
