@@ -126,53 +126,65 @@ __global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *_
     }
     double d0 = 0, d3 = 0, dent = 0;
     ff f0{0.f, 0.f}, f3{0.f, 0.f}, fent{0.f, 0.f};
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        const C a = psi[i];
-        if constexpr (c128) {
-            // magnitude tests on the exponent fields (integer compares; FP64
-            // compares would run on the FP64 pipe): field < 1053 is |v| < 2^30,
-            // field >= 963 is |v| >= 2^-60
-            const uint32_t ex = ((uint32_t)__double2hiint((double)a.x) >> 20) & 0x7FFu;
-            const uint32_t ey = ((uint32_t)__double2hiint((double)a.y) >> 20) & 0x7FFu;
-            if (ex < 1053u && ey < 1053u) {
-                // x and y as float-float (values below 2^-60 add less than 2^-120
-                // to p and count as zero), p and its sums in float-float
-                const ff x = ex >= 963u ? ff_from_double((double)a.x) : ff{0.f, 0.f};
-                const ff y = ey >= 963u ? ff_from_double((double)a.y) : ff{0.f, 0.f};
-                const ff p = ff_add(ff_mul(x, x), ff_mul(y, y));
-                f0 = ff_add(f0, p);
-                if (NSTAT == 4) {
-                    f3 = ff_add(f3, ff_mul(p, p));
-                    if (p.hi >= 0x1p-79f) {
-                        fent = ff_add(fent, ff_p_ln_p(lt, p));
-                    } else if (p.hi > 0.f) {
-                        const double pd = (double)p.hi + (double)p.lo;
-                        if (pd >= 2.2250738585072014e-308) dent += pd * log(pd);
+    // each thread loads kAhead amplitudes (block-strided, so every load of a
+    // warp is contiguous) before it adds them up: more loads in flight
+    constexpr int kAhead = c128 ? 4 : 8;
+    const uint64_t span = (uint64_t)blockDim.x * kAhead;
+    for (uint64_t base = (uint64_t)blockIdx.x * span; base < N; base += (uint64_t)gridDim.x * span) {
+        C av[kAhead];
+#pragma unroll
+        for (int k = 0; k < kAhead; k++) {
+            const uint64_t i = base + (uint64_t)k * blockDim.x + threadIdx.x;
+            av[k] = i < N ? psi[i] : C{};   // a zero amplitude adds nothing
+        }
+#pragma unroll
+        for (int k = 0; k < kAhead; k++) {
+            const C a = av[k];
+            if constexpr (c128) {
+                // magnitude tests on the exponent fields (integer compares; FP64
+                // compares would run on the FP64 pipe): field < 1053 is |v| < 2^30,
+                // field >= 963 is |v| >= 2^-60
+                const uint32_t ex = ((uint32_t)__double2hiint((double)a.x) >> 20) & 0x7FFu;
+                const uint32_t ey = ((uint32_t)__double2hiint((double)a.y) >> 20) & 0x7FFu;
+                if (ex < 1053u && ey < 1053u) {
+                    // x and y as float-float (values below 2^-60 add less than 2^-120
+                    // to p and count as zero), p and its sums in float-float
+                    const ff x = ex >= 963u ? ff_from_double((double)a.x) : ff{0.f, 0.f};
+                    const ff y = ey >= 963u ? ff_from_double((double)a.y) : ff{0.f, 0.f};
+                    const ff p = ff_add(ff_mul(x, x), ff_mul(y, y));
+                    f0 = ff_add(f0, p);
+                    if (NSTAT == 4) {
+                        f3 = ff_add(f3, ff_mul(p, p));
+                        if (p.hi >= 0x1p-79f) {
+                            fent = ff_add(fent, ff_p_ln_p(lt, p));
+                        } else if (p.hi > 0.f) {
+                            const double pd = (double)p.hi + (double)p.lo;
+                            if (pd >= 2.2250738585072014e-308) dent += pd * log(pd);
+                        }
+                    }
+                } else {
+                    // an amplitude of 2^30 or more (unnormalised input): FP64 throughout
+                    const double p = fma((double)a.x, (double)a.x, (double)a.y * (double)a.y);
+                    d0 += p;
+                    if (NSTAT == 4) {
+                        d3 = fma(p, p, d3);
+                        dent += p * log(p);
                     }
                 }
             } else {
-                // an amplitude of 2^30 or more (unnormalised input): FP64 throughout
-                const double p = fma((double)a.x, (double)a.x, (double)a.y * (double)a.y);
-                d0 += p;
+                // complex64 amplitudes carry FP32 errors (2^-24 relative): p, p^2
+                // and the logarithm of p are formed in FP32 (one rounding each, the
+                // logarithm a few ulp), and the terms add up in float-float
+                const float p = fmaf((float)a.x, (float)a.x, __fmul_rn((float)a.y, (float)a.y));
+                f0 = ff_add_f(f0, p);
                 if (NSTAT == 4) {
-                    d3 = fma(p, p, d3);
-                    dent += p * log(p);
-                }
-            }
-        } else {
-            const ff p = ff_add(ff_sqr_f((float)a.x), ff_sqr_f((float)a.y));
-            f0 = ff_add(f0, p);
-            if (NSTAT == 4) {
-                f3 = ff_add(f3, ff_mul(p, p));
-                if (p.hi >= 0x1p-79f && p.hi <= 0x1p100f) {
-                    // complex64 amplitudes carry FP32 errors (2^-24 relative), so
-                    // the logarithm of p is taken in FP32 (a few ulp); the terms
-                    // still add up in float-float
-                    fent = ff_add(fent, ff{p.hi * __logf(p.hi), 0.f});
-                } else if (p.hi > 0.f) {
-                    const double pd = (double)p.hi + (double)p.lo;
-                    if (pd >= 2.2250738585072014e-308) dent += pd * log(pd);
+                    f3 = ff_add_f(f3, __fmul_rn(p, p));
+                    if (p >= 0x1p-79f && p <= 0x1p100f) {
+                        fent = ff_add_f(fent, __fmul_rn(p, __logf(p)));
+                    } else if (p > 0.f) {
+                        const double pd = (double)p;
+                        if (pd >= 2.2250738585072014e-308) dent += pd * log(pd);
+                    }
                 }
             }
         }
