@@ -117,6 +117,14 @@ def test_schedule_rejects_bad_input():
         qs.qs_schedule_build(n, bad, k_max=5)
 
 
+def test_state_setters_refuse_a_null_state():
+    """Host-side argument checks of the path and phase-fold settings (no GPU)."""
+    for call in (lambda: qs.qs_set_phase_fold(None, 1), lambda: qs.qs_set_path(None, qs.QS_PATH_AUTO)):
+        with pytest.raises(qs.QSError) as e:
+            call()
+        assert e.value.code == qs.QS_EINVAL
+
+
 def test_schedule_from_ops_sorts_qubits_and_permutes():
     from inputs import random_unitary
     U = random_unitary(3, 1)
