@@ -272,6 +272,23 @@ def test_sampling_bit_exact(dtype, n):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_empty_inputs(dtype):
+    """Degenerate calls: a schedule without ops leaves the state as it is (bit
+    for bit), and zero draws return an empty array."""
+    n = 9
+    psi = f32_round(random_state(n, 3)) if dtype == qs.QS_C64 else random_state(n, 3)
+    sc = qs.qs_schedule_from_ops(n, [])
+    try:
+        with State(n, dtype) as s:
+            qs.qs_set_amplitudes(s.h, psi)
+            qs.qs_run_circuit(s.h, sc)
+            assert np.array_equal(qs.qs_get_amplitudes(s.h), psi)
+            assert qs.qs_sample(s.h, 1, 0).size == 0
+    finally:
+        qs.qs_schedule_free(sc)
+
+
 def test_init_states():
     for n in (1, 7, 15):
         with State(n, qs.QS_C128) as s:

@@ -205,3 +205,19 @@ def test_supremacy_circuit_final_layer_folds(dtype):
     assert ms[last] == -1
     want = sim.run_circuit(n, qs.gates_to_tuples(g))
     assert np.max(np.abs(got - want)) <= (1e-12 if dtype == qs.QS_C128 else 2e-6)
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_fold_of_the_identity_phase(dtype):
+    """A phase op with no terms (all coefficients 0, no pairs) folds into the
+    sweep and leaves the cluster's result bit for bit as it is."""
+    targets = (3, 5, 6, 9, 11)
+    U = random_unitary(5, 40)
+    psi = random_state(N, 41)
+    if dtype == qs.QS_C64:
+        psi = f32_round(psi)
+    ops = [(qs.QS_OP_DENSE, targets, U), (qs.QS_OP_PHASE, [], np.zeros(N, dtype=np.int64))]
+    got, ms = lib_run(N, dtype, ops, psi=psi)
+    alone, _ = lib_run(N, dtype, ops[:1], psi=psi)
+    assert ms[1] == -1
+    assert np.array_equal(got, alone)
