@@ -175,8 +175,17 @@ int qs_sample(qs_state *s, uint64_t seed, int64_t m, uint64_t *out);
  * cudaMalloc / cudaFree; synchronises `stream` before returning. */
 int qs_stats_static(const void *dev_amp, int n, int dtype, void *stream, double out[4]);
 
-/* Wait for all work queued on the state's stream. */
+/* Wait for all work queued on the state's stream; QS_ETIMEOUT (once, the word
+ * is cleared) if a tensor-core kernel's bounded wait ran out since the last
+ * check. */
 int qs_synchronize(qs_state *s);
+
+/* Exercises the failure path of the bounded waits: one thread waits on an
+ * mbarrier nothing arrives on, gives up after 1000 tries (microseconds to
+ * milliseconds), records the expiry in the state's status word and returns.
+ * Returns QS_ETIMEOUT and clears the word; the state and the context stay
+ * usable.  No GPU fault or hang.  QS_EINVAL for a null state. */
+int qs_selftest_timeout(qs_state *s);
 
 /* ------------------------------------------------------------------------
  * Circuits (Fig. 1 caption; Sec. 3.6).

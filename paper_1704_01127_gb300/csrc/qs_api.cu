@@ -752,6 +752,15 @@ extern "C" int qs_synchronize(qs_state *s)
     return qs_check_status(s);
 }
 
+extern "C" int qs_selftest_timeout(qs_state *s)
+{
+    if (!s) return qs_fail(QS_EINVAL, "qs_selftest_timeout: null state");
+    int rc = qs_launch_wait_selftest(s, 1000);
+    if (rc) return rc;
+    QS_CUDA(cudaStreamSynchronize((cudaStream_t)s->stream), "qs_selftest_timeout");
+    return qs_check_status(s);
+}
+
 // --------------------------------------------------------------------------
 // Allocation-free statistics (no counterpart in the paper).
 //

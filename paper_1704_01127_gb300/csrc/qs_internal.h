@@ -143,3 +143,5 @@ size_t qs_tc_pack_bytes(int dtype);
 // dev_post: a folded phase op (qs_post_phase, device) or null.
 int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack, uint64_t grow,
                         const void *dev_post = nullptr);
+// One bounded mbarrier wait that cannot complete (qs_selftest_timeout).
+int qs_launch_wait_selftest(qs_state *s, long polls);

@@ -808,6 +808,21 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     if (warp == 0) tmem_dealloc(tmem, kTmemCols128);
 }
 
+// The bounded-wait failure path on its own: one thread waits on an mbarrier
+// that nothing arrives on, gives up after `polls` tries, records the expiry
+// in the status word and returns (the tensor-core sweeps do the same when
+// their MMAs or partner warps never answer).
+__global__ void k_wait_selftest(int *__restrict__ status, long polls)
+{
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x != 0) return;
+    mbar_init(smem_u32(&mbar), 1);
+    fence_mbar_init();
+    bool done = false;
+    for (long it = 0; it < polls && !done; it++) done = mbar_try_wait(smem_u32(&mbar), 0);
+    if (!done) atomicExch(status, 1);
+}
+
 bool g_attr_set[2][2][64] = {};   // [complex64][folded phase][device]
 
 }  // namespace
@@ -978,4 +993,14 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
     s->sup_fix = fx & ~(grow & tm);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "tc launch: %s", cudaGetErrorString(e));
+}
+
+int qs_launch_wait_selftest(qs_state *s, long polls)
+{
+    int *status;
+    int rc = qs_state_status(s, &status);
+    if (rc) return rc;
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)s->stream>>>(status, polls);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "wait self-test launch: %s", cudaGetErrorString(e));
 }

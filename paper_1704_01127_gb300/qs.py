@@ -84,6 +84,7 @@ _SIGS = {
     "qs_set_device": ([ctypes.c_int], ctypes.c_int),
     "qs_set_path": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_set_phase_fold": ([_VP, ctypes.c_int], ctypes.c_int),
+    "qs_selftest_timeout": ([_VP], ctypes.c_int),
     "qs_stats_static": ([_VP, ctypes.c_int, ctypes.c_int, _VP, _DP], ctypes.c_int),
     "qs_batch_circuit_params": ([ctypes.c_uint64, _IP, _IP, _IP], ctypes.c_int),
     "qs_op_features": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP, ctypes.c_int, ctypes.c_int,
@@ -283,6 +284,11 @@ def qs_sample(h, seed, m):
 
 def qs_synchronize(h):
     _check(lib().qs_synchronize(h))
+
+
+def qs_selftest_timeout(h):
+    """Status code of one bounded wait that runs out (QS_ETIMEOUT expected)."""
+    return lib().qs_selftest_timeout(h)
 
 
 # --------------------------------------------------------------- circuit API

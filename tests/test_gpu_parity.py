@@ -289,6 +289,27 @@ def test_empty_inputs(dtype):
         qs.qs_schedule_free(sc)
 
 
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_bounded_wait_expiry_is_reported(dtype):
+    """A bounded mbarrier wait that nothing completes reports QS_ETIMEOUT once;
+    the word is cleared and the state keeps working (a cluster then matches
+    the oracle).  No fault or hang is involved."""
+    n = 10
+    psi = f32_round(random_state(n, 8)) if dtype == qs.QS_C64 else random_state(n, 8)
+    U = random_unitary(5, 9)
+    ref = psi.copy()
+    sim.apply_kq(ref, [1, 3, 4, 7, 9], U)
+    with State(n, dtype) as s:
+        assert qs.qs_selftest_timeout(s.h) == qs.QS_ETIMEOUT
+        qs.qs_synchronize(s.h)                       # cleared: no error now
+        qs.qs_set_amplitudes(s.h, psi)
+        qs.qs_set_path(s.h, qs.QS_PATH_TENSOR)
+        qs.qs_apply_cluster(s.h, [1, 3, 4, 7, 9], U)
+        qs.qs_synchronize(s.h)
+        got = qs.qs_get_amplitudes(s.h)
+    assert np.max(np.abs(got - ref)) <= SWEEP_TOL[dtype]
+
+
 def test_init_states():
     for n in (1, 7, 15):
         with State(n, qs.QS_C128) as s:
