@@ -23,6 +23,21 @@ follow:
     its qubits); the largest wins (ties: fewer qubits, then the lower seed);
     its gates are removed from the queues; repeat until no gate is left.
 
+With commute_diagonal the same rule runs on a relaxed order.  Diagonal gates
+commute (their matrices are diagonal), so on a qubit a diagonal gate may run
+before earlier unassigned gates of that qubit when all of them are diagonal; a
+non-diagonal gate keeps its place:
+
+  * available(g, q): every unassigned gate before g on q is diagonal and g is
+    diagonal, or no unassigned gate precedes g on q; ready(g): available on
+    each of its qubits;
+  * closure(S): sweep the qubits of S in ascending order; on each, walk its
+    unassigned gates in order: take a gate that acts only on S and is ready,
+    pass over a diagonal gate that is not taken, stop at a non-diagonal one;
+    repeat sweeps until one takes nothing;
+  * growth candidates (and seeds): per qubit, its first unassigned gate (not
+    yet in the cluster), if ready; the rest as above.
+
 A cluster made only of diagonal gates (T, T^dagger, CZ) becomes a phase op;
 neighbouring phase ops in the op list are merged (diagonal gates commute).
 With fuse=False every gate is an op of its own (the plain gate-by-gate form).
@@ -113,6 +128,93 @@ def clusters(n, gates, k_max):
     return out
 
 
+def clusters_commuting(n, gates, k_max):
+    """Greedy clusters when diagonal gates may pass one another on a qubit."""
+    assert k_max >= 2
+    gqs = [tuple(qs) for (_, _, qs) in gates]
+    diag = [name in _gates.DIAGONAL for (_, name, _) in gates]
+    queues = [[] for _ in range(n)]
+    for i, qs in enumerate(gqs):
+        for q in qs:
+            queues[q].append(i)
+    done = set()
+
+    def available(g, q, taken):
+        for h in queues[q]:
+            if h == g:
+                return True
+            if h in done or h in taken:
+                continue
+            if not (diag[h] and diag[g]):
+                return False
+        return False
+
+    def ready(g, taken):
+        return all(available(g, q, taken) for q in gqs[g])
+
+    def closure(S):
+        taken, order = set(), []
+        changed = True
+        while changed:
+            changed = False
+            for q in sorted(S):
+                for g in queues[q]:
+                    if g in done or g in taken:
+                        continue
+                    if not set(gqs[g]) <= S:
+                        if not diag[g]:
+                            break
+                        continue
+                    if ready(g, taken):
+                        taken.add(g)
+                        order.append(g)
+                        changed = True
+                    elif not diag[g]:
+                        break
+        return order
+
+    def candidates(members):
+        taken = set(members)
+        out = set()
+        for q in range(n):
+            for g in queues[q]:
+                if g in done or g in taken:
+                    continue
+                if ready(g, taken):
+                    out.add(g)
+                break
+        return sorted(out)
+
+    def grow(seed):
+        S = set(gqs[seed])
+        members = closure(S)
+        while True:
+            best = None
+            for g in candidates(members):
+                qs = set(gqs[g])
+                if qs <= S or len(S | qs) > k_max:
+                    continue
+                m2 = closure(S | qs)
+                key = (len(m2), -len(S | qs), -g)
+                if best is None or key > best[0]:
+                    best = (key, S | qs, m2)
+            if best is None or len(best[2]) <= len(members):
+                return members, S
+            _, S, members = best
+
+    out = []
+    while len(done) < len(gates):
+        best, best_key = None, None
+        for s in candidates([]):
+            members, S = grow(s)
+            key = (len(members), -len(S), -s)
+            if best_key is None or key > best_key:
+                best, best_key = members, key
+        done.update(best)
+        out.append(best)
+    return out
+
+
 def cluster_unitary(gates, members, qubits):
     """Product of the member gates embedded in the 2^k space of `qubits`."""
     k = len(qubits)
@@ -142,11 +244,11 @@ def _phase_op(n, gates, members):
             "coeff": coeff % 8, "edges": edges}
 
 
-def schedule(n, gates, k_max=5, fuse=True):
+def schedule(n, gates, k_max=5, fuse=True, commute_diagonal=True):
     """Op list: dicts with kind 'dense' (qubits, gates, matrix) or 'phase'
     (qubits, gates, coeff, edges)."""
     if fuse:
-        groups = clusters(n, gates, k_max)
+        groups = clusters_commuting(n, gates, k_max) if commute_diagonal else clusters(n, gates, k_max)
     else:
         groups = [[i] for i in range(len(gates))]
     ops = []

@@ -256,6 +256,173 @@ void make_phase(int n, const std::vector<qs_gate> &g, const std::vector<int> &me
         if ((support >> q) & 1) op.qubits[j++] = q;
 }
 
+// The same greedy closure rule with diagonal gates free to pass one another:
+// on a qubit, a gate may run before earlier unassigned gates of that qubit
+// when it and all of them are diagonal (diagonal matrices commute, so the
+// product is unchanged); a non-diagonal gate keeps its place.
+//   available(g, q): every unassigned gate before g on q is diagonal, and so
+//                    is g (or none precedes it);
+//   ready(g):        available on each of its qubits;
+//   closure(S):      sweeps over the qubits of S, ascending; on each, the
+//                    unassigned gates in order: take a gate that acts only on
+//                    S and is ready, pass over a diagonal gate that is not
+//                    taken, stop at a non-diagonal one; repeat until a sweep
+//                    takes nothing;
+//   candidates:      per qubit, its first unassigned gate, if ready;
+//   seeds, growth and ties as in Clusterer.
+struct DiagClusterer {
+    int n;
+    const std::vector<qs_gate> &g;
+    std::vector<std::vector<int>> queue;   // per qubit, gate indices in order
+    std::vector<uint64_t> gmask;
+    std::vector<char> diag, done;
+    std::vector<int> first;                // per qubit: first gate of queue not done
+    mutable std::vector<int> mark;         // gates taken by the closure being built
+    mutable int stamp = 0;
+
+    DiagClusterer(int n_, const std::vector<qs_gate> &gates)
+        : n(n_), g(gates), queue(n_), gmask(gates.size()), diag(gates.size()), done(gates.size(), 0),
+          first(n_, 0), mark(gates.size(), 0)
+    {
+        for (size_t i = 0; i < g.size(); i++) {
+            gmask[i] = 1ULL << g[i].q0;
+            queue[g[i].q0].push_back((int)i);
+            if (g[i].q1 >= 0) {
+                gmask[i] |= 1ULL << g[i].q1;
+                queue[g[i].q1].push_back((int)i);
+            }
+            diag[i] = is_diagonal(g[i].kind);
+        }
+    }
+
+    bool taken(int gi) const { return done[gi] || mark[gi] == stamp; }
+
+    bool available(int q, int gi) const
+    {
+        for (size_t i = first[q]; i < queue[q].size(); i++) {
+            const int h = queue[q][i];
+            if (h == gi) return true;
+            if (taken(h)) continue;
+            if (!(diag[h] && diag[gi])) return false;
+        }
+        return false;
+    }
+
+    bool ready(int gi) const
+    {
+        for (uint64_t m = gmask[gi]; m; m &= m - 1)
+            if (!available(__builtin_ctzll(m), gi)) return false;
+        return true;
+    }
+
+    void closure(uint64_t S, std::vector<int> &members) const
+    {
+        ++stamp;
+        members.clear();
+        bool changed = true;
+        while (changed) {
+            changed = false;
+            for (int q = 0; q < n; q++) {
+                if (!((S >> q) & 1)) continue;
+                for (size_t i = first[q]; i < queue[q].size(); i++) {
+                    const int gi = queue[q][i];
+                    if (taken(gi)) continue;
+                    if (gmask[gi] & ~S) {
+                        if (!diag[gi]) break;
+                        continue;
+                    }
+                    if (ready(gi)) {
+                        mark[gi] = stamp;
+                        members.push_back(gi);
+                        changed = true;
+                    } else if (!diag[gi]) {
+                        break;
+                    }
+                }
+            }
+        }
+    }
+
+    // per qubit, its first gate not done and not in `members`, if ready
+    std::vector<int> candidates(const std::vector<int> &members) const
+    {
+        ++stamp;
+        for (int gi : members) mark[gi] = stamp;
+        std::vector<int> c;
+        for (int q = 0; q < n; q++)
+            for (size_t i = first[q]; i < queue[q].size(); i++) {
+                const int gi = queue[q][i];
+                if (taken(gi)) continue;
+                if (ready(gi)) c.push_back(gi);
+                break;
+            }
+        std::sort(c.begin(), c.end());
+        c.erase(std::unique(c.begin(), c.end()), c.end());
+        return c;
+    }
+
+    void grow(int seed, int k_max, std::vector<int> &members, uint64_t &S) const
+    {
+        S = gmask[seed];
+        closure(S, members);
+        std::vector<int> m2, best_m;
+        for (;;) {
+            bool have = false;
+            int best_len = 0, best_bits = 0, best_g = 0;
+            uint64_t best_S = 0;
+            for (int gi : candidates(members)) {
+                const uint64_t qs = gmask[gi];
+                if (!(qs & ~S)) continue;
+                const uint64_t S2 = S | qs;
+                const int bits = __builtin_popcountll(S2);
+                if (bits > k_max) continue;
+                closure(S2, m2);
+                const int len = (int)m2.size();
+                const bool better = !have || len > best_len ||
+                                    (len == best_len && (bits < best_bits || (bits == best_bits && gi < best_g)));
+                if (better) {
+                    have = true;
+                    best_len = len; best_bits = bits; best_g = gi; best_S = S2;
+                    best_m = m2;
+                }
+            }
+            if (!have || best_len <= (int)members.size()) break;
+            S = best_S;
+            members = best_m;
+        }
+    }
+
+    std::vector<std::vector<int>> run(int k_max)
+    {
+        size_t remaining = g.size();
+        std::vector<std::vector<int>> out;
+        std::vector<int> members;
+        while (remaining) {
+            bool have = false;
+            std::vector<int> best;
+            int best_len = 0, best_bits = 0, best_s = 0;
+            for (int sd : candidates({})) {
+                uint64_t S;
+                grow(sd, k_max, members, S);
+                const int len = (int)members.size(), bits = __builtin_popcountll(S);
+                const bool better = !have || len > best_len ||
+                                    (len == best_len && (bits < best_bits || (bits == best_bits && sd < best_s)));
+                if (better) {
+                    have = true;
+                    best_len = len; best_bits = bits; best_s = sd;
+                    best = members;
+                }
+            }
+            for (int gi : best) done[gi] = 1;
+            for (int q = 0; q < n; q++)
+                while (first[q] < (int)queue[q].size() && done[queue[q][first[q]]]) first[q]++;
+            remaining -= best.size();
+            out.push_back(best);
+        }
+        return out;
+    }
+};
+
 void make_dense(const std::vector<qs_gate> &g, const std::vector<int> &members, qs_op_host &op)
 {
     op.kind = QS_OP_DENSE;
@@ -371,7 +538,10 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
     for (int i = 0; i < n_gates; i++)
         if (!check_gate(n, g[i])) return qs_fail(QS_EINVAL, "qs_schedule_build: bad gate %d", i);
     std::vector<std::vector<int>> groups;
-    if (opts->fuse) {
+    if (opts->fuse && opts->commute_diagonal) {
+        DiagClusterer cl(n, g);
+        groups = cl.run(opts->k_max);
+    } else if (opts->fuse) {
         Clusterer cl(n, g);
         groups = cl.run(opts->k_max);
     } else {

@@ -299,10 +299,40 @@ def test_clusters_partition_and_respect_kmax(k_max):
 
 
 @pytest.mark.parametrize("k_max", [2, 3, 4, 5])
-def test_fused_schedule_equals_gate_by_gate(k_max):
+def test_commuting_clusters_keep_every_non_diagonal_gate_in_place(k_max):
+    """With diagonal gates free to pass one another, the clusters still cover
+    every gate once within k_max qubits, and on every qubit each non-diagonal
+    gate is applied after all earlier gates of that qubit and before all later
+    ones (only runs of diagonal gates are reordered)."""
+    n, gates = circuit.supremacy_circuit(4, 5, 20, seed=1)
+    cl = schedule.clusters_commuting(n, gates, k_max)
+    flat = sorted(g for c in cl for g in c)
+    assert flat == list(range(len(gates)))
+    when = {}
+    for ci, c in enumerate(cl):
+        assert len(set(q for g in c for q in gates[g][2])) <= k_max
+        for i, g in enumerate(c):
+            when[g] = (ci, i)
+    reordered = False
+    for q in range(n):
+        seq = [i for i, (_, _, qs) in enumerate(gates) if q in qs]
+        for j, h in enumerate(seq):
+            if gates[h][1] in G.DIAGONAL:
+                continue
+            assert all(when[a] < when[h] for a in seq[:j])
+            assert all(when[b] > when[h] for b in seq[j + 1:])
+        reordered = reordered or [when[g] for g in seq] != sorted(when[g] for g in seq)
+    assert reordered                       # the relaxation is used on this circuit
+    if k_max >= 4:                         # where it pays: fewer clusters (greedy is not monotone below)
+        assert len(cl) < len(schedule.clusters(n, gates, k_max))
+
+
+@pytest.mark.parametrize("commute", [False, True])
+@pytest.mark.parametrize("k_max", [2, 3, 4, 5])
+def test_fused_schedule_equals_gate_by_gate(k_max, commute):
     n, gates = circuit.supremacy_circuit(4, 4, 12, seed=4)
     ref = sim.run_circuit(n, gates)
-    ops = schedule.schedule(n, gates, k_max=k_max)
+    ops = schedule.schedule(n, gates, k_max=k_max, commute_diagonal=commute)
     for op in ops:
         if op["kind"] == "dense":
             U = op["matrix"]
