@@ -12,6 +12,7 @@ With --gpus N > 1 (under torchrun) every rank simulates its own circuits
 (replicas; no data exchange between GPUs).
 """
 import argparse
+import concurrent.futures
 import json
 import os
 import statistics
@@ -194,9 +195,18 @@ def run_ours(args):
     def on_tensor_cores(kind, k):
         return kind == "dense" and n >= 5 and ((dtype == qs.QS_C64 and k >= 4) or (dtype == qs.QS_C128 and k >= 2))
 
-    def one_step(seed, record):
+    # a1-a3 run on the host; the next step's are prepared in a second thread
+    # while the GPU runs this one (ctypes releases the GIL in library calls)
+    prep_pool = concurrent.futures.ThreadPoolExecutor(max_workers=1)
+
+    def prepare(seed):
         nq, gates = qs.qs_supremacy_circuit(rows, cols, cycles, seed, removed=removed)       # a1
-        sc = qs.qs_schedule_build(nq, gates, k_max=k_max, fuse=not args.plain)                # a2, a3
+        return qs.qs_schedule_build(nq, gates, k_max=k_max, fuse=not args.plain)              # a2, a3
+
+    def one_step(prepared, next_seed, record):
+        """Runs the prepared schedule; returns (stats, ops, next prepared)."""
+        sc = prepared.result()
+        nxt = prep_pool.submit(prepare, next_seed)
         try:
             qs.qs_init_basis(h, 0)
             op_ms = qs.qs_run_circuit_timed(h, sc)                                            # a4-a6
@@ -222,13 +232,16 @@ def run_ours(args):
                     else:
                         partial_ms.append(float(op_ms[i]))
                 launches[0] += ran + 1 + 2 + fills
-            return st, len(op_ms)
+            return st, len(op_ms), nxt
         finally:
             qs.qs_schedule_free(sc)
 
-    seeds = [rank * 1000 + s for s in range(args.warmup + args.steps)]
-    for s in seeds[:args.warmup]:
-        one_step(s, False)
+    # one seed more than steps: the last timed step prepares one more schedule,
+    # so the timed region holds as many preparations as steps
+    seeds = [rank * 1000 + s for s in range(args.warmup + args.steps + 1)]
+    prepared = prep_pool.submit(prepare, seeds[0])
+    for i in range(args.warmup):
+        _, _, prepared = one_step(prepared, seeds[i + 1], False)
     torch.cuda.synchronize()
     barrier(dist)
     torch.cuda.synchronize()
@@ -238,11 +251,13 @@ def run_ours(args):
         ev0.record(stream)
         t0 = time.perf_counter()
         stats = None
-        for s in seeds[args.warmup:]:
-            stats, nops = one_step(s, True)
+        for i in range(args.warmup, args.warmup + args.steps):
+            stats, nops, prepared = one_step(prepared, seeds[i + 1], True)
+        qs.qs_schedule_free(prepared.result())
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+    prep_pool.shutdown()
     barrier(dist)
     dev_s = ev0.elapsed_time(ev1) / 1e3
     elapsed = max_over_ranks(dist, max(dev_s, wall))
@@ -291,7 +306,7 @@ def run_ours(args):
     # plain gate-by-gate form of the same circuit (the comparison of the metric)
     plain = None
     if not args.plain and not args.no_plain and rank == 0:
-        nq, gates = qs.qs_supremacy_circuit(rows, cols, cycles, seeds[-1], removed=removed)
+        nq, gates = qs.qs_supremacy_circuit(rows, cols, cycles, seeds[args.warmup + args.steps - 1], removed=removed)
         sc = qs.qs_schedule_build(nq, gates, fuse=False)
         try:
             qs.qs_init_basis(h, 0)
