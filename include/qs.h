@@ -244,6 +244,15 @@ typedef struct {
                                    * (30-qubit 5x6 depth 25: 28-29 dense clusters at
                                    * k_max 5 instead of 36).  0: every qubit keeps its
                                    * gate order (the paper's rule, Sec. 3.6). */
+    int32_t search_runs;          /* with commute_diagonal: 0 or 1, the greedy rule
+                                   * alone; R > 1, the best of R runs, the first the
+                                   * greedy rule and the others choosing cluster j
+                                   * as option SplitMix64(0x5EEDC105 + r, j) mod m
+                                   * of the m clusters within one gate of the
+                                   * largest (ordered as the greedy rule ranks
+                                   * them); the fewest dense clusters win, then the
+                                   * fewest clusters, then the lower r.  Runs go on
+                                   * host threads. */
 } qs_sched_opts;
 
 /* Build a schedule for an n-qubit gate list.  With fuse, gates are packed into

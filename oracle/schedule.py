@@ -36,7 +36,13 @@ non-diagonal gate keeps its place:
     pass over a diagonal gate that is not taken, stop at a non-diagonal one;
     repeat sweeps until one takes nothing;
   * growth candidates (and seeds): per qubit, its first unassigned gate (not
-    yet in the cluster), if ready; the rest as above.
+    yet in the cluster), if ready; the rest as above;
+  * search (search_runs R > 1): run 0 is the rule above; in run r >= 1 the
+    clusters grown from all seeds are ranked as the rule ranks them (more
+    gates, then fewer qubits, then the lower seed), and cluster j of the run
+    is the one at position SplitMix64(SEARCH_SEED + r, j) mod m among the m
+    within one gate of the largest; the run with the fewest dense clusters is
+    kept (then the fewest clusters, then the lowest r).
 
 A cluster made only of diagonal gates (T, T^dagger, CZ) becomes a phase op;
 neighbouring phase ops in the op list are merged (diagonal gates commute).
@@ -49,6 +55,7 @@ pre-permutes the matrix to sorted qubit order).
 """
 import numpy as np
 
+from . import circuit as _circuit
 from . import gates as _gates
 from . import sim as _sim
 
@@ -128,8 +135,25 @@ def clusters(n, gates, k_max):
     return out
 
 
-def clusters_commuting(n, gates, k_max):
-    """Greedy clusters when diagonal gates may pass one another on a qubit."""
+SEARCH_SEED = 0x5EEDC105
+
+
+def clusters_commuting(n, gates, k_max, search_runs=1):
+    """Clusters when diagonal gates may pass one another on a qubit: the best
+    of search_runs runs (run 0 the greedy rule)."""
+    def cost(cl):
+        dense = sum(1 for c in cl if not all(gates[g][1] in _gates.DIAGONAL for g in c))
+        return dense, len(cl)
+
+    best = None
+    for r in range(max(1, search_runs)):
+        cl = _commuting_run(n, gates, k_max, None if r == 0 else SEARCH_SEED + r)
+        if best is None or cost(cl) < cost(best):
+            best = cl
+    return best
+
+
+def _commuting_run(n, gates, k_max, rseed):
     assert k_max >= 2
     gqs = [tuple(qs) for (_, _, qs) in gates]
     diag = [name in _gates.DIAGONAL for (_, name, _) in gates]
@@ -204,12 +228,16 @@ def clusters_commuting(n, gates, k_max):
 
     out = []
     while len(done) < len(gates):
-        best, best_key = None, None
+        options = []
         for s in candidates([]):
             members, S = grow(s)
-            key = (len(members), -len(S), -s)
-            if best_key is None or key > best_key:
-                best, best_key = members, key
+            options.append(((len(members), -len(S), -s), members))
+        options.sort(key=lambda o: o[0], reverse=True)
+        pick = 0
+        if rseed is not None:
+            m = sum(1 for key, _ in options if key[0] >= options[0][0][0] - 1)
+            pick = _circuit.splitmix64(rseed, len(out)) % m
+        best = options[pick][1]
         done.update(best)
         out.append(best)
     return out
@@ -244,11 +272,12 @@ def _phase_op(n, gates, members):
             "coeff": coeff % 8, "edges": edges}
 
 
-def schedule(n, gates, k_max=5, fuse=True, commute_diagonal=True):
+def schedule(n, gates, k_max=5, fuse=True, commute_diagonal=True, search_runs=1):
     """Op list: dicts with kind 'dense' (qubits, gates, matrix) or 'phase'
     (qubits, gates, coeff, edges)."""
     if fuse:
-        groups = clusters_commuting(n, gates, k_max) if commute_diagonal else clusters(n, gates, k_max)
+        groups = (clusters_commuting(n, gates, k_max, search_runs) if commute_diagonal
+                  else clusters(n, gates, k_max))
     else:
         groups = [[i] for i in range(len(gates))]
     ops = []

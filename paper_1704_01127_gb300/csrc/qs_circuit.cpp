@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <set>
+#include <thread>
 #include <vector>
 
 #include "qs_internal.h"
@@ -256,6 +257,9 @@ void make_phase(int n, const std::vector<qs_gate> &g, const std::vector<int> &me
         if ((support >> q) & 1) op.qubits[j++] = q;
 }
 
+// seed of the randomized clustering runs (run r uses kSearchSeed + r)
+constexpr uint64_t kSearchSeed = 0x5EEDC105ULL;
+
 // The same greedy closure rule with diagonal gates free to pass one another:
 // on a qubit, a gate may run before earlier unassigned gates of that qubit
 // when it and all of them are diagonal (diagonal matrices commute, so the
@@ -392,27 +396,40 @@ struct DiagClusterer {
         }
     }
 
-    std::vector<std::vector<int>> run(int k_max)
+    // randomized = false: the greedy rule (the cluster with the most gates,
+    // then fewer qubits, then the lower seed).  randomized: cluster j of the
+    // run is option splitmix64(rseed, j) mod m of the m clusters within one
+    // gate of the largest, in that same order.
+    std::vector<std::vector<int>> run(int k_max, bool randomized = false, uint64_t rseed = 0)
     {
+        struct Opt {
+            int len, bits, seed;
+            std::vector<int> members;
+        };
         size_t remaining = g.size();
         std::vector<std::vector<int>> out;
         std::vector<int> members;
+        uint64_t step = 0;
         while (remaining) {
-            bool have = false;
-            std::vector<int> best;
-            int best_len = 0, best_bits = 0, best_s = 0;
+            std::vector<Opt> opts;
             for (int sd : candidates({})) {
                 uint64_t S;
                 grow(sd, k_max, members, S);
-                const int len = (int)members.size(), bits = __builtin_popcountll(S);
-                const bool better = !have || len > best_len ||
-                                    (len == best_len && (bits < best_bits || (bits == best_bits && sd < best_s)));
-                if (better) {
-                    have = true;
-                    best_len = len; best_bits = bits; best_s = sd;
-                    best = members;
-                }
+                opts.push_back({(int)members.size(), __builtin_popcountll(S), sd, members});
             }
+            std::sort(opts.begin(), opts.end(), [](const Opt &a, const Opt &b) {
+                if (a.len != b.len) return a.len > b.len;
+                if (a.bits != b.bits) return a.bits < b.bits;
+                return a.seed < b.seed;
+            });
+            size_t pick = 0;
+            if (randomized) {
+                size_t m = 0;
+                while (m < opts.size() && opts[m].len >= opts[0].len - 1) m++;
+                pick = (size_t)(splitmix64(rseed, step) % m);
+            }
+            step++;
+            const std::vector<int> &best = opts[pick].members;
             for (int gi : best) done[gi] = 1;
             for (int q = 0; q < n; q++)
                 while (first[q] < (int)queue[q].size() && done[queue[q][first[q]]]) first[q]++;
@@ -539,8 +556,38 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
         if (!check_gate(n, g[i])) return qs_fail(QS_EINVAL, "qs_schedule_build: bad gate %d", i);
     std::vector<std::vector<int>> groups;
     if (opts->fuse && opts->commute_diagonal) {
-        DiagClusterer cl(n, g);
-        groups = cl.run(opts->k_max);
+        // run 0: the greedy rule; runs 1..R-1 pick at random among near-best
+        // clusters.  The runs are independent and go on host threads.
+        const int runs = std::max(1, (int)opts->search_runs);
+        std::vector<std::vector<std::vector<int>>> res(runs);
+        auto one = [&](int r) {
+            DiagClusterer cl(n, g);
+            res[r] = cl.run(opts->k_max, r > 0, kSearchSeed + (uint64_t)r);
+        };
+        std::vector<std::thread> pool;
+        for (int r = 1; r < runs; r++) pool.emplace_back(one, r);
+        one(0);
+        for (auto &t : pool) t.join();
+        // sweeps cost time, phase ops little: fewest dense clusters, then
+        // fewest clusters, then the lowest r
+        auto dense_count = [&](const std::vector<std::vector<int>> &cl) {
+            int d = 0;
+            for (const auto &c : cl) {
+                bool diag = true;
+                for (int gi : c) diag = diag && is_diagonal(g[gi].kind);
+                d += !diag;
+            }
+            return d;
+        };
+        int best = 0, best_dense = dense_count(res[0]);
+        for (int r = 1; r < runs; r++) {
+            const int d = dense_count(res[r]);
+            if (d < best_dense || (d == best_dense && res[r].size() < res[best].size())) {
+                best = r;
+                best_dense = d;
+            }
+        }
+        groups = std::move(res[best]);
     } else if (opts->fuse) {
         Clusterer cl(n, g);
         groups = cl.run(opts->k_max);

@@ -62,8 +62,8 @@ def _lib_ops(n, gates, **kw):
 def test_schedule_bit_exact_with_oracle(grid, depth, seed, k_max, commute):
     n, g = qs.qs_supremacy_circuit(grid[0], grid[1], depth, seed)
     tuples = qs.gates_to_tuples(g)
-    lib_ops = _lib_ops(n, g, k_max=k_max, commute_diagonal=commute)
-    or_ops = schedule.schedule(n, tuples, k_max=k_max, commute_diagonal=commute)
+    lib_ops = _lib_ops(n, g, k_max=k_max, commute_diagonal=commute, search_runs=1)
+    or_ops = schedule.schedule(n, tuples, k_max=k_max, commute_diagonal=commute, search_runs=1)
     assert len(lib_ops) == len(or_ops)
     for a, b in zip(lib_ops, or_ops):
         assert a["kind"] == b["kind"]
@@ -74,6 +74,18 @@ def test_schedule_bit_exact_with_oracle(grid, depth, seed, k_max, commute):
         else:
             assert list(a["coeff"]) == list(b["coeff"])
             assert a["edges"] == [tuple(e) for e in b["edges"]]
+
+
+@pytest.mark.parametrize("grid,depth,seed,k_max", [((5, 6), 25, 0, 5), ((4, 5), 20, 3, 4)])
+def test_schedule_search_bit_exact_with_oracle(grid, depth, seed, k_max):
+    """The best of 8 clustering runs (threads in the library, one after another
+    in the oracle): the same clusters, never more than the greedy rule's."""
+    n, g = qs.qs_supremacy_circuit(grid[0], grid[1], depth, seed)
+    tuples = qs.gates_to_tuples(g)
+    lib_ops = _lib_ops(n, g, k_max=k_max, search_runs=8)
+    or_ops = schedule.schedule(n, tuples, k_max=k_max, search_runs=8)
+    assert [op["gates"] for op in lib_ops] == [tuple(op["gates"]) for op in or_ops]
+    assert len(lib_ops) <= len(_lib_ops(n, g, k_max=k_max, search_runs=1))
 
 
 @pytest.mark.parametrize("grid,depth,seed", [((5, 6), 25, 1), ((4, 8), 25, 1), ((4, 4), 10, 0), ((3, 11), 40, 2)])
