@@ -244,8 +244,8 @@ typedef struct {
                                    * (30-qubit 5x6 depth 25: 28-29 dense clusters at
                                    * k_max 5 instead of 36).  0: every qubit keeps its
                                    * gate order (the paper's rule, Sec. 3.6). */
-    int32_t search_runs;          /* with commute_diagonal: 0 or 1, the greedy rule
-                                   * alone; R > 1, the best of R runs, the first the
+    int32_t search_runs;          /* 0..64; with commute_diagonal: 0 or 1, the greedy
+                                   * rule alone; R > 1, the best of R runs, the first the
                                    * greedy rule and the others choosing cluster j
                                    * as option SplitMix64(0x5EEDC105 + r, j) mod m
                                    * of the m clusters within one gate of the

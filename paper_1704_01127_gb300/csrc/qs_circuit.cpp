@@ -259,6 +259,7 @@ void make_phase(int n, const std::vector<qs_gate> &g, const std::vector<int> &me
 
 // seed of the randomized clustering runs (run r uses kSearchSeed + r)
 constexpr uint64_t kSearchSeed = 0x5EEDC105ULL;
+constexpr int kMaxSearchRuns = 64;
 
 // The same greedy closure rule with diagonal gates free to pass one another:
 // on a qubit, a gate may run before earlier unassigned gates of that qubit
@@ -551,6 +552,9 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
         return qs_fail(QS_EINVAL, "qs_schedule_build: bad arguments");
     if (opts->fuse && (opts->k_max < 2 || opts->k_max > QS_MAX_K))
         return qs_fail(QS_EINVAL, "qs_schedule_build: k_max %d not in [2, %d]", opts->k_max, QS_MAX_K);
+    if (opts->search_runs < 0 || opts->search_runs > kMaxSearchRuns)
+        return qs_fail(QS_EINVAL, "qs_schedule_build: search_runs %d not in [0, %d]", opts->search_runs,
+                       kMaxSearchRuns);
     std::vector<qs_gate> g(gates, gates + n_gates);
     for (int i = 0; i < n_gates; i++)
         if (!check_gate(n, g[i])) return qs_fail(QS_EINVAL, "qs_schedule_build: bad gate %d", i);
@@ -560,14 +564,27 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
         // clusters.  The runs are independent and go on host threads.
         const int runs = std::max(1, (int)opts->search_runs);
         std::vector<std::vector<std::vector<int>>> res(runs);
+        std::vector<char> failed(runs, 0);
         auto one = [&](int r) {
-            DiagClusterer cl(n, g);
-            res[r] = cl.run(opts->k_max, r > 0, kSearchSeed + (uint64_t)r);
+            try {
+                DiagClusterer cl(n, g);
+                res[r] = cl.run(opts->k_max, r > 0, kSearchSeed + (uint64_t)r);
+            } catch (...) {
+                failed[r] = 1;                 // out of host memory
+            }
         };
         std::vector<std::thread> pool;
-        for (int r = 1; r < runs; r++) pool.emplace_back(one, r);
+        for (int r = 1; r < runs; r++) {
+            try {
+                pool.emplace_back(one, r);
+            } catch (...) {
+                one(r);                        // no thread to be had: run it here
+            }
+        }
         one(0);
         for (auto &t : pool) t.join();
+        for (int r = 0; r < runs; r++)
+            if (failed[r]) return qs_fail(QS_ENOMEM, "qs_schedule_build: out of host memory");
         // sweeps cost time, phase ops little: fewest dense clusters, then
         // fewest clusters, then the lowest r
         auto dense_count = [&](const std::vector<std::vector<int>> &cl) {

@@ -129,6 +129,9 @@ def test_schedule_rejects_bad_input():
     n, g = qs.qs_supremacy_circuit(4, 4, 10, 0)
     with pytest.raises(qs.QSError):
         qs.qs_schedule_build(n, g, k_max=6)
+    for runs in (-1, 65):
+        with pytest.raises(qs.QSError):
+            qs.qs_schedule_build(n, g, k_max=5, search_runs=runs)
     bad = g.copy()
     bad[3]["q0"] = 99
     with pytest.raises(qs.QSError):
