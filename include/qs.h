@@ -250,9 +250,15 @@ typedef struct {
                                    * as option SplitMix64(0x5EEDC105 + r, j) mod m
                                    * of the m clusters within one gate of the
                                    * largest (ordered as the greedy rule ranks
-                                   * them); the fewest dense clusters win, then the
-                                   * fewest clusters, then the lower r.  Runs go on
-                                   * host threads. */
+                                   * them).  The run of lowest cost wins, then the
+                                   * fewest clusters, then the lower r; cost = the
+                                   * number of dense clusters, or with
+                                   * search_from_basis each dense cluster weighted by
+                                   * 2^(|support| - n), the support growing by its
+                                   * qubits from none (the sweep sizes after
+                                   * qs_init_basis).  Runs go on host threads. */
+    int32_t search_from_basis;    /* 1: the state will start as a basis state (see
+                                   * search_runs); 0: any state. */
 } qs_sched_opts;
 
 /* Build a schedule for an n-qubit gate list.  With fuse, gates are packed into

@@ -41,8 +41,11 @@ non-diagonal gate keeps its place:
     clusters grown from all seeds are ranked as the rule ranks them (more
     gates, then fewer qubits, then the lower seed), and cluster j of the run
     is the one at position SplitMix64(SEARCH_SEED + r, j) mod m among the m
-    within one gate of the largest; the run with the fewest dense clusters is
-    kept (then the fewest clusters, then the lowest r).
+    within one gate of the largest; the run of lowest cost is kept (then the
+    fewest clusters, then the lowest r), the cost being its number of dense
+    clusters or, with from_basis, the sum over its dense clusters of
+    2^(|support| - n), the support growing by each dense cluster's qubits from
+    none (the sizes of the sweeps after a basis state).
 
 A cluster made only of diagonal gates (T, T^dagger, CZ) becomes a phase op;
 neighbouring phase ops in the op list are merged (diagonal gates commute).
@@ -138,12 +141,17 @@ def clusters(n, gates, k_max):
 SEARCH_SEED = 0x5EEDC105
 
 
-def clusters_commuting(n, gates, k_max, search_runs=1):
+def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True):
     """Clusters when diagonal gates may pass one another on a qubit: the best
     of search_runs runs (run 0 the greedy rule)."""
     def cost(cl):
-        dense = sum(1 for c in cl if not all(gates[g][1] in _gates.DIAGONAL for g in c))
-        return dense, len(cl)
+        total, support = 0.0, set()
+        for c in cl:
+            if all(gates[g][1] in _gates.DIAGONAL for g in c):
+                continue
+            support |= set(q for g in c for q in gates[g][2])
+            total += 2.0 ** (len(support) - n) if from_basis else 1.0
+        return total, len(cl)
 
     best = None
     for r in range(max(1, search_runs)):
@@ -272,11 +280,11 @@ def _phase_op(n, gates, members):
             "coeff": coeff % 8, "edges": edges}
 
 
-def schedule(n, gates, k_max=5, fuse=True, commute_diagonal=True, search_runs=1):
+def schedule(n, gates, k_max=5, fuse=True, commute_diagonal=True, search_runs=1, search_from_basis=True):
     """Op list: dicts with kind 'dense' (qubits, gates, matrix) or 'phase'
     (qubits, gates, coeff, edges)."""
     if fuse:
-        groups = (clusters_commuting(n, gates, k_max, search_runs) if commute_diagonal
+        groups = (clusters_commuting(n, gates, k_max, search_runs, search_from_basis) if commute_diagonal
                   else clusters(n, gates, k_max))
     else:
         groups = [[i] for i in range(len(gates))]

@@ -257,6 +257,8 @@ void make_phase(int n, const std::vector<qs_gate> &g, const std::vector<int> &me
         if ((support >> q) & 1) op.qubits[j++] = q;
 }
 
+uint64_t gmask_of(const qs_gate &x) { return (1ULL << x.q0) | (x.q1 >= 0 ? 1ULL << x.q1 : 0ULL); }
+
 // seed of the randomized clustering runs (run r uses kSearchSeed + r)
 constexpr uint64_t kSearchSeed = 0x5EEDC105ULL;
 constexpr int kMaxSearchRuns = 64;
@@ -585,23 +587,34 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
         for (auto &t : pool) t.join();
         for (int r = 0; r < runs; r++)
             if (failed[r]) return qs_fail(QS_ENOMEM, "qs_schedule_build: out of host memory");
-        // sweeps cost time, phase ops little: fewest dense clusters, then
-        // fewest clusters, then the lowest r
-        auto dense_count = [&](const std::vector<std::vector<int>> &cl) {
-            int d = 0;
-            for (const auto &c : cl) {
+        // sweeps cost time, phase ops little.  The cost of a run: its dense
+        // clusters, each weighted by 2^(|support| - n) when the state starts as
+        // a basis state (the support grows by each dense cluster's qubits),
+        // else 1; the lowest cost wins, then fewer clusters, then the lower r.
+        // (Sums of powers of two from 2^-n to 1: exact.)
+        auto cost = [&](const std::vector<std::vector<int>> &cl) {
+            double c = 0.0;
+            uint64_t sup = 0;
+            for (const auto &grp : cl) {
                 bool diag = true;
-                for (int gi : c) diag = diag && is_diagonal(g[gi].kind);
-                d += !diag;
+                uint64_t qs = 0;
+                for (int gi : grp) {
+                    diag = diag && is_diagonal(g[gi].kind);
+                    qs |= gmask_of(g[gi]);
+                }
+                if (diag) continue;
+                sup |= qs;
+                c += opts->search_from_basis ? std::ldexp(1.0, __builtin_popcountll(sup) - n) : 1.0;
             }
-            return d;
+            return c;
         };
-        int best = 0, best_dense = dense_count(res[0]);
+        int best = 0;
+        double best_cost = cost(res[0]);
         for (int r = 1; r < runs; r++) {
-            const int d = dense_count(res[r]);
-            if (d < best_dense || (d == best_dense && res[r].size() < res[best].size())) {
+            const double c = cost(res[r]);
+            if (c < best_cost || (c == best_cost && res[r].size() < res[best].size())) {
                 best = r;
-                best_dense = d;
+                best_cost = c;
             }
         }
         groups = std::move(res[best]);

@@ -76,16 +76,21 @@ def test_schedule_bit_exact_with_oracle(grid, depth, seed, k_max, commute):
             assert a["edges"] == [tuple(e) for e in b["edges"]]
 
 
-@pytest.mark.parametrize("grid,depth,seed,k_max", [((5, 6), 25, 0, 5), ((4, 5), 20, 3, 4)])
-def test_schedule_search_bit_exact_with_oracle(grid, depth, seed, k_max):
+@pytest.mark.parametrize("from_basis", [False, True])
+@pytest.mark.parametrize("grid,depth,seed,k_max", [((5, 6), 25, 4, 5), ((4, 5), 20, 3, 4)])
+def test_schedule_search_bit_exact_with_oracle(grid, depth, seed, k_max, from_basis):
     """The best of 8 clustering runs (threads in the library, one after another
-    in the oracle): the same clusters, never more than the greedy rule's."""
+    in the oracle): the same clusters; by dense-cluster count, never more dense
+    clusters than the greedy rule's."""
     n, g = qs.qs_supremacy_circuit(grid[0], grid[1], depth, seed)
     tuples = qs.gates_to_tuples(g)
-    lib_ops = _lib_ops(n, g, k_max=k_max, search_runs=8)
-    or_ops = schedule.schedule(n, tuples, k_max=k_max, search_runs=8)
+    lib_ops = _lib_ops(n, g, k_max=k_max, search_runs=8, search_from_basis=from_basis)
+    or_ops = schedule.schedule(n, tuples, k_max=k_max, search_runs=8, search_from_basis=from_basis)
     assert [op["gates"] for op in lib_ops] == [tuple(op["gates"]) for op in or_ops]
-    assert len(lib_ops) <= len(_lib_ops(n, g, k_max=k_max, search_runs=1))
+    if not from_basis:
+        def dense(ops):
+            return sum(op["kind"] == "dense" for op in ops)
+        assert dense(lib_ops) <= dense(_lib_ops(n, g, k_max=k_max, search_runs=1))
 
 
 @pytest.mark.parametrize("grid,depth,seed", [((5, 6), 25, 1), ((4, 8), 25, 1), ((4, 4), 10, 0), ((3, 11), 40, 2)])
