@@ -250,7 +250,11 @@ typedef struct {
                                    * as option SplitMix64(0x5EEDC105 + r, j) mod m
                                    * of the m clusters within one gate of the
                                    * largest (ordered as the greedy rule ranks
-                                   * them).  The run of lowest cost wins, then the
+                                   * them), and four more taking, while the dense
+                                   * clusters so far leave some qubit out, the
+                                   * cluster within s = 0..3 gates of the largest
+                                   * that adds the fewest qubits to them.  The
+                                   * run of lowest cost wins, then the
                                    * fewest clusters, then the lower r; cost = the
                                    * number of dense clusters, or with
                                    * search_from_basis each dense cluster weighted by

@@ -41,7 +41,11 @@ non-diagonal gate keeps its place:
     clusters grown from all seeds are ranked as the rule ranks them (more
     gates, then fewer qubits, then the lower seed), and cluster j of the run
     is the one at position SplitMix64(SEARCH_SEED + r, j) mod m among the m
-    within one gate of the largest; the run of lowest cost is kept (then the
+    within one gate of the largest; four more runs (slack s = 0, 1, 2, 3) take,
+    while the dense clusters taken so far do not cover every qubit, the cluster
+    within s gates of the largest that adds the fewest qubits to them (an
+    all-diagonal one adds none; ties: the first in rank), else the first; the
+    run of lowest cost is kept (then the
     fewest clusters, then the lowest r), the cost being its number of dense
     clusters or, with from_basis, the sum over its dense clusters of
     2^(|support| - n), the support growing by each dense cluster's qubits from
@@ -153,15 +157,21 @@ def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True):
             total += 2.0 ** (len(support) - n) if from_basis else 1.0
         return total, len(cl)
 
+    R = max(1, search_runs)
+    runs = [_commuting_run(n, gates, k_max, None if r == 0 else SEARCH_SEED + r) for r in range(R)]
+    if R > 1:
+        runs += [_commuting_run(n, gates, k_max, None, support_slack=sl) for sl in range(SUPPORT_RUNS)]
     best = None
-    for r in range(max(1, search_runs)):
-        cl = _commuting_run(n, gates, k_max, None if r == 0 else SEARCH_SEED + r)
+    for cl in runs:
         if best is None or cost(cl) < cost(best):
             best = cl
     return best
 
 
-def _commuting_run(n, gates, k_max, rseed):
+SUPPORT_RUNS = 4
+
+
+def _commuting_run(n, gates, k_max, rseed, support_slack=None):
     assert k_max >= 2
     gqs = [tuple(qs) for (_, _, qs) in gates]
     diag = [name in _gates.DIAGONAL for (_, name, _) in gates]
@@ -234,17 +244,26 @@ def _commuting_run(n, gates, k_max, rseed):
                 return members, S
             _, S, members = best
 
-    out = []
+    out, support = [], set()
     while len(done) < len(gates):
         options = []
         for s in candidates([]):
             members, S = grow(s)
-            options.append(((len(members), -len(S), -s), members))
+            options.append(((len(members), -len(S), -s), members, S))
         options.sort(key=lambda o: o[0], reverse=True)
+
+        def dense(o):
+            return not all(diag[g] for g in o[1])
+
         pick = 0
         if rseed is not None:
-            m = sum(1 for key, _ in options if key[0] >= options[0][0][0] - 1)
+            m = sum(1 for o in options if o[0][0] >= options[0][0][0] - 1)
             pick = _circuit.splitmix64(rseed, len(out)) % m
+        elif support_slack is not None and len(support) < n:
+            near = [i for i, o in enumerate(options) if o[0][0] >= options[0][0][0] - support_slack]
+            pick = min(near, key=lambda i: (len(options[i][2] - support) if dense(options[i]) else 0, i))
+        if dense(options[pick]):
+            support |= options[pick][2]
         best = options[pick][1]
         done.update(best)
         out.append(best)

@@ -262,6 +262,7 @@ uint64_t gmask_of(const qs_gate &x) { return (1ULL << x.q0) | (x.q1 >= 0 ? 1ULL 
 // seed of the randomized clustering runs (run r uses kSearchSeed + r)
 constexpr uint64_t kSearchSeed = 0x5EEDC105ULL;
 constexpr int kMaxSearchRuns = 64;
+constexpr int kSupportRuns = 4;
 
 // The same greedy closure rule with diagonal gates free to pass one another:
 // on a qubit, a gate may run before earlier unassigned gates of that qubit
@@ -399,16 +400,23 @@ struct DiagClusterer {
         }
     }
 
-    // randomized = false: the greedy rule (the cluster with the most gates,
-    // then fewer qubits, then the lower seed).  randomized: cluster j of the
-    // run is option splitmix64(rseed, j) mod m of the m clusters within one
-    // gate of the largest, in that same order.
-    std::vector<std::vector<int>> run(int k_max, bool randomized = false, uint64_t rseed = 0)
+    // The clusters grown from all seeds, ranked as the greedy rule ranks them
+    // (more gates, then fewer qubits, then the lower seed), and one of them
+    // taken:  kGreedy the first;  kRandom option splitmix64(rseed, j) mod m of
+    // the m within one gate of the largest (j = cluster index);  kSupport,
+    // while the dense clusters taken so far do not cover every qubit, the one
+    // within `slack` gates of the largest that adds the fewest qubits to them
+    // (an all-diagonal one adds none), then the first in rank; else the first.
+    enum Policy { kGreedy, kRandom, kSupport };
+    std::vector<std::vector<int>> run(int k_max, Policy policy = kGreedy, uint64_t rseed = 0, int slack = 0)
     {
         struct Opt {
             int len, bits, seed;
+            uint64_t S;
             std::vector<int> members;
         };
+        const uint64_t all = n >= 64 ? ~0ULL : ((1ULL << n) - 1);
+        uint64_t sup = 0;
         size_t remaining = g.size();
         std::vector<std::vector<int>> out;
         std::vector<int> members;
@@ -418,20 +426,35 @@ struct DiagClusterer {
             for (int sd : candidates({})) {
                 uint64_t S;
                 grow(sd, k_max, members, S);
-                opts.push_back({(int)members.size(), __builtin_popcountll(S), sd, members});
+                opts.push_back({(int)members.size(), __builtin_popcountll(S), sd, S, members});
             }
             std::sort(opts.begin(), opts.end(), [](const Opt &a, const Opt &b) {
                 if (a.len != b.len) return a.len > b.len;
                 if (a.bits != b.bits) return a.bits < b.bits;
                 return a.seed < b.seed;
             });
+            auto dense_opt = [&](const Opt &o) {
+                for (int gi : o.members)
+                    if (!diag[gi]) return true;
+                return false;
+            };
             size_t pick = 0;
-            if (randomized) {
+            if (policy == kRandom) {
                 size_t m = 0;
                 while (m < opts.size() && opts[m].len >= opts[0].len - 1) m++;
                 pick = (size_t)(splitmix64(rseed, step) % m);
+            } else if (policy == kSupport && sup != all) {
+                int best_new = 1 << 30;
+                for (size_t i = 0; i < opts.size() && opts[i].len >= opts[0].len - slack; i++) {
+                    const int added = dense_opt(opts[i]) ? __builtin_popcountll(opts[i].S & ~sup) : 0;
+                    if (added < best_new) {
+                        best_new = added;
+                        pick = i;
+                    }
+                }
             }
             step++;
+            if (dense_opt(opts[pick])) sup |= opts[pick].S;
             const std::vector<int> &best = opts[pick].members;
             for (int gi : best) done[gi] = 1;
             for (int q = 0; q < n; q++)
@@ -564,13 +587,18 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
     if (opts->fuse && opts->commute_diagonal) {
         // run 0: the greedy rule; runs 1..R-1 pick at random among near-best
         // clusters.  The runs are independent and go on host threads.
-        const int runs = std::max(1, (int)opts->search_runs);
+        // runs 0..R-1: greedy, then random; with R > 1 also kSupportRuns
+        // support-aware runs (slack 0, 1, ...)
+        const int R = std::max(1, (int)opts->search_runs);
+        const int runs = R > 1 ? R + kSupportRuns : 1;
         std::vector<std::vector<std::vector<int>>> res(runs);
         std::vector<char> failed(runs, 0);
         auto one = [&](int r) {
             try {
                 DiagClusterer cl(n, g);
-                res[r] = cl.run(opts->k_max, r > 0, kSearchSeed + (uint64_t)r);
+                if (r == 0) res[r] = cl.run(opts->k_max);
+                else if (r < R) res[r] = cl.run(opts->k_max, DiagClusterer::kRandom, kSearchSeed + (uint64_t)r);
+                else res[r] = cl.run(opts->k_max, DiagClusterer::kSupport, 0, r - R);
             } catch (...) {
                 failed[r] = 1;                 // out of host memory
             }
