@@ -245,22 +245,19 @@ typedef struct {
                                    * k_max 5 instead of 36).  0: every qubit keeps its
                                    * gate order (the paper's rule, Sec. 3.6). */
     int32_t search_runs;          /* 0..64; with commute_diagonal: 0 or 1, the greedy
-                                   * rule alone; R > 1, the best of R runs, the first the
-                                   * greedy rule and the others choosing cluster j
-                                   * as option SplitMix64(0x5EEDC105 + r, j) mod m
-                                   * of the m clusters within one gate of the
-                                   * largest (ordered as the greedy rule ranks
-                                   * them), and four more taking, while the dense
-                                   * clusters so far leave some qubit out, the
-                                   * cluster within s = 0..3 gates of the largest
-                                   * that adds the fewest qubits to them.  The
-                                   * run of lowest cost wins, then the
-                                   * fewest clusters, then the lower r; cost = the
-                                   * number of dense clusters, or with
-                                   * search_from_basis each dense cluster weighted by
-                                   * 2^(|support| - n), the support growing by its
-                                   * qubits from none (the sweep sizes after
-                                   * qs_init_basis).  Runs go on host threads. */
+                                   * rule alone; R > 1, the best of R runs: run 0
+                                   * the greedy rule, run s >= 1 choosing, while the
+                                   * dense clusters taken so far leave some qubit
+                                   * out, among the clusters within s - 1 gates of
+                                   * the largest the one adding the fewest qubits
+                                   * to them (then the greedy rank).  The run of
+                                   * lowest cost wins, then the fewest clusters,
+                                   * then the lower r; cost = the number of dense
+                                   * clusters, or with search_from_basis each dense
+                                   * cluster weighted by 2^(|support| - n), the
+                                   * support growing by its qubits from none (the
+                                   * sweep sizes after qs_init_basis).  Runs go on
+                                   * host threads. */
     int32_t search_from_basis;    /* 1: the state will start as a basis state (see
                                    * search_runs); 0: any state. */
 } qs_sched_opts;

@@ -37,17 +37,14 @@ non-diagonal gate keeps its place:
     repeat sweeps until one takes nothing;
   * growth candidates (and seeds): per qubit, its first unassigned gate (not
     yet in the cluster), if ready; the rest as above;
-  * search (search_runs R > 1): run 0 is the rule above; in run r >= 1 the
-    clusters grown from all seeds are ranked as the rule ranks them (more
-    gates, then fewer qubits, then the lower seed), and cluster j of the run
-    is the one at position SplitMix64(SEARCH_SEED + r, j) mod m among the m
-    within one gate of the largest; four more runs (slack s = 0, 1, 2, 3) take,
-    while the dense clusters taken so far do not cover every qubit, the cluster
-    within s gates of the largest that adds the fewest qubits to them (an
-    all-diagonal one adds none; ties: the first in rank), else the first; the
-    run of lowest cost is kept (then the
-    fewest clusters, then the lowest r), the cost being its number of dense
-    clusters or, with from_basis, the sum over its dense clusters of
+  * search (search_runs R > 1): run 0 is the rule above; run s >= 1 takes,
+    while the dense clusters taken so far do not cover every qubit, among the
+    clusters grown from all seeds (ranked as the rule ranks them: more gates,
+    then fewer qubits, then the lower seed) within s - 1 gates of the largest
+    the one adding the fewest qubits to them (an all-diagonal one adds none;
+    ties: the first in rank), else the first; the run of lowest cost is kept
+    (then the fewest clusters, then the lowest r), the cost being its number
+    of dense clusters or, with from_basis, the sum over its dense clusters of
     2^(|support| - n), the support growing by each dense cluster's qubits from
     none (the sizes of the sweeps after a basis state).
 
@@ -62,7 +59,6 @@ pre-permutes the matrix to sorted qubit order).
 """
 import numpy as np
 
-from . import circuit as _circuit
 from . import gates as _gates
 from . import sim as _sim
 
@@ -142,9 +138,6 @@ def clusters(n, gates, k_max):
     return out
 
 
-SEARCH_SEED = 0x5EEDC105
-
-
 def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True):
     """Clusters when diagonal gates may pass one another on a qubit: the best
     of search_runs runs (run 0 the greedy rule)."""
@@ -157,10 +150,7 @@ def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True):
             total += 2.0 ** (len(support) - n) if from_basis else 1.0
         return total, len(cl)
 
-    R = max(1, search_runs)
-    runs = [_commuting_run(n, gates, k_max, None if r == 0 else SEARCH_SEED + r) for r in range(R)]
-    if R > 1:
-        runs += [_commuting_run(n, gates, k_max, None, support_slack=sl) for sl in range(SUPPORT_RUNS)]
+    runs = [_commuting_run(n, gates, k_max, None if r == 0 else r - 1) for r in range(max(1, search_runs))]
     best = None
     for cl in runs:
         if best is None or cost(cl) < cost(best):
@@ -168,10 +158,7 @@ def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True):
     return best
 
 
-SUPPORT_RUNS = 4
-
-
-def _commuting_run(n, gates, k_max, rseed, support_slack=None):
+def _commuting_run(n, gates, k_max, support_slack):
     assert k_max >= 2
     gqs = [tuple(qs) for (_, _, qs) in gates]
     diag = [name in _gates.DIAGONAL for (_, name, _) in gates]
@@ -256,10 +243,7 @@ def _commuting_run(n, gates, k_max, rseed, support_slack=None):
             return not all(diag[g] for g in o[1])
 
         pick = 0
-        if rseed is not None:
-            m = sum(1 for o in options if o[0][0] >= options[0][0][0] - 1)
-            pick = _circuit.splitmix64(rseed, len(out)) % m
-        elif support_slack is not None and len(support) < n:
+        if support_slack is not None and len(support) < n:
             near = [i for i, o in enumerate(options) if o[0][0] >= options[0][0][0] - support_slack]
             pick = min(near, key=lambda i: (len(options[i][2] - support) if dense(options[i]) else 0, i))
         if dense(options[pick]):

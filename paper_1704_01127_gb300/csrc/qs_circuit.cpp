@@ -259,10 +259,7 @@ void make_phase(int n, const std::vector<qs_gate> &g, const std::vector<int> &me
 
 uint64_t gmask_of(const qs_gate &x) { return (1ULL << x.q0) | (x.q1 >= 0 ? 1ULL << x.q1 : 0ULL); }
 
-// seed of the randomized clustering runs (run r uses kSearchSeed + r)
-constexpr uint64_t kSearchSeed = 0x5EEDC105ULL;
 constexpr int kMaxSearchRuns = 64;
-constexpr int kSupportRuns = 4;
 
 // The same greedy closure rule with diagonal gates free to pass one another:
 // on a qubit, a gate may run before earlier unassigned gates of that qubit
@@ -402,13 +399,11 @@ struct DiagClusterer {
 
     // The clusters grown from all seeds, ranked as the greedy rule ranks them
     // (more gates, then fewer qubits, then the lower seed), and one of them
-    // taken:  kGreedy the first;  kRandom option splitmix64(rseed, j) mod m of
-    // the m within one gate of the largest (j = cluster index);  kSupport,
-    // while the dense clusters taken so far do not cover every qubit, the one
-    // within `slack` gates of the largest that adds the fewest qubits to them
-    // (an all-diagonal one adds none), then the first in rank; else the first.
-    enum Policy { kGreedy, kRandom, kSupport };
-    std::vector<std::vector<int>> run(int k_max, Policy policy = kGreedy, uint64_t rseed = 0, int slack = 0)
+    // taken: with slack < 0 the first; else, while the dense clusters taken so
+    // far do not cover every qubit, the one within `slack` gates of the
+    // largest that adds the fewest qubits to them (an all-diagonal one adds
+    // none), then the first in rank; once they do, the first.
+    std::vector<std::vector<int>> run(int k_max, int slack = -1)
     {
         struct Opt {
             int len, bits, seed;
@@ -420,7 +415,6 @@ struct DiagClusterer {
         size_t remaining = g.size();
         std::vector<std::vector<int>> out;
         std::vector<int> members;
-        uint64_t step = 0;
         while (remaining) {
             std::vector<Opt> opts;
             for (int sd : candidates({})) {
@@ -439,11 +433,7 @@ struct DiagClusterer {
                 return false;
             };
             size_t pick = 0;
-            if (policy == kRandom) {
-                size_t m = 0;
-                while (m < opts.size() && opts[m].len >= opts[0].len - 1) m++;
-                pick = (size_t)(splitmix64(rseed, step) % m);
-            } else if (policy == kSupport && sup != all) {
+            if (slack >= 0 && sup != all) {
                 int best_new = 1 << 30;
                 for (size_t i = 0; i < opts.size() && opts[i].len >= opts[0].len - slack; i++) {
                     const int added = dense_opt(opts[i]) ? __builtin_popcountll(opts[i].S & ~sup) : 0;
@@ -453,7 +443,6 @@ struct DiagClusterer {
                     }
                 }
             }
-            step++;
             if (dense_opt(opts[pick])) sup |= opts[pick].S;
             const std::vector<int> &best = opts[pick].members;
             for (int gi : best) done[gi] = 1;
@@ -585,20 +574,15 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
         if (!check_gate(n, g[i])) return qs_fail(QS_EINVAL, "qs_schedule_build: bad gate %d", i);
     std::vector<std::vector<int>> groups;
     if (opts->fuse && opts->commute_diagonal) {
-        // run 0: the greedy rule; runs 1..R-1 pick at random among near-best
-        // clusters.  The runs are independent and go on host threads.
-        // runs 0..R-1: greedy, then random; with R > 1 also kSupportRuns
-        // support-aware runs (slack 0, 1, ...)
-        const int R = std::max(1, (int)opts->search_runs);
-        const int runs = R > 1 ? R + kSupportRuns : 1;
+        // The runs are independent and go on host threads.
+        // run 0: the greedy rule; run r >= 1: support-aware with slack r - 1
+        const int runs = std::max(1, (int)opts->search_runs);
         std::vector<std::vector<std::vector<int>>> res(runs);
         std::vector<char> failed(runs, 0);
         auto one = [&](int r) {
             try {
                 DiagClusterer cl(n, g);
-                if (r == 0) res[r] = cl.run(opts->k_max);
-                else if (r < R) res[r] = cl.run(opts->k_max, DiagClusterer::kRandom, kSearchSeed + (uint64_t)r);
-                else res[r] = cl.run(opts->k_max, DiagClusterer::kSupport, 0, r - R);
+                res[r] = cl.run(opts->k_max, r - 1);
             } catch (...) {
                 failed[r] = 1;                 // out of host memory
             }

@@ -323,7 +323,7 @@ def gates_to_tuples(gates):
 
 
 def qs_schedule_build(n, gates, k_max=5, fuse=True, merge_phase=True, drop_final_diagonal=False,
-                      commute_diagonal=True, search_runs=32, search_from_basis=True):
+                      commute_diagonal=True, search_runs=17, search_from_basis=True):
     g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
     opts = _SchedOpts(int(k_max), int(bool(fuse)), int(bool(merge_phase)), int(bool(drop_final_diagonal)),
                       int(bool(commute_diagonal)), int(search_runs), int(bool(search_from_basis)))
