@@ -6,6 +6,7 @@
 #include <cstring>
 #include <set>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "qs_internal.h"
@@ -284,6 +285,8 @@ struct DiagClusterer {
     std::vector<int> first;                // per qubit: first gate of queue not done
     mutable std::vector<int> mark;         // gates taken by the closure being built
     mutable int stamp = 0;
+    // closures of this step (the gates done do not change within a step)
+    mutable std::unordered_map<uint64_t, std::vector<int>> memo;
 
     DiagClusterer(int n_, const std::vector<qs_gate> &gates)
         : n(n_), g(gates), queue(n_), gmask(gates.size()), diag(gates.size()), done(gates.size(), 0),
@@ -322,6 +325,11 @@ struct DiagClusterer {
 
     void closure(uint64_t S, std::vector<int> &members) const
     {
+        auto hit = memo.find(S);
+        if (hit != memo.end()) {
+            members = hit->second;
+            return;
+        }
         ++stamp;
         members.clear();
         bool changed = true;
@@ -346,6 +354,7 @@ struct DiagClusterer {
                 }
             }
         }
+        memo.emplace(S, members);
     }
 
     // per qubit, its first gate not done and not in `members`, if ready
@@ -446,6 +455,7 @@ struct DiagClusterer {
             if (dense_opt(opts[pick])) sup |= opts[pick].S;
             const std::vector<int> &best = opts[pick].members;
             for (int gi : best) done[gi] = 1;
+            memo.clear();
             for (int q = 0; q < n; q++)
                 while (first[q] < (int)queue[q].size() && done[queue[q][first[q]]]) first[q]++;
             remaining -= best.size();
