@@ -257,9 +257,17 @@ typedef struct {
                                    * cluster weighted by 2^(|support| - n), the
                                    * support growing by its qubits from none (the
                                    * sweep sizes after qs_init_basis).  Runs go on
-                                   * host threads. */
+                                   * host threads (at most 32). */
     int32_t search_from_basis;    /* 1: the state will start as a basis state (see
                                    * search_runs); 0: any state. */
+    int32_t search_first;         /* 0..16; 0 or 1: each run takes its first cluster
+                                   * by its own rule; F > 1: each of the R runs is
+                                   * made F times, the f-th time (f = 1..F-1) with
+                                   * its first cluster the one of rank f among the
+                                   * clusters grown from all seeds (the last one
+                                   * when there are fewer) -- where the support
+                                   * starts; R x F runs compete as above, run index
+                                   * f * R + r. */
 } qs_sched_opts;
 
 /* Build a schedule for an n-qubit gate list.  With fuse, gates are packed into

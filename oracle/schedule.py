@@ -46,7 +46,10 @@ non-diagonal gate keeps its place:
     (then the fewest clusters, then the lowest r), the cost being its number
     of dense clusters or, with from_basis, the sum over its dense clusters of
     2^(|support| - n), the support growing by each dense cluster's qubits from
-    none (the sizes of the sweeps after a basis state).
+    none (the sizes of the sweeps after a basis state);
+  * where the support starts (search_first F > 1): each of the R runs is also
+    made with its first cluster the one of rank f = 1..F-1 among those grown
+    from all seeds (the last one when there are fewer); run f * R + r.
 
 A cluster made only of diagonal gates (T, T^dagger, CZ) becomes a phase op;
 neighbouring phase ops in the op list are merged (diagonal gates commute).
@@ -138,9 +141,9 @@ def clusters(n, gates, k_max):
     return out
 
 
-def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True):
+def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True, search_first=1):
     """Clusters when diagonal gates may pass one another on a qubit: the best
-    of search_runs runs (run 0 the greedy rule)."""
+    of search_runs x search_first runs (run 0 the greedy rule)."""
     def cost(cl):
         total, support = 0.0, set()
         for c in cl:
@@ -150,7 +153,9 @@ def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True):
             total += 2.0 ** (len(support) - n) if from_basis else 1.0
         return total, len(cl)
 
-    runs = [_commuting_run(n, gates, k_max, None if r == 0 else r - 1) for r in range(max(1, search_runs))]
+    R = max(1, search_runs)
+    runs = [_commuting_run(n, gates, k_max, None if r == 0 else r - 1, f)
+            for f in range(max(1, search_first)) for r in range(R)]
     best = None
     for cl in runs:
         if best is None or cost(cl) < cost(best):
@@ -158,7 +163,7 @@ def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True):
     return best
 
 
-def _commuting_run(n, gates, k_max, support_slack):
+def _commuting_run(n, gates, k_max, support_slack, first_pick=0):
     assert k_max >= 2
     gqs = [tuple(qs) for (_, _, qs) in gates]
     diag = [name in _gates.DIAGONAL for (_, name, _) in gates]
@@ -243,7 +248,9 @@ def _commuting_run(n, gates, k_max, support_slack):
             return not all(diag[g] for g in o[1])
 
         pick = 0
-        if support_slack is not None and len(support) < n:
+        if not out and first_pick > 0:
+            pick = min(first_pick, len(options) - 1)
+        elif support_slack is not None and len(support) < n:
             near = [i for i, o in enumerate(options) if o[0][0] >= options[0][0][0] - support_slack]
             pick = min(near, key=lambda i: (len(options[i][2] - support) if dense(options[i]) else 0, i))
         if dense(options[pick]):
@@ -283,11 +290,13 @@ def _phase_op(n, gates, members):
             "coeff": coeff % 8, "edges": edges}
 
 
-def schedule(n, gates, k_max=5, fuse=True, commute_diagonal=True, search_runs=1, search_from_basis=True):
+def schedule(n, gates, k_max=5, fuse=True, commute_diagonal=True, search_runs=1, search_from_basis=True,
+             search_first=1):
     """Op list: dicts with kind 'dense' (qubits, gates, matrix) or 'phase'
     (qubits, gates, coeff, edges)."""
     if fuse:
-        groups = (clusters_commuting(n, gates, k_max, search_runs, search_from_basis) if commute_diagonal
+        groups = (clusters_commuting(n, gates, k_max, search_runs, search_from_basis, search_first)
+                  if commute_diagonal
                   else clusters(n, gates, k_max))
     else:
         groups = [[i] for i in range(len(gates))]

@@ -2,6 +2,7 @@
 // greedy gate clustering (Sec. 3.6, step 2), FP64 cluster unitaries in sorted
 // qubit order (Sec. 3.2) and diagonal phase ops (Sec. 3.5).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <set>
@@ -261,6 +262,8 @@ void make_phase(int n, const std::vector<qs_gate> &g, const std::vector<int> &me
 uint64_t gmask_of(const qs_gate &x) { return (1ULL << x.q0) | (x.q1 >= 0 ? 1ULL << x.q1 : 0ULL); }
 
 constexpr int kMaxSearchRuns = 64;
+constexpr int kMaxSearchFirst = 16;
+constexpr int kMaxSearchThreads = 32;
 
 // The same greedy closure rule with diagonal gates free to pass one another:
 // on a qubit, a gate may run before earlier unassigned gates of that qubit
@@ -285,7 +288,7 @@ struct DiagClusterer {
     std::vector<int> first;                // per qubit: first gate of queue not done
     mutable std::vector<int> mark;         // gates taken by the closure being built
     mutable int stamp = 0;
-    // closures of this step (the gates done do not change within a step)
+    // closures by qubit set; a step drops those that read a queue it changed
     mutable std::unordered_map<uint64_t, std::vector<int>> memo;
 
     DiagClusterer(int n_, const std::vector<qs_gate> &gates)
@@ -323,20 +326,20 @@ struct DiagClusterer {
         return true;
     }
 
-    void closure(uint64_t S, std::vector<int> &members) const
+    // the closure of S, held in the memo (its nodes stay in place while the
+    // map grows, so the reference lasts until the step drops entries)
+    const std::vector<int> &closure(uint64_t S) const
     {
         auto hit = memo.find(S);
-        if (hit != memo.end()) {
-            members = hit->second;
-            return;
-        }
+        if (hit != memo.end()) return hit->second;
         ++stamp;
-        members.clear();
+        std::vector<int> members;
+        members.reserve(32);
         bool changed = true;
         while (changed) {
             changed = false;
-            for (int q = 0; q < n; q++) {
-                if (!((S >> q) & 1)) continue;
+            for (uint64_t m = S; m; m &= m - 1) {
+                const int q = __builtin_ctzll(m);
                 for (size_t i = first[q]; i < queue[q].size(); i++) {
                     const int gi = queue[q][i];
                     if (taken(gi)) continue;
@@ -354,7 +357,7 @@ struct DiagClusterer {
                 }
             }
         }
-        memo.emplace(S, members);
+        return memo.emplace(S, std::move(members)).first->second;
     }
 
     // per qubit, its first gate not done and not in `members`, if ready
@@ -378,32 +381,31 @@ struct DiagClusterer {
     void grow(int seed, int k_max, std::vector<int> &members, uint64_t &S) const
     {
         S = gmask[seed];
-        closure(S, members);
-        std::vector<int> m2, best_m;
+        const std::vector<int> *cur = &closure(S);
         for (;;) {
-            bool have = false;
+            const std::vector<int> *best_m = nullptr;
             int best_len = 0, best_bits = 0, best_g = 0;
             uint64_t best_S = 0;
-            for (int gi : candidates(members)) {
+            for (int gi : candidates(*cur)) {
                 const uint64_t qs = gmask[gi];
                 if (!(qs & ~S)) continue;
                 const uint64_t S2 = S | qs;
                 const int bits = __builtin_popcountll(S2);
                 if (bits > k_max) continue;
-                closure(S2, m2);
+                const std::vector<int> &m2 = closure(S2);
                 const int len = (int)m2.size();
-                const bool better = !have || len > best_len ||
+                const bool better = !best_m || len > best_len ||
                                     (len == best_len && (bits < best_bits || (bits == best_bits && gi < best_g)));
                 if (better) {
-                    have = true;
                     best_len = len; best_bits = bits; best_g = gi; best_S = S2;
-                    best_m = m2;
+                    best_m = &m2;
                 }
             }
-            if (!have || best_len <= (int)members.size()) break;
+            if (!best_m || best_len <= (int)cur->size()) break;
             S = best_S;
-            members = best_m;
+            cur = best_m;
         }
+        members = *cur;
     }
 
     // The clusters grown from all seeds, ranked as the greedy rule ranks them
@@ -411,8 +413,10 @@ struct DiagClusterer {
     // taken: with slack < 0 the first; else, while the dense clusters taken so
     // far do not cover every qubit, the one within `slack` gates of the
     // largest that adds the fewest qubits to them (an all-diagonal one adds
-    // none), then the first in rank; once they do, the first.
-    std::vector<std::vector<int>> run(int k_max, int slack = -1)
+    // none), then the first in rank; once they do, the first.  With
+    // first_pick > 0 the first cluster of the run is instead the one of that
+    // rank (the last one when there are fewer).
+    std::vector<std::vector<int>> run(int k_max, int slack = -1, int first_pick = 0)
     {
         struct Opt {
             int len, bits, seed;
@@ -442,7 +446,9 @@ struct DiagClusterer {
                 return false;
             };
             size_t pick = 0;
-            if (slack >= 0 && sup != all) {
+            if (out.empty() && first_pick > 0) {
+                pick = std::min((size_t)first_pick, opts.size() - 1);
+            } else if (slack >= 0 && sup != all) {
                 int best_new = 1 << 30;
                 for (size_t i = 0; i < opts.size() && opts[i].len >= opts[0].len - slack; i++) {
                     const int added = dense_opt(opts[i]) ? __builtin_popcountll(opts[i].S & ~sup) : 0;
@@ -455,7 +461,11 @@ struct DiagClusterer {
             if (dense_opt(opts[pick])) sup |= opts[pick].S;
             const std::vector<int> &best = opts[pick].members;
             for (int gi : best) done[gi] = 1;
-            memo.clear();
+            // a closure on S reads only the queues of S's qubits: those that
+            // miss the qubits of the cluster taken stay as they are
+            const uint64_t hit = opts[pick].S;
+            for (auto it = memo.begin(); it != memo.end();)
+                it = (it->first & hit) ? memo.erase(it) : std::next(it);
             for (int q = 0; q < n; q++)
                 while (first[q] < (int)queue[q].size() && done[queue[q][first[q]]]) first[q]++;
             remaining -= best.size();
@@ -579,40 +589,51 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
     if (opts->search_runs < 0 || opts->search_runs > kMaxSearchRuns)
         return qs_fail(QS_EINVAL, "qs_schedule_build: search_runs %d not in [0, %d]", opts->search_runs,
                        kMaxSearchRuns);
+    if (opts->search_first < 0 || opts->search_first > kMaxSearchFirst)
+        return qs_fail(QS_EINVAL, "qs_schedule_build: search_first %d not in [0, %d]", opts->search_first,
+                       kMaxSearchFirst);
     std::vector<qs_gate> g(gates, gates + n_gates);
     for (int i = 0; i < n_gates; i++)
         if (!check_gate(n, g[i])) return qs_fail(QS_EINVAL, "qs_schedule_build: bad gate %d", i);
     std::vector<std::vector<int>> groups;
     if (opts->fuse && opts->commute_diagonal) {
-        // The runs are independent and go on host threads.
-        // run 0: the greedy rule; run r >= 1: support-aware with slack r - 1
-        const int runs = std::max(1, (int)opts->search_runs);
+        // Run i = f * R + r: rule r (0: greedy; r >= 1: support-aware with
+        // slack r - 1) with its first cluster forced to rank f (f = 0: the
+        // rule's own).  The runs are independent; a few host threads take
+        // them in turn.
+        const int R = std::max(1, (int)opts->search_runs);
+        const int runs = R * std::max(1, (int)opts->search_first);
         std::vector<std::vector<std::vector<int>>> res(runs);
         std::vector<char> failed(runs, 0);
-        auto one = [&](int r) {
-            try {
-                DiagClusterer cl(n, g);
-                res[r] = cl.run(opts->k_max, r - 1);
-            } catch (...) {
-                failed[r] = 1;                 // out of host memory
+        std::atomic<int> next{0};
+        auto worker = [&]() {
+            for (int i = next++; i < runs; i = next++) {
+                try {
+                    DiagClusterer cl(n, g);
+                    res[i] = cl.run(opts->k_max, i % R - 1, i / R);
+                } catch (...) {
+                    failed[i] = 1;             // out of host memory
+                }
             }
         };
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        const int n_threads = std::min(runs, std::min(hw, kMaxSearchThreads));
         std::vector<std::thread> pool;
-        for (int r = 1; r < runs; r++) {
+        for (int t = 1; t < n_threads; t++) {
             try {
-                pool.emplace_back(one, r);
+                pool.emplace_back(worker);
             } catch (...) {
-                one(r);                        // no thread to be had: run it here
+                break;                         // no thread to be had: fewer workers
             }
         }
-        one(0);
+        worker();
         for (auto &t : pool) t.join();
-        for (int r = 0; r < runs; r++)
-            if (failed[r]) return qs_fail(QS_ENOMEM, "qs_schedule_build: out of host memory");
+        for (int i = 0; i < runs; i++)
+            if (failed[i]) return qs_fail(QS_ENOMEM, "qs_schedule_build: out of host memory");
         // sweeps cost time, phase ops little.  The cost of a run: its dense
         // clusters, each weighted by 2^(|support| - n) when the state starts as
         // a basis state (the support grows by each dense cluster's qubits),
-        // else 1; the lowest cost wins, then fewer clusters, then the lower r.
+        // else 1; the lowest cost wins, then fewer clusters, then the lower i.
         // (Sums of powers of two from 2^-n to 1: exact.)
         auto cost = [&](const std::vector<std::vector<int>> &cl) {
             double c = 0.0;
@@ -632,10 +653,10 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
         };
         int best = 0;
         double best_cost = cost(res[0]);
-        for (int r = 1; r < runs; r++) {
-            const double c = cost(res[r]);
-            if (c < best_cost || (c == best_cost && res[r].size() < res[best].size())) {
-                best = r;
+        for (int i = 1; i < runs; i++) {
+            const double c = cost(res[i]);
+            if (c < best_cost || (c == best_cost && res[i].size() < res[best].size())) {
+                best = i;
                 best_cost = c;
             }
         }

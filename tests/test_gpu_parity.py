@@ -213,13 +213,13 @@ def test_drop_final_diagonal_keeps_the_distribution(dtype):
     n, g = qs.qs_supremacy_circuit(4, 5, 25, 3)
     ref = sim.run_circuit(n, qs.gates_to_tuples(g))
     # the greedy clustering of this circuit ends with a phase op
-    sc = qs.qs_schedule_build(n, g, k_max=5, search_runs=1)
+    sc = qs.qs_schedule_build(n, g, k_max=5, search_runs=1, search_first=1)
     try:
         last = qs.qs_schedule_op(sc, qs.qs_schedule_num_ops(sc) - 1)["kind"]
     finally:
         qs.qs_schedule_free(sc)
     assert last == "phase"
-    psi, st, p = run_lib(n, g, dtype, k_max=5, drop_final_diagonal=True, search_runs=1)
+    psi, st, p = run_lib(n, g, dtype, k_max=5, drop_final_diagonal=True, search_runs=1, search_first=1)
     assert np.max(np.abs(np.abs(psi) - np.abs(ref))) <= TOL[dtype]
     assert np.max(np.abs(psi - ref)) > 1e-3           # the phases did change
     np.testing.assert_allclose(p, sim.probabilities(ref), rtol=0, atol=1e-13 if dtype == qs.QS_C128 else 1e-7)

@@ -62,7 +62,7 @@ def _lib_ops(n, gates, **kw):
 def test_schedule_bit_exact_with_oracle(grid, depth, seed, k_max, commute):
     n, g = qs.qs_supremacy_circuit(grid[0], grid[1], depth, seed)
     tuples = qs.gates_to_tuples(g)
-    lib_ops = _lib_ops(n, g, k_max=k_max, commute_diagonal=commute, search_runs=1)
+    lib_ops = _lib_ops(n, g, k_max=k_max, commute_diagonal=commute, search_runs=1, search_first=1)
     or_ops = schedule.schedule(n, tuples, k_max=k_max, commute_diagonal=commute, search_runs=1)
     assert len(lib_ops) == len(or_ops)
     for a, b in zip(lib_ops, or_ops):
@@ -76,21 +76,23 @@ def test_schedule_bit_exact_with_oracle(grid, depth, seed, k_max, commute):
             assert a["edges"] == [tuple(e) for e in b["edges"]]
 
 
-@pytest.mark.parametrize("from_basis", [False, True])
+@pytest.mark.parametrize("from_basis,first", [(False, 1), (True, 1), (True, 3)])
 @pytest.mark.parametrize("grid,depth,seed,k_max", [((5, 6), 25, 4, 5), ((4, 5), 20, 3, 4)])
-def test_schedule_search_bit_exact_with_oracle(grid, depth, seed, k_max, from_basis):
-    """The best of 8 clustering runs (threads in the library, one after another
-    in the oracle): the same clusters; by dense-cluster count, never more dense
-    clusters than the greedy rule's."""
+def test_schedule_search_bit_exact_with_oracle(grid, depth, seed, k_max, from_basis, first):
+    """The best of 8 clustering runs, or of 8 x 3 with the first cluster of
+    rank 0, 1 or 2 (threads in the library, one after another in the oracle):
+    the same clusters; by dense-cluster count, never more dense clusters than
+    the greedy rule's."""
     n, g = qs.qs_supremacy_circuit(grid[0], grid[1], depth, seed)
     tuples = qs.gates_to_tuples(g)
-    lib_ops = _lib_ops(n, g, k_max=k_max, search_runs=8, search_from_basis=from_basis)
-    or_ops = schedule.schedule(n, tuples, k_max=k_max, search_runs=8, search_from_basis=from_basis)
+    lib_ops = _lib_ops(n, g, k_max=k_max, search_runs=8, search_from_basis=from_basis, search_first=first)
+    or_ops = schedule.schedule(n, tuples, k_max=k_max, search_runs=8, search_from_basis=from_basis,
+                               search_first=first)
     assert [op["gates"] for op in lib_ops] == [tuple(op["gates"]) for op in or_ops]
     if not from_basis:
         def dense(ops):
             return sum(op["kind"] == "dense" for op in ops)
-        assert dense(lib_ops) <= dense(_lib_ops(n, g, k_max=k_max, search_runs=1))
+        assert dense(lib_ops) <= dense(_lib_ops(n, g, k_max=k_max, search_runs=1, search_first=1))
 
 
 @pytest.mark.parametrize("grid,depth,seed", [((5, 6), 25, 1), ((4, 8), 25, 1), ((4, 4), 10, 0), ((3, 11), 40, 2)])
@@ -137,6 +139,9 @@ def test_schedule_rejects_bad_input():
     for runs in (-1, 65):
         with pytest.raises(qs.QSError):
             qs.qs_schedule_build(n, g, k_max=5, search_runs=runs)
+    for first in (-1, 17):
+        with pytest.raises(qs.QSError):
+            qs.qs_schedule_build(n, g, k_max=5, search_first=first)
     bad = g.copy()
     bad[3]["q0"] = 99
     with pytest.raises(qs.QSError):

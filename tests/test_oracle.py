@@ -309,18 +309,23 @@ def _basis_cost(n, gates, cl):
     return total
 
 
-@pytest.mark.parametrize("k_max,runs", [(2, 1), (3, 1), (4, 1), (5, 1), (5, 17)])
-def test_commuting_clusters_keep_every_non_diagonal_gate_in_place(k_max, runs):
+@pytest.mark.parametrize("k_max,runs,first", [(2, 1, 1), (3, 1, 1), (4, 1, 1), (5, 1, 1), (5, 17, 1),
+                                               (5, 5, 4)])
+def test_commuting_clusters_keep_every_non_diagonal_gate_in_place(k_max, runs, first):
     """With diagonal gates free to pass one another, the clusters still cover
     every gate once within k_max qubits, and on every qubit each non-diagonal
     gate is applied after all earlier gates of that qubit and before all later
-    ones (only runs of diagonal gates are reordered); the search of 17 runs
-    costs no more from |0...0> than the greedy rule alone."""
+    ones (only runs of diagonal gates are reordered); a search costs no more
+    from |0...0> than the greedy rule alone, nor one with more first clusters
+    than the same runs from the rule's own first cluster."""
     n, gates = circuit.supremacy_circuit(4, 5, 20, seed=1)
-    cl = schedule.clusters_commuting(n, gates, k_max, search_runs=runs)
+    cl = schedule.clusters_commuting(n, gates, k_max, search_runs=runs, search_first=first)
     if runs > 1:
         greedy = schedule.clusters_commuting(n, gates, k_max)
         assert _basis_cost(n, gates, cl) <= _basis_cost(n, gates, greedy)
+    if first > 1:
+        narrow = schedule.clusters_commuting(n, gates, k_max, search_runs=runs)
+        assert _basis_cost(n, gates, cl) <= _basis_cost(n, gates, narrow)
     flat = sorted(g for c in cl for g in c)
     assert flat == list(range(len(gates)))
     when = {}
