@@ -270,16 +270,37 @@ __device__ double tree_sum_serial(const T *src, uint64_t start, int len)
     return buf[0];
 }
 
-// One warp per segment of `len` (power of two, >= 32) values.
-template <typename T>
+// The same pairwise tree over LEN values, unrolled: the loads are all issued
+// first and the tree stays in registers (the runtime-length form above keeps
+// its buffer in local memory).
+template <int LEN, typename T>
+__device__ __forceinline__ double tree_sum_fixed(const T *src, uint64_t start)
+{
+    double buf[LEN];
+#pragma unroll
+    for (int i = 0; i < LEN; i++) buf[i] = load_p(src, start + i);
+#pragma unroll
+    for (int w = LEN; w > 1; w >>= 1) {
+#pragma unroll
+        for (int i = 0; i < w / 2; i++) buf[i] = buf[2 * i] + buf[2 * i + 1];
+    }
+    return buf[0];
+}
+
+// One warp per segment of `len` (power of two, >= 32) values; PER > 0: len is
+// 32 PER, summed by the unrolled tree.
+template <typename T, int PER>
 __global__ void k_segment_sums(const T *__restrict__ src, uint64_t nseg, int len, double *__restrict__ out)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const int per = len >> 5;
+    const int per = PER > 0 ? PER : len >> 5;
     for (uint64_t seg = warp; seg < nseg; seg += nwarps) {
-        double v = tree_sum_serial(src, seg * (uint64_t)len + (uint64_t)lane * per, per);
+        const uint64_t start = seg * (uint64_t)len + (uint64_t)lane * per;
+        double v;
+        if constexpr (PER > 0) v = tree_sum_fixed<PER>(src, start);
+        else v = tree_sum_serial(src, start, per);
         for (int o = 1; o < 32; o <<= 1) {
             double w = __shfl_down_sync(0xffffffffu, v, o);
             if ((lane & (2 * o - 1)) == 0) v = v + w;
@@ -400,14 +421,18 @@ int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out)
     cudaStream_t st = (cudaStream_t)s->stream;
     const int sms = sm_count_dev();
     const C *psi = (const C *)s->amp;
-    if (B >= 32)
-        k_segment_sums<C><<<(int)std::min<uint64_t>((nb * 32 + 255) / 256, (uint64_t)sms * 16), 256, 0, st>>>(
-            psi, nb, (int)B, S);
+    const int gb = (int)std::min<uint64_t>((nb * 32 + 255) / 256, (uint64_t)sms * 16);
+    if (B == 1024)
+        k_segment_sums<C, 32><<<gb, 256, 0, st>>>(psi, nb, (int)B, S);
+    else if (B >= 32)
+        k_segment_sums<C, 0><<<gb, 256, 0, st>>>(psi, nb, (int)B, S);
     else
         k_segment_sums_small<C><<<1, 32, 0, st>>>(psi, nb, (int)B, S);
-    if (G >= 32)
-        k_segment_sums<double><<<(int)std::min<uint64_t>((ns * 32 + 255) / 256, (uint64_t)sms * 16), 256, 0, st>>>(
-            S, ns, (int)G, T);
+    const int gs = (int)std::min<uint64_t>((ns * 32 + 255) / 256, (uint64_t)sms * 16);
+    if (G == 1024)
+        k_segment_sums<double, 32><<<gs, 256, 0, st>>>(S, ns, (int)G, T);
+    else if (G >= 32)
+        k_segment_sums<double, 0><<<gs, 256, 0, st>>>(S, ns, (int)G, T);
     else
         k_segment_sums_small<double><<<1, 32, 0, st>>>(S, ns, (int)G, T);
     k_prefix_super<<<1, 1, 0, st>>>(T, ns, Q);

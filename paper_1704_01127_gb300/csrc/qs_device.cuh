@@ -147,10 +147,33 @@ __device__ __forceinline__ double prob(double2 a)
 {
     return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
 }
+// x^2 of a float as a double, exact: the 24-bit significand squared fits in
+// 48 bits, so the product is assembled from integer operations (the same value
+// as the FP64 multiplication of x by itself, without the FP64 pipe, which runs
+// at 1/64 of the FP32 rate on this part).  |x| = m 2^E; m^2 has its leading
+// one at bit t <= 47, so x^2 = 1.f 2^(t + 2E) with f the bits below it; every
+// such square, subnormal x included, is a normal double.
+__device__ __forceinline__ double sq_exact(float x)
+{
+    const uint32_t b = __float_as_uint(x) & 0x7fffffffu;
+    const uint32_t e = b >> 23;
+    if (e == 0xffu) {                                  // inf, nan: the FP64 unit
+        const double d = x;
+        return __dmul_rn(d, d);
+    }
+    const uint32_t m = e ? ((b & 0x7fffffu) | 0x800000u) : b;
+    if (m == 0) return 0.0;
+    const int E = e ? (int)e - 150 : -149;
+    const uint64_t q = (uint64_t)m * m;
+    const int lz = __clzll((long long)q);             // leading one at bit 63 - lz
+    const uint64_t frac = ((q << lz) << 1) >> 12;     // the 52 bits below it
+    const uint64_t bexp = (uint64_t)(63 - lz + 2 * E + 1023);
+    return __longlong_as_double((long long)((bexp << 52) | frac));
+}
+// p = fl(x^2 + y^2) with exact squares: fl(fl(x^2) + fl(y^2)) in FP64.
 __device__ __forceinline__ double prob(float2 a)
 {
-    double x = a.x, y = a.y;
-    return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
+    return __dadd_rn(sq_exact(a.x), sq_exact(a.y));
 }
 
 // Natural logarithm of a positive normal double, table-driven (P. T. P. Tang,

@@ -273,6 +273,34 @@ def test_sampling_bit_exact(dtype, n):
     assert np.array_equal(got, want)
 
 
+def test_c64_probabilities_and_draws_over_every_exponent():
+    """complex64 probabilities build each square from integers (exact, as the
+    FP64 product of the float with itself) and add the two in FP64: bit for bit
+    the FP64 result for floats of every exponent, signed zeros, the smallest
+    and largest subnormals, the smallest normal and the largest finite float;
+    draws from that state are the oracle's."""
+    n = 12
+    g = np.random.default_rng(77)
+    bits = g.integers(0, 1 << 32, size=2 << n, dtype=np.uint64).astype(np.uint32)
+    bits[(bits >> 23 & 0xFF) == 0xFF] &= 0x807FFFFF                 # no inf / nan: exponent 0 instead
+    special = np.array([0.0, -0.0, 1e-45, -1e-45, 1.1754942e-38, 1.1754944e-38, 1.0, -1.0,
+                        0.99999994, 3.4028235e38, -3.4028235e38, 2.0 ** -75, 0.5, 1e-20], dtype=np.float32)
+    bits[:special.size] = special.view(np.uint32)
+    f = bits.view(np.float32).astype(np.float64)
+    psi = f[0::2] + 1j * f[1::2]
+    want = f[0::2] * f[0::2] + f[1::2] * f[1::2]
+    with State(n, qs.QS_C64) as s:
+        qs.qs_set_amplitudes(s.h, psi)
+        got = qs.qs_probabilities(s.h)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+    # the same values normalised (in FP64, then rounded to complex64) for the draws
+    psi = f32_round(psi / np.sqrt(np.sum(want)))
+    with State(n, qs.QS_C64) as s:
+        qs.qs_set_amplitudes(s.h, psi)
+        got = qs.qs_sample(s.h, 99, 4096)
+    assert np.array_equal(got, sim.sample(psi, 99, 4096))
+
+
 @pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
 def test_empty_inputs(dtype):
     """Degenerate calls: a schedule without ops leaves the state as it is (bit
