@@ -342,8 +342,7 @@ def run_ours(args):
             try:
                 qs.qs_init_basis(h, 0)
                 qs.qs_run_circuit(h, sc)              # uploads the schedule's matrices
-                qs.qs_stats(h)
-                qs.qs_sample(h, e2e_seeds[i], m)
+                qs.qs_sample_stats(h, e2e_seeds[i], m)  # statistics and draws, one pass
             finally:
                 qs.qs_schedule_free(sc)
         qs.qs_schedule_free(nxt.result())

@@ -159,6 +159,15 @@ int qs_stats(qs_state *s, double out[4]);
  * sequential across them).  out: m uint64 in host memory.  m >= 0. */
 int qs_sample(qs_state *s, uint64_t seed, int64_t m, uint64_t *out);
 
+/* qs_stats and qs_sample in one call (not in the paper): the same draws, bit
+ * for bit, and the same statistics up to the order of their float-float sums
+ * (relative differences near 1e-15).  For complex64 states of 10 qubits or
+ * more one pass over the state forms both the block sums of the draws and the
+ * statistics; otherwise the statistics take their own pass first.  out: m
+ * uint64 in host memory; stats: 4 host doubles as qs_stats.  Errors as
+ * qs_stats. */
+int qs_sample_stats(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double stats[4]);
+
 /* qs_stats without any allocation.  The paper has no counterpart: this entry
  * exists for callers that may not allocate device memory, for example code that
  * runs while a framework's caching allocator owns the device memory, or code

@@ -113,19 +113,130 @@ __global__ void k_fflog_init() { ff_log_table_init(g_fflog); }
 // range) takes p ln p from the FP64 math library, and complex128 amplitudes of
 // 2^30 or more (unnormalised input) are summed in FP64 throughout; p below the
 // normal double range contributes less than 1e-305 and is left out.
+// Per-thread sums of the statistics; add() takes one amplitude, partials()
+// reduces the block (every thread of the block calls it).
+struct StatsAcc {
+    double d0 = 0, d3 = 0, dent = 0;
+    ff f0{0.f, 0.f}, f3{0.f, 0.f}, fent{0.f, 0.f};
+
+    template <int NSTAT>
+    __device__ __forceinline__ void add(const double2 a, const FFLogTable &lt)
+    {
+        // magnitude tests on the exponent fields (integer compares; FP64
+        // compares would run on the FP64 pipe): field < 1053 is |v| < 2^30,
+        // field >= 963 is |v| >= 2^-60
+        const uint32_t ex = ((uint32_t)__double2hiint(a.x) >> 20) & 0x7FFu;
+        const uint32_t ey = ((uint32_t)__double2hiint(a.y) >> 20) & 0x7FFu;
+        if (ex < 1053u && ey < 1053u) {
+            // x and y as float-float (values below 2^-60 add less than 2^-120
+            // to p and count as zero), p and its sums in float-float
+            const ff x = ex >= 963u ? ff_from_double(a.x) : ff{0.f, 0.f};
+            const ff y = ey >= 963u ? ff_from_double(a.y) : ff{0.f, 0.f};
+            const ff p = ff_add(ff_mul(x, x), ff_mul(y, y));
+            f0 = ff_add(f0, p);
+            if (NSTAT == 4) {
+                f3 = ff_add(f3, ff_mul(p, p));
+                if (p.hi >= 0x1p-79f) {
+                    fent = ff_add(fent, ff_p_ln_p(lt, p));
+                } else if (p.hi > 0.f) {
+                    const double pd = (double)p.hi + (double)p.lo;
+                    if (pd >= 2.2250738585072014e-308) dent += pd * log(pd);
+                }
+            }
+        } else {
+            // an amplitude of 2^30 or more (unnormalised input): FP64 throughout
+            const double p = fma(a.x, a.x, a.y * a.y);
+            d0 += p;
+            if (NSTAT == 4) {
+                d3 = fma(p, p, d3);
+                dent += p * log(p);
+            }
+        }
+    }
+
+    template <int NSTAT>
+    __device__ __forceinline__ void add(const float2 a, const FFLogTable &)
+    {
+        // complex64 amplitudes carry FP32 errors (2^-24 relative): p, p^2
+        // and the logarithm of p are formed in FP32 (one rounding each, the
+        // logarithm a few ulp), and the terms add up in float-float
+        const float p = fmaf(a.x, a.x, __fmul_rn(a.y, a.y));
+        f0 = ff_add_f(f0, p);
+        if (NSTAT == 4) {
+            f3 = ff_add_f(f3, __fmul_rn(p, p));
+            if (p >= 0x1p-79f && p <= 0x1p100f) {
+                fent = ff_add_f(fent, __fmul_rn(p, __logf(p)));
+            } else if (p > 0.f) {
+                const double pd = (double)p;
+                if (pd >= 2.2250738585072014e-308) dent += pd * log(pd);
+            }
+        }
+    }
+
+    // part[blockIdx.x * NSTAT + j]: the block's sums of (p, -p ln p, p, p^2)
+    template <int NSTAT>
+    __device__ void partials(double *__restrict__ part) const
+    {
+        double acc[NSTAT];
+        acc[0] = d0 + ((double)f0.hi + (double)f0.lo);
+        if (NSTAT == 4) {
+            acc[NSTAT > 1 ? 1 : 0] = -(dent + ((double)fent.hi + (double)fent.lo));
+            acc[NSTAT > 2 ? 2 : 0] = acc[0];
+            acc[NSTAT > 3 ? 3 : 0] = d3 + ((double)f3.hi + (double)f3.lo);
+        }
+        __shared__ double red[NSTAT][32];
+#pragma unroll
+        for (int j = 0; j < NSTAT; j++) {
+            double v = acc[j];
+            for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int nw = blockDim.x >> 5;
+#pragma unroll
+            for (int j = 0; j < NSTAT; j++) {
+                double v = threadIdx.x < nw ? red[j][threadIdx.x] : 0.0;
+                for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (threadIdx.x == 0) part[(size_t)blockIdx.x * NSTAT + j] = v;
+            }
+        }
+    }
+};
+
+// The log tables into shared memory (complex128 statistics only).
 template <typename C, int NSTAT>
-__global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *__restrict__ part)
+__device__ __forceinline__ void load_fflog(FFLogTable &lt)
 {
-    constexpr bool c128 = sizeof(C) == 16;
-    __shared__ __align__(16) FFLogTable lt;
-    if (NSTAT == 4 && c128) {
+    if (NSTAT == 4 && sizeof(C) == 16) {
         const uint2 *src = reinterpret_cast<const uint2 *>(&g_fflog);
         uint2 *dst = reinterpret_cast<uint2 *>(&lt);
         for (int i = threadIdx.x; i < (int)(sizeof(FFLogTable) / sizeof(uint2)); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
     }
-    double d0 = 0, d3 = 0, dent = 0;
-    ff f0{0.f, 0.f}, f3{0.f, 0.f}, fent{0.f, 0.f};
+}
+
+// Per-block FP64 partial sums of (p, -p ln p, p, p^2); NSTAT = 1 or 4.  The
+// mean of N p equals the sum of p, and the mean of (N p)^2 is N sum p^2, so
+// the moments cost one product per amplitude; the host applies the factor N.
+// Everything runs in float-float on the FP32 pipe (GB300's FP64 pipe runs at
+// 1/64 of its rate): complex128 amplitudes are split into float-float by bit
+// manipulation (48 of their 53 bits), complex64 ones give p exactly (x^2 and
+// y^2 with their FMA rounding errors).  p, p^2 and p ln p (table-driven log,
+// ff_p_ln_p) are summed per thread in float-float; the rounding errors of
+// those sums are random, about 2^-48 of the partial sum per step, so the
+// total norm of a 30-qubit state carries an error near 1e-15.  p below 2^-79
+// (where the low half of p's float-float form would leave the normal float
+// range) takes p ln p from the FP64 math library, and complex128 amplitudes of
+// 2^30 or more (unnormalised input) are summed in FP64 throughout; p below the
+// normal double range contributes less than 1e-305 and is left out.
+template <typename C, int NSTAT>
+__global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *__restrict__ part)
+{
+    constexpr bool c128 = sizeof(C) == 16;
+    __shared__ __align__(16) FFLogTable lt;
+    load_fflog<C, NSTAT>(lt);
+    StatsAcc acc;
     // each thread loads kAhead amplitudes (block-strided, so every load of a
     // warp is contiguous) before it adds them up: more loads in flight
     constexpr int kAhead = c128 ? 4 : 8;
@@ -138,81 +249,9 @@ __global__ void k_stats_partial(const C *__restrict__ psi, uint64_t N, double *_
             av[k] = i < N ? psi[i] : C{};   // a zero amplitude adds nothing
         }
 #pragma unroll
-        for (int k = 0; k < kAhead; k++) {
-            const C a = av[k];
-            if constexpr (c128) {
-                // magnitude tests on the exponent fields (integer compares; FP64
-                // compares would run on the FP64 pipe): field < 1053 is |v| < 2^30,
-                // field >= 963 is |v| >= 2^-60
-                const uint32_t ex = ((uint32_t)__double2hiint((double)a.x) >> 20) & 0x7FFu;
-                const uint32_t ey = ((uint32_t)__double2hiint((double)a.y) >> 20) & 0x7FFu;
-                if (ex < 1053u && ey < 1053u) {
-                    // x and y as float-float (values below 2^-60 add less than 2^-120
-                    // to p and count as zero), p and its sums in float-float
-                    const ff x = ex >= 963u ? ff_from_double((double)a.x) : ff{0.f, 0.f};
-                    const ff y = ey >= 963u ? ff_from_double((double)a.y) : ff{0.f, 0.f};
-                    const ff p = ff_add(ff_mul(x, x), ff_mul(y, y));
-                    f0 = ff_add(f0, p);
-                    if (NSTAT == 4) {
-                        f3 = ff_add(f3, ff_mul(p, p));
-                        if (p.hi >= 0x1p-79f) {
-                            fent = ff_add(fent, ff_p_ln_p(lt, p));
-                        } else if (p.hi > 0.f) {
-                            const double pd = (double)p.hi + (double)p.lo;
-                            if (pd >= 2.2250738585072014e-308) dent += pd * log(pd);
-                        }
-                    }
-                } else {
-                    // an amplitude of 2^30 or more (unnormalised input): FP64 throughout
-                    const double p = fma((double)a.x, (double)a.x, (double)a.y * (double)a.y);
-                    d0 += p;
-                    if (NSTAT == 4) {
-                        d3 = fma(p, p, d3);
-                        dent += p * log(p);
-                    }
-                }
-            } else {
-                // complex64 amplitudes carry FP32 errors (2^-24 relative): p, p^2
-                // and the logarithm of p are formed in FP32 (one rounding each, the
-                // logarithm a few ulp), and the terms add up in float-float
-                const float p = fmaf((float)a.x, (float)a.x, __fmul_rn((float)a.y, (float)a.y));
-                f0 = ff_add_f(f0, p);
-                if (NSTAT == 4) {
-                    f3 = ff_add_f(f3, __fmul_rn(p, p));
-                    if (p >= 0x1p-79f && p <= 0x1p100f) {
-                        fent = ff_add_f(fent, __fmul_rn(p, __logf(p)));
-                    } else if (p > 0.f) {
-                        const double pd = (double)p;
-                        if (pd >= 2.2250738585072014e-308) dent += pd * log(pd);
-                    }
-                }
-            }
-        }
+        for (int k = 0; k < kAhead; k++) acc.add<NSTAT>(av[k], lt);
     }
-    double acc[NSTAT];
-    acc[0] = d0 + ((double)f0.hi + (double)f0.lo);
-    if (NSTAT == 4) {
-        acc[NSTAT > 1 ? 1 : 0] = -(dent + ((double)fent.hi + (double)fent.lo));
-        acc[NSTAT > 2 ? 2 : 0] = acc[0];
-        acc[NSTAT > 3 ? 3 : 0] = d3 + ((double)f3.hi + (double)f3.lo);
-    }
-    __shared__ double red[NSTAT][32];
-#pragma unroll
-    for (int j = 0; j < NSTAT; j++) {
-        double v = acc[j];
-        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        int nw = blockDim.x >> 5;
-#pragma unroll
-        for (int j = 0; j < NSTAT; j++) {
-            double v = threadIdx.x < nw ? red[j][threadIdx.x] : 0.0;
-            for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (threadIdx.x == 0) part[(size_t)blockIdx.x * NSTAT + j] = v;
-        }
-    }
+    acc.partials<NSTAT>(part);
 }
 
 template <int NSTAT>
@@ -307,6 +346,50 @@ __global__ void k_segment_sums(const T *__restrict__ src, uint64_t nseg, int len
         }
         if (lane == 0) out[seg] = v;
     }
+}
+
+// Block sums of 1024 probabilities, as k_segment_sums<C, 32> (the same tree,
+// built as the values arrive: one pending sum per level, each joined as the
+// left operand of the next), and, from the same loads, the block's partial
+// sums of the statistics as k_stats_partial<C, 4> forms them (in another
+// order).  The block sums use the FP64 unit, the statistics the FP32 one
+// (launched for complex64 states).
+template <typename C>
+__global__ void k_segment_sums_stats(const C *__restrict__ psi, uint64_t nseg, double *__restrict__ out,
+                                     double *__restrict__ part)
+{
+    __shared__ __align__(16) FFLogTable lt;
+    load_fflog<C, 4>(lt);
+    StatsAcc acc;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t seg = warp; seg < nseg; seg += nwarps) {
+        const C *src = psi + seg * 1024 + (uint64_t)lane * 32;
+        double lvl[5];
+        double v = 0.0;
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            const C a = src[i];
+            acc.add<4>(a, lt);
+            v = prob(a);
+            // value i closes the subtrees of the levels where i has a one bit
+#pragma unroll
+            for (int l = 0; l < 5; l++) {
+                if (!((i >> l) & 1)) {
+                    lvl[l] = v;
+                    break;
+                }
+                v = lvl[l] + v;
+            }
+        }
+        for (int o = 1; o < 32; o <<= 1) {
+            double w = __shfl_down_sync(0xffffffffu, v, o);
+            if ((lane & (2 * o - 1)) == 0) v = v + w;
+        }
+        if (lane == 0) out[seg] = v;
+    }
+    acc.partials<4>(part);
 }
 
 // Segments shorter than a warp: one thread per segment.
@@ -406,23 +489,40 @@ int stats_impl(qs_state *s, double *out, int nstat)
     return QS_OK;
 }
 
+// stats (optional): also the statistics of qs_stats.  complex64 states with
+// blocks of 1024 take them from the same pass over the state as the block sums
+// (33.9 ms instead of 7.6 + 29.4 ms for 2^20 draws at 32 qubits); otherwise
+// stats_impl runs first (complex128: the fused pass measured 28.6 ms against
+// 7.2 + 19.7 ms, its FP64 and FP32 work not overlapping).
 template <typename C>
-int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out)
+int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double *stats)
 {
     const uint64_t N = 1ULL << s->n;
     const uint64_t B = std::min<uint64_t>(N, 1024), nb = N / B;
     const uint64_t G = std::min<uint64_t>(nb, 1024), ns = nb / G;
-    size_t bytes = sizeof(double) * (2 * nb + 2 * ns) + sizeof(uint64_t) * (size_t)std::max<int64_t>(m, 1);
+    const int sms = sm_count_dev();
+    const int gb = (int)std::min<uint64_t>((nb * 32 + 255) / 256, (uint64_t)sms * 16);
+    constexpr bool c64 = sizeof(C) == 8;
+    const bool fused = c64 && stats && B == 1024;
+    if (stats && !fused)
+        if (int rc = stats_impl<C>(s, stats, 4)) return rc;
+    cudaStream_t st = (cudaStream_t)s->stream;
+    if (fused)
+        if (int rc = ensure_fflog(st)) return rc;
+    const size_t m_slots = (size_t)std::max<int64_t>(m, 1);
+    size_t bytes = sizeof(double) * (2 * nb + 2 * ns) + sizeof(uint64_t) * m_slots;
+    if (fused) bytes += sizeof(double) * ((size_t)gb * 4 + 4);
     void *scr = nullptr;
     int rc = qs_state_scratch(s, bytes, &scr);
     if (rc) return rc;
     double *S = (double *)scr, *R = S + nb, *T = R + nb, *Q = T + ns;
     uint64_t *dout = (uint64_t *)(Q + ns);
-    cudaStream_t st = (cudaStream_t)s->stream;
-    const int sms = sm_count_dev();
+    double *part = (double *)(dout + m_slots), *res = part + (size_t)gb * 4;
     const C *psi = (const C *)s->amp;
-    const int gb = (int)std::min<uint64_t>((nb * 32 + 255) / 256, (uint64_t)sms * 16);
-    if (B == 1024)
+    if (fused) {
+        if constexpr (c64) k_segment_sums_stats<C><<<gb, 256, 0, st>>>(psi, nb, S, part);
+        k_stats_final<4><<<1, 32, 0, st>>>(part, gb, res);
+    } else if (B == 1024)
         k_segment_sums<C, 32><<<gb, 256, 0, st>>>(psi, nb, (int)B, S);
     else if (B >= 32)
         k_segment_sums<C, 0><<<gb, 256, 0, st>>>(psi, nb, (int)B, S);
@@ -443,7 +543,10 @@ int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out)
     QS_CUDA(cudaGetLastError(), "sampling launch");
     if (m > 0)
         QS_CUDA(cudaMemcpyAsync(out, dout, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, st), "sample copy");
+    if (fused)
+        QS_CUDA(cudaMemcpyAsync(stats, res, sizeof(double) * 4, cudaMemcpyDeviceToHost, st), "stats copy");
     QS_CUDA(cudaStreamSynchronize(st), "sampling sync");
+    if (fused) stats[3] *= (double)N;   // mean of (N p)^2 = N sum p^2
     return QS_OK;
 }
 
@@ -767,7 +870,18 @@ extern "C" int qs_sample(qs_state *s, uint64_t seed, int64_t m, uint64_t *out)
 {
     if (!s || !s->amp || m < 0 || (m > 0 && !out)) return qs_fail(QS_EINVAL, "qs_sample: bad arguments");
     if (int rc = qs_materialize(s)) return rc;
-    return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out) : sample_impl<float2>(s, seed, m, out);
+    return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out, nullptr)
+                               : sample_impl<float2>(s, seed, m, out, nullptr);
+}
+
+extern "C" int qs_sample_stats(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double *stats)
+{
+    if (!s || !s->amp || m < 0 || (m > 0 && !out) || !stats)
+        return qs_fail(QS_EINVAL, "qs_sample_stats: bad arguments");
+    if (int rc = qs_check_status(s)) return rc;
+    if (int rc = qs_materialize(s)) return rc;
+    return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out, stats)
+                               : sample_impl<float2>(s, seed, m, out, stats);
 }
 
 extern "C" int qs_synchronize(qs_state *s)

@@ -69,6 +69,7 @@ _SIGS = {
     "qs_probabilities": ([_VP, _DP, ctypes.c_int], ctypes.c_int),
     "qs_stats": ([_VP, _DP], ctypes.c_int),
     "qs_sample": ([_VP, ctypes.c_uint64, ctypes.c_int64, _U64P], ctypes.c_int),
+    "qs_sample_stats": ([_VP, ctypes.c_uint64, ctypes.c_int64, _U64P, _DP], ctypes.c_int),
     "qs_synchronize": ([_VP], ctypes.c_int),
     "qs_supremacy_circuit": ([ctypes.c_int, ctypes.c_int, _IP, ctypes.c_int, ctypes.c_int,
                               ctypes.c_uint64, _IP, _VP, ctypes.c_int, _IP], ctypes.c_int),
@@ -282,6 +283,14 @@ def qs_sample(h, seed, m):
     out = np.zeros(int(m), dtype=np.uint64)
     _check(lib().qs_sample(h, ctypes.c_uint64(int(seed)), int(m), out.ctypes.data_as(_U64P)))
     return out
+
+
+def qs_sample_stats(h, seed, m):
+    """(draws as qs_sample, statistics as qs_stats) from one pass."""
+    out = np.zeros(int(m), dtype=np.uint64)
+    st = np.zeros(4, dtype=np.float64)
+    _check(lib().qs_sample_stats(h, ctypes.c_uint64(int(seed)), int(m), out.ctypes.data_as(_U64P), _dp(st)))
+    return out, tuple(float(x) for x in st)
 
 
 def qs_synchronize(h):

@@ -302,6 +302,31 @@ def test_c64_probabilities_and_draws_over_every_exponent():
 
 
 @pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+@pytest.mark.parametrize("n", [8, 12, 21])
+def test_sample_stats_in_one_pass(dtype, n):
+    """qs_sample_stats: the draws of qs_sample (and of the oracle) bit for bit;
+    the statistics of qs_stats up to the order of the float-float sums, and the
+    oracle's.  n = 8 has blocks shorter than 1024 (statistics in their own
+    pass), n = 12 one block of 1024 per warp and a single thread block, n = 21
+    many thread blocks."""
+    psi = f32_round(random_state(n, 60 + n)) if dtype == qs.QS_C64 else random_state(n, 60 + n)
+    m = 4096
+    with State(n, dtype) as s:
+        qs.qs_set_amplitudes(s.h, psi)
+        draws, st = qs.qs_sample_stats(s.h, 555 + n, m)
+        alone = qs.qs_sample(s.h, 555 + n, m)
+        st_alone = qs.qs_stats(s.h)
+        assert qs.qs_sample_stats(s.h, 1, 0)[0].size == 0
+    assert np.array_equal(draws, alone)
+    assert np.array_equal(draws, sim.sample(psi, 555 + n, m))
+    # complex64 statistics form p, p^2 and p ln p in FP32 (relative 1e-7)
+    tol_oracle = 1e-10 if dtype == qs.QS_C128 else 1e-6
+    for a, b, c in zip(st, st_alone, sim.stats(psi)):
+        assert abs(a - b) <= 1e-13 * max(1.0, abs(b))
+        assert abs(a - c) <= tol_oracle * max(1.0, abs(c))
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
 def test_empty_inputs(dtype):
     """Degenerate calls: a schedule without ops leaves the state as it is (bit
     for bit), and zero draws return an empty array."""
