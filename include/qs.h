@@ -257,9 +257,10 @@ typedef struct {
                                    * rule alone; R > 1, the best of R runs: run 0
                                    * the greedy rule, run s >= 1 choosing, while the
                                    * dense clusters taken so far leave some qubit
-                                   * out, among the clusters within s - 1 gates of
-                                   * the largest the one adding the fewest qubits
-                                   * to them (then the greedy rank).  The run of
+                                   * out, among the clusters within
+                                   * search_slack0 + s - 1 gates of the largest the
+                                   * one adding the fewest qubits to them (then the
+                                   * greedy rank).  The run of
                                    * lowest cost wins, then the fewest clusters,
                                    * then the lower r; cost = the number of dense
                                    * clusters, or with search_from_basis each dense
@@ -277,6 +278,8 @@ typedef struct {
                                    * when there are fewer) -- where the support
                                    * starts; R x F runs compete as above, run index
                                    * f * R + r. */
+    int32_t search_slack0;        /* 0..64: the slack of support-aware run 1 (see
+                                   * search_runs); 0 gives slacks 0..R-2. */
 } qs_sched_opts;
 
 /* Build a schedule for an n-qubit gate list.  With fuse, gates are packed into

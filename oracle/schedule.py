@@ -40,9 +40,9 @@ non-diagonal gate keeps its place:
   * search (search_runs R > 1): run 0 is the rule above; run s >= 1 takes,
     while the dense clusters taken so far do not cover every qubit, among the
     clusters grown from all seeds (ranked as the rule ranks them: more gates,
-    then fewer qubits, then the lower seed) within s - 1 gates of the largest
-    the one adding the fewest qubits to them (an all-diagonal one adds none;
-    ties: the first in rank), else the first; the run of lowest cost is kept
+    then fewer qubits, then the lower seed) within search_slack0 + s - 1
+    gates of the largest the one adding the fewest qubits to them (an
+    all-diagonal one adds none; ties: the first in rank), else the first; the run of lowest cost is kept
     (then the fewest clusters, then the lowest r), the cost being its number
     of dense clusters or, with from_basis, the sum over its dense clusters of
     2^(|support| - n), the support growing by each dense cluster's qubits from
@@ -141,7 +141,7 @@ def clusters(n, gates, k_max):
     return out
 
 
-def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True, search_first=1):
+def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True, search_first=1, search_slack0=0):
     """Clusters when diagonal gates may pass one another on a qubit: the best
     of search_runs x search_first runs (run 0 the greedy rule)."""
     def cost(cl):
@@ -154,7 +154,7 @@ def clusters_commuting(n, gates, k_max, search_runs=1, from_basis=True, search_f
         return total, len(cl)
 
     R = max(1, search_runs)
-    runs = [_commuting_run(n, gates, k_max, None if r == 0 else r - 1, f)
+    runs = [_commuting_run(n, gates, k_max, None if r == 0 else search_slack0 + r - 1, f)
             for f in range(max(1, search_first)) for r in range(R)]
     best = None
     for cl in runs:
@@ -291,11 +291,11 @@ def _phase_op(n, gates, members):
 
 
 def schedule(n, gates, k_max=5, fuse=True, commute_diagonal=True, search_runs=1, search_from_basis=True,
-             search_first=1):
+             search_first=1, search_slack0=0):
     """Op list: dicts with kind 'dense' (qubits, gates, matrix) or 'phase'
     (qubits, gates, coeff, edges)."""
     if fuse:
-        groups = (clusters_commuting(n, gates, k_max, search_runs, search_from_basis, search_first)
+        groups = (clusters_commuting(n, gates, k_max, search_runs, search_from_basis, search_first, search_slack0)
                   if commute_diagonal
                   else clusters(n, gates, k_max))
     else:

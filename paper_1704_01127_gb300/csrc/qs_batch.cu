@@ -489,7 +489,7 @@ extern "C" int qs_batch_autotune(int n_circ, const int *n_qubits, const qs_gate 
     int rc = QS_OK;
     for (int km : {3, 4, 5}) {
         std::vector<qs_schedule *> sc(n_circ, nullptr);
-        qs_sched_opts o = {km, 1, 1, 0, 1, 1, 1, 1};
+        qs_sched_opts o = {km, 1, 1, 0, 1, 1, 1, 1, 0};
         for (int c = 0; c < n_circ && !rc; c++) rc = qs_schedule_build(n_qubits[c], gates[c], n_gates[c], &o, &sc[c]);
         qs_batch *b = nullptr;
         if (!rc) rc = qs_batch_create(n_circ, sc.data(), dtype, stream, &b);

@@ -263,6 +263,7 @@ uint64_t gmask_of(const qs_gate &x) { return (1ULL << x.q0) | (x.q1 >= 0 ? 1ULL 
 
 constexpr int kMaxSearchRuns = 64;
 constexpr int kMaxSearchFirst = 16;
+constexpr int kMaxSearchSlack0 = 64;
 constexpr int kMaxSearchThreads = 32;
 
 // The same greedy closure rule with diagonal gates free to pass one another:
@@ -592,15 +593,18 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
     if (opts->search_first < 0 || opts->search_first > kMaxSearchFirst)
         return qs_fail(QS_EINVAL, "qs_schedule_build: search_first %d not in [0, %d]", opts->search_first,
                        kMaxSearchFirst);
+    if (opts->search_slack0 < 0 || opts->search_slack0 > kMaxSearchSlack0)
+        return qs_fail(QS_EINVAL, "qs_schedule_build: search_slack0 %d not in [0, %d]", opts->search_slack0,
+                       kMaxSearchSlack0);
     std::vector<qs_gate> g(gates, gates + n_gates);
     for (int i = 0; i < n_gates; i++)
         if (!check_gate(n, g[i])) return qs_fail(QS_EINVAL, "qs_schedule_build: bad gate %d", i);
     std::vector<std::vector<int>> groups;
     if (opts->fuse && opts->commute_diagonal) {
         // Run i = f * R + r: rule r (0: greedy; r >= 1: support-aware with
-        // slack r - 1) with its first cluster forced to rank f (f = 0: the
-        // rule's own).  The runs are independent; a few host threads take
-        // them in turn.
+        // slack search_slack0 + r - 1) with its first cluster forced to rank f
+        // (f = 0: the rule's own).  The runs are independent; a few host
+        // threads take them in turn.
         const int R = std::max(1, (int)opts->search_runs);
         const int runs = R * std::max(1, (int)opts->search_first);
         std::vector<std::vector<std::vector<int>>> res(runs);
@@ -610,7 +614,8 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
             for (int i = next++; i < runs; i = next++) {
                 try {
                     DiagClusterer cl(n, g);
-                    res[i] = cl.run(opts->k_max, i % R - 1, i / R);
+                    const int r = i % R;
+                    res[i] = cl.run(opts->k_max, r == 0 ? -1 : opts->search_slack0 + r - 1, i / R);
                 } catch (...) {
                     failed[i] = 1;             // out of host memory
                 }

@@ -608,7 +608,7 @@ extern "C" int qs_plan_circuit(int n, const qs_gate *gates, int n_gates, int dty
     double best_t = 1e300;
     int best_k = 0;
     for (int km = 2; km <= QS_MAX_K; km++) {
-        qs_sched_opts o = {km, 1, 1, 0, 1, 1, 1, 1};
+        qs_sched_opts o = {km, 1, 1, 0, 1, 1, 1, 1, 0};
         qs_schedule *sc = nullptr;
         int rc = qs_schedule_build(n, gates, n_gates, &o, &sc);
         if (rc) {

@@ -34,7 +34,8 @@ class _SchedOpts(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int32), ("fuse", ctypes.c_int32),
                 ("merge_phase", ctypes.c_int32), ("drop_final_diagonal", ctypes.c_int32),
                 ("commute_diagonal", ctypes.c_int32), ("search_runs", ctypes.c_int32),
-                ("search_from_basis", ctypes.c_int32), ("search_first", ctypes.c_int32)]
+                ("search_from_basis", ctypes.c_int32), ("search_first", ctypes.c_int32),
+                ("search_slack0", ctypes.c_int32)]
 
 
 class _OpInfo(ctypes.Structure):
@@ -332,11 +333,12 @@ def gates_to_tuples(gates):
 
 
 def qs_schedule_build(n, gates, k_max=5, fuse=True, merge_phase=True, drop_final_diagonal=False,
-                      commute_diagonal=True, search_runs=17, search_from_basis=True, search_first=8):
+                      commute_diagonal=True, search_runs=9, search_from_basis=True, search_first=16,
+                      search_slack0=9):
     g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
     opts = _SchedOpts(int(k_max), int(bool(fuse)), int(bool(merge_phase)), int(bool(drop_final_diagonal)),
                       int(bool(commute_diagonal)), int(search_runs), int(bool(search_from_basis)),
-                      int(search_first))
+                      int(search_first), int(search_slack0))
     h = _VP()
     _check(lib().qs_schedule_build(int(n), g.ctypes.data_as(_VP), int(g.size), ctypes.byref(opts),
                                    ctypes.byref(h)))

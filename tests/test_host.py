@@ -76,18 +76,19 @@ def test_schedule_bit_exact_with_oracle(grid, depth, seed, k_max, commute):
             assert a["edges"] == [tuple(e) for e in b["edges"]]
 
 
-@pytest.mark.parametrize("from_basis,first", [(False, 1), (True, 1), (True, 3)])
+@pytest.mark.parametrize("from_basis,first,slack0", [(False, 1, 0), (True, 1, 0), (True, 3, 0), (True, 4, 9)])
 @pytest.mark.parametrize("grid,depth,seed,k_max", [((5, 6), 25, 4, 5), ((4, 5), 20, 3, 4)])
-def test_schedule_search_bit_exact_with_oracle(grid, depth, seed, k_max, from_basis, first):
+def test_schedule_search_bit_exact_with_oracle(grid, depth, seed, k_max, from_basis, first, slack0):
     """The best of 8 clustering runs, or of 8 x 3 with the first cluster of
-    rank 0, 1 or 2 (threads in the library, one after another in the oracle):
-    the same clusters; by dense-cluster count, never more dense clusters than
-    the greedy rule's."""
+    rank 0, 1 or 2, or of 8 x 4 with slacks from 9 (threads in the library,
+    one after another in the oracle): the same clusters; by dense-cluster
+    count, never more dense clusters than the greedy rule's."""
     n, g = qs.qs_supremacy_circuit(grid[0], grid[1], depth, seed)
     tuples = qs.gates_to_tuples(g)
-    lib_ops = _lib_ops(n, g, k_max=k_max, search_runs=8, search_from_basis=from_basis, search_first=first)
+    lib_ops = _lib_ops(n, g, k_max=k_max, search_runs=8, search_from_basis=from_basis, search_first=first,
+                       search_slack0=slack0)
     or_ops = schedule.schedule(n, tuples, k_max=k_max, search_runs=8, search_from_basis=from_basis,
-                               search_first=first)
+                               search_first=first, search_slack0=slack0)
     assert [op["gates"] for op in lib_ops] == [tuple(op["gates"]) for op in or_ops]
     if not from_basis:
         def dense(ops):
@@ -142,6 +143,9 @@ def test_schedule_rejects_bad_input():
     for first in (-1, 17):
         with pytest.raises(qs.QSError):
             qs.qs_schedule_build(n, g, k_max=5, search_first=first)
+    for slack0 in (-1, 65):
+        with pytest.raises(qs.QSError):
+            qs.qs_schedule_build(n, g, k_max=5, search_slack0=slack0)
     bad = g.copy()
     bad[3]["q0"] = 99
     with pytest.raises(qs.QSError):
