@@ -5,9 +5,9 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <set>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "qs_internal.h"
@@ -266,6 +266,83 @@ constexpr int kMaxSearchFirst = 16;
 constexpr int kMaxSearchSlack0 = 64;
 constexpr int kMaxSearchThreads = 32;
 
+// Closures by qubit set: open addressing with linear probing over the 64-bit
+// masks (a set is never empty, so 0 marks a free slot, and never holds all 64
+// qubits, so ~0 marks a dropped one); the member lists live in a deque, so a
+// reference stays valid while the table grows.  drop() marks the sets that
+// meet a mask as dropped; the table is rebuilt when few free slots are left.
+struct ClosureMemo {
+    static constexpr uint64_t kDropped = ~0ULL;
+    std::vector<uint64_t> key = std::vector<uint64_t>(1024, 0);
+    std::vector<int> slot = std::vector<int>(1024, 0);
+    std::deque<std::vector<int>> vals;
+    std::vector<int> free_vals;
+    size_t used = 0, dropped = 0;
+    int shift = 64 - 10;
+
+    size_t home(uint64_t k) const { return (size_t)((k * 0x9E3779B97F4A7C15ULL) >> shift); }
+
+    const std::vector<int> *find(uint64_t k) const
+    {
+        const size_t mask = key.size() - 1;
+        for (size_t i = home(k);; i = (i + 1) & mask) {
+            if (key[i] == k) return &vals[slot[i]];
+            if (key[i] == 0) return nullptr;
+        }
+    }
+
+    void place(uint64_t k, int vi)
+    {
+        const size_t mask = key.size() - 1;
+        size_t i = home(k);
+        while (key[i] != 0 && key[i] != kDropped) i = (i + 1) & mask;
+        if (key[i] == kDropped) dropped--;
+        key[i] = k;
+        slot[i] = vi;
+    }
+
+    // k is not in the table
+    const std::vector<int> &insert(uint64_t k, std::vector<int> &&v)
+    {
+        if (2 * (used + dropped + 1) > key.size()) rehash(4 * (used + 1) > key.size() ? 2 * key.size() : key.size());
+        int vi;
+        if (!free_vals.empty()) {
+            vi = free_vals.back();
+            free_vals.pop_back();
+            vals[vi] = std::move(v);
+        } else {
+            vi = (int)vals.size();
+            vals.push_back(std::move(v));
+        }
+        place(k, vi);
+        used++;
+        return vals[vi];
+    }
+
+    void drop(uint64_t hit)
+    {
+        for (size_t i = 0; i < key.size(); i++) {
+            if (key[i] == 0 || key[i] == kDropped || !(key[i] & hit)) continue;
+            key[i] = kDropped;
+            free_vals.push_back(slot[i]);
+            used--;
+            dropped++;
+        }
+    }
+
+    void rehash(size_t cap)
+    {
+        std::vector<uint64_t> old_key(cap, 0);
+        std::vector<int> old_slot(cap, 0);
+        old_key.swap(key);
+        old_slot.swap(slot);
+        shift = 64 - __builtin_ctzll(cap);
+        dropped = 0;
+        for (size_t i = 0; i < old_key.size(); i++)
+            if (old_key[i] != 0 && old_key[i] != kDropped) place(old_key[i], old_slot[i]);
+    }
+};
+
 // The same greedy closure rule with diagonal gates free to pass one another:
 // on a qubit, a gate may run before earlier unassigned gates of that qubit
 // when it and all of them are diagonal (diagonal matrices commute, so the
@@ -290,7 +367,8 @@ struct DiagClusterer {
     mutable std::vector<int> mark;         // gates taken by the closure being built
     mutable int stamp = 0;
     // closures by qubit set; a step drops those that read a queue it changed
-    mutable std::unordered_map<uint64_t, std::vector<int>> memo;
+    mutable ClosureMemo memo;
+    mutable std::vector<int> cand;         // the last result of candidates()
 
     DiagClusterer(int n_, const std::vector<qs_gate> &gates)
         : n(n_), g(gates), queue(n_), gmask(gates.size()), diag(gates.size()), done(gates.size(), 0),
@@ -320,19 +398,11 @@ struct DiagClusterer {
         return false;
     }
 
-    bool ready(int gi) const
-    {
-        for (uint64_t m = gmask[gi]; m; m &= m - 1)
-            if (!available(__builtin_ctzll(m), gi)) return false;
-        return true;
-    }
-
-    // the closure of S, held in the memo (its nodes stay in place while the
-    // map grows, so the reference lasts until the step drops entries)
+    // the closure of S, held in the memo (the reference lasts until the step
+    // drops entries)
     const std::vector<int> &closure(uint64_t S) const
     {
-        auto hit = memo.find(S);
-        if (hit != memo.end()) return hit->second;
+        if (const std::vector<int> *hit = memo.find(S)) return *hit;
         ++stamp;
         std::vector<int> members;
         members.reserve(32);
@@ -341,37 +411,53 @@ struct DiagClusterer {
             changed = false;
             for (uint64_t m = S; m; m &= m - 1) {
                 const int q = __builtin_ctzll(m);
+                // the scan stops at the first untaken non-diagonal gate, so
+                // every untaken gate it has passed on q is diagonal: gi is
+                // available on q when it is diagonal or none was passed, and
+                // ready when also available on its other qubit
+                bool passed = false;
                 for (size_t i = first[q]; i < queue[q].size(); i++) {
                     const int gi = queue[q][i];
                     if (taken(gi)) continue;
                     if (gmask[gi] & ~S) {
                         if (!diag[gi]) break;
+                        passed = true;
                         continue;
                     }
-                    if (ready(gi)) {
+                    bool ok = !passed || diag[gi];
+                    const uint64_t other = gmask[gi] & ~(1ULL << q);
+                    if (ok && other) ok = available(__builtin_ctzll(other), gi);
+                    if (ok) {
                         mark[gi] = stamp;
                         members.push_back(gi);
                         changed = true;
                     } else if (!diag[gi]) {
                         break;
+                    } else {
+                        passed = true;
                     }
                 }
             }
         }
-        return memo.emplace(S, std::move(members)).first->second;
+        return memo.insert(S, std::move(members));
     }
 
-    // per qubit, its first gate not done and not in `members`, if ready
-    std::vector<int> candidates(const std::vector<int> &members) const
+    // per qubit, its first gate not done and not in `members`, if ready (in
+    // a buffer that the next call overwrites)
+    const std::vector<int> &candidates(const std::vector<int> &members) const
     {
         ++stamp;
         for (int gi : members) mark[gi] = stamp;
-        std::vector<int> c;
+        std::vector<int> &c = cand;
+        c.clear();
         for (int q = 0; q < n; q++)
             for (size_t i = first[q]; i < queue[q].size(); i++) {
                 const int gi = queue[q][i];
                 if (taken(gi)) continue;
-                if (ready(gi)) c.push_back(gi);
+                // first untaken gate on q: available there; ready when also
+                // available on its other qubit
+                const uint64_t other = gmask[gi] & ~(1ULL << q);
+                if (!other || available(__builtin_ctzll(other), gi)) c.push_back(gi);
                 break;
             }
         std::sort(c.begin(), c.end());
@@ -431,7 +517,8 @@ struct DiagClusterer {
         std::vector<int> members;
         while (remaining) {
             std::vector<Opt> opts;
-            for (int sd : candidates({})) {
+            const std::vector<int> seeds = candidates({});
+            for (int sd : seeds) {
                 uint64_t S;
                 grow(sd, k_max, members, S);
                 opts.push_back({(int)members.size(), __builtin_popcountll(S), sd, S, members});
@@ -464,9 +551,7 @@ struct DiagClusterer {
             for (int gi : best) done[gi] = 1;
             // a closure on S reads only the queues of S's qubits: those that
             // miss the qubits of the cluster taken stay as they are
-            const uint64_t hit = opts[pick].S;
-            for (auto it = memo.begin(); it != memo.end();)
-                it = (it->first & hit) ? memo.erase(it) : std::next(it);
+            memo.drop(opts[pick].S);
             for (int q = 0; q < n; q++)
                 while (first[q] < (int)queue[q].size() && done[queue[q][first[q]]]) first[q]++;
             remaining -= best.size();

@@ -333,8 +333,8 @@ def gates_to_tuples(gates):
 
 
 def qs_schedule_build(n, gates, k_max=5, fuse=True, merge_phase=True, drop_final_diagonal=False,
-                      commute_diagonal=True, search_runs=9, search_from_basis=True, search_first=16,
-                      search_slack0=9):
+                      commute_diagonal=True, search_runs=13, search_from_basis=True, search_first=16,
+                      search_slack0=5):
     g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
     opts = _SchedOpts(int(k_max), int(bool(fuse)), int(bool(merge_phase)), int(bool(drop_final_diagonal)),
                       int(bool(commute_diagonal)), int(search_runs), int(bool(search_from_basis)),
