@@ -404,7 +404,9 @@ def run_batch(args):
         r, c, d = qs.qs_batch_circuit_params(s)
         circs.append(qs.qs_supremacy_circuit(r, c, d, s))
     k_max, C, T, tune_ms = qs.qs_batch_autotune(circs, qs.QS_C64, stream)
-    scheds = [qs.qs_schedule_build(n, g, k_max=k_max) for (n, g) in circs]
+    # the greedy clustering rule, as the autotuner's schedules (the 208-run
+    # search would spend ~10 s of host time on 512 small circuits)
+    scheds = [qs.qs_schedule_build(n, g, k_max=k_max, search_runs=1, search_first=1) for (n, g) in circs]
     b = qs.qs_batch_create(scheds, qs.QS_C64, stream)
     qs.qs_batch_set_config(b, C, T)
     for _ in range(args.warmup):
