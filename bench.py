@@ -13,6 +13,7 @@ With --gpus N > 1 (under torchrun) every rank simulates its own circuits
 """
 import argparse
 import concurrent.futures
+import inspect
 import json
 import os
 import statistics
@@ -375,7 +376,8 @@ def run_ours(args):
             rows, cols, n, cycles, dt, "gate by gate" if args.plain else "fused k<=%d + phase diagonals" % k_max),
             "seeds": "rank*1000 + step", "l2": "state %.1f GiB > L2 129 MB (no flush needed)" % (state_bytes / 2**30),
             "parallelism": "replicas" if world > 1 else "single GPU",
-            "phase_fold": not args.no_fold},
+            "phase_fold": not args.no_fold,
+            "cluster_search": _search_config(qs, args.plain)},
         "roofline": roof, "sweeps": sweeps, "plain": plain,
         "speedup_vs_plain": (plain["s_per_circuit"] / per_circuit) if plain else None,
         "porter_thomas": {"sum_p": stats[0], "entropy": stats[1], "m2": stats[3]},
@@ -523,6 +525,18 @@ def run_learned(args):
             "config": {"workload": "learned scheduling: 4x7, 5x6, 3x11 grids, 30 CZ cycles, c64 and c128"},
             "harness": {"timings": int(T.size), "seconds": harness_s}, "fit": dict(rep, seconds=fit_s),
             "circuits": rows, "geomean_gain_learned_vs_analytic": geo}
+
+
+def _search_config(qs, plain):
+    """The clustering search the schedules were built with (the binding's
+    defaults), as reported in the JSON line."""
+    if plain:
+        return None
+    p = inspect.signature(qs.qs_schedule_build).parameters
+    R, F, s0 = (p[k].default for k in ("search_runs", "search_first", "search_slack0"))
+    return {"runs": R * F, "first_clusters": F,
+            "rules": "greedy + support-aware slack %d..%d" % (s0, s0 + R - 2),
+            "cost": "sum over dense sweeps of 2^(|support| - n) from |0...0>"}
 
 
 # ------------------------------------------------------------ oracle (CPU) leg
