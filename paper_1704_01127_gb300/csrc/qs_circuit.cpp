@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <memory>
+#include <new>
 #include <set>
 #include <thread>
 #include <vector>
@@ -593,9 +595,8 @@ void make_dense(const std::vector<qs_gate> &g, const std::vector<int> &members, 
 
 // ------------------------------------------------------------------ public API
 
-extern "C" int qs_supremacy_circuit(int rows, int cols, const int *removed_rc, int n_removed,
-                                    int cz_cycles, uint64_t seed, int *n_qubits,
-                                    qs_gate *gates, int max_gates, int *n_gates)
+static int supremacy_circuit_impl(int rows, int cols, const int *removed_rc, int n_removed, int cz_cycles,
+                                  uint64_t seed, int *n_qubits, qs_gate *gates, int max_gates, int *n_gates)
 {
     if (rows < 1 || cols < 1 || rows * cols > 4096 || cz_cycles < 0 || n_removed < 0 ||
         (n_removed > 0 && !removed_rc) || !n_qubits || !n_gates || max_gates < 0 ||
@@ -665,8 +666,8 @@ extern "C" int qs_supremacy_circuit(int rows, int cols, const int *removed_rc, i
     return QS_OK;
 }
 
-extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
-                                 const qs_sched_opts *opts, qs_schedule **out)
+static int schedule_build_impl(int n, const qs_gate *gates, int n_gates, const qs_sched_opts *opts,
+                               qs_schedule **out)
 {
     if (!out || n < 1 || n > QS_MAX_QUBITS || n_gates < 0 || (n_gates > 0 && !gates) || !opts)
         return qs_fail(QS_EINVAL, "qs_schedule_build: bad arguments");
@@ -757,7 +758,7 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
     } else {
         for (int i = 0; i < n_gates; i++) groups.push_back({i});
     }
-    qs_schedule *sc = new (std::nothrow) qs_schedule();
+    std::unique_ptr<qs_schedule> sc(new (std::nothrow) qs_schedule());
     if (!sc) return qs_fail(QS_ENOMEM, "qs_schedule_build: out of host memory");
     sc->n = n;
     for (auto &members : groups) {
@@ -783,7 +784,7 @@ extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
     // the output distribution does not see them (Sec. 3.6)
     if (opts->drop_final_diagonal)
         while (!sc->ops.empty() && sc->ops.back().kind == QS_OP_PHASE) sc->ops.pop_back();
-    *out = sc;
+    *out = sc.release();
     return QS_OK;
 }
 
@@ -823,14 +824,14 @@ static bool phase_from_pool(int n, int n_pairs, const double *pool, int64_t pool
     return true;
 }
 
-extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const int *ks,
-                                    const int *qubits, const int64_t *offsets,
-                                    const double *pool, int64_t pool_len, qs_schedule **out)
+static int schedule_from_ops_impl(int n, int n_ops, const int *kinds, const int *ks, const int *qubits,
+                                  const int64_t *offsets, const double *pool, int64_t pool_len,
+                                  qs_schedule **out)
 {
     if (!out || n < 1 || n > QS_MAX_QUBITS || n_ops < 0 ||
         (n_ops > 0 && (!kinds || !ks || !qubits || !offsets || !pool)))
         return qs_fail(QS_EINVAL, "qs_schedule_from_ops: bad arguments");
-    qs_schedule *sc = new (std::nothrow) qs_schedule();
+    std::unique_ptr<qs_schedule> sc(new (std::nothrow) qs_schedule());
     if (!sc) return qs_fail(QS_ENOMEM, "qs_schedule_from_ops: out of host memory");
     sc->n = n;
     for (int i = 0; i < n_ops; i++) {
@@ -838,7 +839,6 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
         if (kinds[i] == QS_OP_PHASE) {
             qs_op_host op;
             if (!phase_from_pool(n, k, pool, pool_len, offsets[i], op)) {
-                delete sc;
                 return qs_fail(QS_EINVAL, "qs_schedule_from_ops: bad phase op %d", i);
             }
             sc->ops.push_back(std::move(op));
@@ -847,7 +847,6 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
         bool dense = kinds[i] == QS_OP_DENSE;
         // both kinds take at most QS_MAX_K qubits here (QS_MAX_K slots per op)
         if ((!dense && kinds[i] != QS_OP_DIAG) || k < 1 || k > QS_MAX_K || k > n) {
-            delete sc;
             return qs_fail(QS_EINVAL, "qs_schedule_from_ops: bad op %d", i);
         }
         // sort qubits ascending and permute the matrix accordingly (Sec. 3.2)
@@ -857,7 +856,6 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
             q[j] = qubits[QS_MAX_K * i + j];
             perm[j] = j;
             if (q[j] < 0 || q[j] >= n || ((seen >> q[j]) & 1)) {
-                delete sc;
                 return qs_fail(QS_EINVAL, "qs_schedule_from_ops: bad qubits in op %d", i);
             }
             seen |= 1ULL << q[j];
@@ -867,7 +865,6 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
         const int d = 1 << k;
         int64_t need = dense ? 2LL * d * d : 2LL * d;
         if (offsets[i] < 0 || offsets[i] + need > pool_len) {
-            delete sc;
             return qs_fail(QS_EINVAL, "qs_schedule_from_ops: op %d reads past the pool", i);
         }
         qs_op_host op;
@@ -898,8 +895,48 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
         }
         sc->ops.push_back(std::move(op));
     }
-    *out = sc;
+    *out = sc.release();
     return QS_OK;
+}
+
+// The entry points of this file: host memory that runs out inside them (a
+// standard container throwing) becomes QS_ENOMEM; no exception crosses the C
+// boundary.
+template <typename F>
+static int guarded(const char *what, F &&f)
+{
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        return qs_fail(QS_ENOMEM, "%s: out of host memory", what);
+    } catch (...) {
+        return qs_fail(QS_EINVAL, "%s: internal error", what);
+    }
+}
+
+extern "C" int qs_supremacy_circuit(int rows, int cols, const int *removed_rc, int n_removed,
+                                    int cz_cycles, uint64_t seed, int *n_qubits,
+                                    qs_gate *gates, int max_gates, int *n_gates)
+{
+    return guarded("qs_supremacy_circuit", [&] {
+        return supremacy_circuit_impl(rows, cols, removed_rc, n_removed, cz_cycles, seed, n_qubits, gates,
+                                      max_gates, n_gates);
+    });
+}
+
+extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
+                                 const qs_sched_opts *opts, qs_schedule **out)
+{
+    return guarded("qs_schedule_build", [&] { return schedule_build_impl(n, gates, n_gates, opts, out); });
+}
+
+extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const int *ks,
+                                    const int *qubits, const int64_t *offsets,
+                                    const double *pool, int64_t pool_len, qs_schedule **out)
+{
+    return guarded("qs_schedule_from_ops", [&] {
+        return schedule_from_ops_impl(n, n_ops, kinds, ks, qubits, offsets, pool, pool_len, out);
+    });
 }
 
 extern "C" int qs_schedule_num_qubits(const qs_schedule *sc) { return sc ? sc->n : 0; }
