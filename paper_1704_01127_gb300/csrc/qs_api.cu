@@ -6,7 +6,9 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <memory>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "qs_device.cuh"
@@ -762,9 +764,11 @@ extern "C" int qs_set_amplitudes(qs_state *s, const double *host)
     if (s->dtype == QS_C128) {
         QS_CUDA(cudaMemcpyAsync(s->amp, host, 16 * N, cudaMemcpyHostToDevice, st), "qs_set_amplitudes");
     } else {
-        std::vector<float> f(2 * N);
+        // a host copy as large as the state (32 GiB at 32 qubits): no throw
+        std::unique_ptr<float[]> f(new (std::nothrow) float[2 * N]);
+        if (!f) return qs_fail(QS_ENOMEM, "qs_set_amplitudes: out of host memory");
         for (uint64_t i = 0; i < 2 * N; i++) f[i] = (float)host[i];
-        QS_CUDA(cudaMemcpyAsync(s->amp, f.data(), 8 * N, cudaMemcpyHostToDevice, st), "qs_set_amplitudes");
+        QS_CUDA(cudaMemcpyAsync(s->amp, f.get(), 8 * N, cudaMemcpyHostToDevice, st), "qs_set_amplitudes");
     }
     QS_CUDA(cudaStreamSynchronize(st), "qs_set_amplitudes sync");
     s->sup_free = ~0ULL;
@@ -783,8 +787,9 @@ extern "C" int qs_get_amplitudes(qs_state *s, double *host)
         QS_CUDA(cudaMemcpyAsync(host, s->amp, 16 * N, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes");
         QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes sync");
     } else {
-        std::vector<float> f(2 * N);
-        QS_CUDA(cudaMemcpyAsync(f.data(), s->amp, 8 * N, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes");
+        std::unique_ptr<float[]> f(new (std::nothrow) float[2 * N]);
+        if (!f) return qs_fail(QS_ENOMEM, "qs_get_amplitudes: out of host memory");
+        QS_CUDA(cudaMemcpyAsync(f.get(), s->amp, 8 * N, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes");
         QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes sync");
         for (uint64_t i = 0; i < 2 * N; i++) host[i] = (double)f[i];
     }
