@@ -96,6 +96,22 @@ def test_schedule_search_bit_exact_with_oracle(grid, depth, seed, k_max, from_ba
         assert dense(lib_ops) <= dense(_lib_ops(n, g, k_max=k_max, search_runs=1, search_first=1))
 
 
+@pytest.mark.parametrize("grid,depth,k_max", [((2, 2), 1, 2), ((2, 2), 2, 3), ((1, 3), 2, 2), ((2, 3), 3, 3),
+                                             ((2, 3), 3, 5)])
+def test_schedule_search_on_tiny_circuits(grid, depth, k_max):
+    """Circuits with fewer candidate first clusters than the search asks for
+    (the rank falls back to the last one) and slacks beyond any cluster's
+    size: the library and the oracle pick the same clusters, and every gate
+    is in exactly one."""
+    n, g = qs.qs_supremacy_circuit(grid[0], grid[1], depth, 0)
+    tuples = qs.gates_to_tuples(g)
+    kw = dict(k_max=k_max, search_runs=5, search_first=16, search_slack0=20)
+    lib_ops = _lib_ops(n, g, **kw)
+    or_ops = schedule.schedule(n, tuples, **kw)
+    assert [op["gates"] for op in lib_ops] == [tuple(op["gates"]) for op in or_ops]
+    assert sorted(x for op in lib_ops for x in op["gates"]) == list(range(len(tuples)))
+
+
 @pytest.mark.parametrize("grid,depth,seed", [((5, 6), 25, 1), ((4, 8), 25, 1), ((4, 4), 10, 0), ((3, 11), 40, 2)])
 def test_drop_final_diagonal_leaves_out_only_the_trailing_phase_ops(grid, depth, seed):
     """Sec. 3.6: the last layer of diagonal gates does not change |psi|^2, so
