@@ -2,6 +2,8 @@
 
 Test infrastructure only.  -ffp-contract=off keeps every product and sum
 separately rounded so that x86-64 and aarch64 hosts agree bit for bit.
+-fopenmp splits the element-wise loops over host threads (the result does not
+depend on the thread count); a compiler without OpenMP builds the serial form.
 """
 import os
 import subprocess
@@ -18,8 +20,11 @@ def build(force=False):
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC",
-                           "-shared", "-o", tmp, SRC, "-lm"])
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, SRC]
+    try:
+        subprocess.check_call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base + ["-lm"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -36,8 +36,19 @@ def lib():
         L.or_splitmix64.restype = ctypes.c_uint64
         L.or_sample.argtypes = [dp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, u64p]
         L.or_sample.restype = ctypes.c_int
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        L.or_max_threads.restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def set_threads(t):
+    """Host threads for the element-wise loops (gates, phases, probabilities)."""
+    lib().or_set_threads(int(t))
+
+
+def max_threads():
+    return int(lib().or_max_threads())
 
 
 def _dp(a):

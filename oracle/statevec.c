@@ -19,6 +19,32 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads.  The element-wise loops below (one gate, one phase product, the
+ * probabilities) update every index, or index pair, on its own, so splitting
+ * their iterations over OpenMP threads gives the serial loop's result bit for
+ * bit.  The reductions (norm, statistics, sampling sums) stay serial: their
+ * order of additions is part of their definition here. */
+void or_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* (a + ib)(c + id) written out; kept as a helper so every complex product in
  * this file is the textbook formula. */
@@ -35,6 +61,7 @@ static inline void cmul(double ar, double ai, double br, double bi, double *cr, 
 void or_apply_1q(double *psi, int n, int q, const double *u)
 {
     uint64_t dim = (uint64_t)1 << n, bit = (uint64_t)1 << q;
+#pragma omp parallel for schedule(static)
     for (uint64_t i0 = 0; i0 < dim; i0++) {
         if (i0 & bit) continue;
         uint64_t i1 = i0 | bit;
@@ -56,6 +83,7 @@ void or_apply_cz(double *psi, int n, int a, int b)
 {
     uint64_t dim = (uint64_t)1 << n;
     uint64_t ma = (uint64_t)1 << a, mb = (uint64_t)1 << b;
+#pragma omp parallel for schedule(static)
     for (uint64_t i = 0; i < dim; i++) {
         if ((i & ma) && (i & mb)) {
             psi[2 * i] = -psi[2 * i];
@@ -121,6 +149,7 @@ int or_apply_diag(double *psi, int n, const int *qubits, int k, const double *d)
     uint64_t dim = (uint64_t)1 << n;
     for (int j = 0; j < k; j++)
         if (qubits[j] < 0 || qubits[j] >= n) return -1;
+#pragma omp parallel for schedule(static)
     for (uint64_t i = 0; i < dim; i++) {
         uint64_t x = 0;
         for (int j = 0; j < k; j++) x |= ((i >> qubits[j]) & 1) << j;
@@ -154,6 +183,7 @@ int or_apply_phase(double *psi, int n, const int *c, int n_edges, const int *edg
     uint64_t dim = (uint64_t)1 << n;
     for (int e = 0; e < 2 * n_edges; e++)
         if (edges[e] < 0 || edges[e] >= n) return -1;
+#pragma omp parallel for schedule(static)
     for (uint64_t i = 0; i < dim; i++) {
         int m = 0;
         for (int q = 0; q < n; q++)
@@ -174,6 +204,7 @@ int or_apply_phase(double *psi, int n, const int *c, int n_edges, const int *edg
 void or_probabilities(const double *psi, int n, double *p)
 {
     uint64_t dim = (uint64_t)1 << n;
+#pragma omp parallel for schedule(static)
     for (uint64_t i = 0; i < dim; i++) {
         double a = psi[2 * i] * psi[2 * i];
         double b = psi[2 * i + 1] * psi[2 * i + 1];

@@ -187,6 +187,47 @@ def test_porter_thomas_moments():
     assert abs(h - (n * math.log(2) - 1 + EULER_GAMMA)) < 0.01
 
 
+def test_threads_give_the_serial_result():
+    """The element-wise loops split over host threads: every index is updated on
+    its own, so any thread count gives the one-thread state bit for bit."""
+    n, gates = circuit.supremacy_circuit(4, 5, 12, seed=4)
+    coeff, edges = random_phase_poly(n, 6, 11)
+    d = random_diag(3, 12)
+    out = []
+    for t in (1, max(2, sim.max_threads())):
+        sim.set_threads(t)
+        psi = sim.run_circuit(n, gates)
+        sim.apply_phase(psi, coeff, edges)
+        sim.apply_diag(psi, [3, 17, 9], d)
+        out.append((psi, sim.probabilities(psi)))
+    sim.set_threads(max(1, sim.max_threads()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_fullsize_golden_files():
+    """The stored full-size oracle amplitudes (tests/golden/fullsize_*.txt):
+    indices as the writer draws them, a unit norm, and sampled N p with the
+    Porter-Thomas mean 1 (2048 draws of Exp(1): standard error 0.022)."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_fullsize
+    from conftest import GOLDEN
+    names = sorted(f for f in os.listdir(GOLDEN) if f.startswith("fullsize_"))
+    assert "fullsize_5x6_d25_s0.txt" in names
+    for name in names:
+        rows = read_golden(name)
+        R, C, D, seed, n = (int(x) for x in rows[0][1:])
+        assert name == make_fullsize.golden_name(R, C, D, seed)
+        assert n == circuit.supremacy_circuit(R, C, 1, seed)[0]
+        st = [float(x) for x in rows[1][1:]]
+        assert abs(st[0] - 1) < 1e-12 and abs(st[2] - 1) < 1e-12 and 1.8 < st[3] < 3.0
+        idx = np.array([int(r[0]) for r in rows[2:]], dtype=np.uint64)
+        assert np.array_equal(idx, make_fullsize.sample_indices(n, idx.size))
+        p = np.array([float(r[1]) ** 2 + float(r[2]) ** 2 for r in rows[2:]])
+        assert abs(np.mean(p[2:]) * 2.0 ** n - 1) < 0.12
+
+
 def test_stats_closed_forms():
     n = 8
     s, h, m1, m2 = sim.stats(sim.uniform_state(n))
