@@ -47,7 +47,11 @@ const char *qs_last_error(void);
  * device (Sec. 2; in place, one buffer, Sec. 3.2).  stream: a cudaStream_t or
  * NULL for the legacy default stream.  Contents are undefined until an init
  * call.  Errors: QS_EINVAL (n < 1 or n > QS_MAX_QUBITS, bad dtype),
- * QS_ENOMEM (cudaMalloc failed). */
+ * QS_ENOMEM (cudaMalloc failed, e.g. more than the free device memory).
+ *
+ * No entry point lets a C++ exception escape: a host allocation that fails
+ * inside any call returns QS_ENOMEM, any other internal exception QS_EINVAL,
+ * with the message in qs_last_error(). */
 int qs_alloc(int n, int dtype, void *stream, qs_state **out);
 
 /* Adopt an existing device buffer of 2^n amplitudes (e.g. a torch tensor's
@@ -97,6 +101,14 @@ int qs_dtype(const qs_state *s);
  * has not written yet (see qs_init_basis) are written first, on the state's
  * stream.  NULL for a null state or when that write fails. */
 void *qs_device_ptr(const qs_state *s);
+
+/* Order later calls on `stream` (a cudaStream_t or NULL for the legacy default
+ * stream) instead of the state's current stream.  Work already queued on the
+ * old stream (sweeps, the state's scratch and status words) is finished first:
+ * the new stream waits on an event recorded on the old one, so the next call
+ * on the new stream never runs beside earlier calls on the old one.  The host
+ * does not block.  QS_EINVAL for a null state, QS_ECUDA if the event cannot
+ * be recorded or waited on. */
 int qs_set_stream(qs_state *s, void *stream);
 
 /* |x>: amplitude x = 1, all others 0 (Sec. 2).  QS_EINVAL if x >= 2^n.
@@ -172,8 +184,10 @@ int qs_sample_stats(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double
  * exists for callers that may not allocate device memory, for example code that
  * runs while a framework's caching allocator owns the device memory, or code
  * that cannot afford the device-wide synchronisation a cudaMalloc implies.
- * dev_amp: 2^n amplitudes of the given dtype in device memory (16-byte
- * aligned, interleaved re, im), read only; out: 4 doubles in host memory, as
+ * dev_amp: 2^n amplitudes of the given dtype in device memory (interleaved
+ * re, im), aligned to one amplitude (16 bytes for QS_C128, 8 for QS_C64; a
+ * view starting at any amplitude of a state qualifies, anything else is
+ * QS_EINVAL), read only; out: 4 doubles in host memory, as
  * qs_stats.  The partial sums use a fixed 32,800-byte array compiled into the
  * library (one per GPU that loads it, held until the process exits); the
  * kernels use at most 1024 blocks, so every n in [1, QS_MAX_QUBITS] fits and

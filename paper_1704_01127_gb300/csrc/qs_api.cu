@@ -637,25 +637,29 @@ extern "C" const char *qs_last_error(void) { return g_err; }
 
 extern "C" int qs_alloc(int n, int dtype, void *stream, qs_state **out)
 {
-    if (!out || n < 1 || n > QS_MAX_QUBITS || (dtype != QS_C64 && dtype != QS_C128))
-        return qs_fail(QS_EINVAL, "qs_alloc: n = %d, dtype = %d not supported", n, dtype);
-    void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, amp_bytes(dtype) << n);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return qs_fail(QS_ENOMEM, "qs_alloc: %zu bytes: %s", amp_bytes(dtype) << n, cudaGetErrorString(e));
-    }
-    int rc = make_state(n, dtype, stream, p, true, out);
-    if (rc) cudaFree(p);
-    return rc;
+    return qs_guard([&]() -> int {
+        if (!out || n < 1 || n > QS_MAX_QUBITS || (dtype != QS_C64 && dtype != QS_C128))
+            return qs_fail(QS_EINVAL, "qs_alloc: n = %d, dtype = %d not supported", n, dtype);
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, amp_bytes(dtype) << n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return qs_fail(QS_ENOMEM, "qs_alloc: %zu bytes: %s", amp_bytes(dtype) << n, cudaGetErrorString(e));
+        }
+        int rc = make_state(n, dtype, stream, p, true, out);
+        if (rc) cudaFree(p);
+        return rc;
+    });
 }
 
 extern "C" int qs_wrap(void *dev_ptr, int n, int dtype, void *stream, qs_state **out)
 {
-    if (!out || !dev_ptr || ((uintptr_t)dev_ptr & 15) || n < 1 || n > QS_MAX_QUBITS ||
-        (dtype != QS_C64 && dtype != QS_C128))
-        return qs_fail(QS_EINVAL, "qs_wrap: bad pointer, n or dtype");
-    return make_state(n, dtype, stream, dev_ptr, false, out);
+    return qs_guard([&]() -> int {
+        if (!out || !dev_ptr || ((uintptr_t)dev_ptr & 15) || n < 1 || n > QS_MAX_QUBITS ||
+            (dtype != QS_C64 && dtype != QS_C128))
+            return qs_fail(QS_EINVAL, "qs_wrap: bad pointer, n or dtype");
+        return make_state(n, dtype, stream, dev_ptr, false, out);
+    });
 }
 
 extern "C" void qs_free(qs_state *s)
@@ -672,16 +676,20 @@ extern "C" void qs_free(qs_state *s)
 
 extern "C" int qs_set_path(qs_state *s, int path)
 {
-    if (!s || path < QS_PATH_AUTO || path > QS_PATH_TENSOR) return qs_fail(QS_EINVAL, "qs_set_path");
-    s->path = path;
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!s || path < QS_PATH_AUTO || path > QS_PATH_TENSOR) return qs_fail(QS_EINVAL, "qs_set_path");
+        s->path = path;
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_set_phase_fold(qs_state *s, int on)
 {
-    if (!s) return qs_fail(QS_EINVAL, "qs_set_phase_fold: null state");
-    s->fold_phase = on != 0;
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!s) return qs_fail(QS_EINVAL, "qs_set_phase_fold: null state");
+        s->fold_phase = on != 0;
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_num_qubits(const qs_state *s) { return s ? s->n : 0; }
@@ -695,9 +703,20 @@ extern "C" void *qs_device_ptr(const qs_state *s)
 }
 extern "C" int qs_set_stream(qs_state *s, void *stream)
 {
-    if (!s) return qs_fail(QS_EINVAL, "qs_set_stream: null state");
-    s->stream = stream;
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!s) return qs_fail(QS_EINVAL, "qs_set_stream: null state");
+        if (stream != s->stream) {
+            // the new stream starts after everything queued on the old one
+            cudaEvent_t ev;
+            QS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "qs_set_stream: event");
+            cudaError_t e = cudaEventRecord(ev, (cudaStream_t)s->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, ev, 0);
+            cudaEventDestroy(ev);
+            if (e != cudaSuccess) return cuda_fail(e, "qs_set_stream");
+        }
+        s->stream = stream;
+        return QS_OK;
+    });
 }
 
 // |x>: one amplitude written, the support set to {x}; the zeros elsewhere are
@@ -706,19 +725,21 @@ extern "C" int qs_set_stream(qs_state *s, void *stream)
 // States on a caller's buffer (qs_wrap) get their zeros at once.
 extern "C" int qs_init_basis(qs_state *s, uint64_t x)
 {
-    if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_basis: null state");
-    if (x >> s->n) return qs_fail(QS_EINVAL, "qs_init_basis: index out of range");
-    cudaStream_t st = (cudaStream_t)s->stream;
-    if (s->dtype == QS_C128)
-        k_set_one<double2><<<1, 1, 0, st>>>((double2 *)s->amp, x);
-    else
-        k_set_one<float2><<<1, 1, 0, st>>>((float2 *)s->amp, x);
-    QS_CUDA(cudaGetLastError(), "qs_init_basis");
-    s->sup_free = 0;
-    s->sup_fix = x;
-    // a wrapped buffer can be read by its owner without a library call: its
-    // zeros are written now
-    return s->owned ? QS_OK : qs_materialize(s);
+    return qs_guard([&]() -> int {
+        if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_basis: null state");
+        if (x >> s->n) return qs_fail(QS_EINVAL, "qs_init_basis: index out of range");
+        cudaStream_t st = (cudaStream_t)s->stream;
+        if (s->dtype == QS_C128)
+            k_set_one<double2><<<1, 1, 0, st>>>((double2 *)s->amp, x);
+        else
+            k_set_one<float2><<<1, 1, 0, st>>>((float2 *)s->amp, x);
+        QS_CUDA(cudaGetLastError(), "qs_init_basis");
+        s->sup_free = 0;
+        s->sup_fix = x;
+        // a wrapped buffer can be read by its owner without a library call: its
+        // zeros are written now
+        return s->owned ? QS_OK : qs_materialize(s);
+    });
 }
 
 int qs_materialize(qs_state *s)
@@ -740,169 +761,191 @@ int qs_materialize(qs_state *s)
 
 extern "C" int qs_init_uniform(qs_state *s)
 {
-    if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_uniform: null state");
-    uint64_t N = 1ULL << s->n;
-    int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count_dev() * 8);
-    cudaStream_t st = (cudaStream_t)s->stream;
-    // 2^{-n/2}: exact power of two for even n; sqrt(0.5) * 2^{-(n-1)/2} for odd n
-    double a = (s->n % 2 == 0) ? ldexp(1.0, -s->n / 2) : sqrt(0.5) * ldexp(1.0, -(s->n - 1) / 2);
-    if (s->dtype == QS_C128)
-        k_fill_uniform<double2, double><<<grid, 256, 0, st>>>((double2 *)s->amp, N, a);
-    else
-        k_fill_uniform<float2, float><<<grid, 256, 0, st>>>((float2 *)s->amp, N, (float)a);
-    QS_CUDA(cudaGetLastError(), "qs_init_uniform");
-    s->sup_free = ~0ULL;
-    s->sup_fix = 0;
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_uniform: null state");
+        uint64_t N = 1ULL << s->n;
+        int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count_dev() * 8);
+        cudaStream_t st = (cudaStream_t)s->stream;
+        // 2^{-n/2}: exact power of two for even n; sqrt(0.5) * 2^{-(n-1)/2} for odd n
+        double a = (s->n % 2 == 0) ? ldexp(1.0, -s->n / 2) : sqrt(0.5) * ldexp(1.0, -(s->n - 1) / 2);
+        if (s->dtype == QS_C128)
+            k_fill_uniform<double2, double><<<grid, 256, 0, st>>>((double2 *)s->amp, N, a);
+        else
+            k_fill_uniform<float2, float><<<grid, 256, 0, st>>>((float2 *)s->amp, N, (float)a);
+        QS_CUDA(cudaGetLastError(), "qs_init_uniform");
+        s->sup_free = ~0ULL;
+        s->sup_fix = 0;
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_set_amplitudes(qs_state *s, const double *host)
 {
-    if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_set_amplitudes: null argument");
-    uint64_t N = 1ULL << s->n;
-    cudaStream_t st = (cudaStream_t)s->stream;
-    if (s->dtype == QS_C128) {
-        QS_CUDA(cudaMemcpyAsync(s->amp, host, 16 * N, cudaMemcpyHostToDevice, st), "qs_set_amplitudes");
-    } else {
-        // a host copy as large as the state (32 GiB at 32 qubits): no throw
-        std::unique_ptr<float[]> f(new (std::nothrow) float[2 * N]);
-        if (!f) return qs_fail(QS_ENOMEM, "qs_set_amplitudes: out of host memory");
-        for (uint64_t i = 0; i < 2 * N; i++) f[i] = (float)host[i];
-        QS_CUDA(cudaMemcpyAsync(s->amp, f.get(), 8 * N, cudaMemcpyHostToDevice, st), "qs_set_amplitudes");
-    }
-    QS_CUDA(cudaStreamSynchronize(st), "qs_set_amplitudes sync");
-    s->sup_free = ~0ULL;
-    s->sup_fix = 0;
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_set_amplitudes: null argument");
+        uint64_t N = 1ULL << s->n;
+        cudaStream_t st = (cudaStream_t)s->stream;
+        if (s->dtype == QS_C128) {
+            QS_CUDA(cudaMemcpyAsync(s->amp, host, 16 * N, cudaMemcpyHostToDevice, st), "qs_set_amplitudes");
+        } else {
+            // a host copy as large as the state (32 GiB at 32 qubits): no throw
+            std::unique_ptr<float[]> f(new (std::nothrow) float[2 * N]);
+            if (!f) return qs_fail(QS_ENOMEM, "qs_set_amplitudes: out of host memory");
+            for (uint64_t i = 0; i < 2 * N; i++) f[i] = (float)host[i];
+            QS_CUDA(cudaMemcpyAsync(s->amp, f.get(), 8 * N, cudaMemcpyHostToDevice, st), "qs_set_amplitudes");
+        }
+        QS_CUDA(cudaStreamSynchronize(st), "qs_set_amplitudes sync");
+        s->sup_free = ~0ULL;
+        s->sup_fix = 0;
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_get_amplitudes(qs_state *s, double *host)
 {
-    if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_get_amplitudes: null argument");
-    if (int rc = qs_check_status(s)) return rc;
-    if (int rc = qs_materialize(s)) return rc;
-    uint64_t N = 1ULL << s->n;
-    cudaStream_t st = (cudaStream_t)s->stream;
-    if (s->dtype == QS_C128) {
-        QS_CUDA(cudaMemcpyAsync(host, s->amp, 16 * N, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes");
-        QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes sync");
-    } else {
-        std::unique_ptr<float[]> f(new (std::nothrow) float[2 * N]);
-        if (!f) return qs_fail(QS_ENOMEM, "qs_get_amplitudes: out of host memory");
-        QS_CUDA(cudaMemcpyAsync(f.get(), s->amp, 8 * N, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes");
-        QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes sync");
-        for (uint64_t i = 0; i < 2 * N; i++) host[i] = (double)f[i];
-    }
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_get_amplitudes: null argument");
+        if (int rc = qs_check_status(s)) return rc;
+        if (int rc = qs_materialize(s)) return rc;
+        uint64_t N = 1ULL << s->n;
+        cudaStream_t st = (cudaStream_t)s->stream;
+        if (s->dtype == QS_C128) {
+            QS_CUDA(cudaMemcpyAsync(host, s->amp, 16 * N, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes");
+            QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes sync");
+        } else {
+            std::unique_ptr<float[]> f(new (std::nothrow) float[2 * N]);
+            if (!f) return qs_fail(QS_ENOMEM, "qs_get_amplitudes: out of host memory");
+            QS_CUDA(cudaMemcpyAsync(f.get(), s->amp, 8 * N, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes");
+            QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes sync");
+            for (uint64_t i = 0; i < 2 * N; i++) host[i] = (double)f[i];
+        }
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_get_amplitudes_at(qs_state *s, const uint64_t *idx, int64_t count, double *out)
 {
-    if (!s || !s->amp || count < 0 || (count > 0 && (!idx || !out)))
-        return qs_fail(QS_EINVAL, "qs_get_amplitudes_at: bad arguments");
-    if (int rc = qs_check_status(s)) return rc;
-    if (int rc = qs_materialize(s)) return rc;
-    const uint64_t N = 1ULL << s->n;
-    cudaStream_t st = (cudaStream_t)s->stream;
-    for (int64_t j = 0; j < count; j++) {
-        if (idx[j] >= N) return qs_fail(QS_EINVAL, "qs_get_amplitudes_at: index %lld out of range", (long long)j);
-        if (s->dtype == QS_C128) {
-            QS_CUDA(cudaMemcpyAsync(out + 2 * j, (double2 *)s->amp + idx[j], 16, cudaMemcpyDeviceToHost, st),
-                    "qs_get_amplitudes_at");
-        } else {
-            float f[2];
-            QS_CUDA(cudaMemcpyAsync(f, (float2 *)s->amp + idx[j], 8, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes_at");
-            QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes_at");
-            out[2 * j] = f[0];
-            out[2 * j + 1] = f[1];
+    return qs_guard([&]() -> int {
+        if (!s || !s->amp || count < 0 || (count > 0 && (!idx || !out)))
+            return qs_fail(QS_EINVAL, "qs_get_amplitudes_at: bad arguments");
+        if (int rc = qs_check_status(s)) return rc;
+        if (int rc = qs_materialize(s)) return rc;
+        const uint64_t N = 1ULL << s->n;
+        cudaStream_t st = (cudaStream_t)s->stream;
+        for (int64_t j = 0; j < count; j++) {
+            if (idx[j] >= N) return qs_fail(QS_EINVAL, "qs_get_amplitudes_at: index %lld out of range", (long long)j);
+            if (s->dtype == QS_C128) {
+                QS_CUDA(cudaMemcpyAsync(out + 2 * j, (double2 *)s->amp + idx[j], 16, cudaMemcpyDeviceToHost, st),
+                        "qs_get_amplitudes_at");
+            } else {
+                float f[2];
+                QS_CUDA(cudaMemcpyAsync(f, (float2 *)s->amp + idx[j], 8, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes_at");
+                QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes_at");
+                out[2 * j] = f[0];
+                out[2 * j + 1] = f[1];
+            }
         }
-    }
-    QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes_at");
-    return QS_OK;
+        QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes_at");
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_norm(qs_state *s, double *out)
 {
-    if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_norm: null argument");
-    if (int rc = qs_check_status(s)) return rc;
-    if (int rc = qs_materialize(s)) return rc;
-    return s->dtype == QS_C128 ? stats_impl<double2>(s, out, 1) : stats_impl<float2>(s, out, 1);
+    return qs_guard([&]() -> int {
+        if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_norm: null argument");
+        if (int rc = qs_check_status(s)) return rc;
+        if (int rc = qs_materialize(s)) return rc;
+        return s->dtype == QS_C128 ? stats_impl<double2>(s, out, 1) : stats_impl<float2>(s, out, 1);
+    });
 }
 
 extern "C" int qs_stats(qs_state *s, double out[4])
 {
-    if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_stats: null argument");
-    if (int rc = qs_check_status(s)) return rc;
-    if (int rc = qs_materialize(s)) return rc;
-    return s->dtype == QS_C128 ? stats_impl<double2>(s, out, 4) : stats_impl<float2>(s, out, 4);
+    return qs_guard([&]() -> int {
+        if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_stats: null argument");
+        if (int rc = qs_check_status(s)) return rc;
+        if (int rc = qs_materialize(s)) return rc;
+        return s->dtype == QS_C128 ? stats_impl<double2>(s, out, 4) : stats_impl<float2>(s, out, 4);
+    });
 }
 
 extern "C" int qs_probabilities(qs_state *s, double *out, int out_on_device)
 {
-    if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_probabilities: null argument");
-    if (int rc = qs_materialize(s)) return rc;
-    const uint64_t N = 1ULL << s->n;
-    cudaStream_t st = (cudaStream_t)s->stream;
-    const int sms = sm_count_dev();
-    auto launch = [&](uint64_t first, uint64_t count, double *dst) {
-        int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)sms * 8);
-        if (s->dtype == QS_C128)
-            k_probs<double2><<<grid, 256, 0, st>>>((const double2 *)s->amp, first, count, dst);
-        else
-            k_probs<float2><<<grid, 256, 0, st>>>((const float2 *)s->amp, first, count, dst);
-    };
-    if (out_on_device) {
-        launch(0, N, out);
-        QS_CUDA(cudaGetLastError(), "qs_probabilities");
+    return qs_guard([&]() -> int {
+        if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_probabilities: null argument");
+        if (int rc = qs_materialize(s)) return rc;
+        const uint64_t N = 1ULL << s->n;
+        cudaStream_t st = (cudaStream_t)s->stream;
+        const int sms = sm_count_dev();
+        auto launch = [&](uint64_t first, uint64_t count, double *dst) {
+            int grid = (int)std::min<uint64_t>((count + 255) / 256, (uint64_t)sms * 8);
+            if (s->dtype == QS_C128)
+                k_probs<double2><<<grid, 256, 0, st>>>((const double2 *)s->amp, first, count, dst);
+            else
+                k_probs<float2><<<grid, 256, 0, st>>>((const float2 *)s->amp, first, count, dst);
+        };
+        if (out_on_device) {
+            launch(0, N, out);
+            QS_CUDA(cudaGetLastError(), "qs_probabilities");
+            return QS_OK;
+        }
+        // host output: chunks of at most 2^25 values through the scratch buffer
+        const uint64_t chunk = std::min<uint64_t>(N, 1ULL << 25);
+        void *scr = nullptr;
+        int rc = qs_state_scratch(s, sizeof(double) * chunk, &scr);
+        if (rc) return rc;
+        for (uint64_t first = 0; first < N; first += chunk) {
+            launch(first, chunk, (double *)scr);
+            QS_CUDA(cudaGetLastError(), "qs_probabilities");
+            QS_CUDA(cudaMemcpyAsync(out + first, scr, sizeof(double) * chunk, cudaMemcpyDeviceToHost, st),
+                    "qs_probabilities copy");
+        }
+        QS_CUDA(cudaStreamSynchronize(st), "qs_probabilities sync");
         return QS_OK;
-    }
-    // host output: chunks of at most 2^25 values through the scratch buffer
-    const uint64_t chunk = std::min<uint64_t>(N, 1ULL << 25);
-    void *scr = nullptr;
-    int rc = qs_state_scratch(s, sizeof(double) * chunk, &scr);
-    if (rc) return rc;
-    for (uint64_t first = 0; first < N; first += chunk) {
-        launch(first, chunk, (double *)scr);
-        QS_CUDA(cudaGetLastError(), "qs_probabilities");
-        QS_CUDA(cudaMemcpyAsync(out + first, scr, sizeof(double) * chunk, cudaMemcpyDeviceToHost, st),
-                "qs_probabilities copy");
-    }
-    QS_CUDA(cudaStreamSynchronize(st), "qs_probabilities sync");
-    return QS_OK;
+    });
 }
 
 extern "C" int qs_sample(qs_state *s, uint64_t seed, int64_t m, uint64_t *out)
 {
-    if (!s || !s->amp || m < 0 || (m > 0 && !out)) return qs_fail(QS_EINVAL, "qs_sample: bad arguments");
-    if (int rc = qs_materialize(s)) return rc;
-    return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out, nullptr)
-                               : sample_impl<float2>(s, seed, m, out, nullptr);
+    return qs_guard([&]() -> int {
+        if (!s || !s->amp || m < 0 || (m > 0 && !out)) return qs_fail(QS_EINVAL, "qs_sample: bad arguments");
+        if (int rc = qs_materialize(s)) return rc;
+        return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out, nullptr)
+                                   : sample_impl<float2>(s, seed, m, out, nullptr);
+    });
 }
 
 extern "C" int qs_sample_stats(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double *stats)
 {
-    if (!s || !s->amp || m < 0 || (m > 0 && !out) || !stats)
-        return qs_fail(QS_EINVAL, "qs_sample_stats: bad arguments");
-    if (int rc = qs_check_status(s)) return rc;
-    if (int rc = qs_materialize(s)) return rc;
-    return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out, stats)
-                               : sample_impl<float2>(s, seed, m, out, stats);
+    return qs_guard([&]() -> int {
+        if (!s || !s->amp || m < 0 || (m > 0 && !out) || !stats)
+            return qs_fail(QS_EINVAL, "qs_sample_stats: bad arguments");
+        if (int rc = qs_check_status(s)) return rc;
+        if (int rc = qs_materialize(s)) return rc;
+        return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out, stats)
+                                   : sample_impl<float2>(s, seed, m, out, stats);
+    });
 }
 
 extern "C" int qs_synchronize(qs_state *s)
 {
-    if (!s) return qs_fail(QS_EINVAL, "qs_synchronize: null state");
-    QS_CUDA(cudaStreamSynchronize((cudaStream_t)s->stream), "qs_synchronize");
-    return qs_check_status(s);
+    return qs_guard([&]() -> int {
+        if (!s) return qs_fail(QS_EINVAL, "qs_synchronize: null state");
+        QS_CUDA(cudaStreamSynchronize((cudaStream_t)s->stream), "qs_synchronize");
+        return qs_check_status(s);
+    });
 }
 
 extern "C" int qs_selftest_timeout(qs_state *s)
 {
-    if (!s) return qs_fail(QS_EINVAL, "qs_selftest_timeout: null state");
-    int rc = qs_launch_wait_selftest(s, 1000);
-    if (rc) return rc;
-    QS_CUDA(cudaStreamSynchronize((cudaStream_t)s->stream), "qs_selftest_timeout");
-    return qs_check_status(s);
+    return qs_guard([&]() -> int {
+        if (!s) return qs_fail(QS_EINVAL, "qs_selftest_timeout: null state");
+        int rc = qs_launch_wait_selftest(s, 1000);
+        if (rc) return rc;
+        QS_CUDA(cudaStreamSynchronize((cudaStream_t)s->stream), "qs_selftest_timeout");
+        return qs_check_status(s);
+    });
 }
 
 // --------------------------------------------------------------------------
@@ -968,12 +1011,16 @@ int stats_static_impl(const void *amp, int n, void *stream, double *out)
 
 extern "C" int qs_stats_static(const void *dev_amp, int n, int dtype, void *stream, double out[4])
 {
-    if (!dev_amp || !out || ((uintptr_t)dev_amp & 15))
-        return qs_fail(QS_EINVAL, "qs_stats_static: null or misaligned pointer");
-    if (n < 1 || n > QS_MAX_QUBITS)
-        return qs_fail(QS_EINVAL, "qs_stats_static: n = %d outside [1, %d]", n, QS_MAX_QUBITS);
-    if (dtype != QS_C64 && dtype != QS_C128)
-        return qs_fail(QS_EINVAL, "qs_stats_static: dtype %d", dtype);
-    return dtype == QS_C128 ? stats_static_impl<double2>(dev_amp, n, stream, out)
-                            : stats_static_impl<float2>(dev_amp, n, stream, out);
+    return qs_guard([&]() -> int {
+        if (!dev_amp || !out) return qs_fail(QS_EINVAL, "qs_stats_static: null pointer");
+        if (n < 1 || n > QS_MAX_QUBITS)
+            return qs_fail(QS_EINVAL, "qs_stats_static: n = %d outside [1, %d]", n, QS_MAX_QUBITS);
+        if (dtype != QS_C64 && dtype != QS_C128)
+            return qs_fail(QS_EINVAL, "qs_stats_static: dtype %d", dtype);
+        // the kernel loads whole amplitudes: aligned to their size
+        if ((uintptr_t)dev_amp & (amp_bytes(dtype) - 1))
+            return qs_fail(QS_EINVAL, "qs_stats_static: pointer not aligned to %zu bytes", amp_bytes(dtype));
+        return dtype == QS_C128 ? stats_static_impl<double2>(dev_amp, n, stream, out)
+                                : stats_static_impl<float2>(dev_amp, n, stream, out);
+    });
 }

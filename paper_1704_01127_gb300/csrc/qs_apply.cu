@@ -515,151 +515,168 @@ int launch_op_dense(qs_state *s, const qs_dev_sched &d, size_t i, const qs_op_ho
 
 extern "C" int qs_apply_cluster(qs_state *s, const int *qubits, int k, const double *U)
 {
-    int rc = check_state(s, "qs_apply_cluster");
-    if (rc) return rc;
-    if ((rc = check_qubits(s, qubits, k, QS_MAX_K, "qs_apply_cluster"))) return rc;
-    if (!U) return qs_fail(QS_EINVAL, "qs_apply_cluster: null matrix");
-    int q[QS_MAX_K];
-    std::vector<double> M;
-    sort_targets(qubits, k, U, true, q, M);
-    const bool tc = s->path == QS_PATH_TENSOR ? s->n >= 5
-                                              : s->path == QS_PATH_AUTO && tc_wanted(s->dtype, k, s->n);
-    if (tc) {
-        std::array<int, 5> q5;
-        std::vector<double> M5;
-        if (k == 5) {
-            for (int j = 0; j < 5; j++) q5[j] = q[j];
-            M5 = M;
-        } else {
-            embed5(q, k, M, s->n, q5, M5);
+    return qs_guard([&]() -> int {
+        int rc = check_state(s, "qs_apply_cluster");
+        if (rc) return rc;
+        if ((rc = check_qubits(s, qubits, k, QS_MAX_K, "qs_apply_cluster"))) return rc;
+        if (!U) return qs_fail(QS_EINVAL, "qs_apply_cluster: null matrix");
+        int q[QS_MAX_K];
+        std::vector<double> M;
+        sort_targets(qubits, k, U, true, q, M);
+        const bool tc = s->path == QS_PATH_TENSOR ? s->n >= 5
+                                                  : s->path == QS_PATH_AUTO && tc_wanted(s->dtype, k, s->n);
+        if (tc) {
+            std::array<int, 5> q5;
+            std::vector<double> M5;
+            if (k == 5) {
+                for (int j = 0; j < 5; j++) q5[j] = q[j];
+                M5 = M;
+            } else {
+                embed5(q, k, M, s->n, q5, M5);
+            }
+            std::vector<uint8_t> p = tc_pack_for(s->dtype, M5);
+            void *dp = nullptr;
+            if ((rc = stage(s, p.data(), p.size(), &dp))) return rc;
+            uint64_t grow = 0;
+            for (int j = 0; j < k; j++) grow |= 1ULL << q[j];
+            return qs_launch_dense5_tc(s, q5.data(), dp, grow);
         }
-        std::vector<uint8_t> p = tc_pack_for(s->dtype, M5);
-        void *dp = nullptr;
-        if ((rc = stage(s, p.data(), p.size(), &dp))) return rc;
-        uint64_t grow = 0;
-        for (int j = 0; j < k; j++) grow |= 1ULL << q[j];
-        return qs_launch_dense5_tc(s, q5.data(), dp, grow);
-    }
-    std::vector<uint8_t> packed = to_real(M, s->dtype);
-    void *dU = nullptr;
-    if ((rc = stage(s, packed.data(), packed.size(), &dU))) return rc;
-    return qs_launch_dense(s, q, k, dU, nullptr);
+        std::vector<uint8_t> packed = to_real(M, s->dtype);
+        void *dU = nullptr;
+        if ((rc = stage(s, packed.data(), packed.size(), &dU))) return rc;
+        return qs_launch_dense(s, q, k, dU, nullptr);
+    });
 }
 
 extern "C" int qs_apply_diag(qs_state *s, const int *qubits, int k, const double *d)
 {
-    int rc = check_state(s, "qs_apply_diag");
-    if (rc) return rc;
-    if ((rc = check_qubits(s, qubits, k, QS_MAX_DIAG_K, "qs_apply_diag"))) return rc;
-    if (!d) return qs_fail(QS_EINVAL, "qs_apply_diag: null table");
-    int q[QS_MAX_DIAG_K];
-    std::vector<double> M;
-    sort_targets(qubits, k, d, false, q, M);
-    std::vector<uint8_t> tab = to_real(M, s->dtype);
-    std::vector<uint8_t> blob(64 + tab.size());
-    std::memcpy(blob.data(), q, sizeof(int) * k);
-    std::memcpy(blob.data() + 64, tab.data(), tab.size());
-    void *dev = nullptr;
-    if ((rc = stage(s, blob.data(), blob.size(), &dev))) return rc;
-    return qs_launch_diag(s, (const int *)dev, k, (const uint8_t *)dev + 64);
+    return qs_guard([&]() -> int {
+        int rc = check_state(s, "qs_apply_diag");
+        if (rc) return rc;
+        if ((rc = check_qubits(s, qubits, k, QS_MAX_DIAG_K, "qs_apply_diag"))) return rc;
+        if (!d) return qs_fail(QS_EINVAL, "qs_apply_diag: null table");
+        int q[QS_MAX_DIAG_K];
+        std::vector<double> M;
+        sort_targets(qubits, k, d, false, q, M);
+        std::vector<uint8_t> tab = to_real(M, s->dtype);
+        std::vector<uint8_t> blob(64 + tab.size());
+        std::memcpy(blob.data(), q, sizeof(int) * k);
+        std::memcpy(blob.data() + 64, tab.data(), tab.size());
+        void *dev = nullptr;
+        if ((rc = stage(s, blob.data(), blob.size(), &dev))) return rc;
+        return qs_launch_diag(s, (const int *)dev, k, (const uint8_t *)dev + 64);
+    });
 }
 
 extern "C" int qs_apply_phase(qs_state *s, const int *coeff, int n_edges, const int *edges)
 {
-    int rc = check_state(s, "qs_apply_phase");
-    if (rc) return rc;
-    if (!coeff || n_edges < 0 || (n_edges > 0 && !edges))
-        return qs_fail(QS_EINVAL, "qs_apply_phase: bad arguments");
-    std::vector<int32_t> c(coeff, coeff + s->n);
-    std::vector<std::pair<int, int>> e;
-    for (int i = 0; i < n_edges; i++) {
-        int a = edges[2 * i], b = edges[2 * i + 1];
-        if (a < 0 || a >= s->n || b < 0 || b >= s->n || a == b)
-            return qs_fail(QS_EINVAL, "qs_apply_phase: bad edge %d", i);
-        e.push_back({a, b});
-    }
-    int n_act;
-    std::vector<uint8_t> blob = qs_pack_phase(s->n, c, e, &n_act);
-    void *dev = nullptr;
-    if ((rc = stage(s, blob.data(), blob.size(), &dev))) return rc;
-    return qs_launch_phase(s, dev, n_act);
+    return qs_guard([&]() -> int {
+        int rc = check_state(s, "qs_apply_phase");
+        if (rc) return rc;
+        if (!coeff || n_edges < 0 || (n_edges > 0 && !edges))
+            return qs_fail(QS_EINVAL, "qs_apply_phase: bad arguments");
+        std::vector<int32_t> c(coeff, coeff + s->n);
+        std::vector<std::pair<int, int>> e;
+        for (int i = 0; i < n_edges; i++) {
+            int a = edges[2 * i], b = edges[2 * i + 1];
+            if (a < 0 || a >= s->n || b < 0 || b >= s->n || a == b)
+                return qs_fail(QS_EINVAL, "qs_apply_phase: bad edge %d", i);
+            e.push_back({a, b});
+        }
+        int n_act;
+        std::vector<uint8_t> blob = qs_pack_phase(s->n, c, e, &n_act);
+        void *dev = nullptr;
+        if ((rc = stage(s, blob.data(), blob.size(), &dev))) return rc;
+        return qs_launch_phase(s, dev, n_act);
+    });
 }
 
 extern "C" int qs_run_circuit(qs_state *s, const qs_schedule *sc)
 {
-    int rc = check_state(s, "qs_run_circuit");
-    if (rc) return rc;
-    if (!sc || sc->n != s->n) return qs_fail(QS_EINVAL, "qs_run_circuit: schedule/state qubit mismatch");
-    if ((rc = ensure_dev_schedule(s, sc))) return rc;
-    const qs_dev_sched &d = sc->dev[s->dtype];
-    for (size_t i = 0; i < sc->ops.size(); i++) {
-        const qs_op_host &op = sc->ops[i];
-        const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
-        if (op.kind == QS_OP_DENSE) {
-            bool folded;
-            rc = launch_op_dense(s, d, i, op, data, &folded);
-            if (folded) i++;   // the phase op after it ran inside the sweep
-        } else if (op.kind == QS_OP_DIAG) {
-            rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
-        } else {
-            rc = qs_launch_phase(s, data, d.n_act[i]);
-        }
+    return qs_guard([&]() -> int {
+        int rc = check_state(s, "qs_run_circuit");
         if (rc) return rc;
-    }
-    return QS_OK;
+        if (!sc || sc->n != s->n) return qs_fail(QS_EINVAL, "qs_run_circuit: schedule/state qubit mismatch");
+        if ((rc = ensure_dev_schedule(s, sc))) return rc;
+        const qs_dev_sched &d = sc->dev[s->dtype];
+        for (size_t i = 0; i < sc->ops.size(); i++) {
+            const qs_op_host &op = sc->ops[i];
+            const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
+            if (op.kind == QS_OP_DENSE) {
+                bool folded;
+                rc = launch_op_dense(s, d, i, op, data, &folded);
+                if (folded) i++;   // the phase op after it ran inside the sweep
+            } else if (op.kind == QS_OP_DIAG) {
+                rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
+            } else {
+                rc = qs_launch_phase(s, data, d.n_act[i]);
+            }
+            if (rc) return rc;
+        }
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *op_ms)
 {
-    int rc = check_state(s, "qs_run_circuit_timed");
-    if (rc) return rc;
-    if (!sc || sc->n != s->n || !op_ms)
-        return qs_fail(QS_EINVAL, "qs_run_circuit_timed: bad schedule or output");
-    if ((rc = ensure_dev_schedule(s, sc))) return rc;
-    const qs_dev_sched &d = sc->dev[s->dtype];
-    cudaStream_t st = (cudaStream_t)s->stream;
-    size_t nops = sc->ops.size();
-    std::vector<cudaEvent_t> ev(nops + 1);
-    std::vector<char> skipped(nops, 0);
-    for (auto &e : ev)
-        if (cudaEventCreate(&e) != cudaSuccess) return qs_fail(QS_ECUDA, "event create");
-    cudaEventRecord(ev[0], st);
-    for (size_t i = 0; i < nops && !rc; i++) {
-        const qs_op_host &op = sc->ops[i];
-        const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
-        bool folded = false;
-        if (op.kind == QS_OP_DENSE) rc = launch_op_dense(s, d, i, op, data, &folded);
-        else if (op.kind == QS_OP_DIAG) rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
-        else rc = qs_launch_phase(s, data, d.n_act[i]);
-        cudaEventRecord(ev[i + 1], st);
-        if (folded) {   // the phase op after it ran inside the sweep
-            skipped[++i] = 1;
-            cudaEventRecord(ev[i + 1], st);
-        }
-    }
-    if (!rc) {
-        cudaError_t e = cudaEventSynchronize(ev[nops]);
-        if (e != cudaSuccess) rc = qs_fail(QS_ECUDA, "qs_run_circuit_timed: %s", cudaGetErrorString(e));
+    return qs_guard([&]() -> int {
+        int rc = check_state(s, "qs_run_circuit_timed");
+        if (rc) return rc;
+        if (!sc || sc->n != s->n || !op_ms)
+            return qs_fail(QS_EINVAL, "qs_run_circuit_timed: bad schedule or output");
+        if ((rc = ensure_dev_schedule(s, sc))) return rc;
+        const qs_dev_sched &d = sc->dev[s->dtype];
+        cudaStream_t st = (cudaStream_t)s->stream;
+        size_t nops = sc->ops.size();
+        std::vector<cudaEvent_t> ev(nops + 1);
+        std::vector<char> skipped(nops, 0);
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return qs_fail(QS_ECUDA, "event create");
+        cudaEventRecord(ev[0], st);
         for (size_t i = 0; i < nops && !rc; i++) {
-            if (skipped[i]) op_ms[i] = -1.0f;
-            else cudaEventElapsedTime(&op_ms[i], ev[i], ev[i + 1]);
+            const qs_op_host &op = sc->ops[i];
+            const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
+            bool folded = false;
+            if (op.kind == QS_OP_DENSE) rc = launch_op_dense(s, d, i, op, data, &folded);
+            else if (op.kind == QS_OP_DIAG) rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
+            else rc = qs_launch_phase(s, data, d.n_act[i]);
+            cudaEventRecord(ev[i + 1], st);
+            if (folded) {   // the phase op after it ran inside the sweep
+                skipped[++i] = 1;
+                cudaEventRecord(ev[i + 1], st);
+            }
         }
-    }
-    for (auto &e : ev) cudaEventDestroy(e);
-    return rc;
+        if (!rc) {
+            cudaError_t e = cudaEventSynchronize(ev[nops]);
+            if (e != cudaSuccess) rc = qs_fail(QS_ECUDA, "qs_run_circuit_timed: %s", cudaGetErrorString(e));
+            for (size_t i = 0; i < nops && !rc; i++) {
+                if (skipped[i]) op_ms[i] = -1.0f;
+                else cudaEventElapsedTime(&op_ms[i], ev[i], ev[i + 1]);
+            }
+        }
+        for (auto &e : ev) cudaEventDestroy(e);
+        return rc;
+    });
 }
 
 extern "C" int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype)
 {
-    if (!sc || (dtype != QS_C64 && dtype != QS_C128)) return qs_fail(QS_EINVAL, "qs_schedule_upload_bytes");
-    qs_dev_sched tmp;
-    return (int64_t)schedule_blob(sc, dtype, tmp).size();
+    int64_t bytes = 0;
+    const int rc = qs_guard([&]() -> int {
+        if (!sc || (dtype != QS_C64 && dtype != QS_C128)) return qs_fail(QS_EINVAL, "qs_schedule_upload_bytes");
+        qs_dev_sched tmp;
+        bytes = (int64_t)schedule_blob(sc, dtype, tmp).size();
+        return QS_OK;
+    });
+    return rc == QS_OK ? bytes : rc;
 }
 
 extern "C" int qs_set_device(int device)
 {
-    cudaError_t e = cudaSetDevice(device);
-    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_set_device(%d): %s", device, cudaGetErrorString(e));
+    return qs_guard([&]() -> int {
+        cudaError_t e = cudaSetDevice(device);
+        return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_set_device(%d): %s", device, cudaGetErrorString(e));
+    });
 }
 
 extern "C" void qs_schedule_free(qs_schedule *sc)

@@ -247,94 +247,98 @@ bool valid_config(int C, int block)
 
 extern "C" int qs_batch_circuit_params(uint64_t seed, int *rows, int *cols, int *cz_cycles)
 {
-    if (!rows || !cols || !cz_cycles) return qs_fail(QS_EINVAL, "qs_batch_circuit_params: null output");
-    static const int grids[3][2] = {{4, 4}, {4, 5}, {3, 7}};
-    const uint64_t r = splitmix64(seed ^ 0x6A09E667F3BCC909ULL, 0);
-    const int g = (int)(r % 3);
-    *rows = grids[g][0];
-    *cols = grids[g][1];
-    *cz_cycles = 8 + (int)((r >> 32) % 33);
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!rows || !cols || !cz_cycles) return qs_fail(QS_EINVAL, "qs_batch_circuit_params: null output");
+        static const int grids[3][2] = {{4, 4}, {4, 5}, {3, 7}};
+        const uint64_t r = splitmix64(seed ^ 0x6A09E667F3BCC909ULL, 0);
+        const int g = (int)(r % 3);
+        *rows = grids[g][0];
+        *cols = grids[g][1];
+        *cz_cycles = 8 + (int)((r >> 32) % 33);
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_batch_create(int n_circ, const qs_schedule *const *scheds, int dtype, void *stream, qs_batch **out)
 {
-    if (!out || n_circ < 1 || !scheds || (dtype != QS_C64 && dtype != QS_C128))
-        return qs_fail(QS_EINVAL, "qs_batch_create: bad arguments");
-    const size_t rsz = dtype == QS_C128 ? 8 : 4;
-    std::vector<BatchCirc> circ(n_circ);
-    std::vector<BatchOp> ops;
-    std::vector<uint8_t> pool;
-    std::vector<double> cost(n_circ, 0.0);
-    qs_batch *b = new (std::nothrow) qs_batch();
-    if (!b) return qs_fail(QS_ENOMEM, "qs_batch_create: out of host memory");
-    b->dtype = dtype;
-    b->n_circ = n_circ;
-    b->stream = stream;
-    uint64_t amp_total = 0;
-    for (int c = 0; c < n_circ; c++) {
-        const qs_schedule *sc = scheds[c];
-        if (!sc || sc->n < 1 || sc->n > 26) {
-            delete b;
-            return qs_fail(QS_EINVAL, "qs_batch_create: circuit %d must have 1..26 qubits", c);
-        }
-        circ[c].n = sc->n;
-        circ[c].n_ops = (int32_t)sc->ops.size();
-        circ[c].op_first = (int64_t)ops.size();
-        circ[c].amp_off = (int64_t)amp_total;
-        b->nq.push_back(sc->n);
-        b->amp_off.push_back(amp_total);
-        amp_total += ((1ULL << sc->n) + 31) & ~31ULL;   // 256-byte aligned states
-        for (const qs_op_host &op : sc->ops) {
-            BatchOp bo;
-            std::memset(&bo, 0, sizeof(bo));
-            bo.kind = op.kind;
-            bo.k = op.k;
-            size_t at = (pool.size() + 255) & ~(size_t)255;
-            if (op.kind == QS_OP_DENSE) {
-                for (int j = 0; j < op.k; j++) bo.q[j] = op.qubits[j];
-                pool.resize(at + op.matrix.size() * rsz);
-                for (size_t i = 0; i < op.matrix.size(); i++) {
-                    if (dtype == QS_C128) std::memcpy(pool.data() + at + 8 * i, &op.matrix[i], 8);
-                    else {
-                        float f = (float)op.matrix[i];
-                        std::memcpy(pool.data() + at + 4 * i, &f, 4);
-                    }
-                }
-                cost[c] += (double)(1ULL << sc->n) * (1 + (1 << op.k) / 8.0);
-            } else if (op.kind == QS_OP_PHASE) {
-                int n_act = 0;
-                std::vector<uint8_t> ph = qs_pack_phase(sc->n, op.coeff, op.edges, &n_act);
-                bo.n_act = n_act;
-                pool.resize(at + ph.size());
-                std::memcpy(pool.data() + at, ph.data(), ph.size());
-                cost[c] += (double)(1ULL << sc->n);
-            } else {
+    return qs_guard([&]() -> int {
+        if (!out || n_circ < 1 || !scheds || (dtype != QS_C64 && dtype != QS_C128))
+            return qs_fail(QS_EINVAL, "qs_batch_create: bad arguments");
+        const size_t rsz = dtype == QS_C128 ? 8 : 4;
+        std::vector<BatchCirc> circ(n_circ);
+        std::vector<BatchOp> ops;
+        std::vector<uint8_t> pool;
+        std::vector<double> cost(n_circ, 0.0);
+        qs_batch *b = new (std::nothrow) qs_batch();
+        if (!b) return qs_fail(QS_ENOMEM, "qs_batch_create: out of host memory");
+        b->dtype = dtype;
+        b->n_circ = n_circ;
+        b->stream = stream;
+        uint64_t amp_total = 0;
+        for (int c = 0; c < n_circ; c++) {
+            const qs_schedule *sc = scheds[c];
+            if (!sc || sc->n < 1 || sc->n > 26) {
                 delete b;
-                return qs_fail(QS_EUNSUPPORTED, "qs_batch_create: table diagonals are not batched");
+                return qs_fail(QS_EINVAL, "qs_batch_create: circuit %d must have 1..26 qubits", c);
             }
-            bo.data = at;
-            ops.push_back(bo);
+            circ[c].n = sc->n;
+            circ[c].n_ops = (int32_t)sc->ops.size();
+            circ[c].op_first = (int64_t)ops.size();
+            circ[c].amp_off = (int64_t)amp_total;
+            b->nq.push_back(sc->n);
+            b->amp_off.push_back(amp_total);
+            amp_total += ((1ULL << sc->n) + 31) & ~31ULL;   // 256-byte aligned states
+            for (const qs_op_host &op : sc->ops) {
+                BatchOp bo;
+                std::memset(&bo, 0, sizeof(bo));
+                bo.kind = op.kind;
+                bo.k = op.k;
+                size_t at = (pool.size() + 255) & ~(size_t)255;
+                if (op.kind == QS_OP_DENSE) {
+                    for (int j = 0; j < op.k; j++) bo.q[j] = op.qubits[j];
+                    pool.resize(at + op.matrix.size() * rsz);
+                    for (size_t i = 0; i < op.matrix.size(); i++) {
+                        if (dtype == QS_C128) std::memcpy(pool.data() + at + 8 * i, &op.matrix[i], 8);
+                        else {
+                            float f = (float)op.matrix[i];
+                            std::memcpy(pool.data() + at + 4 * i, &f, 4);
+                        }
+                    }
+                    cost[c] += (double)(1ULL << sc->n) * (1 + (1 << op.k) / 8.0);
+                } else if (op.kind == QS_OP_PHASE) {
+                    int n_act = 0;
+                    std::vector<uint8_t> ph = qs_pack_phase(sc->n, op.coeff, op.edges, &n_act);
+                    bo.n_act = n_act;
+                    pool.resize(at + ph.size());
+                    std::memcpy(pool.data() + at, ph.data(), ph.size());
+                    cost[c] += (double)(1ULL << sc->n);
+                } else {
+                    delete b;
+                    return qs_fail(QS_EUNSUPPORTED, "qs_batch_create: table diagonals are not batched");
+                }
+                bo.data = at;
+                ops.push_back(bo);
+            }
         }
-    }
-    std::vector<int> order(n_circ);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-    int rc = QS_OK;
-    cudaError_t e = cudaMalloc(&b->amp, amp_total * 2 * rsz);
-    if (e != cudaSuccess) rc = qs_fail(QS_ENOMEM, "qs_batch_create: states: %s", cudaGetErrorString(e));
-    if (!rc) rc = upload(&b->ops, ops);
-    if (!rc) rc = upload(&b->circ, circ);
-    if (!rc) rc = upload(&b->order, order);
-    if (!rc) rc = upload(&b->pool, pool);
-    if (!rc && (e = cudaMalloc(&b->stats, sizeof(double) * 4 * n_circ)) != cudaSuccess)
-        rc = qs_fail(QS_ENOMEM, "qs_batch_create: stats: %s", cudaGetErrorString(e));
-    if (rc) {
-        qs_batch_free(b);
-        return rc;
-    }
-    *out = b;
-    return QS_OK;
+        std::vector<int> order(n_circ);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+        int rc = QS_OK;
+        cudaError_t e = cudaMalloc(&b->amp, amp_total * 2 * rsz);
+        if (e != cudaSuccess) rc = qs_fail(QS_ENOMEM, "qs_batch_create: states: %s", cudaGetErrorString(e));
+        if (!rc) rc = upload(&b->ops, ops);
+        if (!rc) rc = upload(&b->circ, circ);
+        if (!rc) rc = upload(&b->order, order);
+        if (!rc) rc = upload(&b->pool, pool);
+        if (!rc && (e = cudaMalloc(&b->stats, sizeof(double) * 4 * n_circ)) != cudaSuccess)
+            rc = qs_fail(QS_ENOMEM, "qs_batch_create: stats: %s", cudaGetErrorString(e));
+        if (rc) {
+            qs_batch_free(b);
+            return rc;
+        }
+        *out = b;
+        return QS_OK;
+    });
 }
 
 extern "C" void qs_batch_free(qs_batch *b)
@@ -350,132 +354,146 @@ extern "C" void qs_batch_free(qs_batch *b)
 
 extern "C" int qs_batch_set_config(qs_batch *b, int cluster_ctas, int threads)
 {
-    if (!b || !valid_config(cluster_ctas, threads)) return qs_fail(QS_EINVAL, "qs_batch_set_config");
-    b->cluster = cluster_ctas;
-    b->block = threads;
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!b || !valid_config(cluster_ctas, threads)) return qs_fail(QS_EINVAL, "qs_batch_set_config");
+        b->cluster = cluster_ctas;
+        b->block = threads;
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_batch_get_config(const qs_batch *b, int *cluster_ctas, int *threads)
 {
-    if (!b || !cluster_ctas || !threads) return qs_fail(QS_EINVAL, "qs_batch_get_config");
-    *cluster_ctas = b->cluster;
-    *threads = b->block;
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!b || !cluster_ctas || !threads) return qs_fail(QS_EINVAL, "qs_batch_get_config");
+        *cluster_ctas = b->cluster;
+        *threads = b->block;
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_batch_run(qs_batch *b)
 {
-    if (!b) return qs_fail(QS_EINVAL, "qs_batch_run: null batch");
-    return launch_batch(b, b->cluster, b->block);
+    return qs_guard([&]() -> int {
+        if (!b) return qs_fail(QS_EINVAL, "qs_batch_run: null batch");
+        return launch_batch(b, b->cluster, b->block);
+    });
 }
 
 extern "C" int qs_batch_run_graph(qs_batch *b)
 {
-    if (!b) return qs_fail(QS_EINVAL, "qs_batch_run_graph: null batch");
-    cudaStream_t st = (cudaStream_t)b->stream;
-    if (!st) return qs_fail(QS_EINVAL, "qs_batch_run_graph: needs a non-default stream");
-    if (!b->exec || b->exec_cluster != b->cluster || b->exec_block != b->block) {
-        if (b->exec) {
-            cudaGraphExecDestroy(b->exec);
-            b->exec = nullptr;
+    return qs_guard([&]() -> int {
+        if (!b) return qs_fail(QS_EINVAL, "qs_batch_run_graph: null batch");
+        cudaStream_t st = (cudaStream_t)b->stream;
+        if (!st) return qs_fail(QS_EINVAL, "qs_batch_run_graph: needs a non-default stream");
+        if (!b->exec || b->exec_cluster != b->cluster || b->exec_block != b->block) {
+            if (b->exec) {
+                cudaGraphExecDestroy(b->exec);
+                b->exec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return qs_fail(QS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+            int rc = launch_batch(b, b->cluster, b->block);
+            e = cudaStreamEndCapture(st, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return qs_fail(QS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&b->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                b->exec = nullptr;
+                return qs_fail(QS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            }
+            b->exec_cluster = b->cluster;
+            b->exec_block = b->block;
         }
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return qs_fail(QS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        int rc = launch_batch(b, b->cluster, b->block);
-        e = cudaStreamEndCapture(st, &g);
-        if (rc) {
-            if (g) cudaGraphDestroy(g);
-            return rc;
-        }
-        if (e != cudaSuccess) return qs_fail(QS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&b->exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            b->exec = nullptr;
-            return qs_fail(QS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-        }
-        b->exec_cluster = b->cluster;
-        b->exec_block = b->block;
-    }
-    cudaError_t e = cudaGraphLaunch(b->exec, st);
-    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+        cudaError_t e = cudaGraphLaunch(b->exec, st);
+        return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+    });
 }
 
 extern "C" int qs_batch_stats(qs_batch *b, double *out)
 {
-    if (!b || !out) return qs_fail(QS_EINVAL, "qs_batch_stats: bad arguments");
-    cudaStream_t st = (cudaStream_t)b->stream;
-    if (b->dtype == QS_C128)
-        k_batch_stats<double><<<b->n_circ, 256, 0, st>>>((const BatchCirc *)b->circ, (const double2 *)b->amp,
-                                                         (double *)b->stats);
-    else
-        k_batch_stats<float><<<b->n_circ, 256, 0, st>>>((const BatchCirc *)b->circ, (const float2 *)b->amp,
-                                                        (double *)b->stats);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, b->stats, sizeof(double) * 4 * b->n_circ, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_batch_stats: %s", cudaGetErrorString(e));
+    return qs_guard([&]() -> int {
+        if (!b || !out) return qs_fail(QS_EINVAL, "qs_batch_stats: bad arguments");
+        cudaStream_t st = (cudaStream_t)b->stream;
+        if (b->dtype == QS_C128)
+            k_batch_stats<double><<<b->n_circ, 256, 0, st>>>((const BatchCirc *)b->circ, (const double2 *)b->amp,
+                                                             (double *)b->stats);
+        else
+            k_batch_stats<float><<<b->n_circ, 256, 0, st>>>((const BatchCirc *)b->circ, (const float2 *)b->amp,
+                                                            (double *)b->stats);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, b->stats, sizeof(double) * 4 * b->n_circ, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_batch_stats: %s", cudaGetErrorString(e));
+    });
 }
 
 extern "C" int qs_batch_get_amplitudes(qs_batch *b, int i, double *host)
 {
-    if (!b || !host || i < 0 || i >= b->n_circ) return qs_fail(QS_EINVAL, "qs_batch_get_amplitudes: bad arguments");
-    const uint64_t N = 1ULL << b->nq[i];
-    cudaStream_t st = (cudaStream_t)b->stream;
-    cudaError_t e;
-    if (b->dtype == QS_C128) {
-        e = cudaMemcpyAsync(host, (double2 *)b->amp + b->amp_off[i], 16 * N, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    } else {
-        std::vector<float> f(2 * N);
-        e = cudaMemcpyAsync(f.data(), (float2 *)b->amp + b->amp_off[i], 8 * N, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        for (uint64_t j = 0; j < 2 * N; j++) host[j] = f[j];
-    }
-    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_batch_get_amplitudes: %s", cudaGetErrorString(e));
+    return qs_guard([&]() -> int {
+        if (!b || !host || i < 0 || i >= b->n_circ) return qs_fail(QS_EINVAL, "qs_batch_get_amplitudes: bad arguments");
+        const uint64_t N = 1ULL << b->nq[i];
+        cudaStream_t st = (cudaStream_t)b->stream;
+        cudaError_t e;
+        if (b->dtype == QS_C128) {
+            e = cudaMemcpyAsync(host, (double2 *)b->amp + b->amp_off[i], 16 * N, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        } else {
+            std::vector<float> f(2 * N);
+            e = cudaMemcpyAsync(f.data(), (float2 *)b->amp + b->amp_off[i], 8 * N, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            for (uint64_t j = 0; j < 2 * N; j++) host[j] = f[j];
+        }
+        return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_batch_get_amplitudes: %s", cudaGetErrorString(e));
+    });
 }
 
 // Time every launch configuration (cluster of 1, 2, 4, 8 CTAs x 128, 256, 512
 // threads), keep the fastest in the batch and report it.
 extern "C" int qs_batch_tune(qs_batch *b, int *cluster_ctas, int *threads, float *ms)
 {
-    if (!b) return qs_fail(QS_EINVAL, "qs_batch_tune: null batch");
-    cudaStream_t st = (cudaStream_t)b->stream;
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-        return qs_fail(QS_ECUDA, "qs_batch_tune: events");
-    float best = 1e30f;
-    int bc = 1, bt = 256, rc = QS_OK;
-    for (int C : {1, 2, 4, 8})
-        for (int T : {128, 256, 512}) {
-            if ((rc = launch_batch(b, C, T))) break;   // warm-up
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < 2 && !rc; r++) rc = launch_batch(b, C, T);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                rc = qs_fail(QS_ECUDA, "qs_batch_tune: sync");
-                break;
+    return qs_guard([&]() -> int {
+        if (!b) return qs_fail(QS_EINVAL, "qs_batch_tune: null batch");
+        cudaStream_t st = (cudaStream_t)b->stream;
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+            return qs_fail(QS_ECUDA, "qs_batch_tune: events");
+        float best = 1e30f;
+        int bc = 1, bt = 256, rc = QS_OK;
+        for (int C : {1, 2, 4, 8})
+            for (int T : {128, 256, 512}) {
+                if ((rc = launch_batch(b, C, T))) break;   // warm-up
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 2 && !rc; r++) rc = launch_batch(b, C, T);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = qs_fail(QS_ECUDA, "qs_batch_tune: sync");
+                    break;
+                }
+                float t = 0;
+                cudaEventElapsedTime(&t, e0, e1);
+                t /= 2;
+                if (t < best) {
+                    best = t;
+                    bc = C;
+                    bt = T;
+                }
             }
-            float t = 0;
-            cudaEventElapsedTime(&t, e0, e1);
-            t /= 2;
-            if (t < best) {
-                best = t;
-                bc = C;
-                bt = T;
-            }
-        }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (rc) return rc;
-    b->cluster = bc;
-    b->block = bt;
-    if (cluster_ctas) *cluster_ctas = bc;
-    if (threads) *threads = bt;
-    if (ms) *ms = best;
-    return QS_OK;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        b->cluster = bc;
+        b->block = bt;
+        if (cluster_ctas) *cluster_ctas = bc;
+        if (threads) *threads = bt;
+        if (ms) *ms = best;
+        return QS_OK;
+    });
 }
 
 // Autotune the whole batched path: schedules with k_max in {3, 4, 5}, each
@@ -483,29 +501,31 @@ extern "C" int qs_batch_tune(qs_batch *b, int *cluster_ctas, int *threads, float
 extern "C" int qs_batch_autotune(int n_circ, const int *n_qubits, const qs_gate *const *gates, const int *n_gates,
                                  int dtype, void *stream, int *k_max, int *cluster_ctas, int *threads, float *ms)
 {
-    if (n_circ < 1 || !n_qubits || !gates || !n_gates || !k_max || !cluster_ctas || !threads)
-        return qs_fail(QS_EINVAL, "qs_batch_autotune: bad arguments");
-    float best = 1e30f;
-    int rc = QS_OK;
-    for (int km : {3, 4, 5}) {
-        std::vector<qs_schedule *> sc(n_circ, nullptr);
-        qs_sched_opts o = {km, 1, 1, 0, 1, 1, 1, 1, 0};
-        for (int c = 0; c < n_circ && !rc; c++) rc = qs_schedule_build(n_qubits[c], gates[c], n_gates[c], &o, &sc[c]);
-        qs_batch *b = nullptr;
-        if (!rc) rc = qs_batch_create(n_circ, sc.data(), dtype, stream, &b);
-        int C = 1, T = 256;
-        float t = 0;
-        if (!rc) rc = qs_batch_tune(b, &C, &T, &t);
-        if (!rc && t < best) {
-            best = t;
-            *k_max = km;
-            *cluster_ctas = C;
-            *threads = T;
+    return qs_guard([&]() -> int {
+        if (n_circ < 1 || !n_qubits || !gates || !n_gates || !k_max || !cluster_ctas || !threads)
+            return qs_fail(QS_EINVAL, "qs_batch_autotune: bad arguments");
+        float best = 1e30f;
+        int rc = QS_OK;
+        for (int km : {3, 4, 5}) {
+            std::vector<qs_schedule *> sc(n_circ, nullptr);
+            qs_sched_opts o = {km, 1, 1, 0, 1, 1, 1, 1, 0};
+            for (int c = 0; c < n_circ && !rc; c++) rc = qs_schedule_build(n_qubits[c], gates[c], n_gates[c], &o, &sc[c]);
+            qs_batch *b = nullptr;
+            if (!rc) rc = qs_batch_create(n_circ, sc.data(), dtype, stream, &b);
+            int C = 1, T = 256;
+            float t = 0;
+            if (!rc) rc = qs_batch_tune(b, &C, &T, &t);
+            if (!rc && t < best) {
+                best = t;
+                *k_max = km;
+                *cluster_ctas = C;
+                *threads = T;
+            }
+            qs_batch_free(b);
+            for (qs_schedule *s : sc) qs_schedule_free(s);
+            if (rc) return rc;
         }
-        qs_batch_free(b);
-        for (qs_schedule *s : sc) qs_schedule_free(s);
-        if (rc) return rc;
-    }
-    if (ms) *ms = best;
-    return QS_OK;
+        if (ms) *ms = best;
+        return QS_OK;
+    });
 }

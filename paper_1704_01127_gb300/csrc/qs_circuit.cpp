@@ -918,24 +918,30 @@ extern "C" int qs_supremacy_circuit(int rows, int cols, const int *removed_rc, i
                                     int cz_cycles, uint64_t seed, int *n_qubits,
                                     qs_gate *gates, int max_gates, int *n_gates)
 {
-    return guarded("qs_supremacy_circuit", [&] {
-        return supremacy_circuit_impl(rows, cols, removed_rc, n_removed, cz_cycles, seed, n_qubits, gates,
-                                      max_gates, n_gates);
+    return qs_guard([&]() -> int {
+        return guarded("qs_supremacy_circuit", [&] {
+            return supremacy_circuit_impl(rows, cols, removed_rc, n_removed, cz_cycles, seed, n_qubits, gates,
+                                          max_gates, n_gates);
+        });
     });
 }
 
 extern "C" int qs_schedule_build(int n, const qs_gate *gates, int n_gates,
                                  const qs_sched_opts *opts, qs_schedule **out)
 {
-    return guarded("qs_schedule_build", [&] { return schedule_build_impl(n, gates, n_gates, opts, out); });
+    return qs_guard([&]() -> int {
+        return guarded("qs_schedule_build", [&] { return schedule_build_impl(n, gates, n_gates, opts, out); });
+    });
 }
 
 extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const int *ks,
                                     const int *qubits, const int64_t *offsets,
                                     const double *pool, int64_t pool_len, qs_schedule **out)
 {
-    return guarded("qs_schedule_from_ops", [&] {
-        return schedule_from_ops_impl(n, n_ops, kinds, ks, qubits, offsets, pool, pool_len, out);
+    return qs_guard([&]() -> int {
+        return guarded("qs_schedule_from_ops", [&] {
+            return schedule_from_ops_impl(n, n_ops, kinds, ks, qubits, offsets, pool, pool_len, out);
+        });
     });
 }
 
@@ -945,29 +951,31 @@ extern "C" int qs_schedule_num_ops(const qs_schedule *sc) { return sc ? (int)sc-
 extern "C" int qs_schedule_op(const qs_schedule *sc, int i, qs_op_info *info, double *matrix,
                               int32_t *gate_idx, int32_t *coeff, int32_t *edges)
 {
-    if (!sc || i < 0 || i >= (int)sc->ops.size())
-        return qs_fail(QS_EINVAL, "qs_schedule_op: bad schedule or index");
-    const qs_op_host &op = sc->ops[i];
-    if (info) {
-        std::memset(info, 0, sizeof(*info));
-        info->kind = op.kind;
-        info->k = op.k;
-        for (int j = 0; j < QS_MAX_K && j < op.k; j++) info->qubits[j] = op.qubits[j];
-        info->n_gates = (int32_t)op.gates.size();
-        info->n_edges = (int32_t)op.edges.size();
-    }
-    if (matrix && !op.matrix.empty())
-        std::memcpy(matrix, op.matrix.data(), sizeof(double) * op.matrix.size());
-    if (gate_idx && !op.gates.empty())
-        std::memcpy(gate_idx, op.gates.data(), sizeof(int32_t) * op.gates.size());
-    if (coeff && op.kind == QS_OP_PHASE)
-        std::memcpy(coeff, op.coeff.data(), sizeof(int32_t) * op.coeff.size());
-    if (edges && op.kind == QS_OP_PHASE)
-        for (size_t e = 0; e < op.edges.size(); e++) {
-            edges[2 * e] = op.edges[e].first;
-            edges[2 * e + 1] = op.edges[e].second;
+    return qs_guard([&]() -> int {
+        if (!sc || i < 0 || i >= (int)sc->ops.size())
+            return qs_fail(QS_EINVAL, "qs_schedule_op: bad schedule or index");
+        const qs_op_host &op = sc->ops[i];
+        if (info) {
+            std::memset(info, 0, sizeof(*info));
+            info->kind = op.kind;
+            info->k = op.k;
+            for (int j = 0; j < QS_MAX_K && j < op.k; j++) info->qubits[j] = op.qubits[j];
+            info->n_gates = (int32_t)op.gates.size();
+            info->n_edges = (int32_t)op.edges.size();
         }
-    return QS_OK;
+        if (matrix && !op.matrix.empty())
+            std::memcpy(matrix, op.matrix.data(), sizeof(double) * op.matrix.size());
+        if (gate_idx && !op.gates.empty())
+            std::memcpy(gate_idx, op.gates.data(), sizeof(int32_t) * op.gates.size());
+        if (coeff && op.kind == QS_OP_PHASE)
+            std::memcpy(coeff, op.coeff.data(), sizeof(int32_t) * op.coeff.size());
+        if (edges && op.kind == QS_OP_PHASE)
+            for (size_t e = 0; e < op.edges.size(); e++) {
+                edges[2 * e] = op.edges[e].first;
+                edges[2 * e + 1] = op.edges[e].second;
+            }
+        return QS_OK;
+    });
 }
 
 // Phase op device layout: three coefficient bit-masks and, per qubit a with CZ

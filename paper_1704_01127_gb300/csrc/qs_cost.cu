@@ -238,31 +238,33 @@ void mlp_grad(qs_mlp *M, int B)
 
 extern "C" int qs_mlp_create(uint64_t seed, qs_mlp **out)
 {
-    if (!out) return qs_fail(QS_EINVAL, "qs_mlp_create: null output");
-    qs_mlp *M = new (std::nothrow) qs_mlp();
-    if (!M) return qs_fail(QS_ENOMEM, "qs_mlp_create");
-    std::vector<double> w(kP, 0.0);
-    Rng r(seed);
-    // Glorot-uniform weights, zero biases
-    auto fill = [&](int off, int fan_in, int fan_out, int count) {
-        const double a = std::sqrt(6.0 / (fan_in + fan_out));
-        for (int i = 0; i < count; i++) w[off + i] = (2 * r.uniform() - 1) * a;
-    };
-    fill(oW1, kF, kH, kF * kH);
-    fill(oW2, kH, kH, kH * kH);
-    fill(ow3, kH, 1, kH);
-    cudaError_t e = cudaSuccess;
-    for (double **p : {&M->W, &M->G, &M->m, &M->v})
-        if (e == cudaSuccess) e = cudaMalloc(p, sizeof(double) * kP);
-    if (e == cudaSuccess) e = cudaMemcpy(M->W, w.data(), sizeof(double) * kP, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(M->m, 0, sizeof(double) * kP);
-    if (e == cudaSuccess) e = cudaMemset(M->v, 0, sizeof(double) * kP);
-    if (e != cudaSuccess) {
-        qs_mlp_free(M);
-        return qs_fail(QS_ENOMEM, "qs_mlp_create: %s", cudaGetErrorString(e));
-    }
-    *out = M;
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!out) return qs_fail(QS_EINVAL, "qs_mlp_create: null output");
+        qs_mlp *M = new (std::nothrow) qs_mlp();
+        if (!M) return qs_fail(QS_ENOMEM, "qs_mlp_create");
+        std::vector<double> w(kP, 0.0);
+        Rng r(seed);
+        // Glorot-uniform weights, zero biases
+        auto fill = [&](int off, int fan_in, int fan_out, int count) {
+            const double a = std::sqrt(6.0 / (fan_in + fan_out));
+            for (int i = 0; i < count; i++) w[off + i] = (2 * r.uniform() - 1) * a;
+        };
+        fill(oW1, kF, kH, kF * kH);
+        fill(oW2, kH, kH, kH * kH);
+        fill(ow3, kH, 1, kH);
+        cudaError_t e = cudaSuccess;
+        for (double **p : {&M->W, &M->G, &M->m, &M->v})
+            if (e == cudaSuccess) e = cudaMalloc(p, sizeof(double) * kP);
+        if (e == cudaSuccess) e = cudaMemcpy(M->W, w.data(), sizeof(double) * kP, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(M->m, 0, sizeof(double) * kP);
+        if (e == cudaSuccess) e = cudaMemset(M->v, 0, sizeof(double) * kP);
+        if (e != cudaSuccess) {
+            qs_mlp_free(M);
+            return qs_fail(QS_ENOMEM, "qs_mlp_create: %s", cudaGetErrorString(e));
+        }
+        *out = M;
+        return QS_OK;
+    });
 }
 
 extern "C" void qs_mlp_free(qs_mlp *M)
@@ -277,74 +279,84 @@ extern "C" int qs_mlp_num_params(void) { return kP; }
 
 extern "C" int qs_mlp_get_params(const qs_mlp *M, double *out)
 {
-    if (!M || !out) return qs_fail(QS_EINVAL, "qs_mlp_get_params");
-    cudaError_t e = cudaMemcpy(out, M->W, sizeof(double) * kP, cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_mlp_get_params: %s", cudaGetErrorString(e));
+    return qs_guard([&]() -> int {
+        if (!M || !out) return qs_fail(QS_EINVAL, "qs_mlp_get_params");
+        cudaError_t e = cudaMemcpy(out, M->W, sizeof(double) * kP, cudaMemcpyDeviceToHost);
+        return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_mlp_get_params: %s", cudaGetErrorString(e));
+    });
 }
 
 extern "C" int qs_mlp_set_params(qs_mlp *M, const double *in)
 {
-    if (!M || !in) return qs_fail(QS_EINVAL, "qs_mlp_set_params");
-    cudaError_t e = cudaMemcpy(M->W, in, sizeof(double) * kP, cudaMemcpyHostToDevice);
-    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_mlp_set_params: %s", cudaGetErrorString(e));
+    return qs_guard([&]() -> int {
+        if (!M || !in) return qs_fail(QS_EINVAL, "qs_mlp_set_params");
+        cudaError_t e = cudaMemcpy(M->W, in, sizeof(double) * kP, cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_mlp_set_params: %s", cudaGetErrorString(e));
+    });
 }
 
 extern "C" int qs_mlp_forward(qs_mlp *M, const double *X, int B, double *out)
 {
-    if (!M || !X || !out || B < 1) return qs_fail(QS_EINVAL, "qs_mlp_forward");
-    int rc = mlp_upload(M, X, nullptr, B);
-    if (rc) return rc;
-    mlp_fwd(M, B);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpy(out, M->out, sizeof(double) * B, cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_mlp_forward: %s", cudaGetErrorString(e));
+    return qs_guard([&]() -> int {
+        if (!M || !X || !out || B < 1) return qs_fail(QS_EINVAL, "qs_mlp_forward");
+        int rc = mlp_upload(M, X, nullptr, B);
+        if (rc) return rc;
+        mlp_fwd(M, B);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(out, M->out, sizeof(double) * B, cudaMemcpyDeviceToHost);
+        return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_mlp_forward: %s", cudaGetErrorString(e));
+    });
 }
 
 extern "C" int qs_mlp_gradient(qs_mlp *M, const double *X, const double *Y, int B, double *grad, double *loss)
 {
-    if (!M || !X || !Y || !grad || B < 1) return qs_fail(QS_EINVAL, "qs_mlp_gradient");
-    int rc = mlp_upload(M, X, Y, B);
-    if (rc) return rc;
-    mlp_grad(M, B);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpy(grad, M->G, sizeof(double) * kP, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && loss) {
-        std::vector<double> o(B);
-        e = cudaMemcpy(o.data(), M->out, sizeof(double) * B, cudaMemcpyDeviceToHost);
-        double s = 0;
-        for (int b = 0; b < B; b++) s += (o[b] - Y[b]) * (o[b] - Y[b]);
-        *loss = s / B;
-    }
-    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_mlp_gradient: %s", cudaGetErrorString(e));
+    return qs_guard([&]() -> int {
+        if (!M || !X || !Y || !grad || B < 1) return qs_fail(QS_EINVAL, "qs_mlp_gradient");
+        int rc = mlp_upload(M, X, Y, B);
+        if (rc) return rc;
+        mlp_grad(M, B);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(grad, M->G, sizeof(double) * kP, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && loss) {
+            std::vector<double> o(B);
+            e = cudaMemcpy(o.data(), M->out, sizeof(double) * B, cudaMemcpyDeviceToHost);
+            double s = 0;
+            for (int b = 0; b < B; b++) s += (o[b] - Y[b]) * (o[b] - Y[b]);
+            *loss = s / B;
+        }
+        return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_mlp_gradient: %s", cudaGetErrorString(e));
+    });
 }
 
 extern "C" int qs_mlp_train(qs_mlp *M, const double *X, const double *Y, int B, int epochs, double lr, double *loss)
 {
-    if (!M || !X || !Y || B < 1 || epochs < 0 || !(lr > 0)) return qs_fail(QS_EINVAL, "qs_mlp_train");
-    int rc = mlp_upload(M, X, Y, B);
-    if (rc) return rc;
-    cudaMemset(M->m, 0, sizeof(double) * kP);
-    cudaMemset(M->v, 0, sizeof(double) * kP);
-    const double b1 = 0.9, b2 = 0.999;
-    double p1 = 1, p2 = 1;
-    for (int t = 1; t <= epochs; t++) {
-        mlp_grad(M, B);
-        p1 *= b1;
-        p2 *= b2;
-        const double lr_t = lr * std::sqrt(1 - p2) / (1 - p1);
-        k_adam<<<(kP + 127) / 128, 128>>>(M->W, M->G, M->m, M->v, lr_t, b1, b2, 1e-8);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return qs_fail(QS_ECUDA, "qs_mlp_train: %s", cudaGetErrorString(e));
-    if (loss) {
-        mlp_fwd(M, B);
-        std::vector<double> o(B);
-        e = cudaMemcpy(o.data(), M->out, sizeof(double) * B, cudaMemcpyDeviceToHost);
-        double s = 0;
-        for (int b = 0; b < B; b++) s += (o[b] - Y[b]) * (o[b] - Y[b]);
-        *loss = s / B;
-    }
-    return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_mlp_train: %s", cudaGetErrorString(e));
+    return qs_guard([&]() -> int {
+        if (!M || !X || !Y || B < 1 || epochs < 0 || !(lr > 0)) return qs_fail(QS_EINVAL, "qs_mlp_train");
+        int rc = mlp_upload(M, X, Y, B);
+        if (rc) return rc;
+        cudaMemset(M->m, 0, sizeof(double) * kP);
+        cudaMemset(M->v, 0, sizeof(double) * kP);
+        const double b1 = 0.9, b2 = 0.999;
+        double p1 = 1, p2 = 1;
+        for (int t = 1; t <= epochs; t++) {
+            mlp_grad(M, B);
+            p1 *= b1;
+            p2 *= b2;
+            const double lr_t = lr * std::sqrt(1 - p2) / (1 - p1);
+            k_adam<<<(kP + 127) / 128, 128>>>(M->W, M->G, M->m, M->v, lr_t, b1, b2, 1e-8);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return qs_fail(QS_ECUDA, "qs_mlp_train: %s", cudaGetErrorString(e));
+        if (loss) {
+            mlp_fwd(M, B);
+            std::vector<double> o(B);
+            e = cudaMemcpy(o.data(), M->out, sizeof(double) * B, cudaMemcpyDeviceToHost);
+            double s = 0;
+            for (int b = 0; b < B; b++) s += (o[b] - Y[b]) * (o[b] - Y[b]);
+            *loss = s / B;
+        }
+        return e == cudaSuccess ? QS_OK : qs_fail(QS_ECUDA, "qs_mlp_train: %s", cudaGetErrorString(e));
+    });
 }
 
 // ----------------------------------------------------------- cost model
@@ -359,17 +371,19 @@ struct qs_cost_model {
 
 extern "C" int qs_cost_model_create(double hbm_gbs, qs_cost_model **out)
 {
-    if (!out || !(hbm_gbs > 0)) return qs_fail(QS_EINVAL, "qs_cost_model_create");
-    qs_cost_model *c = new (std::nothrow) qs_cost_model();
-    if (!c) return qs_fail(QS_ENOMEM, "qs_cost_model_create");
-    c->hbm_gbs = hbm_gbs;
-    for (int f = 0; f < kF; f++) {
-        c->fmu[f] = 0;
-        c->fsd[f] = 1;
-        c->fmin[f] = c->fmax[f] = 0;
-    }
-    *out = c;
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!out || !(hbm_gbs > 0)) return qs_fail(QS_EINVAL, "qs_cost_model_create");
+        qs_cost_model *c = new (std::nothrow) qs_cost_model();
+        if (!c) return qs_fail(QS_ENOMEM, "qs_cost_model_create");
+        c->hbm_gbs = hbm_gbs;
+        for (int f = 0; f < kF; f++) {
+            c->fmu[f] = 0;
+            c->fsd[f] = 1;
+            c->fmin[f] = c->fmax[f] = 0;
+        }
+        *out = c;
+        return QS_OK;
+    });
 }
 
 extern "C" void qs_cost_model_free(qs_cost_model *c)
@@ -412,88 +426,92 @@ double median_abs(std::vector<double> v)
 extern "C" int qs_cost_model_fit(qs_cost_model *c, const double *feats, const double *ms, int count, int epochs,
                                  uint64_t seed, double report[4])
 {
-    if (!c || !feats || !ms || count < 20 || epochs < 1) return qs_fail(QS_EINVAL, "qs_cost_model_fit");
-    for (int i = 0; i < count; i++)
-        if (!(ms[i] > 0)) return qs_fail(QS_EINVAL, "qs_cost_model_fit: timing %d not positive", i);
-    // held-out split: every fifth sample (by a seeded hash) is kept for validation
-    std::vector<int> tr, ho;
-    for (int i = 0; i < count; i++) (splitmix64(seed, (uint64_t)i) % 5 == 0 ? ho : tr).push_back(i);
-    if (tr.size() < 10 || ho.empty()) return qs_fail(QS_EINVAL, "qs_cost_model_fit: too few samples");
-    for (int f = 0; f < kF; f++) {
-        double s = 0, s2 = 0, lo = 1e300, hi = -1e300;
-        for (int i : tr) {
-            const double x = feats[(size_t)i * kF + f];
-            s += x;
-            s2 += x * x;
-            lo = std::min(lo, x);
-            hi = std::max(hi, x);
+    return qs_guard([&]() -> int {
+        if (!c || !feats || !ms || count < 20 || epochs < 1) return qs_fail(QS_EINVAL, "qs_cost_model_fit");
+        for (int i = 0; i < count; i++)
+            if (!(ms[i] > 0)) return qs_fail(QS_EINVAL, "qs_cost_model_fit: timing %d not positive", i);
+        // held-out split: every fifth sample (by a seeded hash) is kept for validation
+        std::vector<int> tr, ho;
+        for (int i = 0; i < count; i++) (splitmix64(seed, (uint64_t)i) % 5 == 0 ? ho : tr).push_back(i);
+        if (tr.size() < 10 || ho.empty()) return qs_fail(QS_EINVAL, "qs_cost_model_fit: too few samples");
+        for (int f = 0; f < kF; f++) {
+            double s = 0, s2 = 0, lo = 1e300, hi = -1e300;
+            for (int i : tr) {
+                const double x = feats[(size_t)i * kF + f];
+                s += x;
+                s2 += x * x;
+                lo = std::min(lo, x);
+                hi = std::max(hi, x);
+            }
+            const double mu = s / tr.size(), var = s2 / tr.size() - mu * mu;
+            c->fmu[f] = mu;
+            c->fsd[f] = var > 1e-12 ? std::sqrt(var) : 1.0;
+            c->fmin[f] = lo;
+            c->fmax[f] = hi;
         }
-        const double mu = s / tr.size(), var = s2 / tr.size() - mu * mu;
-        c->fmu[f] = mu;
-        c->fsd[f] = var > 1e-12 ? std::sqrt(var) : 1.0;
-        c->fmin[f] = lo;
-        c->fmax[f] = hi;
-    }
-    double s = 0, s2 = 0;
-    for (int i : tr) {
-        const double y = std::log(ms[i]);
-        s += y;
-        s2 += y * y;
-    }
-    c->ymu = s / tr.size();
-    c->ysd = std::max(1e-6, std::sqrt(std::max(0.0, s2 / tr.size() - c->ymu * c->ymu)));
-    std::vector<double> X(tr.size() * kF), Y(tr.size());
-    for (size_t a = 0; a < tr.size(); a++) {
-        for (int f = 0; f < kF; f++) X[a * kF + f] = (feats[(size_t)tr[a] * kF + f] - c->fmu[f]) / c->fsd[f];
-        Y[a] = (std::log(ms[tr[a]]) - c->ymu) / c->ysd;
-    }
-    if (!c->mlp) {
-        int rc = qs_mlp_create(seed, &c->mlp);
+        double s = 0, s2 = 0;
+        for (int i : tr) {
+            const double y = std::log(ms[i]);
+            s += y;
+            s2 += y * y;
+        }
+        c->ymu = s / tr.size();
+        c->ysd = std::max(1e-6, std::sqrt(std::max(0.0, s2 / tr.size() - c->ymu * c->ymu)));
+        std::vector<double> X(tr.size() * kF), Y(tr.size());
+        for (size_t a = 0; a < tr.size(); a++) {
+            for (int f = 0; f < kF; f++) X[a * kF + f] = (feats[(size_t)tr[a] * kF + f] - c->fmu[f]) / c->fsd[f];
+            Y[a] = (std::log(ms[tr[a]]) - c->ymu) / c->ysd;
+        }
+        if (!c->mlp) {
+            int rc = qs_mlp_create(seed, &c->mlp);
+            if (rc) return rc;
+        }
+        double loss = 0;
+        int rc = qs_mlp_train(c->mlp, X.data(), Y.data(), (int)tr.size(), epochs, 3e-3, &loss);
         if (rc) return rc;
-    }
-    double loss = 0;
-    int rc = qs_mlp_train(c->mlp, X.data(), Y.data(), (int)tr.size(), epochs, 3e-3, &loss);
-    if (rc) return rc;
-    // held-out errors of both models on log-time
-    std::vector<double> hf(ho.size() * kF), pm(ho.size());
-    for (size_t a = 0; a < ho.size(); a++)
-        for (int f = 0; f < kF; f++) hf[a * kF + f] = feats[(size_t)ho[a] * kF + f];
-    if ((rc = mlp_predict_ms(c, hf.data(), (int)ho.size(), pm.data()))) return rc;
-    std::vector<double> em, ea;
-    for (size_t a = 0; a < ho.size(); a++) {
-        const double t = ms[ho[a]];
-        em.push_back(std::fabs(std::log(pm[a] / t)));
-        ea.push_back(std::fabs(std::log(analytic_ms(&hf[a * kF], c->hbm_gbs) / t)));
-    }
-    const double mlp_err = median_abs(em), an_err = median_abs(ea);
-    c->use_mlp = mlp_err < an_err;
-    if (report) {
-        report[0] = loss;
-        report[1] = mlp_err;
-        report[2] = an_err;
-        report[3] = c->use_mlp ? 1.0 : 0.0;
-    }
-    return QS_OK;
+        // held-out errors of both models on log-time
+        std::vector<double> hf(ho.size() * kF), pm(ho.size());
+        for (size_t a = 0; a < ho.size(); a++)
+            for (int f = 0; f < kF; f++) hf[a * kF + f] = feats[(size_t)ho[a] * kF + f];
+        if ((rc = mlp_predict_ms(c, hf.data(), (int)ho.size(), pm.data()))) return rc;
+        std::vector<double> em, ea;
+        for (size_t a = 0; a < ho.size(); a++) {
+            const double t = ms[ho[a]];
+            em.push_back(std::fabs(std::log(pm[a] / t)));
+            ea.push_back(std::fabs(std::log(analytic_ms(&hf[a * kF], c->hbm_gbs) / t)));
+        }
+        const double mlp_err = median_abs(em), an_err = median_abs(ea);
+        c->use_mlp = mlp_err < an_err;
+        if (report) {
+            report[0] = loss;
+            report[1] = mlp_err;
+            report[2] = an_err;
+            report[3] = c->use_mlp ? 1.0 : 0.0;
+        }
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_cost_model_predict(const qs_cost_model *c, const double *feats, int count, int which, double *ms)
 {
-    if (!c || !feats || !ms || count < 0 || which < QS_COST_AUTO || which > QS_COST_MLP)
-        return qs_fail(QS_EINVAL, "qs_cost_model_predict");
-    if (count == 0) return QS_OK;
-    if (which == QS_COST_MLP && !c->mlp) return qs_fail(QS_EINVAL, "qs_cost_model_predict: model not trained");
-    std::vector<double> mlp(count, 0.0);
-    const bool want_mlp = which == QS_COST_MLP || (which == QS_COST_AUTO && c->use_mlp && c->mlp);
-    if (want_mlp) {
-        int rc = mlp_predict_ms(c, feats, count, mlp.data());
-        if (rc) return rc;
-    }
-    for (int i = 0; i < count; i++) {
-        const double *f = feats + (size_t)i * kF;
-        const bool use = which == QS_COST_MLP || (want_mlp && in_range(c, f));
-        ms[i] = use ? mlp[i] : analytic_ms(f, c->hbm_gbs);
-    }
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!c || !feats || !ms || count < 0 || which < QS_COST_AUTO || which > QS_COST_MLP)
+            return qs_fail(QS_EINVAL, "qs_cost_model_predict");
+        if (count == 0) return QS_OK;
+        if (which == QS_COST_MLP && !c->mlp) return qs_fail(QS_EINVAL, "qs_cost_model_predict: model not trained");
+        std::vector<double> mlp(count, 0.0);
+        const bool want_mlp = which == QS_COST_MLP || (which == QS_COST_AUTO && c->use_mlp && c->mlp);
+        if (want_mlp) {
+            int rc = mlp_predict_ms(c, feats, count, mlp.data());
+            if (rc) return rc;
+        }
+        for (int i = 0; i < count; i++) {
+            const double *f = feats + (size_t)i * kF;
+            const bool use = which == QS_COST_MLP || (want_mlp && in_range(c, f));
+            ms[i] = use ? mlp[i] : analytic_ms(f, c->hbm_gbs);
+        }
+        return QS_OK;
+    });
 }
 
 // ----------------------------------------------------------- timing harness
@@ -532,70 +550,72 @@ std::vector<double> timing_unitary(int k, Rng &r)
 extern "C" int qs_cost_sample(int n_min, int n_max, int dtype, int count, uint64_t seed, double max_ms,
                               double *feats, double *ms)
 {
-    if (n_min < 5 || n_max < n_min || n_max > 33 || (dtype != QS_C64 && dtype != QS_C128) || count < 1 || !feats ||
-        !ms || !(max_ms > 0))
-        return qs_fail(QS_EINVAL, "qs_cost_sample: bad arguments");
-    qs_state *big = nullptr;
-    int rc = qs_alloc(n_max, dtype, nullptr, &big);
-    if (rc) return rc;
-    rc = qs_init_uniform(big);
-    Rng r(seed);
-    std::vector<qs_state *> views(n_max + 1, nullptr);
-    for (int n = n_min; n <= n_max && !rc; n++) rc = qs_wrap(big->amp, n, dtype, nullptr, &views[n]);
-    long attempts = 0;
-    for (int i = 0; i < count && !rc;) {
-        if (++attempts > 100L * count + 1000) {
-            rc = qs_fail(QS_EINVAL, "qs_cost_sample: max_ms %.3g rejects almost every op", max_ms);
-            break;
-        }
-        const int n = n_min + r.below(n_max - n_min + 1);
-        qs_schedule sc;
-        sc.n = n;
-        qs_op_host op;
-        int path = QS_PATH_AUTO, n_act = 0, odd = 0;
-        if (r.uniform() < 0.15) {
-            op.kind = QS_OP_PHASE;
-            op.coeff.assign(n, 0);
-            odd = r.uniform() < 0.5;
-            for (int q = 0; q < n; q++) op.coeff[q] = 2 * r.below(4) + (odd && r.uniform() < 0.3 ? 1 : 0);
-            if (odd) op.coeff[r.below(n)] |= 1;
-            const int ne = r.below(2 * n + 1);
-            for (int e = 0; e < ne; e++) {
-                int a = r.below(n), b = r.below(n);
-                if (a != b) op.edges.push_back({std::min(a, b), std::max(a, b)});
+    return qs_guard([&]() -> int {
+        if (n_min < 5 || n_max < n_min || n_max > 33 || (dtype != QS_C64 && dtype != QS_C128) || count < 1 || !feats ||
+            !ms || !(max_ms > 0))
+            return qs_fail(QS_EINVAL, "qs_cost_sample: bad arguments");
+        qs_state *big = nullptr;
+        int rc = qs_alloc(n_max, dtype, nullptr, &big);
+        if (rc) return rc;
+        rc = qs_init_uniform(big);
+        Rng r(seed);
+        std::vector<qs_state *> views(n_max + 1, nullptr);
+        for (int n = n_min; n <= n_max && !rc; n++) rc = qs_wrap(big->amp, n, dtype, nullptr, &views[n]);
+        long attempts = 0;
+        for (int i = 0; i < count && !rc;) {
+            if (++attempts > 100L * count + 1000) {
+                rc = qs_fail(QS_EINVAL, "qs_cost_sample: max_ms %.3g rejects almost every op", max_ms);
+                break;
             }
-            int na;
-            qs_pack_phase(n, op.coeff, op.edges, &na);
-            n_act = na;
-        } else {
-            op.kind = QS_OP_DENSE;
-            op.k = 1 + r.below(5);
-            std::vector<int> perm(n);
-            for (int q = 0; q < n; q++) perm[q] = q;
-            for (int j = 0; j < op.k; j++) std::swap(perm[j], perm[j + r.below(n - j)]);
-            std::sort(perm.begin(), perm.begin() + op.k);
-            for (int j = 0; j < op.k; j++) op.qubits[j] = perm[j];
-            op.matrix = timing_unitary(op.k, r);
-            path = r.uniform() < 0.5 ? QS_PATH_CUDA_CORES : QS_PATH_TENSOR;
-            op.path = path;
+            const int n = n_min + r.below(n_max - n_min + 1);
+            qs_schedule sc;
+            sc.n = n;
+            qs_op_host op;
+            int path = QS_PATH_AUTO, n_act = 0, odd = 0;
+            if (r.uniform() < 0.15) {
+                op.kind = QS_OP_PHASE;
+                op.coeff.assign(n, 0);
+                odd = r.uniform() < 0.5;
+                for (int q = 0; q < n; q++) op.coeff[q] = 2 * r.below(4) + (odd && r.uniform() < 0.3 ? 1 : 0);
+                if (odd) op.coeff[r.below(n)] |= 1;
+                const int ne = r.below(2 * n + 1);
+                for (int e = 0; e < ne; e++) {
+                    int a = r.below(n), b = r.below(n);
+                    if (a != b) op.edges.push_back({std::min(a, b), std::max(a, b)});
+                }
+                int na;
+                qs_pack_phase(n, op.coeff, op.edges, &na);
+                n_act = na;
+            } else {
+                op.kind = QS_OP_DENSE;
+                op.k = 1 + r.below(5);
+                std::vector<int> perm(n);
+                for (int q = 0; q < n; q++) perm[q] = q;
+                for (int j = 0; j < op.k; j++) std::swap(perm[j], perm[j + r.below(n - j)]);
+                std::sort(perm.begin(), perm.begin() + op.k);
+                for (int j = 0; j < op.k; j++) op.qubits[j] = perm[j];
+                op.matrix = timing_unitary(op.k, r);
+                path = r.uniform() < 0.5 ? QS_PATH_CUDA_CORES : QS_PATH_TENSOR;
+                op.path = path;
+            }
+            double f[kF];
+            op_features(n, dtype, op.kind, op.k, op.qubits, path, n_act, odd, f);
+            if (analytic_ms(f, 6696.8) > max_ms) continue;   // skip ops known to be far too slow to time
+            sc.ops.push_back(op);
+            float t[2] = {0, 0};
+            rc = qs_run_circuit_timed(views[n], &sc, &t[0]);   // first run uploads the op
+            if (!rc) rc = qs_run_circuit_timed(views[n], &sc, &t[1]);
+            for (auto &dv : sc.dev)
+                if (dv.pool) cudaFree(dv.pool);
+            if (rc) break;
+            std::memcpy(feats + (size_t)i * kF, f, sizeof(f));
+            ms[i] = std::max(t[1], 1e-4f);
+            i++;
         }
-        double f[kF];
-        op_features(n, dtype, op.kind, op.k, op.qubits, path, n_act, odd, f);
-        if (analytic_ms(f, 6696.8) > max_ms) continue;   // skip ops known to be far too slow to time
-        sc.ops.push_back(op);
-        float t[2] = {0, 0};
-        rc = qs_run_circuit_timed(views[n], &sc, &t[0]);   // first run uploads the op
-        if (!rc) rc = qs_run_circuit_timed(views[n], &sc, &t[1]);
-        for (auto &dv : sc.dev)
-            if (dv.pool) cudaFree(dv.pool);
-        if (rc) break;
-        std::memcpy(feats + (size_t)i * kF, f, sizeof(f));
-        ms[i] = std::max(t[1], 1e-4f);
-        i++;
-    }
-    for (qs_state *v : views) qs_free(v);
-    qs_free(big);
-    return rc;
+        for (qs_state *v : views) qs_free(v);
+        qs_free(big);
+        return rc;
+    });
 }
 
 // ----------------------------------------------------------------- planner
@@ -603,80 +623,84 @@ extern "C" int qs_cost_sample(int n_min, int n_max, int dtype, int count, uint64
 extern "C" int qs_plan_circuit(int n, const qs_gate *gates, int n_gates, int dtype, const qs_cost_model *c, int which,
                                qs_schedule **out, int *k_max_out, double *predicted_ms)
 {
-    if (!out || !c || (dtype != QS_C64 && dtype != QS_C128)) return qs_fail(QS_EINVAL, "qs_plan_circuit");
-    qs_schedule *best = nullptr;
-    double best_t = 1e300;
-    int best_k = 0;
-    for (int km = 2; km <= QS_MAX_K; km++) {
-        qs_sched_opts o = {km, 1, 1, 0, 1, 1, 1, 1, 0};
-        qs_schedule *sc = nullptr;
-        int rc = qs_schedule_build(n, gates, n_gates, &o, &sc);
-        if (rc) {
-            qs_schedule_free(best);
-            return rc;
-        }
-        // candidates: per dense op CUDA cores and (n >= 5) tensor cores
-        std::vector<double> F;
-        std::vector<int> owner, cand_path;
-        for (size_t i = 0; i < sc->ops.size(); i++) {
-            const qs_op_host &op = sc->ops[i];
-            double f[kF];
-            if (op.kind == QS_OP_PHASE) {
-                int na;
-                qs_pack_phase(n, op.coeff, op.edges, &na);
-                int odd = 0;
-                for (int q = 0; q < n; q++) odd |= op.coeff[q] & 1;
-                op_features(n, dtype, op.kind, 0, op.qubits, 0, na, odd, f);
-                F.insert(F.end(), f, f + kF);
-                owner.push_back((int)i);
-                cand_path.push_back(QS_PATH_AUTO);
-                continue;
+    return qs_guard([&]() -> int {
+        if (!out || !c || (dtype != QS_C64 && dtype != QS_C128)) return qs_fail(QS_EINVAL, "qs_plan_circuit");
+        qs_schedule *best = nullptr;
+        double best_t = 1e300;
+        int best_k = 0;
+        for (int km = 2; km <= QS_MAX_K; km++) {
+            qs_sched_opts o = {km, 1, 1, 0, 1, 1, 1, 1, 0};
+            qs_schedule *sc = nullptr;
+            int rc = qs_schedule_build(n, gates, n_gates, &o, &sc);
+            if (rc) {
+                qs_schedule_free(best);
+                return rc;
             }
-            for (int path : {QS_PATH_CUDA_CORES, QS_PATH_TENSOR}) {
-                if (path == QS_PATH_TENSOR && n < 5) continue;
-                op_features(n, dtype, op.kind, op.k, op.qubits, path, 0, 0, f);
-                F.insert(F.end(), f, f + kF);
-                owner.push_back((int)i);
-                cand_path.push_back(path);
+            // candidates: per dense op CUDA cores and (n >= 5) tensor cores
+            std::vector<double> F;
+            std::vector<int> owner, cand_path;
+            for (size_t i = 0; i < sc->ops.size(); i++) {
+                const qs_op_host &op = sc->ops[i];
+                double f[kF];
+                if (op.kind == QS_OP_PHASE) {
+                    int na;
+                    qs_pack_phase(n, op.coeff, op.edges, &na);
+                    int odd = 0;
+                    for (int q = 0; q < n; q++) odd |= op.coeff[q] & 1;
+                    op_features(n, dtype, op.kind, 0, op.qubits, 0, na, odd, f);
+                    F.insert(F.end(), f, f + kF);
+                    owner.push_back((int)i);
+                    cand_path.push_back(QS_PATH_AUTO);
+                    continue;
+                }
+                for (int path : {QS_PATH_CUDA_CORES, QS_PATH_TENSOR}) {
+                    if (path == QS_PATH_TENSOR && n < 5) continue;
+                    op_features(n, dtype, op.kind, op.k, op.qubits, path, 0, 0, f);
+                    F.insert(F.end(), f, f + kF);
+                    owner.push_back((int)i);
+                    cand_path.push_back(path);
+                }
+            }
+            std::vector<double> t(owner.size());
+            rc = qs_cost_model_predict(c, F.data(), (int)owner.size(), which, t.data());
+            if (rc) {
+                qs_schedule_free(sc);
+                qs_schedule_free(best);
+                return rc;
+            }
+            std::vector<double> op_t(sc->ops.size(), 1e300);
+            for (size_t a = 0; a < owner.size(); a++)
+                if (t[a] < op_t[owner[a]]) {
+                    op_t[owner[a]] = t[a];
+                    sc->ops[owner[a]].path = cand_path[a];
+                }
+            double total = 0;
+            for (double x : op_t) total += x;
+            if (total < best_t) {
+                qs_schedule_free(best);
+                best = sc;
+                best_t = total;
+                best_k = km;
+            } else {
+                qs_schedule_free(sc);
             }
         }
-        std::vector<double> t(owner.size());
-        rc = qs_cost_model_predict(c, F.data(), (int)owner.size(), which, t.data());
-        if (rc) {
-            qs_schedule_free(sc);
-            qs_schedule_free(best);
-            return rc;
-        }
-        std::vector<double> op_t(sc->ops.size(), 1e300);
-        for (size_t a = 0; a < owner.size(); a++)
-            if (t[a] < op_t[owner[a]]) {
-                op_t[owner[a]] = t[a];
-                sc->ops[owner[a]].path = cand_path[a];
-            }
-        double total = 0;
-        for (double x : op_t) total += x;
-        if (total < best_t) {
-            qs_schedule_free(best);
-            best = sc;
-            best_t = total;
-            best_k = km;
-        } else {
-            qs_schedule_free(sc);
-        }
-    }
-    *out = best;
-    if (k_max_out) *k_max_out = best_k;
-    if (predicted_ms) *predicted_ms = best_t;
-    return QS_OK;
+        *out = best;
+        if (k_max_out) *k_max_out = best_k;
+        if (predicted_ms) *predicted_ms = best_t;
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_op_features(int n, int dtype, int kind, int k, const int *qubits, int path, int n_act, int odd,
                               double *out)
 {
-    if (!out || n < 1 || (kind == QS_OP_DENSE && (!qubits || k < 1 || k > QS_MAX_K)))
-        return qs_fail(QS_EINVAL, "qs_op_features");
-    op_features(n, dtype, kind, k, qubits, path, n_act, odd, out);
-    return QS_OK;
+    return qs_guard([&]() -> int {
+        if (!out || n < 1 || (kind == QS_OP_DENSE && (!qubits || k < 1 || k > QS_MAX_K)))
+            return qs_fail(QS_EINVAL, "qs_op_features");
+        op_features(n, dtype, kind, k, qubits, path, n_act, odd, out);
+        return QS_OK;
+    });
 }
 
 extern "C" double qs_cost_analytic_ms(const double *features, double hbm_gbs)

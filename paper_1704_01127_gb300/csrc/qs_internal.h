@@ -6,11 +6,30 @@
 #include <array>
 #include <vector>
 #include <utility>
+#include <new>
+#include <exception>
 
 #include "../../include/qs.h"
 
 // Thread-local error message; returns `code` so callers can `return qs_fail(...)`.
 int qs_fail(int code, const char *fmt, ...);
+
+// Every C entry point runs its body through qs_guard, so that no C++ exception
+// crosses the C boundary: a failed host allocation becomes QS_ENOMEM, any other
+// exception QS_EINVAL with its message.
+template <class F>
+int qs_guard(F &&body) noexcept
+{
+    try {
+        return body();
+    } catch (const std::bad_alloc &) {
+        return qs_fail(QS_ENOMEM, "host memory allocation failed");
+    } catch (const std::exception &e) {
+        return qs_fail(QS_EINVAL, "%s", e.what());
+    } catch (...) {
+        return qs_fail(QS_EINVAL, "unexpected exception");
+    }
+}
 
 struct qs_state {
     int n = 0;

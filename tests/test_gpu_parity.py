@@ -392,6 +392,51 @@ def test_errors_leave_gpu_usable():
     assert e.value.code == qs.QS_EINVAL
 
 
+def test_device_allocation_beyond_free_memory_is_enomem():
+    """2^36 complex128 amplitudes (1 TiB) exceed the GPU's memory: QS_ENOMEM,
+    and the device stays usable (a cluster sweep still matches the oracle)."""
+    with pytest.raises(qs.QSError) as e:
+        qs.qs_alloc(36, qs.QS_C128)
+    assert e.value.code == qs.QS_ENOMEM
+    U = random_unitary(3, 5)
+    psi = random_state(12, 6)
+    ref = psi.copy()
+    sim.apply_kq(ref, [1, 7, 4], U)
+    with State(12, qs.QS_C128) as s:
+        qs.qs_set_amplitudes(s.h, psi)
+        qs.qs_apply_cluster(s.h, [1, 7, 4], U)
+        assert np.max(np.abs(qs.qs_get_amplitudes(s.h) - ref)) < SWEEP_TOL[qs.QS_C128]
+
+
+@pytest.mark.parametrize("path", [qs.QS_PATH_CUDA_CORES, qs.QS_PATH_TENSOR])
+def test_stream_switch_between_queued_sweeps(path):
+    """Sweeps queued on one stream, then on another after qs_set_stream: the
+    second stream starts after the first one's work, so the state equals the
+    oracle's (without that ordering the two streams' sweeps and staged
+    matrices would overlap)."""
+    torch = pytest.importorskip("torch")
+    n = 22
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    ops = [(random_qubits(n, 5, 300 + i), random_unitary(5, 400 + i)) for i in range(8)]
+    psi = random_state(n, 17)
+    ref = psi.copy()
+    for q, U in ops:
+        sim.apply_kq(ref, q, U)
+    h = qs.qs_alloc(n, qs.QS_C128, s1)
+    try:
+        qs.qs_set_path(h, path)
+        qs.qs_set_amplitudes(h, psi)
+        for q, U in ops[:4]:
+            qs.qs_apply_cluster(h, q, U)
+        qs.qs_set_stream(h, s2)
+        for q, U in ops[4:]:
+            qs.qs_apply_cluster(h, q, U)
+        out = qs.qs_get_amplitudes(h)
+    finally:
+        qs.qs_free(h)
+    assert np.max(np.abs(out - ref)) < 1e-12
+
+
 def test_wrapped_buffer_basis_start_is_written_in_full():
     """The caller can read a wrapped buffer directly, so qs_init_basis writes
     every amplitude of it at once (no deferred zeros)."""

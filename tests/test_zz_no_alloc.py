@@ -42,3 +42,27 @@ def test_stats_static_rejects_bad_sizes():
             qs.qs_stats_static(ptr, 4, 7)
     finally:
         qs.qs_free(h)
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_stats_static_views_at_any_amplitude(dtype):
+    """A view that starts at amplitude 1 of a state is accepted (aligned to one
+    amplitude); a pointer half an amplitude in is rejected."""
+    size = 16 if dtype == qs.QS_C128 else 8
+    h = qs.qs_alloc(5, dtype)
+    ref = qs.qs_alloc(4, dtype)
+    try:
+        psi = random_state(5, 91)
+        qs.qs_set_amplitudes(h, psi)
+        qs.qs_set_amplitudes(ref, psi[1:17])
+        want = qs.qs_stats(ref)
+        ptr = qs.qs_device_ptr(h)
+        got = qs.qs_stats_static(ptr + size, 4, dtype)
+        for a, b in zip(got, want):
+            assert abs(a - b) <= 1e-12 * max(1.0, abs(b))
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_stats_static(ptr + size // 2, 4, dtype)
+        assert e.value.code == qs.QS_EINVAL
+    finally:
+        qs.qs_free(h)
+        qs.qs_free(ref)
