@@ -366,7 +366,7 @@ def run_ours(args):
         return None
     # the first step touches the freshly allocated 16 GiB array (page faults):
     # it warms up, the second is reported
-    cpu = None if args.no_cpu_baseline else cpu_baseline(args, n_steps=2)[1]
+    cpu = None if args.no_cpu_baseline else cpu_baseline(args)
     line = {
         "metric": METRIC, "value": per_circuit, "unit": "s/circuit", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
@@ -541,50 +541,115 @@ def _search_config(qs, plain):
 
 # ------------------------------------------------------------ oracle (CPU) leg
 
-def cpu_baseline(args, n_steps):
-    """The oracle, as it stands, on a bounded sample of the workload: a few gates
-    of the circuit applied to the full state on the host; the per-circuit time is
-    scaled from the per-gate times."""
-    import numpy as np
+def host_cpu():
+    """CPU model and core count of this host, for the baseline's record."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+
+
+def _oracle_chunks(args):
+    """The workload's circuit from the oracle's generator and a fresh |0...0>."""
     from oracle import circuit as ocircuit
     from oracle import sim as osim
     rows, cols, removed, cycles, dt, k_max = WORKLOADS[args.workload]
     n, gates = ocircuit.supremacy_circuit(rows, cols, cycles, 0, removed=removed)
-    n1 = sum(1 for g in gates if g[1] != "cz")
-    n2 = len(gates) - n1
+    return (rows, cols, cycles), n, gates, osim
+
+
+def _time_gates(osim, psi, gates):
+    t0 = time.perf_counter()
+    for g in gates:
+        osim.apply_gate(psi, g[1], g[2])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args):
+    """The oracle, as it stands, on a bounded sample of the workload: a
+    contiguous run of the circuit's gates applied gate by gate to the full state
+    on the host (all cores, median of three runs), scaled to the whole circuit
+    by its gate count; and the same on one core with a shorter run."""
+    (rows, cols, cycles), n, gates, osim = _oracle_chunks(args)
     psi = osim.basis_state(n, 0)
-    one = [g for g in gates if g[1] != "cz"]
-    two = [g for g in gates if g[1] == "cz"]
-    values = []
-    for step in range(n_steps):
-        g1, g2 = one[step % len(one)], two[step % len(two)]
-        t0 = time.perf_counter()
-        osim.apply_gate(psi, g1[1], g1[2])
-        t1 = time.perf_counter()
-        osim.apply_gate(psi, g2[1], g2[2])
-        t2 = time.perf_counter()
-        values.append(n1 * (t1 - t0) + n2 * (t2 - t1))
+    G = len(gates)
+    cores = os.cpu_count() or 1
+    osim.set_threads(cores)
+    _time_gates(osim, psi, gates[:2])               # first touch of the array
+    used = osim.max_threads()
+    # runs start a quarter, half and three quarters into the circuit, so that
+    # they hold its mix of single-qubit gates and CZs (the first 2^n gates are
+    # all Hadamards)
+    span, runs = 16, []
+    for r in range(3):
+        lo = (r + 1) * G // 4
+        runs.append(_time_gates(osim, psi, gates[lo:lo + span]) * G / span)
+    osim.set_threads(1)
+    span1, runs1 = 2, []
+    for r in range(3):
+        lo = (r + 1) * G // 5
+        runs1.append(_time_gates(osim, psi, gates[lo:lo + span1]) * G / span1)
+    osim.set_threads(cores)
     del psi
-    return [{"value": v, "unit": "s/circuit", "cores": 1, "kind": "oracle",
-             "sample": "one single-qubit gate and one CZ of the %dx%d circuit applied to the full "
-                       "2^%d-amplitude complex128 state (after a warm-up step that first touches the "
-                       "array); scaled by the circuit's %d single-qubit gates and %d CZs" % (
-                           rows, cols, n, n1, n2)} for v in values]
+    cpu = host_cpu()
+    what = ("contiguous runs of %d gates (starting 1/4, 1/2, 3/4 into the circuit for all cores, 1/5, "
+            "2/5, 3/5 for one core) of the %dx%d, %d-cycle circuit (%d gates) applied gate by gate to the "
+            "full 2^%d-amplitude complex128 state by the oracle, after a 2-gate warm-up that first touches "
+            "the array; median of 3 runs, scaled to the whole circuit by its gate count")
+    return {"value": statistics.median(runs), "unit": "s/circuit", "cores": used, "kind": "oracle",
+            "sample": what % (span, rows, cols, cycles, G, n), "cpu": cpu["model"], "nproc": cpu["nproc"],
+            "runs": runs,
+            "single_core": {"value": statistics.median(runs1), "unit": "s/circuit", "cores": 1,
+                            "sample": what % (span1, rows, cols, cycles, G, n), "runs": runs1}}
 
 
 def run_reference(args):
+    """The oracle as the reference arm.  The K timed steps split the workload's
+    circuit into K contiguous runs of gates (ceil(G/K) each; the last may be
+    shorter), applied gate by gate to the full state on all host cores, so the
+    K steps together apply the whole circuit once: `value` is that measured
+    circuit time, `ms_per_step` the mean time of a step.  Each warm-up step
+    applies one gate (the first touches the array)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    res = cpu_baseline(args, args.warmup + args.steps)[args.warmup:]
-    vals = [r["value"] for r in res]
-    v = statistics.median(vals)
-    rows, cols, removed, cycles, dt, k_max = WORKLOADS[args.workload]
-    cb = dict(res[0])
-    cb["value"] = v
+    (rows, cols, cycles), n, gates, osim = _oracle_chunks(args)
+    G = len(gates)
+    cores = os.cpu_count() or 1
+    osim.set_threads(cores)
+    used = osim.max_threads()
+    psi = osim.basis_state(n, 0)
+    for w in range(args.warmup):
+        _time_gates(osim, psi, gates[w % G:w % G + 1])
+    psi[:] = 0
+    psi[0] = 1
+    c = -(-G // args.steps)
+    times, done = [], 0
+    for j in range(args.steps):
+        chunk = gates[j * c:(j + 1) * c]
+        times.append(_time_gates(osim, psi, chunk))
+        done += len(chunk)
+    del psi
+    total = sum(times)
+    v = total if done >= G else total * G / max(done, 1)
+    cpu = host_cpu()
+    sample = ("the %dx%d, %d-cycle circuit (%d gates) applied gate by gate to |0...0> (2^%d complex128 "
+              "amplitudes) by the oracle on %d host threads, split into %d steps of up to %d contiguous "
+              "gates; %s" % (rows, cols, cycles, G, n, used, args.steps, c,
+                             "value = the measured time of the whole circuit" if done >= G else
+                             "value scaled from %d of its gates" % done))
+    cb = {"value": v, "unit": "s/circuit", "cores": used, "kind": "oracle", "sample": sample,
+          "cpu": cpu["model"], "nproc": cpu["nproc"], "gates_timed": done, "circuit_gates": G}
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/circuit", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "%dx%d grid, %d CZ cycles, gate-by-gate complex128 oracle on the host" % (
