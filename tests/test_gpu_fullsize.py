@@ -99,8 +99,11 @@ def test_fullsize_against_oracle(name, dtype):
     print("%s dtype %d: max |dpsi| = %.3e (%.3e of the largest sampled |psi|), stats %s vs oracle %s"
           % (name, dtype, float(np.max(err)), rel, st, ostats))
     assert float(np.max(err)) <= TOL[dtype]
+    # the oracle sums 2^n terms one after another in FP64 (its norm is off by
+    # 1.8e-13 at 30 qubits and 3.5e-12 at 32); the library's float-float sums
+    # are closer to exact, so the statistics agree to the oracle's rounding
     if dtype == qs.QS_C128:
-        assert abs(st[0] - ostats[0]) < 1e-13
+        assert abs(st[0] - ostats[0]) < 1e-11
         assert abs(st[1] - ostats[1]) < 1e-10 * ostats[1]
         assert abs(st[3] - ostats[3]) < 1e-9 * ostats[3]
     else:
