@@ -221,7 +221,9 @@ def test_fullsize_golden_files():
         assert name == make_fullsize.golden_name(R, C, D, seed)
         assert n == circuit.supremacy_circuit(R, C, 1, seed)[0]
         st = [float(x) for x in rows[1][1:]]
-        assert abs(st[0] - 1) < 1e-12 and abs(st[2] - 1) < 1e-12 and 1.8 < st[3] < 3.0
+        # the oracle's norm is a serial FP64 sum of 2^n terms: its rounding
+        # error grows with n (3.5e-12 at 32 qubits)
+        assert abs(st[0] - 1) < 1e-11 and abs(st[2] - 1) < 1e-11 and 1.8 < st[3] < 3.0
         idx = np.array([int(r[0]) for r in rows[2:]], dtype=np.uint64)
         assert np.array_equal(idx, make_fullsize.sample_indices(n, idx.size))
         p = np.array([float(r[1]) ** 2 + float(r[2]) ** 2 for r in rows[2:]])
