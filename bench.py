@@ -168,6 +168,41 @@ def job_seconds_per_circuit(elapsed_max, circuits_per_rank, world):
 
 # ------------------------------------------------------------------ our arm
 
+def classify_sweeps(qs, sc, op_ms, n, dtype):
+    """Split a run started with qs_init_basis into full-state sweeps and sweeps
+    on the support after |0...0> (the library's rule: tensor-core sweeps cover
+    the qubits touched so far; any other op first writes the zeros).
+    Returns ({(kind, k): [ms]}, [partial ms], partial bytes, ops run, fills)."""
+    amp = 16 if dtype == qs.QS_C128 else 8
+    full, free, fills, ran = (1 << n) - 1, 0, 0, 0
+    kernel_ms, partial_ms, partial_bytes = {}, [], 0
+    for i in range(qs.qs_schedule_num_ops(sc)):
+        if op_ms[i] < 0:     # a phase op that ran inside the sweep before it
+            continue
+        ran += 1
+        op = qs.qs_schedule_op(sc, i)
+        k = len(op.get("qubits", ())) if op["kind"] == "dense" else 0
+        was_full = free == full
+        before = bin(free).count("1")
+        touched = 0
+        if op["kind"] == "dense" and n >= 5 and (
+                (dtype == qs.QS_C64 and k >= 4) or (dtype == qs.QS_C128 and k >= 2)):
+            for q in op["qubits"]:
+                free |= 1 << q
+            # reads the support before the sweep, writes it after
+            touched = (1 << before) + (1 << bin(free).count("1"))
+        elif free != full:
+            # zeros written outside the support, then a full sweep
+            free, fills = full, fills + 1
+            touched = 3 << n
+        if was_full:
+            kernel_ms.setdefault((op["kind"], k), []).append(float(op_ms[i]))
+        else:
+            partial_ms.append(float(op_ms[i]))
+            partial_bytes += touched * amp
+    return kernel_ms, partial_ms, partial_bytes, ran, fills
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -191,10 +226,8 @@ def run_ours(args):
 
     kernel_ms = {}      # (kind, k) -> per-launch ms of full-state sweeps in the timed region
     partial_ms = []     # sweeps that ran on part of the state (the support after |0...0>)
+    partial_bytes = [0]  # amplitudes they read and wrote (support before + after), in bytes
     launches = [0]
-
-    def on_tensor_cores(kind, k):
-        return kind == "dense" and n >= 5 and ((dtype == qs.QS_C64 and k >= 4) or (dtype == qs.QS_C128 and k >= 2))
 
     # a1-a3 run on the host; the next step's are prepared in a second thread
     # while the GPU runs this one (ctypes releases the GIL in library calls)
@@ -213,25 +246,11 @@ def run_ours(args):
             op_ms = qs.qs_run_circuit_timed(h, sc)                                            # a4-a6
             st = qs.qs_stats(h)                                                               # a7
             if record:
-                # the library's support after qs_init_basis: tensor-core sweeps
-                # cover the qubits touched so far; any other op writes the zeros
-                full, free, fills, ran = (1 << n) - 1, 0, 0, 0
-                for i in range(qs.qs_schedule_num_ops(sc)):
-                    if op_ms[i] < 0:     # a phase op that ran inside the sweep before it
-                        continue
-                    ran += 1
-                    op = qs.qs_schedule_op(sc, i)
-                    k = len(op.get("qubits", ())) if op["kind"] == "dense" else 0
-                    was_full = free == full
-                    if on_tensor_cores(op["kind"], k):
-                        for q in op["qubits"]:
-                            free |= 1 << q
-                    elif free != full:
-                        free, fills = full, fills + 1
-                    if was_full:
-                        kernel_ms.setdefault((op["kind"], k), []).append(float(op_ms[i]))
-                    else:
-                        partial_ms.append(float(op_ms[i]))
+                km, pm, pb, ran, fills = classify_sweeps(qs, sc, op_ms, n, dtype)
+                for kk, v in km.items():
+                    kernel_ms.setdefault(kk, []).extend(v)
+                partial_ms.extend(pm)
+                partial_bytes[0] += pb
                 launches[0] += ran + 1 + 2 + fills
             return st, len(op_ms), nxt
         finally:
@@ -300,9 +319,13 @@ def run_ours(args):
         "gbs": sweep_bytes / (statistics.mean(v) * 1e-3) / 1e9,
         "hbm_frac": sweep_bytes / (statistics.mean(v) * 1e-3) / 1e9 / hbm_gbs}
         for kk, v in sorted(kernel_ms.items())}
-    sweeps["partial_support"] = {"launches": len(partial_ms), "total_ms": sum(partial_ms),
-                                 "what": "sweeps before the reachable indices cover the state: they read and "
-                                         "write only the support (not in the roofline)"}
+    sweeps["partial_support"] = {
+        "launches": len(partial_ms), "total_ms": sum(partial_ms), "bytes": partial_bytes[0],
+        "gbs": partial_bytes[0] / (sum(partial_ms) * 1e-3) / 1e9 if partial_ms else None,
+        "hbm_frac": partial_bytes[0] / (sum(partial_ms) * 1e-3) / 1e9 / hbm_gbs if partial_ms else None,
+        "what": "sweeps before the reachable indices cover the state: each reads the support before it and "
+                "writes the support after it (2^|support| amplitudes each); bytes = those amplitudes, GB/s over "
+                "their summed device time"}
 
     # plain gate-by-gate form of the same circuit (the comparison of the metric)
     plain = None
@@ -362,6 +385,12 @@ def run_ours(args):
                        "(next circuit's schedule built while this one runs)"}
 
     qs.qs_free(h)
+    extras = rank == 0 and args.workload == "5x6_d25_c128" and not args.plain
+    # the spec form (learned schedule, complex64) on the 30- and 32-qubit
+    # circuits, against the plain complex128 form and the oracle's amplitudes
+    target = target_form(qs, stream, hbm_gbs) if extras and not args.no_target else None
+    # the batched workload: 512 circuits in one graph-replayed persistent launch
+    batch = batch_section(qs, stream, 5, 3)[0] if extras and not args.no_batch else None
     if rank != 0:
         return None
     # the first step touches the freshly allocated 16 GiB array (page faults):
@@ -382,48 +411,48 @@ def run_ours(args):
         "speedup_vs_plain": (plain["s_per_circuit"] / per_circuit) if plain else None,
         "porter_thomas": {"sum_p": stats[0], "entropy": stats[1], "m2": stats[3]},
         "e2e": e2e, "gpu_launches": launches[0], "clocks": clk.summary(), "cpu_baseline": cpu,
+        "target_form": target, "batch512": batch,
     }
     return line
 
 
 # ------------------------------------------------------- batched workload
 
-def run_batch(args):
+def batch_section(qs, stream, steps, warmup, clock_index=None):
     """512 independent circuits (seeds 0..511; grids 4x4 / 4x5 / 3x7, depths
     8..40), complex64, one persistent launch replayed from a CUDA graph, against
-    a loop of single-circuit launches of the same schedules."""
+    a loop of single-circuit launches of the same schedules.  Returns the
+    measured figures and the per-launch device time."""
     import torch
-    from paper_1704_01127_gb300 import build as _build
-    _build.build()
-    import paper_1704_01127_gb300.qs as qs
-    world, rank, local, dist = dist_setup(args)
-    qs.qs_set_device(local)
-    torch.cuda.set_device(local)
-    stream = torch.cuda.Stream()
     n_circ = 512
     circs = []
-    for s in range(n_circ):
-        r, c, d = qs.qs_batch_circuit_params(s)
-        circs.append(qs.qs_supremacy_circuit(r, c, d, s))
+    for s_ in range(n_circ):
+        r, c, d = qs.qs_batch_circuit_params(s_)
+        circs.append(qs.qs_supremacy_circuit(r, c, d, s_))
+    t0 = time.perf_counter()
     k_max, C, T, tune_ms = qs.qs_batch_autotune(circs, qs.QS_C64, stream)
+    tune_s = time.perf_counter() - t0
     # the greedy clustering rule, as the autotuner's schedules (the 208-run
     # search would spend ~10 s of host time on 512 small circuits)
     scheds = [qs.qs_schedule_build(n, g, k_max=k_max, search_runs=1, search_first=1) for (n, g) in circs]
     b = qs.qs_batch_create(scheds, qs.QS_C64, stream)
     qs.qs_batch_set_config(b, C, T)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         qs.qs_batch_run_graph(b)
     torch.cuda.synchronize()
-    barrier(dist)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            qs.qs_batch_run_graph(b)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    elapsed = max_over_ranks(dist, e0.elapsed_time(e1) / 1e3)
+    clk = ClockSampler(clock_index) if clock_index is not None else None
+    if clk:
+        clk.__enter__()
+    e0.record(stream)
+    for _ in range(steps):
+        qs.qs_batch_run_graph(b)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__(None, None, None)
+    elapsed = e0.elapsed_time(e1) / 1e3
     st = qs.qs_batch_stats(b, n_circ)
     qs.qs_batch_free(b)
     # loop of single-circuit launches (default kernel paths), same schedules
@@ -431,6 +460,7 @@ def run_batch(args):
     for (n, _) in circs:
         if n not in states:
             states[n] = qs.qs_alloc(n, qs.QS_C64, stream)
+
     def loop():
         for (n, _), sc in zip(circs, scheds):
             qs.qs_init_basis(states[n], 0)
@@ -446,23 +476,156 @@ def run_batch(args):
         qs.qs_free(h)
     for sc in scheds:
         qs.qs_schedule_free(sc)
+    per_launch = elapsed / steps
+    out = {"workload": "512 circuits (seeds 0..511), grids 4x4/4x5/3x7, 8..40 CZ cycles, c64, one persistent "
+                       "launch per step replayed from a CUDA graph",
+           "autotuned": {"k_max": k_max, "cluster_ctas": C, "threads": T, "tune_ms": tune_ms,
+                         "tune_wall_s": tune_s},
+           "l2": "states total %.0f MB; inputs re-initialised every launch" % (
+               sum(8 << n for (n, _) in circs) / 1e6),
+           "launches": steps, "s_per_launch": per_launch,
+           "circuits_per_s": n_circ / per_launch, "loop_circuits_per_s": n_circ / loop_s,
+           "speedup_vs_loop": loop_s / per_launch,
+           "mean_m2": float(st[:, 3].mean()), "max_norm_drift": float(abs(st[:, 0] - 1).max())}
+    return out, elapsed, (clk.summary() if clk else None)
+
+
+def run_batch(args):
+    """The batched workload on its own (config 4)."""
+    import torch
+    from paper_1704_01127_gb300 import build as _build
+    _build.build()
+    import paper_1704_01127_gb300.qs as qs
+    world, rank, local, dist = dist_setup(args)
+    qs.qs_set_device(local)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    barrier(dist)
+    out, elapsed, clocks = batch_section(qs, stream, args.steps, args.warmup, local)
+    elapsed = max_over_ranks(dist, elapsed)
     if rank != 0:
         return None
     per_launch = elapsed / args.steps
     return {
-        "metric": METRIC, "value": per_launch / n_circ, "unit": "s/circuit", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+        "metric": METRIC, "value": per_launch / 512, "unit": "s/circuit", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_launch * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "512 circuits (seeds 0..511), grids 4x4/4x5/3x7, 8..40 CZ cycles, c64, "
-                               "one persistent launch per step from a CUDA graph",
-                   "autotuned": {"k_max": k_max, "cluster_ctas": C, "threads": T, "tune_ms": tune_ms},
-                   "l2": "states total %.0f MB; inputs re-initialised every launch" % (
-                       sum(8 << n for (n, _) in circs) / 1e6)},
-        "circuits_per_s": n_circ / per_launch, "loop_circuits_per_s": n_circ / loop_s,
-        "speedup_vs_loop": loop_s / per_launch,
-        "mean_m2": float(st[:, 3].mean()), "max_norm_drift": float(abs(st[:, 0] - 1).max()),
-        "gpu_launches": args.steps, "clocks": clk.summary(),
+        "config": {k: out[k] for k in ("workload", "autotuned", "l2")},
+        "circuits_per_s": out["circuits_per_s"], "loop_circuits_per_s": out["loop_circuits_per_s"],
+        "speedup_vs_loop": out["speedup_vs_loop"], "mean_m2": out["mean_m2"],
+        "max_norm_drift": out["max_norm_drift"], "gpu_launches": args.steps, "clocks": clocks,
     }
+
+
+def load_golden_amplitudes(name):
+    """Oracle amplitudes at sampled indices, stored by tests/golden/make_fullsize.py
+    (params, indices, complex values); None if the file is absent."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        return None
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    params = tuple(int(x) for x in rows[0][1:])
+    idx = np.array([int(r[0]) for r in rows[2:]], dtype=np.uint64)
+    amp = np.array([complex(float(r[1]), float(r[2])) for r in rows[2:]], dtype=np.complex128)
+    return params, idx, amp
+
+
+def target_form(qs, stream, hbm_gbs, harness_count=1500):
+    """The learned-schedule complex64 form on the 30-qubit (5x6, seed 0) and
+    32-qubit (4x8, seed 1) circuits with 25 CZ cycles: a cost model fitted on
+    GPU timings of random complex64 ops (26-32 qubits), circuits planned with it
+    (auto fallback) and with the analytic model, each run a4-a7 (|0...0>,
+    sweeps, statistics) and timed with CUDA events (best of 3 after a warm
+    run), amplitudes at the stored oracle indices compared with the oracle, and
+    the plain gate-by-gate complex128 form of the same circuit timed once."""
+    import numpy as np
+    import torch
+    t0 = time.perf_counter()
+    F, T = qs.qs_cost_sample(26, 32, qs.QS_C64, harness_count, seed=64, max_ms=100.0)
+    harness_s = time.perf_counter() - t0
+    cm = qs.qs_cost_model_create(hbm_gbs)
+    t1 = time.perf_counter()
+    rep = qs.qs_cost_model_fit(cm, F, T, epochs=1500, seed=7)
+    fit_s = time.perf_counter() - t1
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(h, sc, reps):
+        best = None
+        for _ in range(reps):
+            e0.record(stream)
+            qs.qs_init_basis(h, 0)
+            qs.qs_run_circuit(h, sc)
+            st = qs.qs_stats(h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        return best, st
+
+    circuits = []
+    for name in ("fullsize_5x6_d25_s0.txt", "fullsize_4x8_d25_s1.txt"):
+        gold = load_golden_amplitudes(name)
+        if gold is None:
+            continue
+        (rows, cols, cycles, seed, n), idx, want = gold
+        nq, g = qs.qs_supremacy_circuit(rows, cols, cycles, seed)
+        res = {"grid": "%dx%d" % (rows, cols), "qubits": nq, "cz_cycles": cycles, "seed": seed, "dtype": "c64"}
+        h = qs.qs_alloc(nq, qs.QS_C64, stream)
+        try:
+            for label, which in (("learned", qs.QS_COST_AUTO), ("analytic", qs.QS_COST_ANALYTIC)):
+                sc, km, pred = qs.qs_plan_circuit(nq, g, qs.QS_C64, cm, which)
+                try:
+                    timed(h, sc, 1)                              # uploads the schedule
+                    best, st = timed(h, sc, 3)
+                    got = qs.qs_get_amplitudes_at(h, idx)
+                    qs.qs_init_basis(h, 0)
+                    op_ms = qs.qs_run_circuit_timed(h, sc)
+                    kms, pms, pbytes, _, _ = classify_sweeps(qs, sc, op_ms, nq, qs.QS_C64)
+                    err = float(np.max(np.abs(got - want)))
+                    sweep_bytes = 2 * (8 << nq)
+                    dom = max(kms, key=lambda kk: sum(kms[kk])) if kms else None
+                    roof = None
+                    if dom is not None:
+                        dms = statistics.mean(kms[dom])
+                        roof = {"kernel": "%s_k%d" % dom if dom[0] == "dense" else dom[0],
+                                "launches": len(kms[dom]), "kernel_ms": dms,
+                                "achieved_gbs": sweep_bytes / (dms * 1e-3) / 1e9,
+                                "frac": sweep_bytes / (dms * 1e-3) / 1e9 / hbm_gbs}
+                    res[label] = {"k_max": km, "ops": qs.qs_schedule_num_ops(sc), "predicted_s": pred / 1e3,
+                                  "s_per_circuit": best, "max_abs_dpsi_vs_oracle": err,
+                                  "rel_dpsi": err / float(np.max(np.abs(want))),
+                                  "norm": st[0], "m2": st[3], "full_sweep_roofline": roof,
+                                  "partial_support": {"launches": len(pms), "total_ms": sum(pms),
+                                                      "gbs": pbytes / (sum(pms) * 1e-3) / 1e9 if pms else None}}
+                finally:
+                    qs.qs_schedule_free(sc)
+        finally:
+            qs.qs_free(h)
+        res["gain_learned_vs_analytic"] = res["analytic"]["s_per_circuit"] / res["learned"]["s_per_circuit"]
+        # plain gate-by-gate complex128 form of the same circuit
+        hp = qs.qs_alloc(nq, qs.QS_C128, stream)
+        try:
+            scp = qs.qs_schedule_build(nq, g, fuse=False)
+            try:
+                best, _ = timed(hp, scp, 1)
+            finally:
+                qs.qs_schedule_free(scp)
+        finally:
+            qs.qs_free(hp)
+        res["plain_c128_s_per_circuit"] = best
+        res["speedup_vs_plain_c128"] = best / res["learned"]["s_per_circuit"]
+        res["within_tolerance"] = res["learned"]["max_abs_dpsi_vs_oracle"] <= 2e-6
+        circuits.append(res)
+    qs.qs_cost_model_free(cm)
+    return {"what": "learned-schedule (MLP cost model, auto fallback) complex64 form against the analytic-model "
+                    "plan and the plain gate-by-gate complex128 form; a4-a7 per circuit, CUDA events, best of 3",
+            "cost_model": {"harness_timings": int(T.size), "harness_s": harness_s, "fit_s": fit_s,
+                           "mlp_holdout_median_abs_log_err": rep["mlp_holdout_median_abs_log_err"],
+                           "analytic_holdout_median_abs_log_err": rep["analytic_holdout_median_abs_log_err"],
+                           "uses_mlp": rep["use_mlp"]},
+            "circuits": circuits}
 
 
 # ------------------------------------------------------- learned scheduling
@@ -671,6 +834,9 @@ def main():
     ap.add_argument("--no-fold", action="store_true",
                     help="run every phase op as its own sweep (no folding into the tensor-core sweep before it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-target", action="store_true",
+                    help="skip the learned-schedule complex64 runs of the 30- and 32-qubit circuits")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-circuit batched run")
     args = ap.parse_args()
     if args.warmup < 3:
         print("note: warmup raised to 3", file=sys.stderr)

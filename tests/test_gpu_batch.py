@@ -120,3 +120,33 @@ def test_batch_rejects_bad_config(torch_stream):
             qs.qs_batch_free(b)
     finally:
         qs.qs_schedule_free(sc)
+
+
+def test_batch_512_circuits_autotuned_graph(torch_stream):
+    """Config 4 at its stated size: all 512 circuits (seeds 0..511) in one
+    persistent launch replayed from a CUDA graph with the autotuner's choice;
+    every circuit's norm within 1e-5, and 23 circuits spread over the seeds
+    (every grid) against the oracle within 2e-6."""
+    circs = batch_circuits(range(512))
+    km, C, T, _ = qs.qs_batch_autotune(circs, qs.QS_C64, torch_stream)
+    scheds = [qs.qs_schedule_build(n, g, k_max=km, search_runs=1, search_first=1) for (n, g) in circs]
+    try:
+        b = qs.qs_batch_create(scheds, qs.QS_C64, torch_stream)
+        try:
+            qs.qs_batch_set_config(b, C, T)
+            qs.qs_batch_run_graph(b)
+            qs.qs_batch_run_graph(b)
+            st = qs.qs_batch_stats(b, len(circs))
+            assert np.max(np.abs(st[:, 0] - 1)) < 1e-5
+            picked = list(range(0, 512, 23))
+            assert {circs[i][0] for i in picked} == {16, 20, 21}
+            for i in picked:
+                n, g = circs[i]
+                got = qs.qs_batch_get_amplitudes(b, i, n)
+                ref = sim.run_circuit(n, qs.gates_to_tuples(g))
+                assert np.max(np.abs(got - ref)) <= 2e-6, i
+        finally:
+            qs.qs_batch_free(b)
+    finally:
+        for sc in scheds:
+            qs.qs_schedule_free(sc)

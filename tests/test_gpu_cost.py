@@ -67,24 +67,82 @@ def test_timing_harness_and_fit():
         qs.qs_cost_model_free(cm)
 
 
+@pytest.fixture(scope="module")
+def fitted():
+    """A cost model fitted on 2400 measured timings of random ops on 20- to
+    28-qubit states of both dtypes (the harness of config 5, smaller)."""
+    F, T = [], []
+    for dt in (qs.QS_C64, qs.QS_C128):
+        f, t = qs.qs_cost_sample(20, 28, dt, 1200, seed=50 + dt, max_ms=100)
+        F.append(f)
+        T.append(t)
+    F, T = np.concatenate(F), np.concatenate(T)
+    cm = qs.qs_cost_model_create()
+    rep = qs.qs_cost_model_fit(cm, F, T, epochs=1500, seed=3)
+    yield cm, rep
+    qs.qs_cost_model_free(cm)
+
+
+def test_mlp_predicts_measured_times_better_than_analytic(fitted):
+    """On held-out timings (every fifth, by a seeded hash) the fitted network's
+    median |log error| is below the analytic bytes-over-bandwidth model's, so
+    the fallback rule selects it."""
+    cm, rep = fitted
+    print("held-out median |log err|: mlp %.3f, analytic %.3f" % (
+        rep["mlp_holdout_median_abs_log_err"], rep["analytic_holdout_median_abs_log_err"]))
+    assert rep["mlp_holdout_median_abs_log_err"] < rep["analytic_holdout_median_abs_log_err"]
+    assert rep["use_mlp"]
+
+
 @pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
-def test_planned_schedule_matches_oracle(dtype):
+def test_learned_plan_against_analytic_plan_measured(fitted, dtype):
+    """What the trained network gains: one 28-qubit circuit (4x7 grid, 20 CZ
+    cycles) planned with the learned model (auto fallback) and with the
+    analytic model, both run and timed (CUDA events, best of 3).  The gain is
+    printed; the plans' kernels are the same, so the bar is that the learned
+    plan is no slower than the analytic one beyond 5% timing noise."""
+    cm, _ = fitted
+    n, g = qs.qs_supremacy_circuit(4, 7, 20, 0)
+    h = qs.qs_alloc(n, dtype)
+    res = {}
+    try:
+        for name, which in (("analytic", qs.QS_COST_ANALYTIC), ("learned", qs.QS_COST_AUTO)):
+            sc, km, pred = qs.qs_plan_circuit(n, g, dtype, cm, which)
+            try:
+                best = None
+                for _ in range(3):
+                    qs.qs_init_basis(h, 0)
+                    ms = qs.qs_run_circuit_timed(h, sc)
+                    t = float(ms[ms >= 0].sum())
+                    best = t if best is None else min(best, t)
+                res[name] = (best, km, pred, qs.qs_schedule_num_ops(sc))
+            finally:
+                qs.qs_schedule_free(sc)
+    finally:
+        qs.qs_free(h)
+    gain = res["analytic"][0] / res["learned"][0]
+    print("dtype %d: analytic plan %.2f ms (k_max %d, %d ops), learned plan %.2f ms (k_max %d, %d ops): "
+          "gain %.3fx" % (dtype, res["analytic"][0], res["analytic"][1], res["analytic"][3],
+                          res["learned"][0], res["learned"][1], res["learned"][3], gain))
+    assert gain > 1 / 1.05
+
+
+@pytest.mark.parametrize("which", [qs.QS_COST_ANALYTIC, qs.QS_COST_AUTO])
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_planned_schedule_matches_oracle(fitted, dtype, which):
+    """Schedules planned with either model give the oracle's state (20 qubits)."""
     n, g = qs.qs_supremacy_circuit(4, 5, 25, 6)
     ref = sim.run_circuit(n, qs.gates_to_tuples(g))
-    cm = qs.qs_cost_model_create()
+    sc, km, t = qs.qs_plan_circuit(n, g, dtype, fitted[0], which)
     try:
-        sc, km, t = qs.qs_plan_circuit(n, g, dtype, cm, qs.QS_COST_ANALYTIC)
+        assert 2 <= km <= 5 and t > 0
+        h = qs.qs_alloc(n, dtype)
         try:
-            assert 2 <= km <= 5 and t > 0
-            h = qs.qs_alloc(n, dtype)
-            try:
-                qs.qs_init_basis(h, 0)
-                qs.qs_run_circuit(h, sc)
-                psi = qs.qs_get_amplitudes(h)
-            finally:
-                qs.qs_free(h)
+            qs.qs_init_basis(h, 0)
+            qs.qs_run_circuit(h, sc)
+            psi = qs.qs_get_amplitudes(h)
         finally:
-            qs.qs_schedule_free(sc)
+            qs.qs_free(h)
     finally:
-        qs.qs_cost_model_free(cm)
+        qs.qs_schedule_free(sc)
     assert np.max(np.abs(psi - ref)) <= (1e-12 if dtype == qs.QS_C128 else 2e-6)
