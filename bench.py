@@ -702,6 +702,95 @@ def _search_config(qs, plain):
             "cost": "sum over dense sweeps of 2^(|support| - n) from |0...0>"}
 
 
+# ------------------------------------------------------- single-kernel timing
+
+def run_kernel(args):
+    """One kernel at a time on a full synthetic state (the per-kernel roofline
+    table and the small cases ncu captures): --kernel dense|diag|phase|stats|
+    sample|fill|mlp, --n qubits, --dtype c64|c128, --k cluster size, --targets
+    (comma list; default the k highest qubits), --path auto|cuda|tensor, --reps
+    launches.  Every launch is timed with CUDA events on the state's stream; the
+    JSON line gives the mean time, the algorithmic bytes of one launch and
+    their rate against the measured HBM copy bandwidth."""
+    import numpy as np
+    import torch
+    from paper_1704_01127_gb300 import build as _build
+    _build.build()
+    import paper_1704_01127_gb300.qs as qs
+    torch.cuda.set_device(0)
+    hbm_gbs, _, peak_src = load_peaks()
+    stream = torch.cuda.Stream()
+    n, k = args.n, args.k
+    dtype = qs.QS_C128 if args.dtype == "c128" else qs.QS_C64
+    amp = 16 if dtype == qs.QS_C128 else 8
+    g = np.random.Generator(np.random.PCG64(12345 + n + 31 * k))
+    targets = [int(x) for x in args.targets.split(",")] if args.targets else list(range(n - k, n))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    times = []
+
+    def timed(fn):
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    if args.kernel == "mlp":
+        net = qs.qs_mlp_create(1)
+        X = g.standard_normal((args.batch, qs.QS_NFEAT))
+        Y = g.standard_normal(args.batch)
+        qs.qs_mlp_train(net, X, Y, 5)
+        t = time.perf_counter()
+        qs.qs_mlp_train(net, X, Y, args.reps)
+        per = (time.perf_counter() - t) / args.reps * 1e3
+        qs.qs_mlp_free(net)
+        print(json.dumps({"kernel": "mlp training epoch (k_mlp_fwd, k_mlp_delta, k_mlp_grad, k_adam)",
+                          "batch": args.batch, "epochs": args.reps, "ms_per_epoch": per}))
+        return None
+    h = qs.qs_alloc(n, dtype, stream)
+    path = {"auto": qs.QS_PATH_AUTO, "cuda": qs.QS_PATH_CUDA_CORES, "tensor": qs.QS_PATH_TENSOR}[args.path]
+    qs.qs_set_path(h, path)
+    qs.qs_init_uniform(h)
+    full = amp << n
+    if args.kernel == "dense":
+        z = g.standard_normal((1 << k, 1 << k)) + 1j * g.standard_normal((1 << k, 1 << k))
+        U, _ = np.linalg.qr(z)
+        fn, what, bytes_ = (lambda: qs.qs_apply_cluster(h, targets, U)), "dense k=%d on %s" % (k, targets), 2 * full
+    elif args.kernel == "diag":
+        d = np.exp(1j * g.uniform(0, 2 * np.pi, 1 << k))
+        fn, what, bytes_ = (lambda: qs.qs_apply_diag(h, targets, d)), "diag k=%d on %s" % (k, targets), 2 * full
+    elif args.kernel == "phase":
+        coeff = g.integers(0, 8, n)
+        edges = [tuple(sorted(int(x) for x in g.permutation(n)[:2])) for _ in range(n)]
+        fn, what, bytes_ = (lambda: qs.qs_apply_phase(h, coeff, edges)), "phase, %d CZ terms" % n, 2 * full
+    elif args.kernel == "stats":
+        fn, what, bytes_ = (lambda: qs.qs_stats(h)), "statistics pass", full
+    elif args.kernel == "sample":
+        fn, what, bytes_ = ((lambda: qs.qs_sample(h, 7, args.m)),
+                            "%d draws (bytes: the block sums read the state once)" % args.m, full)
+    elif args.kernel == "fill":
+        def fn():
+            qs.qs_init_basis(h, 0)
+            qs.qs_device_ptr(h)          # writes the zeros outside the support
+        what, bytes_ = "basis state written in full", full
+    else:
+        raise SystemExit("unknown kernel %s" % args.kernel)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    for _ in range(args.reps):
+        times.append(timed(fn))
+    qs.qs_free(h)
+    ms = statistics.mean(times)
+    print(json.dumps({"kernel": args.kernel, "what": what, "n": n, "dtype": args.dtype, "path": args.path,
+                      "reps": args.reps, "mean_ms": ms, "min_ms": min(times),
+                      "algorithmic_bytes": bytes_, "gbs": bytes_ / (ms * 1e-3) / 1e9,
+                      "hbm_frac": bytes_ / (ms * 1e-3) / 1e9 / hbm_gbs, "peak_gbs": hbm_gbs,
+                      "peak_source": peak_src}))
+    return None
+
+
 # ------------------------------------------------------------ oracle (CPU) leg
 
 def host_cpu():
@@ -837,11 +926,23 @@ def main():
     ap.add_argument("--no-target", action="store_true",
                     help="skip the learned-schedule complex64 runs of the 30- and 32-qubit circuits")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-circuit batched run")
+    ap.add_argument("--kernel", choices=["dense", "diag", "phase", "stats", "sample", "fill", "mlp"],
+                    help="time one kernel on a full synthetic state instead of circuits")
+    ap.add_argument("--n", type=int, default=28)
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c128")
+    ap.add_argument("--targets", default="")
+    ap.add_argument("--path", choices=["auto", "cuda", "tensor"], default="auto")
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--m", type=int, default=1 << 20)
+    ap.add_argument("--batch", type=int, default=4096)
     args = ap.parse_args()
     if args.warmup < 3:
         print("note: warmup raised to 3", file=sys.stderr)
         args.warmup = 3
-    if args.impl == "reference":
+    if args.kernel:
+        line = run_kernel(args)
+    elif args.impl == "reference":
         line = run_reference(args)
     elif args.workload == "batch512_c64":
         line = run_batch(args)
