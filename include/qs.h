@@ -37,6 +37,7 @@ enum { QS_C64 = 0, QS_C128 = 1 };   /* amplitude type: complex float / double */
 
 #define QS_MAX_K 5          /* largest dense cluster (2^5 x 2^5 unitary) */
 #define QS_MAX_DIAG_K 12    /* largest table diagonal */
+#define QS_MAX_SWAP 16      /* most qubit pairs one qs_swap_qubits call exchanges */
 #define QS_MAX_QUBITS 36    /* largest state this build addresses */
 
 typedef struct qs_state qs_state;   /* opaque, owned by the library */
@@ -144,6 +145,15 @@ int qs_apply_cluster(qs_state *s, const int *qubits, int k, const double *U);
  * from the bits qubits[0..k-1] of i as in qs_apply_cluster.  d: 2^k complex128
  * interleaved.  1 <= k <= QS_MAX_DIAG_K. */
 int qs_apply_diag(qs_state *s, const int *qubits, int k, const double *d);
+
+/* Exchange qubit a[j] with qubit b[j] for j < m (the local bit swaps of Sec.
+ * 3.4, used by the bit-location remapping of Sec. 3.6): amplitude i moves to
+ * the index with bits a[j] and b[j] of i exchanged, i.e. the product of the m
+ * SWAP gates (a[j], b[j]).  One sweep over the state in place; swaps that
+ * involve qubits 0-2 go through shared memory so that every global access is
+ * a contiguous run of at least 512 bytes.  The 2m qubits are distinct and in
+ * [0, n); 0 <= m <= QS_MAX_SWAP.  Errors: QS_EINVAL. */
+int qs_swap_qubits(qs_state *s, const int *a, const int *b, int m);
 
 /* Apply a product of T-type phases and CZ gates (Sec. 2, Sec. 3.5: both are
  * diagonal): amplitude i is multiplied by e^{i pi m(i)/4} with

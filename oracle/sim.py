@@ -36,6 +36,8 @@ def lib():
         L.or_splitmix64.restype = ctypes.c_uint64
         L.or_sample.argtypes = [dp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, u64p]
         L.or_sample.restype = ctypes.c_int
+        L.or_apply_swap.argtypes = [dp, ctypes.c_int, ip, ip, ctypes.c_int]
+        L.or_apply_swap.restype = ctypes.c_int
         L.or_set_threads.argtypes = [ctypes.c_int]
         L.or_max_threads.restype = ctypes.c_int
         _lib = L
@@ -102,6 +104,15 @@ def apply_diag(psi, qubits, d):
     q = np.ascontiguousarray(qubits, dtype=np.int32)
     dd = np.ascontiguousarray(d, dtype=np.complex128).view(np.float64)
     rc = lib().or_apply_diag(_dp(psi.view(np.float64)), n, _ip(q), len(q), _dp(dd))
+    assert rc == 0, rc
+
+
+def apply_swap(psi, a, b):
+    """Exchange qubit a[j] with qubit b[j] for every j (index permutation)."""
+    n = _check_state(psi)
+    aa = np.ascontiguousarray(a, dtype=np.int32)
+    bb = np.ascontiguousarray(b, dtype=np.int32)
+    rc = lib().or_apply_swap(_dp(psi.view(np.float64)), n, _ip(aa), _ip(bb), int(aa.size))
     assert rc == 0, rc
 
 

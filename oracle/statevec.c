@@ -141,6 +141,31 @@ int or_apply_kq(double *psi, int n, const int *qubits, int k, const double *U)
     return 0;
 }
 
+/* Exchange of qubits a[j] and b[j], j < m (the local bit swaps of Sec. 3.4):
+ * amplitude i moves to the index with bits a[j] and b[j] of i exchanged.
+ * Written as the permutation itself, through a copy of the state. */
+int or_apply_swap(double *psi, int n, const int *a, const int *b, int m)
+{
+    uint64_t dim = (uint64_t)1 << n;
+    for (int j = 0; j < m; j++)
+        if (a[j] < 0 || a[j] >= n || b[j] < 0 || b[j] >= n) return -1;
+    double *old = (double *)malloc(sizeof(double) * 2 * dim);
+    if (!old) return -2;
+    memcpy(old, psi, sizeof(double) * 2 * dim);
+    for (uint64_t i = 0; i < dim; i++) {
+        uint64_t t = i;
+        for (int j = 0; j < m; j++) {
+            uint64_t ba = (i >> a[j]) & 1, bb = (i >> b[j]) & 1;
+            t &= ~(((uint64_t)1 << a[j]) | ((uint64_t)1 << b[j]));
+            t |= (ba << b[j]) | (bb << a[j]);
+        }
+        psi[2 * t] = old[2 * i];
+        psi[2 * t + 1] = old[2 * i + 1];
+    }
+    free(old);
+    return 0;
+}
+
 /* A diagonal k-qubit gate: amplitude i is multiplied by d[x], x gathered from
  * the bits of i at qubits[0..k-1] exactly as in or_apply_kq. */
 int or_apply_diag(double *psi, int n, const int *qubits, int k, const double *d)

@@ -137,6 +137,9 @@ int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *de
                     const void *dev_tc);
 int qs_launch_diag(qs_state *s, const int *qubits, int k, const void *dev_table);
 int qs_launch_phase(qs_state *s, const void *dev_phase, int n_act);
+// Exchange qubits a[j] <-> b[j] (j < m, validated by the caller) in one sweep.
+int qs_launch_swap(qs_state *s, const int *a, const int *b, int m);
+uint64_t qs_swap_index(uint64_t i, const int *a, const int *b, int m);
 
 // Default kernel-path policy for a dense cluster (qs_apply.cu).
 bool qs_tc_wanted(int dtype, int k, int n);

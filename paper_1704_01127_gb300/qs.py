@@ -87,6 +87,7 @@ _SIGS = {
     "qs_run_circuit_timed": ([_VP, _VP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "qs_set_device": ([ctypes.c_int], ctypes.c_int),
     "qs_set_path": ([_VP, ctypes.c_int], ctypes.c_int),
+    "qs_swap_qubits": ([_VP, _IP, _IP, ctypes.c_int], ctypes.c_int),
     "qs_set_phase_fold": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_selftest_timeout": ([_VP], ctypes.c_int),
     "qs_stats_static": ([_VP, ctypes.c_int, ctypes.c_int, _VP, _DP], ctypes.c_int),
@@ -247,6 +248,14 @@ def qs_apply_diag(h, qubits, d):
     dd = _c128(d)
     assert dd.size == 1 << q.size
     _check(lib().qs_apply_diag(h, _ip(q), int(q.size), _dp(dd.view(np.float64))))
+
+
+def qs_swap_qubits(h, a, b):
+    """Exchange qubit a[j] with qubit b[j] for every j (one sweep)."""
+    aa = np.ascontiguousarray(a, dtype=np.int32)
+    bb = np.ascontiguousarray(b, dtype=np.int32)
+    assert aa.size == bb.size
+    _check(lib().qs_swap_qubits(h, _ip(aa), _ip(bb), int(aa.size)))
 
 
 def qs_apply_phase(h, coeff, edges):

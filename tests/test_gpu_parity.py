@@ -375,6 +375,43 @@ def test_init_states():
             assert psi[-1] == 1 and np.count_nonzero(psi) == 1
 
 
+SWAP_CASES = [
+    (12, [(0, 5)]), (12, [(2, 9), (3, 10), (4, 11)]), (12, [(0, 1), (7, 3)]), (14, [(13, 0), (1, 12), (2, 4)]),
+    (20, [(5, 19), (8, 12)]), (20, [(0, 19), (1, 18), (2, 17), (3, 16), (4, 15)]), (9, [(0, 8), (1, 7), (2, 6)]),
+    (22, [(2, 21), (3, 20), (4, 19)]), (6, [(0, 5), (1, 4), (2, 3)]), (16, [(3, 4)]), (16, []),
+]
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+@pytest.mark.parametrize("n,pairs", SWAP_CASES)
+def test_swap_qubits_bit_exact(dtype, n, pairs):
+    """Qubit exchanges (the tiled kernel when a swapped qubit is below 3, the
+    pairwise one otherwise) move amplitudes bit for bit as the oracle's
+    permutation does."""
+    psi = f32_round(random_state(n, 500 + n + len(pairs)))
+    ref = psi.copy()
+    a, b = [x for x, _ in pairs], [y for _, y in pairs]
+    sim.apply_swap(ref, a, b)
+    with State(n, dtype) as s:
+        qs.qs_set_amplitudes(s.h, psi)
+        qs.qs_swap_qubits(s.h, a, b)
+        assert np.array_equal(qs.qs_get_amplitudes(s.h), ref)
+
+
+def test_swap_qubits_after_basis_start_and_errors():
+    """After qs_init_basis the zeros outside the support are written first; bad
+    arguments are rejected."""
+    with State(10, qs.QS_C128) as s:
+        qs.qs_init_basis(s.h, 0b0000000101)
+        qs.qs_swap_qubits(s.h, [0, 2], [9, 8])
+        out = qs.qs_get_amplitudes(s.h)
+        assert out[0b1100000000] == 1 and np.count_nonzero(out) == 1
+        for a, b in (([0], [0]), ([0, 1], [2, 1]), ([10], [1]), ([-1], [2])):
+            with pytest.raises(qs.QSError) as e:
+                qs.qs_swap_qubits(s.h, a, b)
+            assert e.value.code == qs.QS_EINVAL
+
+
 def test_errors_leave_gpu_usable():
     with State(8, qs.QS_C128) as s:
         for bad in ([0, 0], [8], [-1], list(range(6))):

@@ -116,6 +116,32 @@ def test_apply_kq_reduces_to_1q_and_cz():
     np.testing.assert_allclose(a, b, rtol=0, atol=0)
 
 
+SWAP = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+
+
+@pytest.mark.parametrize("pairs", [[(0, 5)], [(2, 9), (3, 10), (4, 11)], [(0, 1), (7, 3)], [(11, 0), (1, 10)]])
+def test_apply_swap_equals_swap_gates(pairs):
+    """The qubit exchange equals the SWAP gates (a 4x4 permutation matrix
+    applied by the Sec. 3.2 gather) one pair after another, and is its own
+    inverse."""
+    psi = random_state(12, 40 + len(pairs))
+    ref = psi.copy()
+    for (a, b) in pairs:
+        sim.apply_kq(ref, [a, b], SWAP)
+    got = psi.copy()
+    sim.apply_swap(got, [a for a, _ in pairs], [b for _, b in pairs])
+    assert np.array_equal(got, ref)
+    sim.apply_swap(got, [a for a, _ in pairs], [b for _, b in pairs])
+    assert np.array_equal(got, psi)
+
+
+def test_apply_swap_moves_basis_states():
+    """|x> goes to |x with bits a and b exchanged> (Sec. 2 bit convention)."""
+    psi = sim.basis_state(6, 0b000101)
+    sim.apply_swap(psi, [0, 2], [4, 5])
+    assert psi[0b110000] == 1 and np.count_nonzero(psi) == 1
+
+
 def test_apply_diag_equals_embedding():
     n, qubits = 6, [3, 0, 5]
     d = random_diag(3, 9)
