@@ -233,9 +233,15 @@ def run_ours(args):
     # while the GPU runs this one (ctypes releases the GIL in library calls)
     prep_pool = concurrent.futures.ThreadPoolExecutor(max_workers=1)
 
+    # the clustering search leaves cores to the thread that launches kernels
+    qs.qs_set_host_threads(args.search_threads)
+
     def prepare(seed):
+        qs.qs_set_device(local)
         nq, gates = qs.qs_supremacy_circuit(rows, cols, cycles, seed, removed=removed)       # a1
-        return qs.qs_schedule_build(nq, gates, k_max=k_max, fuse=not args.plain)              # a2, a3
+        sc = qs.qs_schedule_build(nq, gates, k_max=k_max, fuse=not args.plain)                # a2, a3
+        qs.qs_schedule_upload(sc, dtype)          # operands packed and copied ahead of the run
+        return sc
 
     def one_step(prepared, next_seed, record):
         """Runs the prepared schedule; returns (stats, ops, next prepared)."""
@@ -405,7 +411,8 @@ def run_ours(args):
             rows, cols, n, cycles, dt, "gate by gate" if args.plain else "fused k<=%d + phase diagonals" % k_max),
             "seeds": "rank*1000 + step", "l2": "state %.1f GiB > L2 129 MB (no flush needed)" % (state_bytes / 2**30),
             "parallelism": "replicas" if world > 1 else "single GPU",
-            "phase_fold": not args.no_fold,
+            "phase_fold": not args.no_fold, "search_threads": args.search_threads,
+            "schedule_upload": "in the preparation thread, ahead of the run",
             "cluster_search": _search_config(qs, args.plain)},
         "roofline": roof, "sweeps": sweeps, "plain": plain,
         "speedup_vs_plain": (plain["s_per_circuit"] / per_circuit) if plain else None,
@@ -926,6 +933,8 @@ def main():
     ap.add_argument("--no-target", action="store_true",
                     help="skip the learned-schedule complex64 runs of the 30- and 32-qubit circuits")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-circuit batched run")
+    ap.add_argument("--search-threads", type=int, default=max(1, (os.cpu_count() or 1) - 2),
+                    help="host threads of the clustering search (the launching thread keeps the rest)")
     ap.add_argument("--kernel", choices=["dense", "diag", "phase", "stats", "sample", "fill", "mlp"],
                     help="time one kernel on a full synthetic state instead of circuits")
     ap.add_argument("--n", type=int, default=28)

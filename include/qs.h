@@ -336,6 +336,21 @@ void qs_schedule_free(qs_schedule *sc);
 /* Bytes qs_run_circuit copies host -> device the first time it runs this
  * schedule on a state of the given dtype (op matrices, tables, phase masks). */
 int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype);
+
+/* Build the schedule's device image for `dtype` (every op's matrix in the
+ * dtype, tensor-core operand planes, folded phase descriptors) and copy it to
+ * the calling thread's current device now, instead of at the first
+ * qs_run_circuit there.  The copy goes through a stream of its own, so a host
+ * thread can prepare the next circuit while kernels of the current one run on
+ * other streams.  A schedule must not be uploaded and run on the same device
+ * from two threads at once.  Errors: QS_EINVAL, QS_ENOMEM, QS_ECUDA. */
+int qs_schedule_upload(const qs_schedule *sc, int dtype);
+
+/* Most host threads the clustering search of qs_schedule_build uses (0, the
+ * default: one per hardware thread).  A caller that launches kernels while a
+ * second thread builds the next schedule can leave cores to the launching
+ * thread.  QS_EINVAL for n < 0. */
+int qs_set_host_threads(int n);
 int qs_schedule_num_qubits(const qs_schedule *sc);
 int qs_schedule_num_ops(const qs_schedule *sc);
 

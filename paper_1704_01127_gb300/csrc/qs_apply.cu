@@ -482,8 +482,18 @@ int ensure_dev_schedule(qs_state *s, const qs_schedule *csc)
         d.pool = nullptr;
         return qs_fail(QS_ENOMEM, "schedule upload: %s", cudaGetErrorString(e));
     }
-    e = cudaMemcpy(d.pool, blob.data(), blob.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return qs_fail(QS_ECUDA, "schedule upload: %s", cudaGetErrorString(e));
+    // copied on a stream of its own that waits for nothing, so an upload made
+    // ahead of time does not wait for kernels running on other streams
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.pool, blob.data(), blob.size(), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaFree(d.pool);
+        d.pool = nullptr;
+        return qs_fail(QS_ECUDA, "schedule upload: %s", cudaGetErrorString(e));
+    }
     d.bytes = blob.size();
     d.device = dev;
     return QS_OK;
@@ -669,6 +679,17 @@ extern "C" int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype)
         return QS_OK;
     });
     return rc == QS_OK ? bytes : rc;
+}
+
+extern "C" int qs_schedule_upload(const qs_schedule *sc, int dtype)
+{
+    return qs_guard([&]() -> int {
+        if (!sc || (dtype != QS_C64 && dtype != QS_C128)) return qs_fail(QS_EINVAL, "qs_schedule_upload");
+        qs_state probe;
+        probe.n = sc->n;
+        probe.dtype = dtype;
+        return ensure_dev_schedule(&probe, sc);
+    });
 }
 
 extern "C" int qs_set_device(int device)

@@ -267,6 +267,7 @@ constexpr int kMaxSearchRuns = 64;
 constexpr int kMaxSearchFirst = 16;
 constexpr int kMaxSearchSlack0 = 64;
 constexpr int kMaxSearchThreads = 32;
+std::atomic<int> g_host_threads{0};   // qs_set_host_threads: 0 = every hardware thread
 
 // Closures by qubit set: open addressing with linear probing over the 64-bit
 // masks (a set is never empty, so 0 marks a free slot, and never holds all 64
@@ -707,7 +708,8 @@ static int schedule_build_impl(int n, const qs_gate *gates, int n_gates, const q
                 }
             }
         };
-        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        if (g_host_threads.load() > 0) hw = std::min(hw, g_host_threads.load());
         const int n_threads = std::min(runs, std::min(hw, kMaxSearchThreads));
         std::vector<std::thread> pool;
         for (int t = 1; t < n_threads; t++) {
@@ -943,6 +945,13 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
             return schedule_from_ops_impl(n, n_ops, kinds, ks, qubits, offsets, pool, pool_len, out);
         });
     });
+}
+
+extern "C" int qs_set_host_threads(int n)
+{
+    if (n < 0) return qs_fail(QS_EINVAL, "qs_set_host_threads: %d < 0", n);
+    g_host_threads.store(n);
+    return QS_OK;
 }
 
 extern "C" int qs_schedule_num_qubits(const qs_schedule *sc) { return sc ? sc->n : 0; }

@@ -87,6 +87,8 @@ _SIGS = {
     "qs_run_circuit_timed": ([_VP, _VP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "qs_set_device": ([ctypes.c_int], ctypes.c_int),
     "qs_set_path": ([_VP, ctypes.c_int], ctypes.c_int),
+    "qs_schedule_upload": ([_VP, ctypes.c_int], ctypes.c_int),
+    "qs_set_host_threads": ([ctypes.c_int], ctypes.c_int),
     "qs_swap_qubits": ([_VP, _IP, _IP, ctypes.c_int], ctypes.c_int),
     "qs_set_phase_fold": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_selftest_timeout": ([_VP], ctypes.c_int),
@@ -441,6 +443,15 @@ def qs_schedule_upload_bytes(sched, dtype):
     if v < 0:
         _check(v)
     return int(v)
+
+
+def qs_schedule_upload(sched, dtype):
+    """Build and copy the schedule's device image for dtype now (current device)."""
+    _check(lib().qs_schedule_upload(sched, int(dtype)))
+
+
+def qs_set_host_threads(n):
+    _check(lib().qs_set_host_threads(int(n)))
 
 
 def qs_stats_static(dev_ptr, n, dtype, stream=None):

@@ -412,6 +412,44 @@ def test_swap_qubits_after_basis_start_and_errors():
             assert e.value.code == qs.QS_EINVAL
 
 
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_schedule_uploaded_ahead_from_another_thread(dtype):
+    """qs_schedule_upload in a second host thread while the first runs another
+    circuit; the uploaded schedule then runs to the oracle's state."""
+    import threading
+    n, g = qs.qs_supremacy_circuit(4, 5, 20, 11)
+    n2, g2 = qs.qs_supremacy_circuit(4, 5, 20, 12)
+    ref = sim.run_circuit(n2, qs.gates_to_tuples(g2))
+    sc1 = qs.qs_schedule_build(n, g, k_max=5)
+    sc2 = qs.qs_schedule_build(n2, g2, k_max=5)
+    try:
+        with State(n, dtype) as s:
+            qs.qs_init_basis(s.h, 0)
+            err = []
+
+            def up():
+                try:
+                    qs.qs_schedule_upload(sc2, dtype)
+                    qs.qs_schedule_upload(sc2, dtype)      # a second call keeps the image
+                except Exception as e:                     # reported below
+                    err.append(e)
+            th = threading.Thread(target=up)
+            th.start()
+            qs.qs_run_circuit(s.h, sc1)
+            th.join()
+            assert not err
+            qs.qs_init_basis(s.h, 0)
+            qs.qs_run_circuit(s.h, sc2)
+            out = qs.qs_get_amplitudes(s.h)
+        assert np.max(np.abs(out - ref)) <= TOL[dtype]
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_schedule_upload(sc2, 5)
+        assert e.value.code == qs.QS_EINVAL
+    finally:
+        qs.qs_schedule_free(sc1)
+        qs.qs_schedule_free(sc2)
+
+
 def test_errors_leave_gpu_usable():
     with State(8, qs.QS_C128) as s:
         for bad in ([0, 0], [8], [-1], list(range(6))):

@@ -226,3 +226,20 @@ def test_batch_circuit_params_match_oracle_and_are_uniform():
     assert set(grids) == {(4, 4), (4, 5), (3, 7)}
     assert all(120 < v < 220 for v in grids.values())
     assert min(depths) == 8 and max(depths) == 40
+
+
+def test_search_threads_do_not_change_the_clusters():
+    """qs_set_host_threads caps the clustering search's host threads; the runs
+    are independent, so one thread and every thread give the same clusters."""
+    n, g = qs.qs_supremacy_circuit(5, 6, 25, 3)
+    out = []
+    try:
+        for t in (1, 3, 0):
+            qs.qs_set_host_threads(t)
+            out.append([op["gates"] for op in _lib_ops(n, g, k_max=5)])
+    finally:
+        qs.qs_set_host_threads(0)
+    assert out[0] == out[1] == out[2]
+    with pytest.raises(qs.QSError) as e:
+        qs.qs_set_host_threads(-1)
+    assert e.value.code == qs.QS_EINVAL
