@@ -240,6 +240,8 @@ def run_ours(args):
         qs.qs_set_device(local)
         nq, gates = qs.qs_supremacy_circuit(rows, cols, cycles, seed, removed=removed)       # a1
         sc = qs.qs_schedule_build(nq, gates, k_max=k_max, fuse=not args.plain)                # a2, a3
+        if args.remap:                            # qubits to index bits (Sec. 3.6)
+            qs.qs_schedule_remap(sc, qs.qs_schedule_choose_remap(sc, dtype))
         qs.qs_schedule_upload(sc, dtype)          # operands packed and copied ahead of the run
         return sc
 
@@ -411,7 +413,7 @@ def run_ours(args):
             rows, cols, n, cycles, dt, "gate by gate" if args.plain else "fused k<=%d + phase diagonals" % k_max),
             "seeds": "rank*1000 + step", "l2": "state %.1f GiB > L2 129 MB (no flush needed)" % (state_bytes / 2**30),
             "parallelism": "replicas" if world > 1 else "single GPU",
-            "phase_fold": not args.no_fold, "search_threads": args.search_threads,
+            "phase_fold": not args.no_fold, "search_threads": args.search_threads, "remap": args.remap,
             "schedule_upload": "in the preparation thread, ahead of the run",
             "cluster_search": _search_config(qs, args.plain)},
         "roofline": roof, "sweeps": sweeps, "plain": plain,
@@ -935,6 +937,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-circuit batched run")
     ap.add_argument("--search-threads", type=int, default=max(1, (os.cpu_count() or 1) - 2),
                     help="host threads of the clustering search (the launching thread keeps the rest)")
+    ap.add_argument("--remap", action="store_true",
+                    help="move each schedule's qubits to the index bits the library picks (Sec. 3.6)")
     ap.add_argument("--kernel", choices=["dense", "diag", "phase", "stats", "sample", "fill", "mlp"],
                     help="time one kernel on a full synthetic state instead of circuits")
     ap.add_argument("--n", type=int, default=28)

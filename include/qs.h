@@ -337,6 +337,32 @@ void qs_schedule_free(qs_schedule *sc);
  * schedule on a state of the given dtype (op matrices, tables, phase masks). */
 int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype);
 
+/* Bit-location remapping (Sec. 3.6: map qubits to index bits so that the
+ * kernels' targets avoid the costly positions; the paper's local bit swaps,
+ * Sec. 3.4, move the data).  loc: n entries, qubit q to index bit loc[q], a set
+ * of exchanges (loc[loc[q]] == q).  qs_schedule_remap relabels every op of the
+ * schedule (dense and diagonal ops get their qubits mapped and their matrices
+ * permuted to ascending order; phase ops their coefficients and CZ pairs), so
+ * qs_schedule_op then reports index bits.  qs_run_circuit first brings the
+ * state's qubits to those bits: free after qs_init_basis (the one amplitude
+ * is written at its new index), one or two exchange sweeps otherwise.  The
+ * state remembers where its qubits are: calls that name qubits or indices
+ * (qs_apply_*, qs_swap_qubits, qs_get_amplitudes_at) translate them, and
+ * calls whose result follows the index order (qs_get_amplitudes,
+ * qs_probabilities, qs_sample, qs_sample_stats, qs_device_ptr) first move
+ * the qubits back to their own bits (one exchange sweep); qs_norm and
+ * qs_stats do not depend on the order.  qs_init_*, qs_set_amplitudes start in
+ * the identity order.  A remapped schedule cannot join a batch.  QS_EINVAL for
+ * a bad loc or a schedule remapped before.
+ * qs_schedule_choose_remap picks loc for a schedule started from |0...0>:
+ * the qubits that are targets of the least dense-sweep work (each sweep
+ * weighted by the share of the state it covers, the support growing by every
+ * dense cluster's qubits) go to index bits 0-1 (complex128) or 0-4
+ * (complex64), exchanged with the qubits there; measured on GB300, 5-qubit
+ * sweeps with targets among those bits take 25-30% longer. */
+int qs_schedule_remap(qs_schedule *sc, const int *loc);
+int qs_schedule_choose_remap(const qs_schedule *sc, int dtype, int *loc);
+
 /* Build the schedule's device image for `dtype` (every op's matrix in the
  * dtype, tensor-core operand planes, folded phase descriptors) and copy it to
  * the calling thread's current device now, instead of at the first

@@ -698,6 +698,7 @@ extern "C" int qs_dtype(const qs_state *s) { return s ? s->dtype : -1; }
 extern "C" void *qs_device_ptr(const qs_state *s)
 {
     if (!s) return nullptr;
+    if (qs_guard([&]() { return qs_order_set(const_cast<qs_state *>(s), nullptr); })) return nullptr;
     if (qs_materialize(const_cast<qs_state *>(s))) return nullptr;
     return s->amp;
 }
@@ -728,6 +729,7 @@ extern "C" int qs_init_basis(qs_state *s, uint64_t x)
     return qs_guard([&]() -> int {
         if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_basis: null state");
         if (x >> s->n) return qs_fail(QS_EINVAL, "qs_init_basis: index out of range");
+        qs_loc_reset(s);   // fresh contents: every qubit at its own bit
         cudaStream_t st = (cudaStream_t)s->stream;
         if (s->dtype == QS_C128)
             k_set_one<double2><<<1, 1, 0, st>>>((double2 *)s->amp, x);
@@ -740,6 +742,19 @@ extern "C" int qs_init_basis(qs_state *s, uint64_t x)
         // zeros are written now
         return s->owned ? QS_OK : qs_materialize(s);
     });
+}
+
+int qs_basis_move(qs_state *s, uint64_t x)
+{
+    cudaStream_t st = (cudaStream_t)s->stream;
+    if (s->dtype == QS_C128)
+        k_set_one<double2><<<1, 1, 0, st>>>((double2 *)s->amp, x);
+    else
+        k_set_one<float2><<<1, 1, 0, st>>>((float2 *)s->amp, x);
+    QS_CUDA(cudaGetLastError(), "basis move");
+    s->sup_free = 0;
+    s->sup_fix = x;
+    return QS_OK;
 }
 
 int qs_materialize(qs_state *s)
@@ -763,6 +778,7 @@ extern "C" int qs_init_uniform(qs_state *s)
 {
     return qs_guard([&]() -> int {
         if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_uniform: null state");
+        qs_loc_reset(s);   // fresh contents: every qubit at its own bit
         uint64_t N = 1ULL << s->n;
         int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count_dev() * 8);
         cudaStream_t st = (cudaStream_t)s->stream;
@@ -783,6 +799,7 @@ extern "C" int qs_set_amplitudes(qs_state *s, const double *host)
 {
     return qs_guard([&]() -> int {
         if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_set_amplitudes: null argument");
+        qs_loc_reset(s);   // fresh contents: every qubit at its own bit
         uint64_t N = 1ULL << s->n;
         cudaStream_t st = (cudaStream_t)s->stream;
         if (s->dtype == QS_C128) {
@@ -806,6 +823,7 @@ extern "C" int qs_get_amplitudes(qs_state *s, double *host)
     return qs_guard([&]() -> int {
         if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_get_amplitudes: null argument");
         if (int rc = qs_check_status(s)) return rc;
+        if (int rc = qs_order_set(s, nullptr)) return rc;   // index order
         if (int rc = qs_materialize(s)) return rc;
         uint64_t N = 1ULL << s->n;
         cudaStream_t st = (cudaStream_t)s->stream;
@@ -832,14 +850,17 @@ extern "C" int qs_get_amplitudes_at(qs_state *s, const uint64_t *idx, int64_t co
         if (int rc = qs_materialize(s)) return rc;
         const uint64_t N = 1ULL << s->n;
         cudaStream_t st = (cudaStream_t)s->stream;
+        const bool moved = !qs_loc_identity(s);
         for (int64_t j = 0; j < count; j++) {
             if (idx[j] >= N) return qs_fail(QS_EINVAL, "qs_get_amplitudes_at: index %lld out of range", (long long)j);
+            // the index in the state's bit order (qubits may sit at other bits)
+            const uint64_t at = moved ? qs_loc_index(s, idx[j]) : idx[j];
             if (s->dtype == QS_C128) {
-                QS_CUDA(cudaMemcpyAsync(out + 2 * j, (double2 *)s->amp + idx[j], 16, cudaMemcpyDeviceToHost, st),
+                QS_CUDA(cudaMemcpyAsync(out + 2 * j, (double2 *)s->amp + at, 16, cudaMemcpyDeviceToHost, st),
                         "qs_get_amplitudes_at");
             } else {
                 float f[2];
-                QS_CUDA(cudaMemcpyAsync(f, (float2 *)s->amp + idx[j], 8, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes_at");
+                QS_CUDA(cudaMemcpyAsync(f, (float2 *)s->amp + at, 8, cudaMemcpyDeviceToHost, st), "qs_get_amplitudes_at");
                 QS_CUDA(cudaStreamSynchronize(st), "qs_get_amplitudes_at");
                 out[2 * j] = f[0];
                 out[2 * j + 1] = f[1];
@@ -874,6 +895,7 @@ extern "C" int qs_probabilities(qs_state *s, double *out, int out_on_device)
 {
     return qs_guard([&]() -> int {
         if (!s || !s->amp || !out) return qs_fail(QS_EINVAL, "qs_probabilities: null argument");
+        if (int rc = qs_order_set(s, nullptr)) return rc;   // index order
         if (int rc = qs_materialize(s)) return rc;
         const uint64_t N = 1ULL << s->n;
         cudaStream_t st = (cudaStream_t)s->stream;
@@ -910,6 +932,7 @@ extern "C" int qs_sample(qs_state *s, uint64_t seed, int64_t m, uint64_t *out)
 {
     return qs_guard([&]() -> int {
         if (!s || !s->amp || m < 0 || (m > 0 && !out)) return qs_fail(QS_EINVAL, "qs_sample: bad arguments");
+        if (int rc = qs_order_set(s, nullptr)) return rc;   // index order
         if (int rc = qs_materialize(s)) return rc;
         return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out, nullptr)
                                    : sample_impl<float2>(s, seed, m, out, nullptr);
@@ -922,6 +945,7 @@ extern "C" int qs_sample_stats(qs_state *s, uint64_t seed, int64_t m, uint64_t *
         if (!s || !s->amp || m < 0 || (m > 0 && !out) || !stats)
             return qs_fail(QS_EINVAL, "qs_sample_stats: bad arguments");
         if (int rc = qs_check_status(s)) return rc;
+        if (int rc = qs_order_set(s, nullptr)) return rc;   // index order
         if (int rc = qs_materialize(s)) return rc;
         return s->dtype == QS_C128 ? sample_impl<double2>(s, seed, m, out, stats)
                                    : sample_impl<float2>(s, seed, m, out, stats);

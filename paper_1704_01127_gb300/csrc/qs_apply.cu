@@ -530,9 +530,10 @@ extern "C" int qs_apply_cluster(qs_state *s, const int *qubits, int k, const dou
         if (rc) return rc;
         if ((rc = check_qubits(s, qubits, k, QS_MAX_K, "qs_apply_cluster"))) return rc;
         if (!U) return qs_fail(QS_EINVAL, "qs_apply_cluster: null matrix");
-        int q[QS_MAX_K];
+        int lq[QS_MAX_K], q[QS_MAX_K];
+        for (int j = 0; j < k; j++) lq[j] = qs_loc(s, qubits[j]);   // the qubits' index bits
         std::vector<double> M;
-        sort_targets(qubits, k, U, true, q, M);
+        sort_targets(lq, k, U, true, q, M);
         const bool tc = s->path == QS_PATH_TENSOR ? s->n >= 5
                                                   : s->path == QS_PATH_AUTO && tc_wanted(s->dtype, k, s->n);
         if (tc) {
@@ -565,9 +566,10 @@ extern "C" int qs_apply_diag(qs_state *s, const int *qubits, int k, const double
         if (rc) return rc;
         if ((rc = check_qubits(s, qubits, k, QS_MAX_DIAG_K, "qs_apply_diag"))) return rc;
         if (!d) return qs_fail(QS_EINVAL, "qs_apply_diag: null table");
-        int q[QS_MAX_DIAG_K];
+        int lq[QS_MAX_DIAG_K], q[QS_MAX_DIAG_K];
+        for (int j = 0; j < k; j++) lq[j] = qs_loc(s, qubits[j]);   // the qubits' index bits
         std::vector<double> M;
-        sort_targets(qubits, k, d, false, q, M);
+        sort_targets(lq, k, d, false, q, M);
         std::vector<uint8_t> tab = to_real(M, s->dtype);
         std::vector<uint8_t> blob(64 + tab.size());
         std::memcpy(blob.data(), q, sizeof(int) * k);
@@ -585,13 +587,15 @@ extern "C" int qs_apply_phase(qs_state *s, const int *coeff, int n_edges, const 
         if (rc) return rc;
         if (!coeff || n_edges < 0 || (n_edges > 0 && !edges))
             return qs_fail(QS_EINVAL, "qs_apply_phase: bad arguments");
-        std::vector<int32_t> c(coeff, coeff + s->n);
+        // coefficients and CZ pairs on the qubits' index bits
+        std::vector<int32_t> c(s->n);
+        for (int q = 0; q < s->n; q++) c[qs_loc(s, q)] = coeff[q];
         std::vector<std::pair<int, int>> e;
         for (int i = 0; i < n_edges; i++) {
             int a = edges[2 * i], b = edges[2 * i + 1];
             if (a < 0 || a >= s->n || b < 0 || b >= s->n || a == b)
                 return qs_fail(QS_EINVAL, "qs_apply_phase: bad edge %d", i);
-            e.push_back({a, b});
+            e.push_back({qs_loc(s, a), qs_loc(s, b)});
         }
         int n_act;
         std::vector<uint8_t> blob = qs_pack_phase(s->n, c, e, &n_act);
@@ -608,6 +612,8 @@ extern "C" int qs_run_circuit(qs_state *s, const qs_schedule *sc)
         if (rc) return rc;
         if (!sc || sc->n != s->n) return qs_fail(QS_EINVAL, "qs_run_circuit: schedule/state qubit mismatch");
         if ((rc = ensure_dev_schedule(s, sc))) return rc;
+        // the schedule's ops name index bits: put the qubits where it expects them
+        if ((rc = qs_order_set(s, sc->remap.empty() ? nullptr : sc->remap.data()))) return rc;
         const qs_dev_sched &d = sc->dev[s->dtype];
         for (size_t i = 0; i < sc->ops.size(); i++) {
             const qs_op_host &op = sc->ops[i];
@@ -635,6 +641,8 @@ extern "C" int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *o
         if (!sc || sc->n != s->n || !op_ms)
             return qs_fail(QS_EINVAL, "qs_run_circuit_timed: bad schedule or output");
         if ((rc = ensure_dev_schedule(s, sc))) return rc;
+        // the schedule's ops name index bits (any exchange sweep is not timed)
+        if ((rc = qs_order_set(s, sc->remap.empty() ? nullptr : sc->remap.data()))) return rc;
         const qs_dev_sched &d = sc->dev[s->dtype];
         cudaStream_t st = (cudaStream_t)s->stream;
         size_t nops = sc->ops.size();
@@ -679,6 +687,84 @@ extern "C" int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype)
         return QS_OK;
     });
     return rc == QS_OK ? bytes : rc;
+}
+
+extern "C" int qs_schedule_remap(qs_schedule *sc, const int *loc)
+{
+    return qs_guard([&]() -> int {
+        if (!sc || !loc) return qs_fail(QS_EINVAL, "qs_schedule_remap: null argument");
+        if (!sc->remap.empty()) return qs_fail(QS_EINVAL, "qs_schedule_remap: schedule already remapped");
+        const int n = sc->n;
+        for (int q = 0; q < n; q++)
+            if (loc[q] < 0 || loc[q] >= n || loc[loc[q]] != q)
+                return qs_fail(QS_EINVAL, "qs_schedule_remap: loc is not a set of exchanges at qubit %d", q);
+        for (qs_op_host &op : sc->ops) {
+            if (op.kind == QS_OP_PHASE) {
+                std::vector<int32_t> c(n);
+                for (int q = 0; q < n; q++) c[loc[q]] = op.coeff[q];
+                op.coeff = c;
+                for (auto &e : op.edges) e = {loc[e.first], loc[e.second]};
+                continue;
+            }
+            int lq[QS_MAX_DIAG_K], q[QS_MAX_DIAG_K];
+            for (int j = 0; j < op.k; j++) lq[j] = loc[op.qubits[j]];
+            std::vector<double> M;
+            sort_targets(lq, op.k, op.matrix.data(), op.kind == QS_OP_DENSE, q, M);
+            for (int j = 0; j < op.k; j++) op.qubits[j] = q[j];
+            op.matrix = M;
+        }
+        for (auto &d : sc->dev) {   // device images describe the old ops
+            if (d.pool) cudaFree(d.pool);
+            d = qs_dev_sched();
+        }
+        sc->remap.assign(loc, loc + n);
+        return QS_OK;
+    });
+}
+
+extern "C" int qs_schedule_choose_remap(const qs_schedule *sc, int dtype, int *loc)
+{
+    return qs_guard([&]() -> int {
+        if (!sc || !loc || (dtype != QS_C64 && dtype != QS_C128))
+            return qs_fail(QS_EINVAL, "qs_schedule_choose_remap: bad arguments");
+        const int n = sc->n;
+        for (int q = 0; q < n; q++) loc[q] = q;
+        // the index bits whose sweeps cost more (measured): 0-1 for complex128,
+        // 0-4 for complex64
+        const int nlow = std::min(n, dtype == QS_C128 ? 2 : 5);
+        if (n < 5 + nlow) return QS_OK;
+        // weight of each qubit: the dense sweeps it is a target of, each
+        // counted by the share of the state it covers from |0...0> (the support
+        // grows by every dense cluster's qubits)
+        std::vector<double> w(n, 0.0);
+        uint64_t sup = 0;
+        for (const qs_op_host &op : sc->ops) {
+            if (op.kind != QS_OP_DENSE) continue;
+            for (int j = 0; j < op.k; j++) sup |= 1ULL << op.qubits[j];
+            const double share = std::ldexp(1.0, __builtin_popcountll(sup) - n);
+            for (int j = 0; j < op.k; j++) w[op.qubits[j]] += share;
+        }
+        // the nlow lightest qubits go to the low bits (ties: a qubit already
+        // there, then the lower qubit)
+        std::vector<int> order(n);
+        for (int q = 0; q < n; q++) order[q] = q;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            if (w[a] != w[b]) return w[a] < w[b];
+            return (a < nlow) > (b < nlow);
+        });
+        std::vector<char> chosen(n, 0);
+        for (int i = 0; i < nlow; i++) chosen[order[i]] = 1;
+        std::vector<int> in, out;              // chosen qubits above, low bits to free
+        for (int q = nlow; q < n; q++)
+            if (chosen[q]) in.push_back(q);
+        for (int b = 0; b < nlow; b++)
+            if (!chosen[b]) out.push_back(b);
+        for (size_t i = 0; i < in.size() && i < out.size(); i++) {
+            loc[in[i]] = out[i];
+            loc[out[i]] = in[i];
+        }
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_schedule_upload(const qs_schedule *sc, int dtype)

@@ -281,6 +281,10 @@ extern "C" int qs_batch_create(int n_circ, const qs_schedule *const *scheds, int
                 delete b;
                 return qs_fail(QS_EINVAL, "qs_batch_create: circuit %d must have 1..26 qubits", c);
             }
+            if (!sc->remap.empty()) {
+                delete b;
+                return qs_fail(QS_EINVAL, "qs_batch_create: circuit %d has a remapped schedule", c);
+            }
             circ[c].n = sc->n;
             circ[c].n_ops = (int32_t)sc->ops.size();
             circ[c].op_first = (int64_t)ops.size();

@@ -54,7 +54,43 @@ struct qs_state {
     // (qs_materialize).  Full support: sup_free = ~0.
     uint64_t sup_free = ~0ULL;
     uint64_t sup_fix = 0;
+    // Bit location of each qubit (the remapping of Sec. 3.6): index bit loc[q]
+    // holds qubit q.  Always a set of disjoint exchanges (loc[loc[q]] == q);
+    // the identity until a remapped schedule runs.  Calls that name qubits or
+    // indices translate them; calls whose result depends on the index order
+    // restore the identity first (one exchange sweep).
+    int loc[64] = {0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21,
+                   22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43,
+                   44, 45, 46, 47, 48, 49, 50, 51, 52, 53, 54, 55, 56, 57, 58, 59, 60, 61, 62, 63};
 };
+
+inline void qs_loc_reset(qs_state *s)
+{
+    for (int q = 0; q < 64; q++) s->loc[q] = q;
+}
+// qubit q -> its index bit in state s
+inline int qs_loc(const qs_state *s, int q) { return s->loc[q]; }
+inline bool qs_loc_identity(const qs_state *s)
+{
+    for (int q = 0; q < s->n; q++)
+        if (s->loc[q] != q) return false;
+    return true;
+}
+// index in qubit order -> index in the state's bit order (and back: the same
+// map, the locations being exchanges)
+inline uint64_t qs_loc_index(const qs_state *s, uint64_t x)
+{
+    uint64_t r = 0;
+    for (int q = 0; q < s->n; q++) r |= ((x >> q) & 1ULL) << s->loc[q];
+    return r;
+}
+// Bring the qubits to the locations `want` (n entries, exchanges) or, for
+// nullptr, to the identity: a relabelling when the state is the lazily
+// written basis state, else exchange sweeps.
+int qs_order_set(qs_state *s, const int *want);
+// After qs_init_basis: move the one amplitude of the support to index x
+// (nothing else written).
+int qs_basis_move(qs_state *s, uint64_t x);
 
 inline uint64_t qs_index_mask(int n) { return n >= 64 ? ~0ULL : ((1ULL << n) - 1); }
 inline bool qs_support_full(const qs_state *s)
@@ -95,6 +131,9 @@ struct qs_dev_sched {
 struct qs_schedule {
     int n = 0;
     std::vector<qs_op_host> ops;
+    // qs_schedule_remap: the ops name index bits, qubit q at bit remap[q]
+    // (exchanges); empty when the ops name the qubits themselves
+    std::vector<int> remap;
     qs_dev_sched dev[2];                 // indexed by dtype
 };
 

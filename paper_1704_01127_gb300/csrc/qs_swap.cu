@@ -25,14 +25,15 @@ namespace {
 constexpr int kPairLow = 3;          // k_swap_pairs when every swapped bit is >= 3
 constexpr int kMaxBlockBits = 11;    // tiled blocks of at most 2^11 amplitudes
 constexpr int kSwapThreads = 256;
+constexpr int kMaxPairs = 32;        // one sweep: up to 32 exchanges (a state has at most 36 qubits)
 
 struct SwapPlan {
     uint64_t amask, bmask;           // bits a_j, b_j
-    int a[QS_MAX_SWAP], b[QS_MAX_SWAP];
+    int a[kMaxPairs], b[kMaxPairs];
     int m;
     int c;                           // tiled: low run bits
     int h;                           // tiled: number of swapped bits >= c
-    int hb[2 * QS_MAX_SWAP];         // tiled: those bits, ascending
+    int hb[2 * kMaxPairs];           // tiled: those bits, ascending
     uint64_t zmask;                  // tiled: bits that do not enumerate blocks (low run + H)
 };
 
@@ -122,6 +123,7 @@ int sm_count()
 int qs_launch_swap(qs_state *s, const int *a, const int *b, int m)
 {
     if (m == 0) return QS_OK;
+    if (m > kMaxPairs) return qs_fail(QS_EINVAL, "swap: %d pairs", m);
     int rc = qs_materialize(s);
     if (rc) return rc;
     SwapPlan p;
@@ -197,6 +199,42 @@ uint64_t qs_swap_index(uint64_t i, const int *a, const int *b, int m)
     return r;
 }
 
+int qs_order_set(qs_state *s, const int *want)
+{
+    int target[64];
+    bool same = true;
+    for (int q = 0; q < s->n; q++) {
+        target[q] = want ? want[q] : q;
+        same = same && target[q] == s->loc[q];
+    }
+    if (same) return QS_OK;
+    if (s->sup_free == 0) {
+        // the lazily written basis state: its one amplitude moves, nothing else
+        const uint64_t x = qs_loc_index(s, s->sup_fix);      // index in qubit order
+        for (int q = 0; q < s->n; q++) s->loc[q] = target[q];
+        return qs_basis_move(s, qs_loc_index(s, x));
+    }
+    // undo the present exchanges, then make the wanted ones
+    int a[kMaxPairs], b[kMaxPairs], m = 0;
+    for (int q = 0; q < s->n; q++)
+        if (s->loc[q] > q) {
+            a[m] = q;
+            b[m++] = s->loc[q];
+        }
+    int rc = qs_launch_swap(s, a, b, m);
+    if (rc) return rc;
+    for (int q = 0; q < s->n; q++) s->loc[q] = q;
+    m = 0;
+    for (int q = 0; q < s->n; q++)
+        if (target[q] > q) {
+            a[m] = q;
+            b[m++] = target[q];
+        }
+    if ((rc = qs_launch_swap(s, a, b, m))) return rc;
+    for (int q = 0; q < s->n; q++) s->loc[q] = target[q];
+    return QS_OK;
+}
+
 extern "C" int qs_swap_qubits(qs_state *s, const int *a, const int *b, int m)
 {
     return qs_guard([&]() -> int {
@@ -211,6 +249,12 @@ extern "C" int qs_swap_qubits(qs_state *s, const int *a, const int *b, int m)
                 seen |= 1ULL << q;
             }
         }
-        return qs_launch_swap(s, a, b, m);
+        // the qubits' present bit locations
+        int pa[QS_MAX_SWAP], pb[QS_MAX_SWAP];
+        for (int j = 0; j < m; j++) {
+            pa[j] = qs_loc(s, a[j]);
+            pb[j] = qs_loc(s, b[j]);
+        }
+        return qs_launch_swap(s, pa, pb, m);
     });
 }

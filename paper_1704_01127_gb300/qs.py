@@ -88,6 +88,8 @@ _SIGS = {
     "qs_set_device": ([ctypes.c_int], ctypes.c_int),
     "qs_set_path": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_schedule_upload": ([_VP, ctypes.c_int], ctypes.c_int),
+    "qs_schedule_remap": ([_VP, _IP], ctypes.c_int),
+    "qs_schedule_choose_remap": ([_VP, ctypes.c_int, _IP], ctypes.c_int),
     "qs_set_host_threads": ([ctypes.c_int], ctypes.c_int),
     "qs_swap_qubits": ([_VP, _IP, _IP, ctypes.c_int], ctypes.c_int),
     "qs_set_phase_fold": ([_VP, ctypes.c_int], ctypes.c_int),
@@ -448,6 +450,20 @@ def qs_schedule_upload_bytes(sched, dtype):
 def qs_schedule_upload(sched, dtype):
     """Build and copy the schedule's device image for dtype now (current device)."""
     _check(lib().qs_schedule_upload(sched, int(dtype)))
+
+
+def qs_schedule_remap(sched, loc):
+    """Relabel the schedule's ops: qubit q to index bit loc[q] (exchanges)."""
+    l = np.ascontiguousarray(loc, dtype=np.int32)
+    _check(lib().qs_schedule_remap(sched, _ip(l)))
+
+
+def qs_schedule_choose_remap(sched, dtype):
+    """The library's pick of loc for a schedule started from |0...0>."""
+    n = lib().qs_schedule_num_qubits(sched)
+    l = np.zeros(n, dtype=np.int32)
+    _check(lib().qs_schedule_choose_remap(sched, int(dtype), _ip(l)))
+    return l
 
 
 def qs_set_host_threads(n):

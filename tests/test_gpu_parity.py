@@ -695,3 +695,69 @@ def test_entropy_table_log_accuracy():
         qs.qs_set_amplitudes(s.h, psi)
         got = qs.qs_stats(s.h)[1]
     assert abs(got - want) <= 1e-13 * max(1.0, abs(want))
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_remapped_schedule_against_oracle(dtype):
+    """A schedule with its qubits moved to other index bits (Sec. 3.6): run from
+    |0...0> (the basis amplitude is only relabelled), then read in every way.
+    Indices and qubits given by the caller are translated; sampling, whole-state
+    reads and probabilities first move the qubits back (one exchange sweep)."""
+    n, g = qs.qs_supremacy_circuit(4, 5, 16, 21)
+    ref = sim.run_circuit(n, qs.gates_to_tuples(g))
+    sc = qs.qs_schedule_build(n, g, k_max=5)
+    loc = np.arange(n)
+    loc[[0, 17, 2, 12, 4, 19]] = [17, 0, 12, 2, 19, 4]
+    qs.qs_schedule_remap(sc, loc)
+    idx = np.array([0, 1, 5, 77, 1 << 17, (1 << n) - 1, 123457], dtype=np.uint64)
+    try:
+        with State(n, dtype) as s:
+            qs.qs_init_basis(s.h, 0)
+            qs.qs_run_circuit(s.h, sc)
+            got = qs.qs_get_amplitudes_at(s.h, idx)
+            assert np.max(np.abs(got - ref[idx.astype(np.int64)])) <= TOL[dtype]
+            st = qs.qs_stats(s.h)
+            assert abs(st[0] - 1) < (1e-13 if dtype == qs.QS_C128 else 1e-5)
+            if dtype == qs.QS_C128:
+                assert np.array_equal(qs.qs_sample(s.h, 99, 2000), sim.sample(ref, 99, 2000))
+            out = qs.qs_get_amplitudes(s.h)
+            assert np.max(np.abs(out - ref)) <= TOL[dtype]
+            # a second run on a state that is not a basis state: exchange sweeps
+            qs.qs_run_circuit(s.h, sc)
+            ref2 = ref.copy()
+            for (_, name, q) in qs.gates_to_tuples(g):
+                sim.apply_gate(ref2, name, q)
+            U = random_unitary(3, 8)
+            qs.qs_apply_cluster(s.h, [0, 17, 6], U)        # qubits named as the caller knows them
+            sim.apply_kq(ref2, [0, 17, 6], U)
+            out = qs.qs_get_amplitudes(s.h)
+            assert np.max(np.abs(out - ref2)) <= 2 * TOL[dtype]
+    finally:
+        qs.qs_schedule_free(sc)
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_remapped_fullsize_against_oracle(dtype):
+    """30 qubits with the library's choice of bit locations: the oracle's stored
+    amplitudes through translated indices."""
+    import os
+    from conftest import GOLDEN, read_golden
+    name = "fullsize_5x6_d25_s0.txt"
+    if not os.path.exists(os.path.join(GOLDEN, name)):
+        pytest.skip("golden file missing")
+    rows = read_golden(name)
+    idx = np.array([int(r[0]) for r in rows[2:]], dtype=np.uint64)
+    want = np.array([complex(float(r[1]), float(r[2])) for r in rows[2:]])
+    n, g = qs.qs_supremacy_circuit(5, 6, 25, 0)
+    sc = qs.qs_schedule_build(n, g, k_max=5)
+    try:
+        loc = qs.qs_schedule_choose_remap(sc, dtype)
+        assert not np.array_equal(loc, np.arange(n))
+        qs.qs_schedule_remap(sc, loc)
+        with State(n, dtype) as s:
+            qs.qs_init_basis(s.h, 0)
+            qs.qs_run_circuit(s.h, sc)
+            got = qs.qs_get_amplitudes_at(s.h, idx)
+    finally:
+        qs.qs_schedule_free(sc)
+    assert np.max(np.abs(got - want)) <= TOL[dtype]

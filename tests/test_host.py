@@ -243,3 +243,68 @@ def test_search_threads_do_not_change_the_clusters():
     with pytest.raises(qs.QSError) as e:
         qs.qs_set_host_threads(-1)
     assert e.value.code == qs.QS_EINVAL
+
+
+def _ops_as_oracle_ops(sc):
+    out = []
+    for i in range(qs.qs_schedule_num_ops(sc)):
+        op = qs.qs_schedule_op(sc, i)
+        out.append(op)
+    return out
+
+
+def _apply_ops(psi, ops):
+    for op in ops:
+        if op["kind"] == "dense":
+            sim.apply_kq(psi, list(op["qubits"]), op["matrix"])
+        elif op["kind"] == "diag":
+            sim.apply_diag(psi, list(op["qubits"]), op["matrix"])
+        else:
+            sim.apply_phase(psi, op["coeff"], op["edges"])
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_schedule_remap_relabels_ops(dtype):
+    """qs_schedule_remap (Sec. 3.6 bit-location mapping): the remapped ops,
+    applied by the oracle to the state with its qubits exchanged as loc says,
+    give the original ops' state with the same exchange; the chooser returns
+    exchanges that move qubits onto the low bits."""
+    from inputs import random_state
+    n, g = qs.qs_supremacy_circuit(3, 4, 12, 5)
+    sc = qs.qs_schedule_build(n, g, k_max=4)
+    try:
+        before = _ops_as_oracle_ops(sc)
+        loc = qs.qs_schedule_choose_remap(sc, dtype)
+        assert all(loc[loc[q]] == q for q in range(n))
+        if np.array_equal(loc, np.arange(n)):     # nothing to gain: test a fixed exchange set
+            loc = np.arange(n)
+            loc[[0, 9, 1, 7]] = [9, 0, 7, 1]
+        qs.qs_schedule_remap(sc, loc)
+        after = _ops_as_oracle_ops(sc)
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_schedule_remap(sc, loc)
+        assert e.value.code == qs.QS_EINVAL
+    finally:
+        qs.qs_schedule_free(sc)
+    a = [q for q in range(n) if loc[q] > q]
+    b = [int(loc[q]) for q in a]
+    psi = random_state(n, 77)
+    ref = psi.copy()
+    _apply_ops(ref, before)
+    sim.apply_swap(ref, a, b)
+    got = psi.copy()
+    sim.apply_swap(got, a, b)
+    _apply_ops(got, after)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+
+
+def test_schedule_remap_rejects_bad_locations():
+    n, g = qs.qs_supremacy_circuit(3, 3, 5, 1)
+    sc = qs.qs_schedule_build(n, g)
+    try:
+        for loc in ([1, 2, 0, 3, 4, 5, 6, 7, 8], [0, 1, 2, 3, 4, 5, 6, 7, 9], [0, 0, 2, 3, 4, 5, 6, 7, 8]):
+            with pytest.raises(qs.QSError) as e:
+                qs.qs_schedule_remap(sc, loc)
+            assert e.value.code == qs.QS_EINVAL
+    finally:
+        qs.qs_schedule_free(sc)
