@@ -96,6 +96,21 @@ int qs_set_path(qs_state *s, int path);
  * state. */
 int qs_set_phase_fold(qs_state *s, int on);
 
+/* Pair sweeps in qs_run_circuit (on by default): for complex64 states of 12 or
+ * more qubits with every amplitude reachable, two consecutive dense ops that
+ * both run on the tensor cores and whose (padded) target qubits number at most
+ * 10 are applied in one sweep.  The GPU form of applying several gates while
+ * a chunk of the state sits in fast memory (Fig. 2 caption, Sec. 4): the
+ * 2^{|T1 u T2|} amplitudes that agree off both clusters' targets pass through
+ * shared memory between the two products, so the state is read and written
+ * once for both.  Results equal the two separate sweeps' bit for bit (the
+ * first cluster's outputs are rounded to float in between, as in HBM).  A
+ * phase op after the second cluster is folded into it as usual;
+ * qs_run_circuit_timed reports the pair's time on the first op and -1 on the
+ * ops that ran inside it.  on = 0 turns pairing off.  QS_EINVAL for a null
+ * state. */
+int qs_set_pair_sweeps(qs_state *s, int on);
+
 int qs_num_qubits(const qs_state *s);
 int qs_dtype(const qs_state *s);
 /* Device pointer to amplitude 0, holding the whole state: zeros the library
@@ -401,9 +416,11 @@ int qs_run_circuit(qs_state *s, const qs_schedule *sc);
 
 /* As qs_run_circuit, recording a CUDA event before and after every op on the
  * state's stream; waits for the stream and writes op i's device time in
- * milliseconds to op_ms[i] (host, qs_schedule_num_ops entries).  A phase op
- * folded into the sweep before it (qs_set_phase_fold) launches nothing and
- * gets op_ms[i] = -1; its time is part of the previous op's. */
+ * milliseconds to op_ms[i] (host, qs_schedule_num_ops entries).  An op that
+ * runs inside the sweep before it launches nothing and gets op_ms[i] = -1:
+ * a phase op folded into a tensor-core sweep (qs_set_phase_fold) or the
+ * second cluster of a pair sweep (qs_set_pair_sweeps); its time is part of
+ * the previous op's. */
 int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *op_ms);
 
 /* ------------------------------------------------------------------------

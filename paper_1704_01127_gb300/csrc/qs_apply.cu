@@ -502,13 +502,36 @@ int ensure_dev_schedule(qs_state *s, const qs_schedule *csc)
 // Kernel path of a dense op: the state's setting if not AUTO, else the op's
 // planned path if any, else the default policy.  *folded: the phase op after
 // it ran inside its tensor-core sweep.
+int path_of(const qs_state *s, const qs_op_host &op)
+{
+    return s->path != QS_PATH_AUTO ? s->path
+           : op.path != QS_PATH_AUTO ? op.path
+           : (tc_wanted(s->dtype, op.k, s->n) ? QS_PATH_TENSOR : QS_PATH_CUDA_CORES);
+}
+
+// Dense ops i and i + 1 as one sweep (qs_pair.cu) when both run on the tensor
+// cores and their target qubits fit one super-group; *skip = the ops after i
+// that ran inside it (the second cluster, and a phase op folded into it).
+bool try_pair(qs_state *s, const qs_schedule *sc, const qs_dev_sched &d, size_t i, int *rc, int *skip)
+{
+    if (!s->pair_sweeps || s->dtype != QS_C64 || i + 1 >= sc->ops.size()) return false;
+    const qs_op_host &a = sc->ops[i], &b = sc->ops[i + 1];
+    if (a.kind != QS_OP_DENSE || b.kind != QS_OP_DENSE || !d.tc_off[i] || !d.tc_off[i + 1]) return false;
+    if (path_of(s, a) != QS_PATH_TENSOR || path_of(s, b) != QS_PATH_TENSOR) return false;
+    if (!qs_pair_possible(s, d.tc_q[i].data(), d.tc_q[i + 1].data())) return false;
+    const uint8_t *da = (const uint8_t *)d.pool + d.offset[i], *db = (const uint8_t *)d.pool + d.offset[i + 1];
+    const bool fold = s->fold_phase && d.fold_off[i + 1];
+    *rc = qs_launch_pair5_tc(s, d.tc_q[i].data(), da + d.tc_off[i], d.tc_q[i + 1].data(),
+                             db + (fold ? d.fold_off[i + 1] : d.tc_off[i + 1]), fold ? db + d.post_off[i + 1] : nullptr);
+    *skip = fold ? 2 : 1;
+    return true;
+}
+
 int launch_op_dense(qs_state *s, const qs_dev_sched &d, size_t i, const qs_op_host &op, const uint8_t *data,
                     bool *folded)
 {
     *folded = false;
-    int path = s->path != QS_PATH_AUTO ? s->path
-               : op.path != QS_PATH_AUTO ? op.path
-               : (tc_wanted(s->dtype, op.k, s->n) ? QS_PATH_TENSOR : QS_PATH_CUDA_CORES);
+    int path = path_of(s, op);
     if (path == QS_PATH_TENSOR && d.tc_off[i]) {
         uint64_t grow = 0;
         for (int j = 0; j < op.k; j++) grow |= 1ULL << op.qubits[j];
@@ -618,7 +641,10 @@ extern "C" int qs_run_circuit(qs_state *s, const qs_schedule *sc)
         for (size_t i = 0; i < sc->ops.size(); i++) {
             const qs_op_host &op = sc->ops[i];
             const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
-            if (op.kind == QS_OP_DENSE) {
+            int skip = 0;
+            if (op.kind == QS_OP_DENSE && try_pair(s, sc, d, i, &rc, &skip)) {
+                i += skip;         // the ops after it that ran inside the pair's sweep
+            } else if (op.kind == QS_OP_DENSE) {
                 bool folded;
                 rc = launch_op_dense(s, d, i, op, data, &folded);
                 if (folded) i++;   // the phase op after it ran inside the sweep
@@ -655,11 +681,19 @@ extern "C" int qs_run_circuit_timed(qs_state *s, const qs_schedule *sc, float *o
             const qs_op_host &op = sc->ops[i];
             const uint8_t *data = (const uint8_t *)d.pool + d.offset[i];
             bool folded = false;
-            if (op.kind == QS_OP_DENSE) rc = launch_op_dense(s, d, i, op, data, &folded);
-            else if (op.kind == QS_OP_DIAG) rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
-            else rc = qs_launch_phase(s, data, d.n_act[i]);
+            int skip = 0;
+            if (op.kind == QS_OP_DENSE && try_pair(s, sc, d, i, &rc, &skip)) {
+                // the second cluster (and a phase op folded into it) ran inside the sweep
+            } else if (op.kind == QS_OP_DENSE) {
+                rc = launch_op_dense(s, d, i, op, data, &folded);
+                skip = folded ? 1 : 0;   // the phase op after it ran inside the sweep
+            } else if (op.kind == QS_OP_DIAG) {
+                rc = qs_launch_diag(s, (const int *)data, op.k, data + 64);
+            } else {
+                rc = qs_launch_phase(s, data, d.n_act[i]);
+            }
             cudaEventRecord(ev[i + 1], st);
-            if (folded) {   // the phase op after it ran inside the sweep
+            for (int j = 0; j < skip; j++) {
                 skipped[++i] = 1;
                 cudaEventRecord(ev[i + 1], st);
             }
@@ -687,6 +721,15 @@ extern "C" int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype)
         return QS_OK;
     });
     return rc == QS_OK ? bytes : rc;
+}
+
+extern "C" int qs_set_pair_sweeps(qs_state *s, int on)
+{
+    return qs_guard([&]() -> int {
+        if (!s) return qs_fail(QS_EINVAL, "qs_set_pair_sweeps: null state");
+        s->pair_sweeps = on != 0;
+        return QS_OK;
+    });
 }
 
 extern "C" int qs_schedule_remap(qs_schedule *sc, const int *loc)

@@ -46,6 +46,7 @@ struct qs_state {
     int *status = nullptr;        // device word set by kernels whose bounded waits ran out
     int path = 0;                 // QS_PATH_*
     bool fold_phase = true;       // qs_set_phase_fold
+    bool pair_sweeps = true;      // qs_set_pair_sweeps
     // Support: amplitudes may be nonzero only at indices i with
     // (i & ~sup_free) == sup_fix.  After qs_init_basis the support is one index
     // and memory outside the support is left unwritten; the tensor-core sweeps
@@ -204,5 +205,10 @@ size_t qs_tc_pack_bytes(int dtype);
 // dev_post: a folded phase op (qs_post_phase, device) or null.
 int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack, uint64_t grow,
                         const void *dev_post = nullptr);
+// Two consecutive 5-qubit clusters (sorted qubits q1, q2; complex64 tensor-core
+// packs) in one sweep: complex64, full support, n >= 12, |q1 u q2| <= 10.
+bool qs_pair_possible(const qs_state *s, const int *q1, const int *q2);
+int qs_launch_pair5_tc(qs_state *s, const int *q1, const void *pack1, const int *q2, const void *pack2,
+                       const void *dev_post = nullptr);
 // One bounded mbarrier wait that cannot complete (qs_selftest_timeout).
 int qs_launch_wait_selftest(qs_state *s, long polls);

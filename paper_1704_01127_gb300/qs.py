@@ -88,6 +88,7 @@ _SIGS = {
     "qs_set_device": ([ctypes.c_int], ctypes.c_int),
     "qs_set_path": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_schedule_upload": ([_VP, ctypes.c_int], ctypes.c_int),
+    "qs_set_pair_sweeps": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_schedule_remap": ([_VP, _IP], ctypes.c_int),
     "qs_schedule_choose_remap": ([_VP, ctypes.c_int, _IP], ctypes.c_int),
     "qs_set_host_threads": ([ctypes.c_int], ctypes.c_int),
@@ -482,6 +483,10 @@ def qs_stats_static(dev_ptr, n, dtype, stream=None):
 
 def qs_set_path(h, path):
     _check(lib().qs_set_path(h, int(path)))
+
+
+def qs_set_pair_sweeps(h, on):
+    _check(lib().qs_set_pair_sweeps(h, 1 if on else 0))
 
 
 def qs_set_phase_fold(h, on):

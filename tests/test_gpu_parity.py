@@ -761,3 +761,69 @@ def test_remapped_fullsize_against_oracle(dtype):
     finally:
         qs.qs_schedule_free(sc)
     assert np.max(np.abs(got - want)) <= TOL[dtype]
+
+
+PAIR_CASES = [
+    (12, [0, 1, 2, 3, 4], [5, 6, 7, 8, 9]), (12, [7, 8, 9, 10, 11], [7, 8, 9, 10, 11]),
+    (13, [0, 3, 6, 8, 9], [1, 2, 4, 5, 7]), (16, [2, 5, 9, 12, 13], [2, 5, 6, 7, 13]),
+    (16, [11, 12, 13, 14, 15], [0, 1, 2, 12, 15]), (20, [15, 16, 17, 18, 19], [10, 11, 12, 18, 19]),
+    (20, [0, 1, 2, 3, 19], [0, 4, 5, 6, 19]),
+]
+
+
+@pytest.mark.parametrize("n,q1,q2", PAIR_CASES)
+def test_pair_sweep_matches_separate_sweeps_and_oracle(n, q1, q2):
+    """Two consecutive 5-qubit complex64 clusters in one sweep (qs_pair.cu):
+    bit for bit the two separate tensor-core sweeps, and within a sweep's
+    rounding of the oracle; with a phase op after them folded into the pair."""
+    U1, U2 = random_unitary(5, 600 + n), random_unitary(5, 700 + n)
+    coeff, edges = random_phase_poly(n, 6, 800 + n)
+    coeff = 2 * (np.asarray(coeff) // 2)            # even coefficients: the phase op folds
+    psi = f32_round(random_state(n, 900 + n))
+    for with_phase in (False, True):
+        ops = [(qs.QS_OP_DENSE, q1, U1), (qs.QS_OP_DENSE, q2, U2)]
+        if with_phase:
+            ops.append((qs.QS_OP_PHASE, edges, coeff))
+        sc = qs.qs_schedule_from_ops(n, ops)
+        outs = []
+        try:
+            for pair in (True, False):
+                with State(n, qs.QS_C64) as s:
+                    qs.qs_set_pair_sweeps(s.h, pair)
+                    qs.qs_set_amplitudes(s.h, psi)
+                    ms = qs.qs_run_circuit_timed(s.h, sc)
+                    outs.append(qs.qs_get_amplitudes(s.h))
+                    if pair:
+                        assert ms[0] > 0 and ms[1] == -1
+        finally:
+            qs.qs_schedule_free(sc)
+        assert np.array_equal(outs[0], outs[1])
+        ref = psi.copy()
+        sim.apply_kq(ref, q1, U1)
+        sim.apply_kq(ref, q2, U2)
+        if with_phase:
+            sim.apply_phase(ref, coeff, edges)
+        assert np.max(np.abs(outs[0] - ref)) < 2 * SWEEP_TOL[qs.QS_C64]
+
+
+def test_pair_sweeps_in_a_circuit_bit_exact():
+    """A 24-qubit circuit (4x6 grid, 20 CZ cycles) with pair sweeps on and off: the same state bit for
+    bit, within 2e-6 of the oracle."""
+    n, g = qs.qs_supremacy_circuit(4, 6, 20, 5)
+    ref = sim.run_circuit(n, qs.gates_to_tuples(g))
+    sc = qs.qs_schedule_build(n, g, k_max=5)
+    outs, paired = [], 0
+    try:
+        for pair in (True, False):
+            with State(n, qs.QS_C64) as s:
+                qs.qs_set_pair_sweeps(s.h, pair)
+                qs.qs_init_basis(s.h, 0)
+                ms = qs.qs_run_circuit_timed(s.h, sc)
+                if pair:
+                    paired = sum(1 for i in range(len(ms)) if ms[i] < 0 and qs.qs_schedule_op(sc, i)["kind"] == "dense")
+                outs.append(qs.qs_get_amplitudes(s.h))
+    finally:
+        qs.qs_schedule_free(sc)
+    assert paired >= 1
+    assert np.array_equal(outs[0], outs[1])
+    assert np.max(np.abs(outs[0] - ref)) <= 2e-6
