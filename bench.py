@@ -774,7 +774,19 @@ def run_kernel(args):
     qs.qs_set_path(h, path)
     qs.qs_init_uniform(h)
     full = amp << n
-    if args.kernel == "dense":
+    if args.kernel == "pair":
+        # two 5-qubit clusters in a row, as one pair sweep (qs_set_pair_sweeps) or two
+        t2 = [int(x) for x in args.targets2.split(",")] if args.targets2 else list(range(n - 10, n - 5))
+        ops = []
+        for tg in (targets, t2):
+            z = g.standard_normal((32, 32)) + 1j * g.standard_normal((32, 32))
+            ops.append((qs.QS_OP_DENSE, tg, np.linalg.qr(z)[0]))
+        sc = qs.qs_schedule_from_ops(n, ops)
+        qs.qs_set_pair_sweeps(h, not args.no_pair)
+        fn = lambda: qs.qs_run_circuit(h, sc)
+        what, bytes_ = ("two clusters on %s then %s, %s" % (targets, t2, "separate sweeps" if args.no_pair
+                                                             else "one pair sweep")), 2 * full
+    elif args.kernel == "dense":
         z = g.standard_normal((1 << k, 1 << k)) + 1j * g.standard_normal((1 << k, 1 << k))
         U, _ = np.linalg.qr(z)
         fn, what, bytes_ = (lambda: qs.qs_apply_cluster(h, targets, U)), "dense k=%d on %s" % (k, targets), 2 * full
@@ -951,12 +963,14 @@ def main():
                     help="host threads of the clustering search (the launching thread keeps the rest)")
     ap.add_argument("--remap", action="store_true",
                     help="move each schedule's qubits to the index bits the library picks (Sec. 3.6)")
-    ap.add_argument("--kernel", choices=["dense", "diag", "phase", "stats", "sample", "fill", "mlp"],
+    ap.add_argument("--kernel", choices=["dense", "pair", "diag", "phase", "stats", "sample", "fill", "mlp"],
                     help="time one kernel on a full synthetic state instead of circuits")
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--k", type=int, default=5)
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c128")
     ap.add_argument("--targets", default="")
+    ap.add_argument("--targets2", default="", help="--kernel pair: the second cluster's targets")
+    ap.add_argument("--no-pair", action="store_true", help="--kernel pair: two separate sweeps")
     ap.add_argument("--path", choices=["auto", "cuda", "tensor"], default="auto")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--m", type=int, default=1 << 20)

@@ -378,6 +378,26 @@ int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype);
 int qs_schedule_remap(qs_schedule *sc, const int *loc);
 int qs_schedule_choose_remap(const qs_schedule *sc, int dtype, int *loc);
 
+/* Stages for a state held as 2^n_global parts (Sec. 3.4, Sec. 3.6 steps 1 and
+ * 3): the top n_global index bits of a stage hold its global qubits, on which
+ * the stage applies no gate except diagonal ones (CZ, T; Sec. 3.5 applies
+ * those as conditional phases of a part).  The gate list is split greedily in
+ * its order: a gate joins the present stage unless it is a non-diagonal gate
+ * on a global qubit or shares a qubit with a gate left for later; the next
+ * stage's global qubits are the n_global whose next non-diagonal gate comes
+ * last.  Each stage is clustered with opts (qs_schedule_build) and remapped
+ * (qs_schedule_remap) so that its global qubits sit at the top bits; running
+ * the stages in order with qs_run_circuit moves the qubits between stages,
+ * the global-to-local swap: on one GPU one or two exchange sweeps
+ * (qs_swap_qubits), where a multi-GPU form would exchange the parts' data
+ * (Sec. 3.4 all-to-all).  stages: room for max_stages schedules, each freed
+ * with qs_schedule_free; *n_stages stages made; stage_of_gate (nullable):
+ * n_gates entries, the stage of every gate.  Errors: QS_EINVAL (bad arguments,
+ * more than max_stages stages, no gate runnable with n_global global
+ * qubits). */
+int qs_plan_stages(int n, const qs_gate *gates, int n_gates, int n_global, const qs_sched_opts *opts,
+                   qs_schedule **stages, int max_stages, int *n_stages, int *stage_of_gate);
+
 /* Build the schedule's device image for `dtype` (every op's matrix in the
  * dtype, tensor-core operand planes, folded phase descriptors) and copy it to
  * the calling thread's current device now, instead of at the first

@@ -730,6 +730,7 @@ extern "C" int qs_init_basis(qs_state *s, uint64_t x)
         if (!s || !s->amp) return qs_fail(QS_EINVAL, "qs_init_basis: null state");
         if (x >> s->n) return qs_fail(QS_EINVAL, "qs_init_basis: index out of range");
         qs_loc_reset(s);   // fresh contents: every qubit at its own bit
+        s->perm_invariant = false;
         cudaStream_t st = (cudaStream_t)s->stream;
         if (s->dtype == QS_C128)
             k_set_one<double2><<<1, 1, 0, st>>>((double2 *)s->amp, x);
@@ -746,6 +747,7 @@ extern "C" int qs_init_basis(qs_state *s, uint64_t x)
 
 int qs_basis_move(qs_state *s, uint64_t x)
 {
+    s->perm_invariant = false;
     cudaStream_t st = (cudaStream_t)s->stream;
     if (s->dtype == QS_C128)
         k_set_one<double2><<<1, 1, 0, st>>>((double2 *)s->amp, x);
@@ -791,6 +793,7 @@ extern "C" int qs_init_uniform(qs_state *s)
         QS_CUDA(cudaGetLastError(), "qs_init_uniform");
         s->sup_free = ~0ULL;
         s->sup_fix = 0;
+        s->perm_invariant = true;   // every amplitude equal
         return QS_OK;
     });
 }
@@ -800,6 +803,7 @@ extern "C" int qs_set_amplitudes(qs_state *s, const double *host)
     return qs_guard([&]() -> int {
         if (!s || !s->amp || !host) return qs_fail(QS_EINVAL, "qs_set_amplitudes: null argument");
         qs_loc_reset(s);   // fresh contents: every qubit at its own bit
+        s->perm_invariant = false;
         uint64_t N = 1ULL << s->n;
         cudaStream_t st = (cudaStream_t)s->stream;
         if (s->dtype == QS_C128) {

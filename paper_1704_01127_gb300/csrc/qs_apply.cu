@@ -169,6 +169,7 @@ bool qs_tc_wanted(int dtype, int k, int n)
 int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *dev_matrix,
                     const void *dev_tc)
 {
+    s->perm_invariant = false;
     if (k == 5 && dev_tc) return qs_launch_dense5_tc(s, sorted_qubits, dev_tc, ~0ULL);
     int rc = qs_materialize(s);   // the CUDA-core sweeps read every amplitude
     if (rc) return rc;
@@ -178,6 +179,7 @@ int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *de
 
 int qs_launch_diag(qs_state *s, const int *dev_qubits, int k, const void *dev_table)
 {
+    s->perm_invariant = false;
     int rc = qs_materialize(s);
     if (rc) return rc;
     uint64_t N = 1ULL << s->n;
@@ -194,6 +196,7 @@ int qs_launch_diag(qs_state *s, const int *dev_qubits, int k, const void *dev_ta
 
 int qs_launch_phase(qs_state *s, const void *dev_phase, int n_act)
 {
+    s->perm_invariant = false;
     int rc = qs_materialize(s);
     if (rc) return rc;
     const int L = s->n < kPhaseLowBits ? s->n : kPhaseLowBits;

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <limits>
 #include <memory>
 #include <new>
 #include <set>
@@ -943,6 +944,113 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
     return qs_guard([&]() -> int {
         return guarded("qs_schedule_from_ops", [&] {
             return schedule_from_ops_impl(n, n_ops, kinds, ks, qubits, offsets, pool, pool_len, out);
+        });
+    });
+}
+
+// Stages for a state spread over 2^g parts (Sec. 3.4, Sec. 3.6 steps 1 and 3).
+// The top g index bits of a stage hold its global qubits, on which no gate of
+// the stage may act except diagonal ones (CZ, T: Sec. 3.5 applies them as
+// conditional phases).  Greedy, in the gate list's order: a gate joins the
+// present stage unless it is a non-diagonal gate on a global qubit or shares a
+// qubit with a gate already left for later (so every qubit keeps its gate
+// order).  The next stage's global qubits are the g whose next non-diagonal
+// gate comes last (ties: the present global qubits, then the higher qubit),
+// which keeps the number of global-to-local swaps small.
+static int plan_stages_impl(int n, const qs_gate *gates, int n_gates, int g, const qs_sched_opts *opts,
+                            qs_schedule **stages, int max_stages, int *n_stages, int *stage_of_gate)
+{
+    if (n < 2 || n > QS_MAX_QUBITS || g < 0 || g >= n || n_gates < 0 || (n_gates > 0 && !gates) || !opts ||
+        !stages || max_stages < 1 || !n_stages)
+        return qs_fail(QS_EINVAL, "qs_plan_stages: bad arguments");
+    for (int i = 0; i < n_gates; i++)
+        if (!check_gate(n, gates[i])) return qs_fail(QS_EINVAL, "qs_plan_stages: bad gate %d", i);
+    std::vector<int> remaining(n_gates);
+    for (int i = 0; i < n_gates; i++) remaining[i] = i;
+    auto choose_global = [&](const std::vector<int> &rem, uint64_t current) {
+        std::vector<long> next(n, std::numeric_limits<long>::max());
+        for (size_t p = 0; p < rem.size(); p++) {
+            const qs_gate &x = gates[rem[p]];
+            if (is_diagonal(x.kind)) continue;
+            if (next[x.q0] == std::numeric_limits<long>::max()) next[x.q0] = (long)p;
+        }
+        std::vector<int> order(n);
+        for (int q = 0; q < n; q++) order[q] = q;
+        std::sort(order.begin(), order.end(), [&](int a, int b) {
+            if (next[a] != next[b]) return next[a] > next[b];
+            const bool ca = (current >> a) & 1, cb = (current >> b) & 1;
+            if (ca != cb) return ca;
+            return a > b;
+        });
+        uint64_t G = 0;
+        for (int i = 0; i < g; i++) G |= 1ULL << order[i];
+        return G;
+    };
+    int count = 0;
+    uint64_t G = choose_global(remaining, 0);
+    while (!remaining.empty()) {
+        std::vector<int> take, rest;
+        uint64_t blocked = 0;
+        for (int gi : remaining) {
+            const qs_gate &x = gates[gi];
+            const uint64_t qm = gmask_of(x);
+            if ((qm & blocked) || (!is_diagonal(x.kind) && (qm & G))) {
+                rest.push_back(gi);
+                blocked |= qm;
+            } else {
+                take.push_back(gi);
+            }
+        }
+        if (take.empty()) {
+            for (int i = 0; i < count; i++) qs_schedule_free(stages[i]);
+            return qs_fail(QS_EINVAL, "qs_plan_stages: no gate can run with %d global qubits", g);
+        }
+        if (count >= max_stages) {
+            for (int i = 0; i < count; i++) qs_schedule_free(stages[i]);
+            return qs_fail(QS_EINVAL, "qs_plan_stages: more than %d stages", max_stages);
+        }
+        std::vector<qs_gate> sub(take.size());
+        for (size_t i = 0; i < take.size(); i++) {
+            sub[i] = gates[take[i]];
+            if (stage_of_gate) stage_of_gate[take[i]] = count;
+        }
+        qs_schedule *sc = nullptr;
+        int rc = schedule_build_impl(n, sub.data(), (int)sub.size(), opts, &sc);
+        if (rc) {
+            for (int i = 0; i < count; i++) qs_schedule_free(stages[i]);
+            return rc;
+        }
+        // the stage's global qubits at the top g index bits: each one below
+        // exchanged with a top bit whose own qubit is local
+        int loc[64];
+        for (int q = 0; q < n; q++) loc[q] = q;
+        int t = n - 1;
+        for (int q = 0; q < n - g; q++) {
+            if (!((G >> q) & 1)) continue;
+            while ((G >> t) & 1) t--;
+            loc[q] = t;
+            loc[t] = q;
+            t--;
+        }
+        if ((rc = qs_schedule_remap(sc, loc))) {
+            qs_schedule_free(sc);
+            for (int i = 0; i < count; i++) qs_schedule_free(stages[i]);
+            return rc;
+        }
+        stages[count++] = sc;
+        remaining = std::move(rest);
+        if (!remaining.empty()) G = choose_global(remaining, G);
+    }
+    *n_stages = count;
+    return QS_OK;
+}
+
+extern "C" int qs_plan_stages(int n, const qs_gate *gates, int n_gates, int n_global, const qs_sched_opts *opts,
+                              qs_schedule **stages, int max_stages, int *n_stages, int *stage_of_gate)
+{
+    return qs_guard([&]() -> int {
+        return guarded("qs_plan_stages", [&] {
+            return plan_stages_impl(n, gates, n_gates, n_global, opts, stages, max_stages, n_stages, stage_of_gate);
         });
     });
 }

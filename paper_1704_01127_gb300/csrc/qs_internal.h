@@ -47,6 +47,9 @@ struct qs_state {
     int path = 0;                 // QS_PATH_*
     bool fold_phase = true;       // qs_set_phase_fold
     bool pair_sweeps = true;      // qs_set_pair_sweeps
+    // every amplitude equal (qs_init_uniform, nothing applied since): any
+    // exchange of qubits leaves the state as it is
+    bool perm_invariant = false;
     // Support: amplitudes may be nonzero only at indices i with
     // (i & ~sup_free) == sup_fix.  After qs_init_basis the support is one index
     // and memory outside the support is left unwritten; the tensor-core sweeps

@@ -63,6 +63,15 @@ __device__ __forceinline__ uint64_t sg_base(uint64_t g, uint64_t zmask)
     return g;
 }
 
+// Slot of tile element i in X: the low four bits are mixed with a hash of the
+// others (a bijection on 12-bit indices), so that the lanes of a warp, whose
+// indices differ in the clusters' non-target bits, spread over the shared
+// memory banks instead of landing on one.
+__device__ __forceinline__ uint32_t xslot(uint32_t i)
+{
+    return i ^ (((i >> 4) * 0x9E3779B1u) >> 28);
+}
+
 __device__ __forceinline__ void bar_sub(int sub)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "r"(kRows) : "memory");
@@ -234,11 +243,11 @@ k_pair5_tc_c64(float2 *__restrict__ psi, uint64_t n_tiles, PairLayout lay, const
         tc_fence_before();
         bar_sub(sub);   // every thread has read A's products out of TMEM; the MMAs are done with A
 #pragma unroll
-        for (int m = 0; m < 32; m++) X[xrow | g1 | ts.mem[0][m]] = v[m];
+        for (int m = 0; m < 32; m++) X[xslot(xrow | g1 | ts.mem[0][m])] = v[m];
         bar_sub(sub);
         // ---- phase 2: cluster 2 from the shared-memory tile
 #pragma unroll
-        for (int m = 0; m < 32; m++) v[m] = X[xrow | g2 | ts.mem[1][m]];
+        for (int m = 0; m < 32; m++) v[m] = X[xslot(xrow | g2 | ts.mem[1][m])];
         bar_sub(sub);   // X read before the planes overwrite it
         split_row(v, A_h, A_t, row);
         fence_proxy_async();
@@ -288,6 +297,7 @@ bool qs_pair_possible(const qs_state *s, const int *q1, const int *q2)
 int qs_launch_pair5_tc(qs_state *s, const int *q1, const void *pack1, const int *q2, const void *pack2,
                        const void *dev_post)
 {
+    s->perm_invariant = false;
     if (!qs_pair_possible(s, q1, q2)) return qs_fail(QS_EINVAL, "pair sweep: not applicable");
     PairLayout lay;
     std::memset(&lay, 0, sizeof(lay));

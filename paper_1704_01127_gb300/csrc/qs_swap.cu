@@ -122,6 +122,7 @@ int sm_count()
 
 int qs_launch_swap(qs_state *s, const int *a, const int *b, int m)
 {
+    s->perm_invariant = false;
     if (m == 0) return QS_OK;
     if (m > kMaxPairs) return qs_fail(QS_EINVAL, "swap: %d pairs", m);
     int rc = qs_materialize(s);
@@ -208,6 +209,11 @@ int qs_order_set(qs_state *s, const int *want)
         same = same && target[q] == s->loc[q];
     }
     if (same) return QS_OK;
+    if (s->perm_invariant) {
+        // every amplitude equal: the qubits change places without moving data
+        for (int q = 0; q < s->n; q++) s->loc[q] = target[q];
+        return QS_OK;
+    }
     if (s->sup_free == 0) {
         // the lazily written basis state: its one amplitude moves, nothing else
         const uint64_t x = qs_loc_index(s, s->sup_fix);      // index in qubit order

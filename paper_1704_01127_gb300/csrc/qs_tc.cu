@@ -676,6 +676,7 @@ size_t qs_tc_pack_bytes(int dtype) { return dtype == QS_C64 ? 2 * kBBytesF32 : k
 int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_pack, uint64_t grow,
                         const void *dev_post)
 {
+    s->perm_invariant = false;
     const bool c64 = s->dtype == QS_C64, fold = dev_post != nullptr;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

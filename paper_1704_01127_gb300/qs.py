@@ -90,6 +90,8 @@ _SIGS = {
     "qs_schedule_upload": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_set_pair_sweeps": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_schedule_remap": ([_VP, _IP], ctypes.c_int),
+    "qs_plan_stages": ([ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_VP), ctypes.c_int, _IP,
+                        _IP], ctypes.c_int),
     "qs_schedule_choose_remap": ([_VP, ctypes.c_int, _IP], ctypes.c_int),
     "qs_set_host_threads": ([ctypes.c_int], ctypes.c_int),
     "qs_swap_qubits": ([_VP, _IP, _IP, ctypes.c_int], ctypes.c_int),
@@ -357,6 +359,24 @@ def qs_schedule_build(n, gates, k_max=5, fuse=True, merge_phase=True, drop_final
     _check(lib().qs_schedule_build(int(n), g.ctypes.data_as(_VP), int(g.size), ctypes.byref(opts),
                                    ctypes.byref(h)))
     return h
+
+
+def qs_plan_stages(n, gates, n_global, k_max=5, max_stages=64, **kw):
+    """(list of stage schedules, stage of every gate); see qs_schedule_build
+    for the clustering options."""
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    d = dict(fuse=True, merge_phase=True, drop_final_diagonal=False, commute_diagonal=True, search_runs=13,
+             search_from_basis=True, search_first=16, search_slack0=5)
+    d.update(kw)
+    opts = _SchedOpts(int(k_max), int(d["fuse"]), int(d["merge_phase"]), int(d["drop_final_diagonal"]),
+                      int(d["commute_diagonal"]), int(d["search_runs"]), int(d["search_from_basis"]),
+                      int(d["search_first"]), int(d["search_slack0"]))
+    arr = (_VP * max_stages)()
+    cnt = ctypes.c_int()
+    of = np.zeros(max(g.size, 1), dtype=np.int32)
+    _check(lib().qs_plan_stages(int(n), g.ctypes.data_as(_VP), int(g.size), int(n_global), ctypes.byref(opts), arr,
+                                int(max_stages), ctypes.byref(cnt), _ip(of)))
+    return [arr[i] for i in range(cnt.value)], of[:g.size]
 
 
 def qs_schedule_from_ops(n, ops):
