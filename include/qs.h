@@ -377,6 +377,9 @@ int64_t qs_schedule_upload_bytes(const qs_schedule *sc, int dtype);
  * sweeps with targets among those bits take 25-30% longer. */
 int qs_schedule_remap(qs_schedule *sc, const int *loc);
 int qs_schedule_choose_remap(const qs_schedule *sc, int dtype, int *loc);
+/* The schedule's qubit-to-bit map: n entries, the identity for a schedule
+ * never remapped.  QS_EINVAL for null arguments. */
+int qs_schedule_get_remap(const qs_schedule *sc, int *loc);
 
 /* Stages for a state held as 2^n_global parts (Sec. 3.4, Sec. 3.6 steps 1 and
  * 3): the top n_global index bits of a stage hold its global qubits, on which

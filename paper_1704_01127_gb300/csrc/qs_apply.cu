@@ -768,6 +768,15 @@ extern "C" int qs_schedule_remap(qs_schedule *sc, const int *loc)
     });
 }
 
+extern "C" int qs_schedule_get_remap(const qs_schedule *sc, int *loc)
+{
+    return qs_guard([&]() -> int {
+        if (!sc || !loc) return qs_fail(QS_EINVAL, "qs_schedule_get_remap: null argument");
+        for (int q = 0; q < sc->n; q++) loc[q] = sc->remap.empty() ? q : sc->remap[q];
+        return QS_OK;
+    });
+}
+
 extern "C" int qs_schedule_choose_remap(const qs_schedule *sc, int dtype, int *loc)
 {
     return qs_guard([&]() -> int {

@@ -170,7 +170,9 @@ k_pair5_tc_c64(float2 *__restrict__ psi, uint64_t n_tiles, PairLayout lay, const
     const uint32_t b2h = smem_u32(B2), b2t = b2h + (uint32_t)(kBPack / 2);
     const uint32_t mb = smem_u32(&mbar[sub]);
     const int gbits = lay.u - 5;
-    const int sgl = row >> gbits, grow = row & ((1 << gbits) - 1);
+    // neighbouring rows take neighbouring super-groups (the lowest bits off
+    // U), then the groups inside one
+    const int sgl = row & ((1 << (7 - gbits)) - 1), grow = row >> (7 - gbits);
     const uint64_t per_tile = 1ULL << (12 - lay.u);
     const uint32_t xrow = (uint32_t)sgl << lay.u;
     const uint32_t g1 = ts.grp[0][grow], g2 = ts.grp[1][grow];

@@ -90,6 +90,7 @@ _SIGS = {
     "qs_schedule_upload": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_set_pair_sweeps": ([_VP, ctypes.c_int], ctypes.c_int),
     "qs_schedule_remap": ([_VP, _IP], ctypes.c_int),
+    "qs_schedule_get_remap": ([_VP, _IP], ctypes.c_int),
     "qs_plan_stages": ([ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_VP), ctypes.c_int, _IP,
                         _IP], ctypes.c_int),
     "qs_schedule_choose_remap": ([_VP, ctypes.c_int, _IP], ctypes.c_int),
@@ -477,6 +478,13 @@ def qs_schedule_remap(sched, loc):
     """Relabel the schedule's ops: qubit q to index bit loc[q] (exchanges)."""
     l = np.ascontiguousarray(loc, dtype=np.int32)
     _check(lib().qs_schedule_remap(sched, _ip(l)))
+
+
+def qs_schedule_get_remap(sched):
+    n = lib().qs_schedule_num_qubits(sched)
+    l = np.zeros(n, dtype=np.int32)
+    _check(lib().qs_schedule_get_remap(sched, _ip(l)))
+    return l
 
 
 def qs_schedule_choose_remap(sched, dtype):

@@ -827,3 +827,55 @@ def test_pair_sweeps_in_a_circuit_bit_exact():
     assert paired >= 1
     assert np.array_equal(outs[0], outs[1])
     assert np.max(np.abs(outs[0] - ref)) <= 2e-6
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+@pytest.mark.parametrize("g,uniform", [(3, False), (4, True)])
+def test_staged_run_against_oracle(dtype, g, uniform):
+    """Stages for a state held as 2^g parts (qs_plan_stages, Sec. 3.4/3.6) run
+    in turn on one GPU: between stages the global and local qubits change
+    places by exchange sweeps.  From |0...0> (the whole circuit) or from the
+    uniform state (the circuit without its H layer, Sec. 3.6)."""
+    n, gates = qs.qs_supremacy_circuit(4, 5, 20, 13)
+    ref = sim.run_circuit(n, qs.gates_to_tuples(gates))
+    body = gates[gates["cycle"] > 0] if uniform else gates
+    stages, _ = qs.qs_plan_stages(n, body, g)
+    try:
+        assert len(stages) >= 2
+        with State(n, dtype) as s:
+            if uniform:
+                qs.qs_init_uniform(s.h)
+            else:
+                qs.qs_init_basis(s.h, 0)
+            for sc in stages:
+                qs.qs_run_circuit(s.h, sc)
+            out = qs.qs_get_amplitudes(s.h)
+    finally:
+        for sc in stages:
+            qs.qs_schedule_free(sc)
+    assert np.max(np.abs(out - ref)) <= TOL[dtype]
+
+
+def test_staged_30_qubits_against_oracle():
+    """30 qubits as 8 parts (3 global qubits), from the uniform state: the
+    stored oracle amplitudes within 1e-12."""
+    import os
+    from conftest import GOLDEN, read_golden
+    name = "fullsize_5x6_d25_s0.txt"
+    if not os.path.exists(os.path.join(GOLDEN, name)):
+        pytest.skip("golden file missing")
+    rows = read_golden(name)
+    idx = np.array([int(r[0]) for r in rows[2:]], dtype=np.uint64)
+    want = np.array([complex(float(r[1]), float(r[2])) for r in rows[2:]])
+    n, gates = qs.qs_supremacy_circuit(5, 6, 25, 0)
+    stages, _ = qs.qs_plan_stages(n, gates[gates["cycle"] > 0], 3)
+    try:
+        with State(n, qs.QS_C128) as s:
+            qs.qs_init_uniform(s.h)
+            for sc in stages:
+                qs.qs_run_circuit(s.h, sc)
+            got = qs.qs_get_amplitudes_at(s.h, idx)
+    finally:
+        for sc in stages:
+            qs.qs_schedule_free(sc)
+    assert np.max(np.abs(got - want)) <= 1e-12

@@ -308,3 +308,66 @@ def test_schedule_remap_rejects_bad_locations():
             assert e.value.code == qs.QS_EINVAL
     finally:
         qs.qs_schedule_free(sc)
+
+
+def _loc_pairs(loc):
+    return [q for q in range(len(loc)) if loc[q] > q], [int(loc[q]) for q in range(len(loc)) if loc[q] > q]
+
+
+@pytest.mark.parametrize("grid,depth,g", [((3, 4), 10, 2), ((4, 4), 12, 3), ((3, 5), 14, 4)])
+def test_stage_plan_is_valid_and_reproduces_the_circuit(grid, depth, g):
+    """qs_plan_stages (Sec. 3.6 steps 1 and 3): every gate in one stage; no
+    non-diagonal gate on a stage's global qubits (those at its top g bits);
+    each qubit's gates in non-decreasing stage order; and the stages' ops,
+    applied by the oracle with the qubit exchanges between stages (the
+    global-to-local swaps), give the oracle's state."""
+    from inputs import random_state
+    n, gates = qs.qs_supremacy_circuit(grid[0], grid[1], depth, 7)
+    tuples = qs.gates_to_tuples(gates)
+    stages, of = qs.qs_plan_stages(n, gates, g, k_max=4, search_runs=1, search_first=1)
+    try:
+        assert of.min() >= 0 and of.max() == len(stages) - 1
+        locs = [qs.qs_schedule_get_remap(sc) for sc in stages]
+        for k, loc in enumerate(locs):
+            assert all(loc[loc[q]] == q for q in range(n))
+            glob = {q for q in range(n) if loc[q] >= n - g}
+            assert len(glob) == g
+            for i in range(len(tuples)):
+                if of[i] == k and tuples[i][1] not in ("cz", "t", "tdg"):
+                    assert not (set(tuples[i][2]) & glob), (k, tuples[i])
+        last = {}
+        for i, (_, name, qq) in enumerate(tuples):
+            for q in qq:
+                assert of[i] >= last.get(q, 0)
+                last[q] = of[i]
+        psi = random_state(n, 3)
+        ref = psi.copy()
+        for (_, name, qq) in tuples:
+            sim.apply_gate(ref, name, qq)
+        cur = np.arange(n)
+        for sc, loc in zip(stages, locs):
+            sim.apply_swap(psi, *_loc_pairs(cur))       # back to every qubit at its own bit
+            sim.apply_swap(psi, *_loc_pairs(loc))       # this stage's places
+            cur = loc
+            _apply_ops(psi, _ops_as_oracle_ops(sc))
+        sim.apply_swap(psi, *_loc_pairs(cur))
+        np.testing.assert_allclose(psi, ref, rtol=0, atol=1e-13)
+    finally:
+        for sc in stages:
+            qs.qs_schedule_free(sc)
+
+
+def test_stage_plan_36_qubits_one_swap_from_the_uniform_state():
+    """Sec. 3.5: with diagonal gates applied on global qubits, the 36-qubit
+    circuit on 64 parts needs one global-to-local swap (the H layer replaced by
+    the uniform start state, Sec. 3.6).  This project's circuits follow its own
+    reading of the CZ layouts, so the count is a check against the paper's,
+    not its instances."""
+    n, gates = qs.qs_supremacy_circuit(6, 6, 24, 0)
+    body = gates[gates["cycle"] > 0]
+    stages, _ = qs.qs_plan_stages(n, body, 6, search_runs=1, search_first=1)
+    try:
+        assert len(stages) - 1 == 1
+    finally:
+        for sc in stages:
+            qs.qs_schedule_free(sc)
