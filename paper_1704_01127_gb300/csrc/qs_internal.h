@@ -46,7 +46,7 @@ struct qs_state {
     int *status = nullptr;        // device word set by kernels whose bounded waits ran out
     int path = 0;                 // QS_PATH_*
     bool fold_phase = true;       // qs_set_phase_fold
-    bool pair_sweeps = true;      // qs_set_pair_sweeps
+    bool pair_sweeps = false;     // qs_set_pair_sweeps
     // every amplitude equal (qs_init_uniform, nothing applied since): any
     // exchange of qubits leaves the state as it is
     bool perm_invariant = false;
