@@ -465,6 +465,95 @@ __global__ void k_draw(const C *__restrict__ psi, const double *__restrict__ Q, 
     }
 }
 
+// ---- draws by binary search over stored running sums (blocks of 1024)
+//
+// The per-draw scan above adds the probabilities of one block to R_b one
+// after another until the sum passes u.  The same sums, in the same order,
+// can be formed once for every block: c_{b,x} = R_b + p_{bB} + ... + p_{bB+x}
+// (sequential FP64 additions).  They do not decrease (p >= 0 and rounding is
+// monotone), so the scan's answer, the first x with c_{b,x} > u (B - 1 when
+// there is none), is found by binary search: bit for bit the same outcome.
+
+// Block sums of 1024 probabilities as k_segment_sums<C, 32> forms them, and the
+// probabilities themselves stored (p[i] = prob(psi[i])).
+template <typename C>
+__global__ void k_block_sums_store(const C *__restrict__ psi, uint64_t nseg, double *__restrict__ out,
+                                   double *__restrict__ p)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t seg = warp; seg < nseg; seg += nwarps) {
+        const uint64_t start = seg * 1024 + (uint64_t)lane * 32;
+        double buf[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) buf[i] = prob(psi[start + i]);
+#pragma unroll
+        for (int i = 0; i < 32; i += 2)
+            *reinterpret_cast<double2 *>(p + start + i) = make_double2(buf[i], buf[i + 1]);
+#pragma unroll
+        for (int w = 32; w > 1; w >>= 1) {
+#pragma unroll
+            for (int i = 0; i < w / 2; i++) buf[i] = buf[2 * i] + buf[2 * i + 1];
+        }
+        double v = buf[0];
+        for (int o = 1; o < 32; o <<= 1) {
+            double w = __shfl_down_sync(0xffffffffu, v, o);
+            if ((lane & (2 * o - 1)) == 0) v = v + w;
+        }
+        if (lane == 0) out[seg] = v;
+    }
+}
+
+// In place: p[bB + x] <- c_{b,x} = R_b + p_{bB} + ... + p_{bB+x}.  Lane l of a
+// warp owns block 32 w + l; the warp moves its 32 blocks through shared memory
+// 32 values at a time, so every global access is a 256-byte run.
+constexpr int kRunThreads = 128;
+
+__global__ void __launch_bounds__(kRunThreads) k_running_sums(double *__restrict__ p, const double *__restrict__ R,
+                                                              uint64_t nb)
+{
+    __shared__ double tile[kRunThreads / 32][32][33];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < nb; g += nwarps) {
+        const uint64_t b0 = g * 32;
+        const int nblk = nb - b0 < 32 ? (int)(nb - b0) : 32;
+        double c = lane < nblk ? R[b0 + lane] : 0.0;
+        for (int x0 = 0; x0 < 1024; x0 += 32) {
+            for (int r = 0; r < nblk; r++) tile[wl][r][lane] = p[(b0 + r) * 1024 + x0 + lane];
+            __syncwarp();
+            if (lane < nblk)
+                for (int x = 0; x < 32; x++) {
+                    c = c + tile[wl][lane][x];
+                    tile[wl][lane][x] = c;
+                }
+            __syncwarp();
+            for (int r = 0; r < nblk; r++) p[(b0 + r) * 1024 + x0 + lane] = tile[wl][r][lane];
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void k_draw_search(const double *__restrict__ c, const double *__restrict__ Q,
+                              const double *__restrict__ R, uint64_t ns, uint64_t G, uint64_t seed, int64_t m,
+                              uint64_t *__restrict__ out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const double u = (double)(splitmix64(seed, (uint64_t)j) >> 11) * 0x1.0p-53;
+        const uint64_t s = last_le(Q, ns, u);
+        const uint64_t b = s * G + last_le(R + s * G, G, u);
+        const double *cb = c + b * 1024;
+        uint64_t lo = 0, hi = 1024;          // first x with cb[x] > u, 1023 when none
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) / 2;
+            if (cb[mid] > u) hi = mid; else lo = mid + 1;
+        }
+        out[j] = b * 1024 + (lo < 1024 ? lo : 1023);
+    }
+}
+
 template <typename C>
 int stats_impl(qs_state *s, double *out, int nstat)
 {
@@ -514,9 +603,20 @@ int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double *st
     const size_t m_slots = (size_t)std::max<int64_t>(m, 1);
     size_t bytes = sizeof(double) * (2 * nb + 2 * ns) + sizeof(uint64_t) * m_slots;
     if (fused) bytes += sizeof(double) * ((size_t)gb * 4 + 4);
+    // complex128 with blocks of 1024: the running sums of every block are
+    // stored (N doubles of scratch) and the draws search them; without room
+    // for them, the draws scan the block as before (the same outcomes)
+    bool search = !c64 && B == 1024 && m > 0;
     void *scr = nullptr;
-    int rc = qs_state_scratch(s, bytes, &scr);
+    int rc = qs_state_scratch(s, bytes + (search ? sizeof(double) * N : 0), &scr);
+    if (rc && search) {
+        cudaGetLastError();   // the failed allocation is not an error of the later launches
+        search = false;
+        rc = qs_state_scratch(s, bytes, &scr);
+    }
     if (rc) return rc;
+    double *P = (double *)scr;                       // probabilities, then running sums
+    if (search) scr = (void *)(P + N);
     double *S = (double *)scr, *R = S + nb, *T = R + nb, *Q = T + ns;
     uint64_t *dout = (uint64_t *)(Q + ns);
     double *part = (double *)(dout + m_slots), *res = part + (size_t)gb * 4;
@@ -524,7 +624,9 @@ int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double *st
     if (fused) {
         if constexpr (c64) k_segment_sums_stats<C><<<gb, 256, 0, st>>>(psi, nb, S, part);
         k_stats_final<4><<<1, 32, 0, st>>>(part, gb, res);
-    } else if (B == 1024)
+    } else if (search)
+        k_block_sums_store<C><<<gb, 256, 0, st>>>(psi, nb, S, P);
+    else if (B == 1024)
         k_segment_sums<C, 32><<<gb, 256, 0, st>>>(psi, nb, (int)B, S);
     else if (B >= 32)
         k_segment_sums<C, 0><<<gb, 256, 0, st>>>(psi, nb, (int)B, S);
@@ -539,9 +641,15 @@ int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double *st
         k_segment_sums_small<double><<<1, 32, 0, st>>>(S, ns, (int)G, T);
     k_prefix_super<<<1, 1, 0, st>>>(T, ns, Q);
     k_prefix_blocks<<<(int)std::min<uint64_t>((ns + 127) / 128, 1024), 128, 0, st>>>(S, Q, ns, G, R);
-    if (m > 0)
+    if (search) {
+        const int gr = (int)std::min<uint64_t>((nb + kRunThreads - 1) / kRunThreads, (uint64_t)sms * 16);
+        k_running_sums<<<gr, kRunThreads, 0, st>>>(P, R, nb);
+        k_draw_search<<<(int)std::min<int64_t>((m + 255) / 256, (int64_t)sms * 16), 256, 0, st>>>(
+            P, Q, R, ns, G, seed, m, dout);
+    } else if (m > 0) {
         k_draw<C><<<(int)std::min<int64_t>((m + 255) / 256, (int64_t)sms * 16), 256, 0, st>>>(
             psi, Q, R, ns, G, B, seed, m, dout);
+    }
     QS_CUDA(cudaGetLastError(), "sampling launch");
     if (m > 0)
         QS_CUDA(cudaMemcpyAsync(out, dout, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, st), "sample copy");
