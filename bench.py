@@ -614,7 +614,9 @@ def target_form(qs, stream, hbm_gbs, harness_count=1500):
                                 "launches": len(kms[dom]), "kernel_ms": dms,
                                 "achieved_gbs": sweep_bytes / (dms * 1e-3) / 1e9,
                                 "frac": sweep_bytes / (dms * 1e-3) / 1e9 / hbm_gbs}
+                    moved = int(np.sum(qs.qs_schedule_get_remap(sc) != np.arange(nq)))
                     res[label] = {"k_max": km, "ops": qs.qs_schedule_num_ops(sc), "predicted_s": pred / 1e3,
+                                  "qubits_moved": moved,
                                   "s_per_circuit": best, "max_abs_dpsi_vs_oracle": err,
                                   "rel_dpsi": err / float(np.max(np.abs(want))),
                                   "norm": st[0], "m2": st[3], "full_sweep_roofline": roof,

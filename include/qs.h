@@ -541,9 +541,17 @@ int qs_cost_model_fit(qs_cost_model *c, const double *features, const double *ms
 /* Predicted ms.  QS_COST_AUTO: the MLP where it was chosen by the fit and the
  * features lie inside the training range, the analytic model elsewhere. */
 int qs_cost_model_predict(const qs_cost_model *c, const double *features, int count, int which, double *ms);
-/* Plan a circuit: for k_max in 2..5 build the schedule, choose each dense op's
- * kernel path (CUDA or tensor cores) by predicted time, keep the k_max with the
- * smallest predicted total.  The schedule records the chosen paths. */
+/* Plan a circuit started from |0...0>: for k_max in 2..5 build the schedule
+ * with qs_schedule_build's default clustering search, choose each dense op's
+ * kernel path (CUDA or tensor cores) by predicted time, and predict the
+ * schedule as it is and with the exchanges of qs_schedule_choose_remap (Sec.
+ * 3.6 bit-location mapping), keeping the faster; keep the k_max with the
+ * smallest predicted total.  Tensor-core sweeps on the support after
+ * |0...0> are predicted with the support's size as the state size; a phase
+ * op right after a tensor-core sweep counts as folded.  The schedule records
+ * the chosen paths and, when chosen, the exchanges (qs_schedule_get_remap).
+ * The analytic model sees no difference between the two bit placements (it
+ * counts bytes), so only a fitted network moves qubits. */
 int qs_plan_circuit(int n, const qs_gate *gates, int n_gates, int dtype, const qs_cost_model *c, int which,
                     qs_schedule **out, int *k_max, double *predicted_ms);
 

@@ -620,6 +620,79 @@ extern "C" int qs_cost_sample(int n_min, int n_max, int dtype, int count, uint64
 
 // ----------------------------------------------------------------- planner
 
+// Predicted time of a schedule's ops (ms) with the qubits moved to the bits
+// loc names (nullable: as they are), and each dense op's cheaper kernel path.
+// From |0...0> the tensor-core sweeps cover only the support so far (the
+// qubits of the dense ops before and including them): their features take
+// that support's size as the state size.  A phase op right after a
+// tensor-core sweep is folded into it (no time of its own).
+static int plan_cost(const qs_schedule *sc, int dtype, const qs_cost_model *c, int which, const int *loc,
+                     double *total, std::vector<int> *paths)
+{
+    const int n = sc->n;
+    std::vector<double> F;
+    std::vector<int> owner, cand_path;
+    uint64_t sup = 0;
+    const uint64_t all = n >= 64 ? ~0ULL : ((1ULL << n) - 1);
+    bool prev_tc = false;
+    for (size_t i = 0; i < sc->ops.size(); i++) {
+        const qs_op_host &op = sc->ops[i];
+        double f[kF];
+        if (op.kind == QS_OP_PHASE) {
+            if (prev_tc) {
+                prev_tc = false;
+                continue;                      // folded into the sweep before it
+            }
+            int na;
+            qs_pack_phase(n, op.coeff, op.edges, &na);
+            int odd = 0;
+            for (int q = 0; q < n; q++) odd |= op.coeff[q] & 1;
+            op_features(n, dtype, op.kind, 0, op.qubits, 0, na, odd, f);
+            F.insert(F.end(), f, f + kF);
+            owner.push_back((int)i);
+            cand_path.push_back(QS_PATH_AUTO);
+            sup = all;                         // phase sweeps cover the whole state
+            continue;
+        }
+        int q[QS_MAX_DIAG_K];
+        for (int j = 0; j < op.k; j++) q[j] = loc ? loc[op.qubits[j]] : op.qubits[j];
+        std::sort(q, q + op.k);
+        uint64_t grown = sup;
+        for (int j = 0; j < op.k; j++) grown |= 1ULL << q[j];
+        for (int path : {QS_PATH_CUDA_CORES, QS_PATH_TENSOR}) {
+            if (path == QS_PATH_TENSOR && n < 5) continue;
+            // a tensor-core sweep on a partial support works on 2^|support| amplitudes
+            const int neff = (path == QS_PATH_TENSOR && grown != all) ? std::max(5, __builtin_popcountll(grown)) : n;
+            op_features(neff, dtype, op.kind, op.k, q, path, 0, 0, f);
+            F.insert(F.end(), f, f + kF);
+            owner.push_back((int)i);
+            cand_path.push_back(path);
+        }
+        sup = grown;
+        prev_tc = n >= 5;
+    }
+    std::vector<double> t(owner.size());
+    if (!owner.empty()) {
+        int rc = qs_cost_model_predict(c, F.data(), (int)owner.size(), which, t.data());
+        if (rc) return rc;
+    }
+    std::vector<double> op_t(sc->ops.size(), 0.0);
+    std::vector<char> seen(sc->ops.size(), 0);
+    if (paths) paths->assign(sc->ops.size(), QS_PATH_AUTO);
+    for (size_t a = 0; a < owner.size(); a++) {
+        const int i = owner[a];
+        if (!seen[i] || t[a] < op_t[i]) {
+            op_t[i] = t[a];
+            seen[i] = 1;
+            if (paths) (*paths)[i] = cand_path[a];
+        }
+    }
+    double sum = 0;
+    for (double x : op_t) sum += x;
+    *total = sum;
+    return QS_OK;
+}
+
 extern "C" int qs_plan_circuit(int n, const qs_gate *gates, int n_gates, int dtype, const qs_cost_model *c, int which,
                                qs_schedule **out, int *k_max_out, double *predicted_ms)
 {
@@ -628,61 +701,62 @@ extern "C" int qs_plan_circuit(int n, const qs_gate *gates, int n_gates, int dty
         qs_schedule *best = nullptr;
         double best_t = 1e300;
         int best_k = 0;
+        std::vector<int> best_loc;
+        std::vector<int> best_paths;
         for (int km = 2; km <= QS_MAX_K; km++) {
-            qs_sched_opts o = {km, 1, 1, 0, 1, 1, 1, 1, 0};
+            // the clustering search of qs_schedule_build's defaults
+            qs_sched_opts o = {km, 1, 1, 0, 1, 13, 1, 16, 5};
             qs_schedule *sc = nullptr;
             int rc = qs_schedule_build(n, gates, n_gates, &o, &sc);
             if (rc) {
                 qs_schedule_free(best);
                 return rc;
             }
-            // candidates: per dense op CUDA cores and (n >= 5) tensor cores
-            std::vector<double> F;
-            std::vector<int> owner, cand_path;
-            for (size_t i = 0; i < sc->ops.size(); i++) {
-                const qs_op_host &op = sc->ops[i];
-                double f[kF];
-                if (op.kind == QS_OP_PHASE) {
-                    int na;
-                    qs_pack_phase(n, op.coeff, op.edges, &na);
-                    int odd = 0;
-                    for (int q = 0; q < n; q++) odd |= op.coeff[q] & 1;
-                    op_features(n, dtype, op.kind, 0, op.qubits, 0, na, odd, f);
-                    F.insert(F.end(), f, f + kF);
-                    owner.push_back((int)i);
-                    cand_path.push_back(QS_PATH_AUTO);
-                    continue;
-                }
-                for (int path : {QS_PATH_CUDA_CORES, QS_PATH_TENSOR}) {
-                    if (path == QS_PATH_TENSOR && n < 5) continue;
-                    op_features(n, dtype, op.kind, op.k, op.qubits, path, 0, 0, f);
-                    F.insert(F.end(), f, f + kF);
-                    owner.push_back((int)i);
-                    cand_path.push_back(path);
-                }
-            }
-            std::vector<double> t(owner.size());
-            rc = qs_cost_model_predict(c, F.data(), (int)owner.size(), which, t.data());
-            if (rc) {
+            double t0 = 0, t1 = 0;
+            std::vector<int> paths0, paths1;
+            if ((rc = plan_cost(sc, dtype, c, which, nullptr, &t0, &paths0))) {
                 qs_schedule_free(sc);
                 qs_schedule_free(best);
                 return rc;
             }
-            std::vector<double> op_t(sc->ops.size(), 1e300);
-            for (size_t a = 0; a < owner.size(); a++)
-                if (t[a] < op_t[owner[a]]) {
-                    op_t[owner[a]] = t[a];
-                    sc->ops[owner[a]].path = cand_path[a];
+            // the same schedule with its qubits moved off the costly low bits
+            // (qs_schedule_choose_remap), kept if the model predicts it faster
+            std::vector<int> loc(n);
+            bool moved = false;
+            if ((rc = qs_schedule_choose_remap(sc, dtype, loc.data()))) {
+                qs_schedule_free(sc);
+                qs_schedule_free(best);
+                return rc;
+            }
+            for (int q = 0; q < n; q++) moved = moved || loc[q] != q;
+            bool use_loc = false;
+            if (moved) {
+                if ((rc = plan_cost(sc, dtype, c, which, loc.data(), &t1, &paths1))) {
+                    qs_schedule_free(sc);
+                    qs_schedule_free(best);
+                    return rc;
                 }
-            double total = 0;
-            for (double x : op_t) total += x;
-            if (total < best_t) {
+                use_loc = t1 < t0 * (1.0 - 1e-9);
+            }
+            const double t = use_loc ? t1 : t0;
+            if (t < best_t) {
                 qs_schedule_free(best);
                 best = sc;
-                best_t = total;
+                best_t = t;
                 best_k = km;
+                best_loc = use_loc ? loc : std::vector<int>();
+                best_paths = use_loc ? paths1 : paths0;
             } else {
                 qs_schedule_free(sc);
+            }
+        }
+        for (size_t i = 0; i < best->ops.size(); i++)
+            if (best->ops[i].kind == QS_OP_DENSE) best->ops[i].path = best_paths[i];
+        if (!best_loc.empty()) {
+            int rc = qs_schedule_remap(best, best_loc.data());
+            if (rc) {
+                qs_schedule_free(best);
+                return rc;
             }
         }
         *out = best;
