@@ -26,6 +26,7 @@ constexpr int kPairLow = 3;          // k_swap_pairs when every swapped bit is >
 constexpr int kMaxBlockBits = 11;    // tiled blocks of at most 2^11 amplitudes
 constexpr int kSwapThreads = 256;
 constexpr int kMaxPairs = 32;        // one sweep: up to 32 exchanges (a state has at most 36 qubits)
+constexpr size_t kTiledBytes = 32768; // amplitudes a tiled pass holds in shared memory
 
 struct SwapPlan {
     uint64_t amask, bmask;           // bits a_j, b_j
@@ -78,8 +79,11 @@ k_swap_tiled(C *__restrict__ psi, uint64_t n_blocks, SwapPlan p)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int run = 1 << p.c, B = run << p.h;
+    // nb consecutive blocks per pass (32 KB of amplitudes), so that every
+    // thread has several loads in flight before the barrier
+    const int nb = (int)(kTiledBytes / sizeof(C)) / B > 0 ? (int)(kTiledBytes / sizeof(C)) / B : 1;
     C *buf = reinterpret_cast<C *>(smem_raw);
-    uint16_t *src = reinterpret_cast<uint16_t *>(smem_raw + sizeof(C) * B);
+    uint16_t *src = reinterpret_cast<uint16_t *>(smem_raw + sizeof(C) * (size_t)B * nb);
     // position q = (s, t) of a block (run s, offset t) holds, after the sweep,
     // the amplitude from position src[q]: P applied to q's index bits
     for (int q = threadIdx.x; q < B; q += blockDim.x) {
@@ -91,21 +95,25 @@ k_swap_tiled(C *__restrict__ psi, uint64_t n_blocks, SwapPlan p)
         for (int j = 0; j < p.h; j++) fs |= (int)((from >> p.hb[j]) & 1ULL) << j;
         src[q] = (uint16_t)((fs << p.c) | (int)(from & (uint64_t)(run - 1)));
     }
-    for (uint64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
-        const uint64_t base = block_base(blk, p.zmask);
-        __syncthreads();   // the previous block's writes have read buf; src is ready
-        for (int q = threadIdx.x; q < B; q += blockDim.x) {
-            const int s = q >> p.c, t = q & (run - 1);
+    const uint64_t n_pass = (n_blocks + nb - 1) / nb;
+    for (uint64_t pass = blockIdx.x; pass < n_pass; pass += gridDim.x) {
+        __syncthreads();   // the previous pass's writes have read buf; src is ready
+        for (int e = threadIdx.x; e < B * nb; e += blockDim.x) {
+            const uint64_t blk = pass * nb + (uint64_t)(e / B);
+            if (blk >= n_blocks) continue;
+            const int q = e % B, s = q >> p.c, t = q & (run - 1);
             uint64_t off = (uint64_t)t;
             for (int j = 0; j < p.h; j++) off |= (uint64_t)((s >> j) & 1) << p.hb[j];
-            buf[q] = psi[base + off];
+            buf[e] = psi[block_base(blk, p.zmask) + off];
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < B; q += blockDim.x) {
-            const int s = q >> p.c, t = q & (run - 1);
+        for (int e = threadIdx.x; e < B * nb; e += blockDim.x) {
+            const uint64_t blk = pass * nb + (uint64_t)(e / B);
+            if (blk >= n_blocks) continue;
+            const int q = e % B, s = q >> p.c, t = q & (run - 1);
             uint64_t off = (uint64_t)t;
             for (int j = 0; j < p.h; j++) off |= (uint64_t)((s >> j) & 1) << p.hb[j];
-            psi[base + off] = buf[src[q]];
+            psi[block_base(blk, p.zmask) + off] = buf[(e / B) * B + src[q]];
         }
     }
 }
@@ -163,12 +171,15 @@ int qs_launch_swap(qs_state *s, const int *a, const int *b, int m)
             p.h = h;
             p.zmask = (1ULL << c) - 1;
             for (int j = 0; j < h; j++) p.zmask |= 1ULL << p.hb[j];
-            smem = ((size_t)(c128 ? 16 : 8) + 2) << (c + h);
+            const size_t B = (size_t)1 << (c + h), asz = c128 ? 16 : 8;
+            const size_t nb = std::max<size_t>(1, kTiledBytes / asz / B);
+            smem = asz * B * nb + 2 * B;
         }
     }
     if (tiled) {
         const uint64_t n_blocks = N >> (p.c + p.h);
-        const int grid = (int)std::min<uint64_t>(n_blocks, (uint64_t)sms * 4);
+        const uint64_t nb = std::max<uint64_t>(1, kTiledBytes / (c128 ? 16 : 8) >> (p.c + p.h));
+        const int grid = (int)std::min<uint64_t>((n_blocks + nb - 1) / nb, (uint64_t)sms * 6);
         if (c128)
             k_swap_tiled<double2><<<grid, kSwapThreads, smem, st>>>((double2 *)s->amp, n_blocks, p);
         else
