@@ -36,6 +36,7 @@ struct SwapPlan {
     int h;                           // tiled: number of swapped bits >= c
     int hb[2 * kMaxPairs];           // tiled: those bits, ascending
     uint64_t zmask;                  // tiled: bits that do not enumerate blocks (low run + H)
+    int lnb;                         // tiled: log2 of the blocks one pass holds
 };
 
 __host__ __device__ __forceinline__ uint64_t swap_bits(uint64_t i, const SwapPlan &p)
@@ -78,12 +79,14 @@ __global__ void __launch_bounds__(kSwapThreads)
 k_swap_tiled(C *__restrict__ psi, uint64_t n_blocks, SwapPlan p)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    const int run = 1 << p.c, B = run << p.h;
+    const int lb = p.c + p.h, B = 1 << lb, run = 1 << p.c;
     // nb consecutive blocks per pass (32 KB of amplitudes), so that every
     // thread has several loads in flight before the barrier
-    const int nb = (int)(kTiledBytes / sizeof(C)) / B > 0 ? (int)(kTiledBytes / sizeof(C)) / B : 1;
+    const int lnb = p.lnb, nb = 1 << lnb;
     C *buf = reinterpret_cast<C *>(smem_raw);
-    uint16_t *src = reinterpret_cast<uint16_t *>(smem_raw + sizeof(C) * (size_t)B * nb);
+    uint64_t *jdep = reinterpret_cast<uint64_t *>(smem_raw + sizeof(C) * ((size_t)B << lnb));
+    uint64_t *hoff = jdep + nb;                 // offset of run s: its H bits
+    uint16_t *src = reinterpret_cast<uint16_t *>(hoff + (1 << p.h));
     // position q = (s, t) of a block (run s, offset t) holds, after the sweep,
     // the amplitude from position src[q]: P applied to q's index bits
     for (int q = threadIdx.x; q < B; q += blockDim.x) {
@@ -95,25 +98,28 @@ k_swap_tiled(C *__restrict__ psi, uint64_t n_blocks, SwapPlan p)
         for (int j = 0; j < p.h; j++) fs |= (int)((from >> p.hb[j]) & 1ULL) << j;
         src[q] = (uint16_t)((fs << p.c) | (int)(from & (uint64_t)(run - 1)));
     }
-    const uint64_t n_pass = (n_blocks + nb - 1) / nb;
+    for (int s = threadIdx.x; s < (1 << p.h); s += blockDim.x) {
+        uint64_t o = 0;
+        for (int j = 0; j < p.h; j++) o |= (uint64_t)((s >> j) & 1) << p.hb[j];
+        hoff[s] = o;
+    }
+    // block pass * nb + j starts at block_base(pass * nb) + block_base(j): the
+    // low lnb bits of a block index come from j alone
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) jdep[j] = block_base((uint64_t)j, p.zmask);
+    const uint64_t n_pass = (n_blocks + nb - 1) >> lnb;
     for (uint64_t pass = blockIdx.x; pass < n_pass; pass += gridDim.x) {
-        __syncthreads();   // the previous pass's writes have read buf; src is ready
-        for (int e = threadIdx.x; e < B * nb; e += blockDim.x) {
-            const uint64_t blk = pass * nb + (uint64_t)(e / B);
-            if (blk >= n_blocks) continue;
-            const int q = e % B, s = q >> p.c, t = q & (run - 1);
-            uint64_t off = (uint64_t)t;
-            for (int j = 0; j < p.h; j++) off |= (uint64_t)((s >> j) & 1) << p.hb[j];
-            buf[e] = psi[block_base(blk, p.zmask) + off];
+        const uint64_t pbase = block_base(pass << lnb, p.zmask);
+        __syncthreads();   // the previous pass's writes have read buf; the tables are ready
+        for (int e = threadIdx.x; e < (B << lnb); e += blockDim.x) {
+            const int j = e >> lb, q = e & (B - 1);
+            if ((pass << lnb) + (uint64_t)j >= n_blocks) continue;
+            buf[e] = psi[pbase + jdep[j] + hoff[q >> p.c] + (uint64_t)(q & (run - 1))];
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < B * nb; e += blockDim.x) {
-            const uint64_t blk = pass * nb + (uint64_t)(e / B);
-            if (blk >= n_blocks) continue;
-            const int q = e % B, s = q >> p.c, t = q & (run - 1);
-            uint64_t off = (uint64_t)t;
-            for (int j = 0; j < p.h; j++) off |= (uint64_t)((s >> j) & 1) << p.hb[j];
-            psi[block_base(blk, p.zmask) + off] = buf[(e / B) * B + src[q]];
+        for (int e = threadIdx.x; e < (B << lnb); e += blockDim.x) {
+            const int j = e >> lb, q = e & (B - 1);
+            if ((pass << lnb) + (uint64_t)j >= n_blocks) continue;
+            psi[pbase + jdep[j] + hoff[q >> p.c] + (uint64_t)(q & (run - 1))] = buf[(j << lb) + src[q]];
         }
     }
 }
@@ -173,13 +179,14 @@ int qs_launch_swap(qs_state *s, const int *a, const int *b, int m)
             for (int j = 0; j < h; j++) p.zmask |= 1ULL << p.hb[j];
             const size_t B = (size_t)1 << (c + h), asz = c128 ? 16 : 8;
             const size_t nb = std::max<size_t>(1, kTiledBytes / asz / B);
-            smem = asz * B * nb + 2 * B;
+            p.lnb = __builtin_ctzll(nb);
+            smem = asz * B * nb + 8 * nb + 8 * ((size_t)1 << h) + 2 * B;
         }
     }
     if (tiled) {
         const uint64_t n_blocks = N >> (p.c + p.h);
-        const uint64_t nb = std::max<uint64_t>(1, kTiledBytes / (c128 ? 16 : 8) >> (p.c + p.h));
-        const int grid = (int)std::min<uint64_t>((n_blocks + nb - 1) / nb, (uint64_t)sms * 6);
+        const uint64_t nb = 1ULL << p.lnb;
+        const int grid = (int)std::min<uint64_t>((n_blocks + nb - 1) / nb, (uint64_t)sms * 5);
         if (c128)
             k_swap_tiled<double2><<<grid, kSwapThreads, smem, st>>>((double2 *)s->amp, n_blocks, p);
         else
