@@ -792,6 +792,11 @@ def run_kernel(args):
         z = g.standard_normal((1 << k, 1 << k)) + 1j * g.standard_normal((1 << k, 1 << k))
         U, _ = np.linalg.qr(z)
         fn, what, bytes_ = (lambda: qs.qs_apply_cluster(h, targets, U)), "dense k=%d on %s" % (k, targets), 2 * full
+    elif args.kernel == "swap":
+        # exchange qubits targets[j] <-> targets2[j] (qs_swap_qubits)
+        a = [int(x) for x in args.targets.split(",")] if args.targets else [2, 3, 4]
+        b = [int(x) for x in args.targets2.split(",")] if args.targets2 else list(range(n - 1, n - 1 - len(a), -1))
+        fn, what, bytes_ = (lambda: qs.qs_swap_qubits(h, a, b)), "exchange of %s with %s" % (a, b), 2 * full
     elif args.kernel == "diag":
         d = np.exp(1j * g.uniform(0, 2 * np.pi, 1 << k))
         fn, what, bytes_ = (lambda: qs.qs_apply_diag(h, targets, d)), "diag k=%d on %s" % (k, targets), 2 * full
@@ -965,7 +970,7 @@ def main():
                     help="host threads of the clustering search (the launching thread keeps the rest)")
     ap.add_argument("--remap", action="store_true",
                     help="move each schedule's qubits to the index bits the library picks (Sec. 3.6)")
-    ap.add_argument("--kernel", choices=["dense", "pair", "diag", "phase", "stats", "sample", "fill", "mlp"],
+    ap.add_argument("--kernel", choices=["dense", "pair", "swap", "diag", "phase", "stats", "sample", "fill", "mlp"],
                     help="time one kernel on a full synthetic state instead of circuits")
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--k", type=int, default=5)
