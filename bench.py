@@ -696,7 +696,8 @@ def run_learned(args):
                     times.append(float(ms[ms >= 0].sum()))   # -1: a phase op run inside the sweep before it
                 paths = [qs.qs_schedule_op(sc, i) for i in range(qs.qs_schedule_num_ops(sc))]
                 res[name] = {"k_max": km, "predicted_s": pred / 1e3, "measured_s": min(times) / 1e3,
-                             "ops": len(paths)}
+                             "ops": len(paths),
+                             "qubits_moved": int(np.sum(qs.qs_schedule_get_remap(sc) != np.arange(n)))}
                 qs.qs_schedule_free(sc)
             res["gain"] = res["analytic"]["measured_s"] / res["learned"]["measured_s"]
             qs.qs_free(h)
