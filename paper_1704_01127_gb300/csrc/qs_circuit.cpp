@@ -668,8 +668,14 @@ static int supremacy_circuit_impl(int rows, int cols, const int *removed_rc, int
     return QS_OK;
 }
 
+static int schedule_from_groups(int n, const std::vector<qs_gate> &g, const std::vector<std::vector<int>> &groups,
+                                const qs_sched_opts *opts, qs_schedule **out);
+
+// ranked (nullable): also the best ranked_max distinct clusterings of the
+// search, best first
 static int schedule_build_impl(int n, const qs_gate *gates, int n_gates, const qs_sched_opts *opts,
-                               qs_schedule **out)
+                               qs_schedule **out, std::vector<std::vector<std::vector<int>>> *ranked = nullptr,
+                               int ranked_max = 0)
 {
     if (!out || n < 1 || n > QS_MAX_QUBITS || n_gates < 0 || (n_gates > 0 && !gates) || !opts)
         return qs_fail(QS_EINVAL, "qs_schedule_build: bad arguments");
@@ -745,22 +751,41 @@ static int schedule_build_impl(int n, const qs_gate *gates, int n_gates, const q
             }
             return c;
         };
-        int best = 0;
-        double best_cost = cost(res[0]);
-        for (int i = 1; i < runs; i++) {
-            const double c = cost(res[i]);
-            if (c < best_cost || (c == best_cost && res[i].size() < res[best].size())) {
-                best = i;
-                best_cost = c;
+        // runs ranked: lowest cost, then fewer clusters, then the lower i
+        std::vector<double> costs(runs);
+        for (int i = 0; i < runs; i++) costs[i] = cost(res[i]);
+        std::vector<int> rank(runs);
+        for (int i = 0; i < runs; i++) rank[i] = i;
+        std::stable_sort(rank.begin(), rank.end(), [&](int a, int b) {
+            if (costs[a] != costs[b]) return costs[a] < costs[b];
+            return res[a].size() < res[b].size();
+        });
+        if (ranked) {
+            // distinct clusterings only, best first
+            for (int i : rank) {
+                bool dup = false;
+                for (const auto &r : *ranked) dup = dup || r == res[i];
+                if (!dup) ranked->push_back(res[i]);
+                if ((int)ranked->size() >= ranked_max) break;
             }
         }
-        groups = std::move(res[best]);
+        groups = std::move(res[rank[0]]);
     } else if (opts->fuse) {
         Clusterer cl(n, g);
         groups = cl.run(opts->k_max);
     } else {
         for (int i = 0; i < n_gates; i++) groups.push_back({i});
     }
+    if (ranked && ranked->empty()) ranked->push_back(groups);
+    return schedule_from_groups(n, g, groups, opts, out);
+}
+
+// Ops of a schedule from its clusters (gate index lists, in order): all-diagonal
+// clusters become phase ops (neighbours merged with merge_phase), the others
+// dense ops with their FP64 unitaries.
+static int schedule_from_groups(int n, const std::vector<qs_gate> &g, const std::vector<std::vector<int>> &groups,
+                                const qs_sched_opts *opts, qs_schedule **out)
+{
     std::unique_ptr<qs_schedule> sc(new (std::nothrow) qs_schedule());
     if (!sc) return qs_fail(QS_ENOMEM, "qs_schedule_build: out of host memory");
     sc->n = n;
@@ -946,6 +971,23 @@ extern "C" int qs_schedule_from_ops(int n, int n_ops, const int *kinds, const in
             return schedule_from_ops_impl(n, n_ops, kinds, ks, qubits, offsets, pool, pool_len, out);
         });
     });
+}
+
+int qs_schedule_build_ranked(int n, const qs_gate *gates, int n_gates, const qs_sched_opts *opts, int top,
+                             std::vector<qs_schedule *> &out)
+{
+    std::vector<std::vector<std::vector<int>>> ranked;
+    qs_schedule *first = nullptr;
+    int rc = schedule_build_impl(n, gates, n_gates, opts, &first, &ranked, std::max(1, top));
+    if (rc) return rc;
+    out.push_back(first);
+    std::vector<qs_gate> g(gates, gates + n_gates);
+    for (size_t i = 1; i < ranked.size(); i++) {
+        qs_schedule *sc = nullptr;
+        if ((rc = schedule_from_groups(n, g, ranked[i], opts, &sc))) return rc;
+        out.push_back(sc);
+    }
+    return QS_OK;
 }
 
 // Stages for a state spread over 2^g parts (Sec. 3.4, Sec. 3.6 steps 1 and 3).

@@ -620,6 +620,8 @@ extern "C" int qs_cost_sample(int n_min, int n_max, int dtype, int count, uint64
 
 // ----------------------------------------------------------------- planner
 
+constexpr int kCandidates = 8;   // search runs the planner predicts per k_max
+
 // Predicted time of a schedule's ops (ms) with the qubits moved to the bits
 // loc names (nullable: as they are), and each dense op's cheaper kernel path.
 // From |0...0> the tensor-core sweeps cover only the support so far (the
@@ -704,18 +706,22 @@ extern "C" int qs_plan_circuit(int n, const qs_gate *gates, int n_gates, int dty
         std::vector<int> best_loc;
         std::vector<int> best_paths;
         for (int km = 2; km <= QS_MAX_K; km++) {
-            // the clustering search of qs_schedule_build's defaults
+            // the clustering search of qs_schedule_build's defaults; its best
+            // kCandidates distinct runs by analytic cost are each predicted
             qs_sched_opts o = {km, 1, 1, 0, 1, 13, 1, 16, 5};
-            qs_schedule *sc = nullptr;
-            int rc = qs_schedule_build(n, gates, n_gates, &o, &sc);
+            std::vector<qs_schedule *> cands;
+            int rc = qs_schedule_build_ranked(n, gates, n_gates, &o, kCandidates, cands);
             if (rc) {
+                for (qs_schedule *x : cands) qs_schedule_free(x);
                 qs_schedule_free(best);
                 return rc;
             }
+          for (size_t ci = 0; ci < cands.size(); ci++) {
+            qs_schedule *sc = cands[ci];
             double t0 = 0, t1 = 0;
             std::vector<int> paths0, paths1;
             if ((rc = plan_cost(sc, dtype, c, which, nullptr, &t0, &paths0))) {
-                qs_schedule_free(sc);
+                for (size_t cj = ci; cj < cands.size(); cj++) qs_schedule_free(cands[cj]);
                 qs_schedule_free(best);
                 return rc;
             }
@@ -724,7 +730,7 @@ extern "C" int qs_plan_circuit(int n, const qs_gate *gates, int n_gates, int dty
             std::vector<int> loc(n);
             bool moved = false;
             if ((rc = qs_schedule_choose_remap(sc, dtype, loc.data()))) {
-                qs_schedule_free(sc);
+                for (size_t cj = ci; cj < cands.size(); cj++) qs_schedule_free(cands[cj]);
                 qs_schedule_free(best);
                 return rc;
             }
@@ -732,7 +738,7 @@ extern "C" int qs_plan_circuit(int n, const qs_gate *gates, int n_gates, int dty
             bool use_loc = false;
             if (moved) {
                 if ((rc = plan_cost(sc, dtype, c, which, loc.data(), &t1, &paths1))) {
-                    qs_schedule_free(sc);
+                    for (size_t cj = ci; cj < cands.size(); cj++) qs_schedule_free(cands[cj]);
                     qs_schedule_free(best);
                     return rc;
                 }
@@ -749,6 +755,8 @@ extern "C" int qs_plan_circuit(int n, const qs_gate *gates, int n_gates, int dty
             } else {
                 qs_schedule_free(sc);
             }
+            cands[ci] = nullptr;
+          }
         }
         for (size_t i = 0; i < best->ops.size(); i++)
             if (best->ops[i].kind == QS_OP_DENSE) best->ops[i].path = best_paths[i];

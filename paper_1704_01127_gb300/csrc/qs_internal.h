@@ -180,6 +180,11 @@ int qs_launch_dense(qs_state *s, const int *sorted_qubits, int k, const void *de
                     const void *dev_tc);
 int qs_launch_diag(qs_state *s, const int *qubits, int k, const void *dev_table);
 int qs_launch_phase(qs_state *s, const void *dev_phase, int n_act);
+// Schedules of the clustering search's best `top` distinct runs (qs_schedule_build's
+// ranking: lowest analytic cost, then fewer clusters), best first; the first is
+// the schedule qs_schedule_build returns.  The caller frees them.
+int qs_schedule_build_ranked(int n, const qs_gate *gates, int n_gates, const qs_sched_opts *opts, int top,
+                             std::vector<qs_schedule *> &out);
 // Exchange qubits a[j] <-> b[j] (j < m, validated by the caller) in one sweep.
 int qs_launch_swap(qs_state *s, const int *a, const int *b, int m);
 uint64_t qs_swap_index(uint64_t i, const int *a, const int *b, int m);
