@@ -514,23 +514,36 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
                 }
                 tc_fence_after();
                 const uint32_t Xr = rowX[it & 1][row];
-#pragma unroll 1
+                // the half's accumulators reduced to the exact partial sums P, Q and
+                // the rounded low part, then the half is released to the next
+                // tile's MMAs before the FP64 rebuild and the stores
+                int Pv[kEpiCols / 4][4], Qv[kEpiCols / 4][4], Rv[kEpiCols / 4][4];
+#pragma unroll
                 for (int c = 0; c < kEpiCols / 4; c++) {
-                    const int col = kEpiCols * cq + 4 * c;     // column within the half
+                    const int col = kEpiCols * cq + 4 * c;
                     float D[kDiags][4];
 #pragma unroll
                     for (int d = 0; d < kDiags; d++) tmem_ld4(lane_addr + 256 * h + kHalfN * d + col, D[d]);
                     tmem_wait_ld();
+                    // T = P 2^32 + Q 2^16 + r with P = D_0 2^8 + D_1 and
+                    // Q = D_2 2^8 + D_3 exact in 32 bits (|D_d| <= 2^22)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        Pv[c][q] = exact_int(D[0][q]) * 256 + exact_int(D[1][q]);
+                        Qv[c][q] = exact_int(D[2][q]) * 256 + exact_int(D[3][q]);
+                        Rv[c][q] = __float2int_rn(fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]) * 256.0f);
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&mbar_free[h]));   // the half's accumulators are read
+#pragma unroll
+                for (int c = 0; c < kEpiCols / 4; c++) {
+                    const int col = kEpiCols * cq + 4 * c;     // column within the half
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
-                        // T = P 2^32 + Q 2^16 + r with P = D_0 2^8 + D_1 and
-                        // Q = D_2 2^8 + D_3 exact in 32 bits (|D_d| <= 2^22)
-                        const int P = exact_int(D[0][q]) * 256 + exact_int(D[1][q]);
-                        const int Q = exact_int(D[2][q]) * 256 + exact_int(D[3][q]);
-                        const float L = fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]);
-                        const long long T = ((long long)P << 32) + ((long long)Q << 16) +
-                                            (long long)__float2int_rn(L * 256.0f);
+                        const int P = Pv[c][q], Q = Qv[c][q];
+                        const long long T = ((long long)P << 32) + ((long long)Q << 16) + (long long)Rv[c][q];
                         const double dv = __ll2double_rn(T);
                         const uint32_t hi = (uint32_t)__double2hiint(dv);
                         // T = 0 gives +0.0 (hi = 0); otherwise add the scale to the exponent
@@ -549,8 +562,6 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
                                                        __hiloint2double((int)hw[3], (int)lw[3]));
                     }
                 }
-                tc_fence_before();
-                mbar_arrive(smem_u32(&mbar_free[h]));
             }
         }
     }
