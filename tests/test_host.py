@@ -371,3 +371,23 @@ def test_stage_plan_36_qubits_one_swap_from_the_uniform_state():
     finally:
         for sc in stages:
             qs.qs_schedule_free(sc)
+
+
+def test_stage_plan_edge_cases():
+    """No global qubits: one stage, the whole circuit; more global qubits than
+    can ever be free of a non-diagonal gate: rejected; bad counts rejected."""
+    n, gates = qs.qs_supremacy_circuit(3, 3, 6, 2)
+    stages, of = qs.qs_plan_stages(n, gates, 0, search_runs=1, search_first=1)
+    try:
+        assert len(stages) == 1 and set(of.tolist()) == {0}
+        assert list(qs.qs_schedule_get_remap(stages[0])) == list(range(n))
+    finally:
+        for sc in stages:
+            qs.qs_schedule_free(sc)
+    for g in (n, -1):
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_plan_stages(n, gates, g)
+        assert e.value.code == qs.QS_EINVAL
+    with pytest.raises(qs.QSError) as e:      # every qubit starts with an H: 8 of 9 global cannot start
+        qs.qs_plan_stages(n, gates, 8, max_stages=2)
+    assert e.value.code == qs.QS_EINVAL
