@@ -83,8 +83,11 @@ k_swap_tiled(C *__restrict__ psi, uint64_t n_blocks, SwapPlan p)
     // nb consecutive blocks per pass (32 KB of amplitudes), so that every
     // thread has several loads in flight before the barrier
     const int lnb = p.lnb, nb = 1 << lnb;
+    // buf holds each run with one element of padding, so that the permuted
+    // reads (runs 2^c elements apart) fall in different banks
     C *buf = reinterpret_cast<C *>(smem_raw);
-    uint64_t *jdep = reinterpret_cast<uint64_t *>(smem_raw + sizeof(C) * ((size_t)B << lnb));
+    const int prun = run + 1;
+    uint64_t *jdep = reinterpret_cast<uint64_t *>(smem_raw + sizeof(C) * ((size_t)prun << (p.h + lnb)));
     uint64_t *hoff = jdep + nb;                 // offset of run s: its H bits
     uint16_t *src = reinterpret_cast<uint16_t *>(hoff + (1 << p.h));
     // position q = (s, t) of a block (run s, offset t) holds, after the sweep,
@@ -113,13 +116,16 @@ k_swap_tiled(C *__restrict__ psi, uint64_t n_blocks, SwapPlan p)
         for (int e = threadIdx.x; e < (B << lnb); e += blockDim.x) {
             const int j = e >> lb, q = e & (B - 1);
             if ((pass << lnb) + (uint64_t)j >= n_blocks) continue;
-            buf[e] = psi[pbase + jdep[j] + hoff[q >> p.c] + (uint64_t)(q & (run - 1))];
+            buf[((j << p.h) + (q >> p.c)) * prun + (q & (run - 1))] =
+                psi[pbase + jdep[j] + hoff[q >> p.c] + (uint64_t)(q & (run - 1))];
         }
         __syncthreads();
         for (int e = threadIdx.x; e < (B << lnb); e += blockDim.x) {
             const int j = e >> lb, q = e & (B - 1);
             if ((pass << lnb) + (uint64_t)j >= n_blocks) continue;
-            psi[pbase + jdep[j] + hoff[q >> p.c] + (uint64_t)(q & (run - 1))] = buf[(j << lb) + src[q]];
+            const int f = src[q];
+            psi[pbase + jdep[j] + hoff[q >> p.c] + (uint64_t)(q & (run - 1))] =
+                buf[((j << p.h) + (f >> p.c)) * prun + (f & (run - 1))];
         }
     }
 }
@@ -180,7 +186,7 @@ int qs_launch_swap(qs_state *s, const int *a, const int *b, int m)
             const size_t B = (size_t)1 << (c + h), asz = c128 ? 16 : 8;
             const size_t nb = std::max<size_t>(1, kTiledBytes / asz / B);
             p.lnb = __builtin_ctzll(nb);
-            smem = asz * B * nb + 8 * nb + 8 * ((size_t)1 << h) + 2 * B;
+            smem = asz * (((size_t)1 << c) + 1) * ((size_t)1 << h) * nb + 8 * nb + 8 * ((size_t)1 << h) + 2 * B;
         }
     }
     if (tiled) {
