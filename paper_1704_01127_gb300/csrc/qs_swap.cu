@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kSwapThreads)
 k_swap_tiled(C *__restrict__ psi, uint64_t n_blocks, SwapPlan p)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
+    constexpr int VEC = sizeof(C) == 8 ? 2 : 1;
     const int lb = p.c + p.h, B = 1 << lb, run = 1 << p.c;
     // nb consecutive blocks per pass (32 KB of amplitudes), so that every
     // thread has several loads in flight before the barrier
@@ -113,19 +114,35 @@ k_swap_tiled(C *__restrict__ psi, uint64_t n_blocks, SwapPlan p)
     for (uint64_t pass = blockIdx.x; pass < n_pass; pass += gridDim.x) {
         const uint64_t pbase = block_base(pass << lnb, p.zmask);
         __syncthreads();   // the previous pass's writes have read buf; the tables are ready
-        for (int e = threadIdx.x; e < (B << lnb); e += blockDim.x) {
+        // VEC neighbouring elements of a run per thread (16-byte global accesses
+        // for complex64; a run is at least 8 elements)
+        for (int e = threadIdx.x * VEC; e < (B << lnb); e += blockDim.x * VEC) {
             const int j = e >> lb, q = e & (B - 1);
             if ((pass << lnb) + (uint64_t)j >= n_blocks) continue;
-            buf[((j << p.h) + (q >> p.c)) * prun + (q & (run - 1))] =
-                psi[pbase + jdep[j] + hoff[q >> p.c] + (uint64_t)(q & (run - 1))];
+            const C *g = psi + pbase + jdep[j] + hoff[q >> p.c] + (uint64_t)(q & (run - 1));
+            C *d = buf + ((j << p.h) + (q >> p.c)) * prun + (q & (run - 1));
+            if constexpr (VEC == 2) {
+                const float4 w = *reinterpret_cast<const float4 *>(g);
+                d[0] = make_float2(w.x, w.y);
+                d[1] = make_float2(w.z, w.w);
+            } else {
+                d[0] = g[0];
+            }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < (B << lnb); e += blockDim.x) {
+        for (int e = threadIdx.x * VEC; e < (B << lnb); e += blockDim.x * VEC) {
             const int j = e >> lb, q = e & (B - 1);
             if ((pass << lnb) + (uint64_t)j >= n_blocks) continue;
-            const int f = src[q];
-            psi[pbase + jdep[j] + hoff[q >> p.c] + (uint64_t)(q & (run - 1))] =
-                buf[((j << p.h) + (f >> p.c)) * prun + (f & (run - 1))];
+            C *g = psi + pbase + jdep[j] + hoff[q >> p.c] + (uint64_t)(q & (run - 1));
+            const int f0 = src[q];
+            const C v0 = buf[((j << p.h) + (f0 >> p.c)) * prun + (f0 & (run - 1))];
+            if constexpr (VEC == 2) {
+                const int f1 = src[q + 1];
+                const C v1 = buf[((j << p.h) + (f1 >> p.c)) * prun + (f1 & (run - 1))];
+                *reinterpret_cast<float4 *>(g) = make_float4(v0.x, v0.y, v1.x, v1.y);
+            } else {
+                g[0] = v0;
+            }
         }
     }
 }
