@@ -189,9 +189,11 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const
 //
 // Each row r (group) is scaled by its largest exponent E_r and each column n of
 // B^T by its largest exponent G_n; a value m 2^{e-1075} becomes the fixed-point
-// integer F = round(m 2^{e-E-7}) (half to even), |F| <= 2^46, so
-// F = sum_{s<6} d_s 2^{8(5-s)}
-// with balanced digits d_s in [-128, 127] (exact in fp16).  With A_i, B_j the
+// integer F = round(m 2^{e-E-7}) (half to even, on the magnitude), |F| <= 2^46,
+// so |F| = sum_{s<6} (b_s - 128) 2^{8(5-s)} with b_s the bytes of
+// |F| + 0x808080808080, and the state digits are d_s = sigma (b_s - 128), sigma
+// the value's sign (|d_s| <= 128, exact in fp16; the unitary's digits are the
+// balanced bytes of its two's complement fixed point).  With A_i, B_j the
 // digit planes and T = sum_{d<=6} D_d 2^{8(5-d)},
 //   sum_k a_rk b_kn ~ 2^{E_r + G_n - 2096} T[r][n],  D_d = sum_{i+j=d} (A_i B_j^T),
 // and the planes with i + j = d <= 6 are summed in accumulator D_d (TMEM; the
@@ -199,8 +201,9 @@ k_dense5_tc_c64(float2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const
 // digits is an integer of magnitude <= 2^14 and a 64-term sum <= 2^20, so
 // D_0..D_3 (at most four products) are exact integers of magnitude <= 2^22 in
 // FP32; D_4..D_6 carry weight <= 2^-32 and are combined in FP32.  The FP64
-// result is one int64 -> double conversion with the scale added to the
-// exponent field.
+// result is one int64 -> double conversion of T = P 2^32 + Q 2^16 + R
+// (P = D_0 2^8 + D_1, Q = D_2 2^8 + D_3 exact in 32 bits, R the rounded low
+// part), assembled in 32-bit halves, with the scale added to the exponent field.
 // ----------------------------------------------------------------------------
 constexpr int kSlices = 6;                                   // digit planes of A (the state)
 constexpr int kSlicesB = 7;                                  // digit planes of B (the unitary)
@@ -217,44 +220,56 @@ __host__ __device__ __forceinline__ uint32_t cm_off16(int row, int k)
     return (uint32_t)((((row >> 3) * (kK / 8)) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// Fixed point of a double relative to biased exponent E (|F| <= 2^46, rounded
-// to nearest), plus the digit bias, as an unsigned 64-bit integer.
-__device__ __forceinline__ uint64_t fixed48(double a, int E)
+// |F| of a double relative to biased row exponent E, rounded half to even (the
+// structured amplitudes of early circuit layers hit exact ties often, and
+// rounding ties up would bias the norm), plus the digit bias 0x808080808080, as
+// two 32-bit words.  Members within 2^25 of the row's largest value (sh < 32;
+// E7f = E + 7, or a value that sends every member to the general path when
+// E < 25) take 32-bit funnel shifts: the round bit and the bits below it sit in
+// x = lo << (32 - sh), and the increment is [x > 2^31 - lsb] (above half, or
+// exactly half with an odd truncated value).
+__device__ __forceinline__ void mag48(double a, int E, int E7f, uint32_t &flo, uint32_t &fhi)
 {
-    const uint64_t bits = (uint64_t)__double_as_longlong(a);
-    const int e = (int)((bits >> 52) & 0x7FF);
-    const int shift = E + 7 - e;
-    uint64_t F = 0;
-    if (e != 0 && shift < 60) {
-        const uint64_t m = (bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-        // round half to even: the structured amplitudes of early circuit layers
-        // hit exact ties often, and rounding ties up would bias the norm
-        F = (m + (1ULL << (shift - 1)) - 1 + ((m >> shift) & 1)) >> shift;
-        if (bits >> 63) F = 0 - F;
+    const uint32_t hi = (uint32_t)__double2hiint(a), lo = (uint32_t)__double2loint(a);
+    const int sh = E7f - (int)((hi & 0x7FFFFFFFu) >> 20);
+    uint32_t tlo, thi, inc;
+    if ((uint32_t)sh < 32u) {
+        const uint32_t mh = (hi & 0x000FFFFFu) | 0x00100000u;
+        tlo = __funnelshift_r(lo, mh, sh);
+        thi = mh >> sh;
+        const uint32_t x = lo << (32 - sh);
+        inc = x > 0x80000000u - (tlo & 1u) ? 1u : 0u;
+    } else {
+        const int e = (int)((hi >> 20) & 0x7FF), shift = E + 7 - e;
+        uint64_t F = 0;
+        if (e != 0 && shift < 60) {
+            const uint64_t m = ((uint64_t)(hi & 0x000FFFFFu) << 32 | lo) | (1ULL << 52);
+            F = (m + (1ULL << (shift - 1)) - 1 + ((m >> shift) & 1)) >> shift;
+        }
+        tlo = (uint32_t)F;
+        thi = (uint32_t)(F >> 32);
+        inc = 0;
     }
-    return F + 0x808080808080ULL;
+    const uint64_t F = ((uint64_t)thi << 32 | tlo) + inc + 0x808080808080ULL;
+    flo = (uint32_t)F;
+    fhi = (uint32_t)(F >> 32);
 }
 
-// Digit planes in fp16: a byte b becomes the fp16 value 1024 + b when the
-// byte 0x64 is put above it, and one f16x2 add of -1152 gives two balanced
-// digits b - 128 (exact).  Bytes (k, k') of two words w0, w1 (the real and
-// imaginary parts of one amplitude) are first gathered into one word.
-__device__ __forceinline__ uint32_t f16x2_digits(uint32_t pairs, uint32_t sel)
+// Signed digit pair of one plane: the bytes (re, im) become fp16 1024 + b by a
+// byte permute, and one f16x2 FMA with the amplitude's signs s (+-1 per half)
+// gives s (b - 128): w s + (-1152 s).
+__device__ __forceinline__ uint32_t f16x2_sdigits(uint32_t pairs, uint32_t sel, uint32_t sg, uint32_t nsg)
 {
     uint32_t r;
     const uint32_t w = __byte_perm(pairs, 0x64646464u, sel);
-    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(w), "r"(0xE480E480u));
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(w), "r"(sg), "r"(nsg));
     return r;
 }
 
-// exact int from an fp32 integer of magnitude <= 2^22
-__device__ __forceinline__ int exact_int(float x)
-{
-    return __float_as_int(x + 12582912.0f) - 0x4B400000;
-}
-
 constexpr int kSplitThreads = 512;
-constexpr int kEpiThreads = 512;
+constexpr int kEpiThreads = 384;                    // 3 warps per TMEM lane quarter
+constexpr int kIssueThreads = 32;                   // one warp: issues the MMAs
+constexpr int kC128Threads = kSplitThreads + kEpiThreads + kIssueThreads;
 constexpr int kSplitParts = kSplitThreads / kRows;   // splitter threads per row
 constexpr int kMPT = 32 / kSplitParts;               // amplitudes per splitter thread
 
@@ -282,27 +297,33 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 }
 
 // ----------------------------------------------------------------------------
-// complex128 kernel: one CTA per SM, two warp-specialised groups (as built:
-// 512 + 512 threads; 512 + 256 measured within 1%, slower with low targets).
-//   splitters (kSplitThreads / 128 threads per row, kMPT amplitudes each):
-//     copy tile t+1 into a 64 KB stage with cp.async while tile t is
+// complex128 kernel: one CTA per SM, three warp-specialised groups:
+//   splitters (512 threads, kSplitThreads / 128 per row, kMPT amplitudes
+//     each): copy tile t+1 into a 64 KB stage with cp.async while tile t is
 //     processed; find the row exponents and the fixed-point values of tile t
 //     while the MMAs of tile t-1 still read the digit planes, then write the
-//     planes; thread 0 issues the MMAs;
-//   epilogue (kEpiThreads / 128 threads per row, kEpiCols columns of each
-//     half): rebuild FP64 results from the accumulators and store them.
+//     planes;
+//   issuer (one warp, one thread): issues the MMAs.  The tensor pipe takes
+//     few instructions ahead, so the issuing thread waits about as long as
+//     the MMAs run (~4K cycles a tile); on its own warp that wait holds up
+//     no splitter (issued by splitter thread 0: 10.2 ms per 30-qubit sweep,
+//     here 8.35 ms together with the arithmetic below);
+//   epilogue (384 threads, three warps per TMEM lane quarter, 3 + 3 + 2 and
+//     2 + 3 + 3 four-column chunks of the two halves): rebuild FP64 results
+//     from the accumulators and store them.
 // The output columns come in two halves of 32, so that the tensor cores work
 // on one half while the epilogue reads the other.
 //   TMEM: half h holds D_0..D_6 for its 32 columns at columns 256 h + 32 d.
 //   B:    4 KB blocks (half h, plane j) at (7 h + j) * 4 KB, so for A plane i
 //         one MMA with N = 32 (7 - i) reads B planes 0..6-i of half h and
 //         writes D_i..D_6 of that half (24 MMAs per half, 48 per tile).
-// Hand-offs per tile: mbar_mma[h] (tcgen05.commit after half h's MMAs; half 1's
-// also releases the A planes), mbar_free[h] (one arrival per epilogue thread
-// when half h's accumulators are read).  All waits are bounded.
+// Hand-offs per tile: mbar_planes (splitter thread 0 after the planes are
+// written), mbar_mma[h] (tcgen05.commit after half h's MMAs; half 1's also
+// releases the A planes), mbar_free[h] (one arrival per epilogue thread when
+// half h's accumulators are read).  All waits are bounded.
 // ----------------------------------------------------------------------------
 constexpr int kHalfN = 32;
-constexpr int kEpiCols = kHalfN * kRows / kEpiThreads;    // columns of each half per epilogue thread
+constexpr int kEpiMaxChunks = 3;                          // 4-column chunks of a half per epilogue warp (3, 3, 2 / 2, 3, 3)
 constexpr uint32_t kBlockB = (uint32_t)kHalfN * kK * 2;   // 4 KB: one plane of one half
 
 // instruction descriptor: D fp32, A and B fp16 (format 0), both K-major,
@@ -338,7 +359,7 @@ constexpr size_t kStageC128 = (size_t)kSplitThreads * kMPT * 16;   // raw next t
 constexpr size_t kSmemC128Pipe = kSmemC128 + kStageC128;
 
 template <bool kPost>
-__global__ void __launch_bounds__(kSplitThreads + kEpiThreads, 1)
+__global__ void __launch_bounds__(kC128Threads, 1)
 k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const uint8_t *__restrict__ bpack,
                       const qs_post_phase *__restrict__ post, int *__restrict__ status)
 {
@@ -346,7 +367,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     uint8_t *A = smem;
     uint8_t *B = smem + kSlices * kPlaneA;
     uint4 *stage = reinterpret_cast<uint4 *>(smem + kSmemC128);   // [8][512] x 16 B
-    __shared__ __align__(8) uint64_t mbar_mma[2], mbar_free[2];
+    __shared__ __align__(8) uint64_t mbar_mma[2], mbar_free[2], mbar_planes;
     __shared__ uint64_t moff[32];         // offset of member x within a group
     __shared__ uint32_t tmem_base_s;
     __shared__ int rowexp[kSplitParts][kRows];
@@ -381,6 +402,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             mbar_init(smem_u32(&mbar_mma[h]), 1);
             mbar_init(smem_u32(&mbar_free[h]), kEpiThreads);
         }
+        mbar_init(smem_u32(&mbar_planes), 1);
         fence_mbar_init();
         abort_flag = 0;
     }
@@ -434,17 +456,14 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             int E = rowexp[0][row];
 #pragma unroll
             for (int q = 1; q < kSplitParts; q++) E = max(E, rowexp[q][row]);
-            // the epilogue of tile it-2 has released both halves (thread 0 waited
-            // for it before issuing tile it-1), so slot it & 1 is free
-            if (part == 0) rowX[it & 1][row] = (uint32_t)(E - 2096) << 20;
-            uint32_t glo[2 * kMPT], ghi[2 * kMPT];
+            const int E7f = E >= 25 ? E + 7 : 0x40000000;
+            uint32_t glo[2 * kMPT], ghi[2 * kMPT], sgn[kMPT];
 #pragma unroll
             for (int x = 0; x < kMPT; x++) {
-                const uint64_t g0 = fixed48(v[x].x, E), g1 = fixed48(v[x].y, E);
-                glo[2 * x] = (uint32_t)g0;
-                ghi[2 * x] = (uint32_t)(g0 >> 32);
-                glo[2 * x + 1] = (uint32_t)g1;
-                ghi[2 * x + 1] = (uint32_t)(g1 >> 32);
+                mag48(v[x].x, E, E7f, glo[2 * x], ghi[2 * x]);
+                mag48(v[x].y, E, E7f, glo[2 * x + 1], ghi[2 * x + 1]);
+                // sign bits of re (bit 15) and im (bit 31)
+                sgn[x] = __byte_perm((uint32_t)__double2hiint(v[x].x), (uint32_t)__double2hiint(v[x].y), 0x7632u) & 0x80008000u;
             }
             // tile it-1's MMAs (both halves) must have finished reading the planes
             const bool ok = it == 0 || mbar_wait_bounded(smem_u32(&mbar_mma[1]), (it - 1) & 1);
@@ -452,6 +471,9 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
                 if (tid == 0) atomicExch(status, 1);
                 break;
             }
+            // tile it-1's half-1 MMAs were issued after the epilogue had read
+            // tile it-2's scale, so slot it & 1 is free
+            if (part == 0) rowX[it & 1][row] = (uint32_t)(E - 2096) << 20;
 #pragma unroll
             for (int c = 0; c < kMPT / 4; c++) {
                 uint8_t *dst = A + cm_off16(row, 2 * kMPT * part + 8 * c);
@@ -462,12 +484,13 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
                     const uint32_t yh = __byte_perm(ghi[2 * x], ghi[2 * x + 1], 0x5410u);
                     const uint32_t y23 = __byte_perm(glo[2 * x], glo[2 * x + 1], 0x7632u);
                     const uint32_t y01 = __byte_perm(glo[2 * x], glo[2 * x + 1], 0x5410u);
-                    pl[0][j] = f16x2_digits(yh, 0x4341u);    // byte 5 of F
-                    pl[1][j] = f16x2_digits(yh, 0x4240u);    // byte 4
-                    pl[2][j] = f16x2_digits(y23, 0x4341u);   // byte 3
-                    pl[3][j] = f16x2_digits(y23, 0x4240u);   // byte 2
-                    pl[4][j] = f16x2_digits(y01, 0x4341u);   // byte 1
-                    pl[5][j] = f16x2_digits(y01, 0x4240u);   // byte 0
+                    const uint32_t sg = sgn[x] | 0x3C003C00u, nsg = sgn[x] ^ 0xE480E480u;   // +-1, -+1152
+                    pl[0][j] = f16x2_sdigits(yh, 0x4341u, sg, nsg);    // byte 5 of |F|
+                    pl[1][j] = f16x2_sdigits(yh, 0x4240u, sg, nsg);    // byte 4
+                    pl[2][j] = f16x2_sdigits(y23, 0x4341u, sg, nsg);   // byte 3
+                    pl[3][j] = f16x2_sdigits(y23, 0x4240u, sg, nsg);   // byte 2
+                    pl[4][j] = f16x2_sdigits(y01, 0x4341u, sg, nsg);   // byte 1
+                    pl[5][j] = f16x2_sdigits(y01, 0x4240u, sg, nsg);   // byte 0
                 }
 #pragma unroll
                 for (int sl = 0; sl < kSlices; sl++)
@@ -475,27 +498,43 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             }
             fence_proxy_async();
             bar_split();
-            if (tid == 0) {
+            if (tid == 0) mbar_arrive(smem_u32(&mbar_planes));   // planes of tile it are written
+        }
+        cp_async_wait_all();
+    } else if (tid >= kSplitThreads + kEpiThreads) {
+        // ---------------------------------------------------------------- issuer
+        if (tid == kSplitThreads + kEpiThreads) {
+            const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+            int it = 0;
+            for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, it++) {
+                if (!mbar_wait_bounded(smem_u32(&mbar_planes), it & 1) || abort_flag) {
+                    atomicExch(status, 1);
+                    abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
                 // half h of tile it-1 must have been read out before half h of tile it
-                for (int h = 0; h < 2; h++) {
+                bool ok = true;
+                for (int h = 0; h < 2 && ok; h++) {
                     if (it > 0 && !mbar_wait_bounded(smem_u32(&mbar_free[h]), (it - 1) & 1)) {
                         atomicExch(status, 1);
                         abort_flag = 1;
+                        ok = false;
                         break;
                     }
                     tc_fence_after();
                     issue_c128_half(tmem, a0, b0, h);
                     mma_commit(smem_u32(&mbar_mma[h]));
                 }
+                if (!ok) break;
             }
+            // leave only after the last MMAs are complete (they read this CTA's planes)
+            if (it > 0 && !abort_flag) mbar_wait_bounded(smem_u32(&mbar_mma[1]), (it - 1) & 1);
         }
-        cp_async_wait_all();
-        // leave only after the last MMAs are complete (they read this CTA's planes)
-        if (tid == 0 && it > 0 && !abort_flag) mbar_wait_bounded(smem_u32(&mbar_mma[1]), (it - 1) & 1);
     } else {
         // ------------------------------------------------------------- epilogue
-        const int ew = warp - kSplitThreads / 32;                 // 0 .. 15
-        const int row = 32 * (warp & 3) + (tid & 31), cq = ew >> 2;   // columns kEpiCols cq .. of each half
+        const int ew = warp - kSplitThreads / 32;                 // 0 .. 11
+        const int row = 32 * (warp & 3) + (tid & 31), ej = ew >> 2;   // warp ej of its lane quarter
         const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         int it = 0;
         bool failed = false;
@@ -517,34 +556,52 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
                 // the half's accumulators reduced to the exact partial sums P, Q and
                 // the rounded low part, then the half is released to the next
                 // tile's MMAs before the FP64 rebuild and the stores
-                int Pv[kEpiCols / 4][4], Qv[kEpiCols / 4][4], Rv[kEpiCols / 4][4];
+                // this warp's chunks of the half: 3, 3, 2 (half 0) and 2, 3, 3 (half 1)
+                const int c0 = h == 0 ? 3 * ej : (ej == 0 ? 0 : 3 * ej - 1);
+                const int nc = h == 0 ? (ej < 2 ? 3 : 2) : (ej == 0 ? 2 : 3);
+                int Pv[kEpiMaxChunks][4], Qv[kEpiMaxChunks][4], Rv[kEpiMaxChunks][4];
 #pragma unroll
-                for (int c = 0; c < kEpiCols / 4; c++) {
-                    const int col = kEpiCols * cq + 4 * c;
+                for (int c = 0; c < kEpiMaxChunks; c++) {
+                    if (c >= nc) break;
+                    const int col = 4 * (c0 + c);
                     float D[kDiags][4];
 #pragma unroll
-                    for (int d = 0; d < kDiags; d++) tmem_ld4(lane_addr + 256 * h + kHalfN * d + col, D[d]);
+                    for (int d = 0; d < 4; d++) tmem_ld4(lane_addr + 256 * h + kHalfN * d + col, D[d]);
                     tmem_wait_ld();
                     // T = P 2^32 + Q 2^16 + r with P = D_0 2^8 + D_1 and
                     // Q = D_2 2^8 + D_3 exact in 32 bits (|D_d| <= 2^22)
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
-                        Pv[c][q] = exact_int(D[0][q]) * 256 + exact_int(D[1][q]);
-                        Qv[c][q] = exact_int(D[2][q]) * 256 + exact_int(D[3][q]);
-                        Rv[c][q] = __float2int_rn(fmaf(fmaf(D[6][q], 0.00390625f, D[5][q]), 0.00390625f, D[4][q]) * 256.0f);
+                        // raw words 0x4B400000 + D_d; P and Q carry 257 * 0x4B400000
+                        Pv[c][q] = (int)((uint32_t)__float_as_int(D[0][q] + 12582912.0f) * 256u + (uint32_t)__float_as_int(D[1][q] + 12582912.0f));
+                        Qv[c][q] = (int)((uint32_t)__float_as_int(D[2][q] + 12582912.0f) * 256u + (uint32_t)__float_as_int(D[3][q] + 12582912.0f));
+                    }
+#pragma unroll
+                    for (int d = 4; d < kDiags; d++) tmem_ld4(lane_addr + 256 * h + kHalfN * d + col, D[d]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        Rv[c][q] = __float2int_rn(fmaf(D[4][q], 256.0f, fmaf(D[6][q], 0.00390625f, D[5][q])));
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(smem_u32(&mbar_free[h]));   // the half's accumulators are read
 #pragma unroll
-                for (int c = 0; c < kEpiCols / 4; c++) {
-                    const int col = kEpiCols * cq + 4 * c;     // column within the half
+                for (int c = 0; c < kEpiMaxChunks; c++) {
+                    if (c >= nc) break;
+                    const int col = 4 * (c0 + c);              // column within the half
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
-                        const int P = Pv[c][q], Q = Qv[c][q];
-                        const long long T = ((long long)P << 32) + ((long long)Q << 16) + (long long)Rv[c][q];
-                        const double dv = __ll2double_rn(T);
+                        // T = (P - K) 2^32 + (Q - K) 2^16 + R, K = 257 * 0x4B400000 = 0x8B400000 (mod 2^32)
+                        const int R = Rv[c][q];
+                        const int Qt = (int)((uint32_t)Qv[c][q] - 0x8B400000u);
+                        uint32_t tl, th;
+                        asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;"
+                            : "=r"(tl), "=r"(th)
+                            : "r"((uint32_t)Qt << 16), "r"((uint32_t)R), "r"((uint32_t)Pv[c][q] + (uint32_t)(Qt >> 16)),
+                              "r"((uint32_t)(R >> 31) - 0x8B400000u));
+                        const double dv = __ll2double_rn((long long)((uint64_t)th << 32 | tl));
                         const uint32_t hi = (uint32_t)__double2hiint(dv);
                         // T = 0 gives +0.0 (hi = 0); otherwise add the scale to the exponent
                         hw[q] = hi == 0 ? 0u : hi + Xr + colX[kHalfN * h + col + q];
@@ -742,10 +799,10 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
     } else {
         int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms);
         if (fold)
-            k_dense5_tc_c128_pipe<true><<<grid, kSplitThreads + kEpiThreads, kSmemC128Pipe, st>>>(
+            k_dense5_tc_c128_pipe<true><<<grid, kC128Threads, kSmemC128Pipe, st>>>(
                 (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, post, status);
         else
-            k_dense5_tc_c128_pipe<false><<<grid, kSplitThreads + kEpiThreads, kSmemC128Pipe, st>>>(
+            k_dense5_tc_c128_pipe<false><<<grid, kC128Threads, kSmemC128Pipe, st>>>(
                 (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, post, status);
     }
     // amplitudes on the padding targets of an embedded cluster keep their
