@@ -228,7 +228,11 @@ int qs_stats_static(const void *dev_amp, int n, int dtype, void *stream, double 
 
 /* Wait for all work queued on the state's stream; QS_ETIMEOUT (once, the word
  * is cleared) if a tensor-core kernel's bounded wait ran out since the last
- * check. */
+ * check; QS_EINVAL (once) if a complex128 tensor-core sweep met amplitudes
+ * above ~2^1010 in magnitude, whose results could pass the double range (its
+ * outputs are then not meaningful).  Rows below ~2^-970 are swept with their
+ * scale raised, so no result leaves the normal range (absolute error
+ * ~2^-1015). */
 int qs_synchronize(qs_state *s);
 
 /* Exercises the failure path of the bounded waits: one thread waits on an

@@ -734,7 +734,8 @@ int qs_check_status(qs_state *s)
     QS_CUDA(cudaStreamSynchronize(st), "status read");
     if (v) {
         cudaMemsetAsync(s->status, 0, sizeof(int), st);
-        return qs_fail(QS_ETIMEOUT, "a kernel's bounded wait ran out (status %d)", v);
+        if (v & 1) return qs_fail(QS_ETIMEOUT, "a kernel's bounded wait ran out (status %d)", v);
+        return qs_fail(QS_EINVAL, "amplitudes above ~2^1010 in magnitude: outside the complex128 tensor-core sweep's range");
     }
     return QS_OK;
 }

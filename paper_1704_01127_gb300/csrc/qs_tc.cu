@@ -228,31 +228,48 @@ __host__ __device__ __forceinline__ uint32_t cm_off16(int row, int k)
 // E < 25) take 32-bit funnel shifts: the round bit and the bits below it sit in
 // x = lo << (32 - sh), and the increment is [x > 2^31 - lsb] (above half, or
 // exactly half with an odd truncated value).
-__device__ __forceinline__ void mag48(double a, int E, int E7f, uint32_t &flo, uint32_t &fhi)
+__device__ uint32_t g_qs_one = 1;   // read at run time, so the multiplies below stay on the FMA pipe
+
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t imadhi(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+__device__ __forceinline__ void mag48(double a, int E, int E7f, uint32_t one, uint32_t &flo, uint32_t &fhi)
 {
     const uint32_t hi = (uint32_t)__double2hiint(a), lo = (uint32_t)__double2loint(a);
-    const int sh = E7f - (int)((hi & 0x7FFFFFFFu) >> 20);
-    uint32_t tlo, thi, inc;
+    // e = |hi| >> 20, sh = E7f - e, both on the FMA pipe
+    const uint32_t e = imadhi(hi & 0x7FFFFFFFu, one << 12);
+    const int sh = (int)imad(e, 0u - one, (uint32_t)E7f);
     if ((uint32_t)sh < 32u) {
         const uint32_t mh = (hi & 0x000FFFFFu) | 0x00100000u;
-        tlo = __funnelshift_r(lo, mh, sh);
-        thi = mh >> sh;
-        const uint32_t x = lo << (32 - sh);
-        inc = x > 0x80000000u - (tlo & 1u) ? 1u : 0u;
+        const uint32_t tlo = __funnelshift_r(lo, mh, sh);
+        const uint32_t thi = mh >> sh;
+        const uint32_t x = lo << imad((uint32_t)sh, 0u - one, 32u);
+        // carry of x + (2^31 - 1 + lsb) = [x > 2^31 - lsb]: the rounding
+        // increment, added with the digit bias in one carry chain
+        const uint32_t c1 = imad(tlo & 1u, one, 0x7FFFFFFFu);
+        asm("{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %2, %3;\n\taddc.cc.u32 %0, %4, 0x80808080;\n\taddc.u32 %1, %5, 0x8080;\n\t}"
+            : "=r"(flo), "=r"(fhi) : "r"(x), "r"(c1), "r"(tlo), "r"(thi));
     } else {
-        const int e = (int)((hi >> 20) & 0x7FF), shift = E + 7 - e;
+        const int ee = (int)((hi >> 20) & 0x7FF), shift = E + 7 - ee;
         uint64_t F = 0;
-        if (e != 0 && shift < 60) {
+        if (ee != 0 && shift < 60) {
             const uint64_t m = ((uint64_t)(hi & 0x000FFFFFu) << 32 | lo) | (1ULL << 52);
             F = (m + (1ULL << (shift - 1)) - 1 + ((m >> shift) & 1)) >> shift;
         }
-        tlo = (uint32_t)F;
-        thi = (uint32_t)(F >> 32);
-        inc = 0;
+        F += 0x808080808080ULL;
+        flo = (uint32_t)F;
+        fhi = (uint32_t)(F >> 32);
     }
-    const uint64_t F = ((uint64_t)thi << 32 | tlo) + inc + 0x808080808080ULL;
-    flo = (uint32_t)F;
-    fhi = (uint32_t)(F >> 32);
 }
 
 // Signed digit pair of one plane: the bytes (re, im) become fp16 1024 + b by a
@@ -373,6 +390,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     __shared__ int rowexp[kSplitParts][kRows];
     // exponent-field terms, added modulo 2^32 (only the sum must fit):
     __shared__ uint32_t rowX[2][kRows];   // (E_r - 2096) << 20 of the last two tiles
+    __shared__ int gext[2];               // smallest and largest G_n
     __shared__ uint32_t colX[kN];         // G_n << 20
     __shared__ volatile int abort_flag;
     __shared__ PostSmem ps;               // a phase op folded into the sweep (kPost)
@@ -390,6 +408,15 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
         }
         const int *G = reinterpret_cast<const int *>(bpack + kSlicesB * kPlaneB);
         if (tid < kN) colX[tid] = (uint32_t)G[tid] << 20;
+        if (tid == 0) {
+            int lo = 2047, hi = 0;
+            for (int n = 0; n < kN; n++) {
+                lo = min(lo, G[n]);
+                hi = max(hi, G[n]);
+            }
+            gext[0] = lo;
+            gext[1] = hi;
+        }
         if (tid < 32) moff[tid] = off5(tid, t);
         if constexpr (kPost) post_load(ps, post, tid, blockDim.x);
     }
@@ -417,6 +444,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
         // ------------------------------------------------------------ splitters
         const int row = tid & (kRows - 1), part = tid >> 7;
         const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+        const uint32_t one = *(volatile uint32_t *)&g_qs_one;
         const uint32_t stage_a = smem_u32(stage) + 16u * tid;
         // this thread's kMPT amplitudes of tile tl into its own stage slots
         // (slot x at x * kSplitThreads + tid): asynchronous, a whole iteration ahead
@@ -456,12 +484,19 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             int E = rowexp[0][row];
 #pragma unroll
             for (int q = 1; q < kSplitParts; q++) E = max(E, rowexp[q][row]);
+            // a result's exponent field is that of T (1023 .. 1085 for T != 0)
+            // plus E + G_n - 2096.  Rows below ~2^-970 take E >= 1074 - min G_n
+            // (no result leaves the normal range; they keep fewer bits, an
+            // absolute error near 2^-1015); rows whose results could pass
+            // 2^1024 (magnitudes above ~2^1010) are flagged, status bit 2
+            E = max(E, 1074 - ((volatile int *)gext)[0]);
+            if (part == 0 && E + ((volatile int *)gext)[1] > 3057) atomicOr(status, 2);
             const int E7f = E >= 25 ? E + 7 : 0x40000000;
             uint32_t glo[2 * kMPT], ghi[2 * kMPT], sgn[kMPT];
 #pragma unroll
             for (int x = 0; x < kMPT; x++) {
-                mag48(v[x].x, E, E7f, glo[2 * x], ghi[2 * x]);
-                mag48(v[x].y, E, E7f, glo[2 * x + 1], ghi[2 * x + 1]);
+                mag48(v[x].x, E, E7f, one, glo[2 * x], ghi[2 * x]);
+                mag48(v[x].y, E, E7f, one, glo[2 * x + 1], ghi[2 * x + 1]);
                 // sign bits of re (bit 15) and im (bit 31)
                 sgn[x] = __byte_perm((uint32_t)__double2hiint(v[x].x), (uint32_t)__double2hiint(v[x].y), 0x7632u) & 0x80008000u;
             }

@@ -681,6 +681,62 @@ def test_tc_c128_zero_and_tiny_rows():
     assert np.all(out[: 1 << 9] == 0)
 
 
+@pytest.mark.parametrize("targets", [[8, 9, 10, 11, 12], [0, 1, 2, 3, 4], [2, 5, 7, 10, 12]])
+def test_tc_c128_fixed_point_paths(targets):
+    """Members far below their row's largest value (the fixed point's general
+    path, gaps past 2^25 and 2^60), exact rounding ties, zeros and subnormal
+    inputs, and a state whose every row lies below 2^-998 (the general path
+    for whole rows, results down in the subnormal range): one sweep against
+    the FP64 oracle within 2^-44 of the largest input magnitude (the split
+    keeps 47 bits below each row's top), or 2^-1000 for rows below ~2^-970,
+    whose scale is raised so that no result leaves the normal double range."""
+    n = 13
+    g = np.random.Generator(np.random.PCG64(sum(targets)))
+    u = g.integers(0, 71, 1 << n)
+    psi = np.ldexp(1.0, -u) * np.exp(1j * g.uniform(0, 2 * np.pi, 1 << n))
+    # rows led by 1.0 with ties of the 2^45 fixed point: (2k + 1) 2^-46
+    lead = g.choice(1 << n, 64, replace=False)
+    psi[lead] = 1.0
+    ties = g.choice(1 << n, 512, replace=False)
+    psi[ties] = (2 * g.integers(0, 8, 512) + 1) * 2.0 ** -46 * np.where(g.random(512) < 0.5, -1, 1)
+    psi[g.choice(1 << n, 256, replace=False)] = 0
+    psi[g.choice(1 << n, 64, replace=False)] = 1e-310
+    U = random_unitary(5, 31 + targets[0])
+    tiny = random_state(n, 41) * 1e-301
+    for state in (psi, tiny):
+        ref = state.copy()
+        sim.apply_kq(ref, targets, U)
+        with State(n, qs.QS_C128) as s:
+            qs.qs_set_path(s.h, qs.QS_PATH_TENSOR)
+            qs.qs_set_amplitudes(s.h, state)
+            qs.qs_apply_cluster(s.h, targets, U)
+            out = qs.qs_get_amplitudes(s.h)
+        assert np.max(np.abs(out - ref)) <= max(2.0 ** -44 * np.max(np.abs(state)), 2.0 ** -1000), targets
+        assert np.all(np.isfinite(out))
+
+
+def test_tc_c128_out_of_range_reported():
+    """Amplitudes near 2^1016, whose results could pass the double range, are
+    reported (QS_EINVAL at the next synchronising call, once) instead of
+    returned as wrong numbers; the state then runs normal sweeps again."""
+    n = 12
+    U = random_unitary(5, 3)
+    with State(n, qs.QS_C128) as s:
+        qs.qs_set_path(s.h, qs.QS_PATH_TENSOR)
+        qs.qs_set_amplitudes(s.h, random_state(n, 4) * 2.0 ** 1022)
+        qs.qs_apply_cluster(s.h, [7, 8, 9, 10, 11], U)
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_synchronize(s.h)
+        assert e.value.code == qs.QS_EINVAL
+        qs.qs_synchronize(s.h)
+        psi = random_state(n, 5)
+        ref = psi.copy()
+        sim.apply_kq(ref, [7, 8, 9, 10, 11], U)
+        qs.qs_set_amplitudes(s.h, psi)
+        qs.qs_apply_cluster(s.h, [7, 8, 9, 10, 11], U)
+        assert np.max(np.abs(qs.qs_get_amplitudes(s.h) - ref)) < SWEEP_TOL[qs.QS_C128]
+
+
 def test_entropy_table_log_accuracy():
     """The table-driven logarithm of the entropy reduction against libm on
     probabilities spread over many binades (closed form: -sum p ln p)."""
