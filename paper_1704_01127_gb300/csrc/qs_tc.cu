@@ -223,7 +223,8 @@ __host__ __device__ __forceinline__ uint32_t cm_off16(int row, int k)
 // |F| of a double relative to biased row exponent E, rounded half to even (the
 // structured amplitudes of early circuit layers hit exact ties often, and
 // rounding ties up would bias the norm), plus the digit bias 0x808080808080, as
-// two 32-bit words.  Members within 2^25 of the row's largest value (sh < 32;
+// two 32-bit words; the high word also gets 0x6464 in its top bytes (|F| + bias
+// < 2^48), the fp16 exponent byte its two digit planes pair with.  Members within 2^25 of the row's largest value (sh < 32;
 // E7f = E + 7, or a value that sends every member to the general path when
 // E < 25) take 32-bit funnel shifts: the round bit and the bits below it sit in
 // x = lo << (32 - sh), and the increment is [x > 2^31 - lsb] (above half, or
@@ -257,7 +258,7 @@ __device__ __forceinline__ void mag48(double a, int E, int E7f, uint32_t one, ui
         // carry of x + (2^31 - 1 + lsb) = [x > 2^31 - lsb]: the rounding
         // increment, added with the digit bias in one carry chain
         const uint32_t c1 = imad(tlo & 1u, one, 0x7FFFFFFFu);
-        asm("{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %2, %3;\n\taddc.cc.u32 %0, %4, 0x80808080;\n\taddc.u32 %1, %5, 0x8080;\n\t}"
+        asm("{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %2, %3;\n\taddc.cc.u32 %0, %4, 0x80808080;\n\taddc.u32 %1, %5, 0x64648080;\n\t}"
             : "=r"(flo), "=r"(fhi) : "r"(x), "r"(c1), "r"(tlo), "r"(thi));
     } else {
         const int ee = (int)((hi >> 20) & 0x7FF), shift = E + 7 - ee;
@@ -266,10 +267,19 @@ __device__ __forceinline__ void mag48(double a, int E, int E7f, uint32_t one, ui
             const uint64_t m = ((uint64_t)(hi & 0x000FFFFFu) << 32 | lo) | (1ULL << 52);
             F = (m + (1ULL << (shift - 1)) - 1 + ((m >> shift) & 1)) >> shift;
         }
-        F += 0x808080808080ULL;
+        F += 0x6464808080808080ULL;
         flo = (uint32_t)F;
         fhi = (uint32_t)(F >> 32);
     }
+}
+
+// The same from two words whose bytes 3 are 0x64 (the high words of |F| + bias)
+__device__ __forceinline__ uint32_t f16x2_sdigits2(uint32_t w0, uint32_t w1, uint32_t sel, uint32_t sg, uint32_t nsg)
+{
+    uint32_t r;
+    const uint32_t w = __byte_perm(w0, w1, sel);
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(w), "r"(sg), "r"(nsg));
+    return r;
 }
 
 // Signed digit pair of one plane: the bytes (re, im) become fp16 1024 + b by a
@@ -502,10 +512,6 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             }
             // tile it-1's MMAs (both halves) must have finished reading the planes
             const bool ok = it == 0 || mbar_wait_bounded(smem_u32(&mbar_mma[1]), (it - 1) & 1);
-            if (bar_split_or(!ok || abort_flag)) {
-                if (tid == 0) atomicExch(status, 1);
-                break;
-            }
             // tile it-1's half-1 MMAs were issued after the epilogue had read
             // tile it-2's scale, so slot it & 1 is free
             if (part == 0) rowX[it & 1][row] = (uint32_t)(E - 2096) << 20;
@@ -516,12 +522,13 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const int x = 4 * c + j;           // words 2x (re), 2x+1 (im)
-                    const uint32_t yh = __byte_perm(ghi[2 * x], ghi[2 * x + 1], 0x5410u);
                     const uint32_t y23 = __byte_perm(glo[2 * x], glo[2 * x + 1], 0x7632u);
                     const uint32_t y01 = __byte_perm(glo[2 * x], glo[2 * x + 1], 0x5410u);
                     const uint32_t sg = sgn[x] | 0x3C003C00u, nsg = sgn[x] ^ 0xE480E480u;   // +-1, -+1152
-                    pl[0][j] = f16x2_sdigits(yh, 0x4341u, sg, nsg);    // byte 5 of |F|
-                    pl[1][j] = f16x2_sdigits(yh, 0x4240u, sg, nsg);    // byte 4
+                    // the high words carry 0x64 in their top bytes: bytes 5 and 4
+                    // of |F| pair with it directly
+                    pl[0][j] = f16x2_sdigits2(ghi[2 * x], ghi[2 * x + 1], 0x7531u, sg, nsg);   // byte 5 of |F|
+                    pl[1][j] = f16x2_sdigits2(ghi[2 * x], ghi[2 * x + 1], 0x7430u, sg, nsg);   // byte 4
                     pl[2][j] = f16x2_sdigits(y23, 0x4341u, sg, nsg);   // byte 3
                     pl[3][j] = f16x2_sdigits(y23, 0x4240u, sg, nsg);   // byte 2
                     pl[4][j] = f16x2_sdigits(y01, 0x4341u, sg, nsg);   // byte 1
@@ -532,7 +539,12 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
                     *reinterpret_cast<uint4 *>(dst + sl * kPlaneA) = make_uint4(pl[sl][0], pl[sl][1], pl[sl][2], pl[sl][3]);
             }
             fence_proxy_async();
-            bar_split();
+            // every splitter has written its planes (and seen tile it-1's MMAs
+            // finish, or the abort)
+            if (bar_split_or(!ok || abort_flag)) {
+                if (tid == 0) atomicExch(status, 1);
+                break;
+            }
             if (tid == 0) mbar_arrive(smem_u32(&mbar_planes));   // planes of tile it are written
         }
         cp_async_wait_all();
