@@ -334,7 +334,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 //     few instructions ahead, so the issuing thread waits about as long as
 //     the MMAs run (~4K cycles a tile); on its own warp that wait holds up
 //     no splitter (issued by splitter thread 0: 10.2 ms per 30-qubit sweep,
-//     here 8.35 ms together with the arithmetic below);
+//     here 8.2 ms together with the arithmetic below);
 //   epilogue (384 threads, three warps per TMEM lane quarter, 3 + 3 + 2 and
 //     2 + 3 + 3 four-column chunks of the two halves): rebuild FP64 results
 //     from the accumulators and store them.
