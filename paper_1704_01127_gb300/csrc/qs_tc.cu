@@ -326,15 +326,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 // ----------------------------------------------------------------------------
 // complex128 kernel: one CTA per SM, three warp-specialised groups:
 //   splitters (512 threads, kSplitThreads / 128 per row, kMPT amplitudes
-//     each): copy tile t+1 into a 64 KB stage with cp.async while tile t is
-//     processed; find the row exponents and the fixed-point values of tile t
-//     while the MMAs of tile t-1 still read the digit planes, then write the
-//     planes;
+//     each): copy tile t+1 into a 64 KB stage while tile t is processed
+//     (kBulk: full-state tiles whose member runs are 2 KB, as 32 bulk copies
+//     from lane 0 of each splitter warp once the stage is read; otherwise
+//     16-byte cp.async of each thread's own slots, which hold the issuing
+//     warps up ~3K cycles a tile); find the row exponents and the fixed-point
+//     values of tile t while the MMAs of tile t-1 still read the digit planes,
+//     then write the planes;
 //   issuer (one warp, one thread): issues the MMAs.  The tensor pipe takes
 //     few instructions ahead, so the issuing thread waits about as long as
 //     the MMAs run (~4K cycles a tile); on its own warp that wait holds up
 //     no splitter (issued by splitter thread 0: 10.2 ms per 30-qubit sweep,
-//     here 8.2 ms together with the arithmetic below);
+//     here 7.9 ms together with the arithmetic below and the bulk copies);
 //   epilogue (384 threads, three warps per TMEM lane quarter, 3 + 3 + 2 and
 //     2 + 3 + 3 four-column chunks of the two halves): rebuild FP64 results
 //     from the accumulators and store them.
@@ -374,6 +377,16 @@ __device__ __forceinline__ void issue_c128_half(uint32_t tmem, uint32_t a0, uint
     }
 }
 
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
 // 16-byte asynchronous global -> shared copy (zero fill when bytes = 0)
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *gptr, uint32_t bytes)
 {
@@ -385,7 +398,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr size_t kStageC128 = (size_t)kSplitThreads * kMPT * 16;   // raw next tile: 64 KB
 constexpr size_t kSmemC128Pipe = kSmemC128 + kStageC128;
 
-template <bool kPost>
+template <bool kPost, bool kBulk>
 __global__ void __launch_bounds__(kC128Threads, 1)
 k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const uint8_t *__restrict__ bpack,
                       const qs_post_phase *__restrict__ post, int *__restrict__ status)
@@ -394,7 +407,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     uint8_t *A = smem;
     uint8_t *B = smem + kSlices * kPlaneA;
     uint4 *stage = reinterpret_cast<uint4 *>(smem + kSmemC128);   // [8][512] x 16 B
-    __shared__ __align__(8) uint64_t mbar_mma[2], mbar_free[2], mbar_planes;
+    __shared__ __align__(8) uint64_t mbar_mma[2], mbar_free[2], mbar_planes, mbar_full;
     __shared__ uint64_t moff[32];         // offset of member x within a group
     __shared__ uint32_t tmem_base_s;
     __shared__ int rowexp[kSplitParts][kRows];
@@ -440,6 +453,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             mbar_init(smem_u32(&mbar_free[h]), kEpiThreads);
         }
         mbar_init(smem_u32(&mbar_planes), 1);
+        mbar_init(smem_u32(&mbar_full), kSplitThreads / 32);
         fence_mbar_init();
         abort_flag = 0;
     }
@@ -469,10 +483,36 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             }
             cp_async_commit();
         };
-        prefetch(blockIdx.x);
+        // full-state tiles whose rows are 128 consecutive amplitudes (every
+        // target >= 7): member m is one 2 KB run, copied by lane 0 of splitter
+        // warp m >> 1 into slots (m & 7) of splitters 128 (m >> 3) .. + 127
+        // (kBulk: the launcher checked that every tile is such a full-state tile)
+        constexpr bool bulk = kBulk;
+        const uint32_t mfull = smem_u32(&mbar_full), stage_s = smem_u32(stage);
+        auto fill = [&](uint64_t tl) {
+            if ((tid & 31) == 0) {
+                const double2 *tb = psi + tile_base(tl * kRows, t);
+                mbar_arrive_expect_tx(mfull, 4096u);
+                for (int m = 2 * (tid >> 5); m < 2 * (tid >> 5) + 2; m++)
+                    bulk_g2s(stage_s + 8192u * (m & 7) + 2048u * (m >> 3), tb + moff[m], 2048u, mfull);
+            }
+        };
+        int pending = -1;   // tile whose bulk copies are in flight
+        if constexpr (bulk) {
+            fill(blockIdx.x);
+            pending = 0;
+        } else {
+            prefetch(blockIdx.x);
+        }
         int it = 0;
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, it++) {
-            cp_async_wait_all();
+            bool full_ok = true;
+            if constexpr (bulk) {
+                full_ok = mbar_wait_bounded(mfull, it & 1);
+                if (full_ok) pending = -1;
+            } else {
+                cp_async_wait_all();
+            }
             double2 v[kMPT];
 #pragma unroll
             for (int x = 0; x < kMPT; x++) {
@@ -488,9 +528,24 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             // emax depends on every slot read above, so the shared loads are
             // complete before the next tile's copies may overwrite the slots
             asm volatile("" ::"r"(emax) : "memory");
-            prefetch(tile + gridDim.x);
+            if constexpr (!bulk) prefetch(tile + gridDim.x);
             rowexp[part][row] = (int)(emax >> 20);
-            bar_split();
+            if constexpr (bulk) {
+                if (bar_split_or(!full_ok || abort_flag)) {
+                    if (tid == 0) atomicExch(status, 1);
+                    abort_flag = 1;
+                    break;
+                }
+            } else {
+                bar_split();
+            }
+            // every splitter has read the stage: the next tile's runs
+            if constexpr (bulk) {
+                if (tile + gridDim.x < n_tiles) {
+                    fill(tile + gridDim.x);
+                    pending = it + 1;
+                }
+            }
             int E = rowexp[0][row];
 #pragma unroll
             for (int q = 1; q < kSplitParts; q++) E = max(E, rowexp[q][row]);
@@ -548,6 +603,8 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             if (tid == 0) mbar_arrive(smem_u32(&mbar_planes));   // planes of tile it are written
         }
         cp_async_wait_all();
+        // bulk copies still in flight land before the CTA leaves
+        if (pending >= 0) mbar_wait_bounded(mfull, pending & 1);
     } else if (tid >= kSplitThreads + kEpiThreads) {
         // ---------------------------------------------------------------- issuer
         if (tid == kSplitThreads + kEpiThreads) {
@@ -689,6 +746,7 @@ __global__ void k_wait_selftest(int *__restrict__ status, long polls)
 }
 
 bool g_attr_set[2][2][64] = {};   // [complex64][folded phase][device]
+bool g_attr_bulk[2][64] = {};     // complex128 bulk-copy instantiations: [folded phase][device]
 
 }  // namespace
 
@@ -799,8 +857,8 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
     if (dev < 0 || dev >= 64) return qs_fail(QS_EUNSUPPORTED, "device %d", dev);
     if (!g_attr_set[c64][fold][dev]) {
         const void *fn = c64 ? (fold ? (const void *)k_dense5_tc_c64<true> : (const void *)k_dense5_tc_c64<false>)
-                             : (fold ? (const void *)k_dense5_tc_c128_pipe<true>
-                                     : (const void *)k_dense5_tc_c128_pipe<false>);
+                             : (fold ? (const void *)k_dense5_tc_c128_pipe<true, false>
+                                     : (const void *)k_dense5_tc_c128_pipe<false, false>);
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(c64 ? kSmemF32 : kSmemC128Pipe));
         if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
@@ -830,6 +888,16 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
     t.pairs = c64 && t.q[0] == 0 && ((uintptr_t)s->amp & 15) == 0;
     const uint64_t groups = 1ULL << __builtin_popcountll(G);
     const uint64_t tiles = (groups + kRows - 1) / kRows;
+    // complex128 tiles of 128 consecutive amplitudes per member (no inserted
+    // bit below bit 7), all members read: bulk copies of the stage
+    const bool bulk = !c64 && (t.zmask & 0x7Full) == 0 && groups % kRows == 0 && t.mmask == 0xFFFFFFFFu;
+    if (bulk && !g_attr_bulk[fold][dev]) {
+        cudaError_t e = cudaFuncSetAttribute(fold ? (const void *)k_dense5_tc_c128_pipe<true, true>
+                                                  : (const void *)k_dense5_tc_c128_pipe<false, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemC128Pipe);
+        if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
+        g_attr_bulk[fold][dev] = true;
+    }
     int *status;
     int rc = qs_state_status(s, &status);
     if (rc) return rc;
@@ -845,12 +913,10 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
                                                                  (const float *)dev_pack, post, status);
     } else {
         int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms);
-        if (fold)
-            k_dense5_tc_c128_pipe<true><<<grid, kC128Threads, kSmemC128Pipe, st>>>(
-                (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, post, status);
-        else
-            k_dense5_tc_c128_pipe<false><<<grid, kC128Threads, kSmemC128Pipe, st>>>(
-                (double2 *)s->amp, groups, t, (const uint8_t *)dev_pack, post, status);
+        auto *fn = fold ? (bulk ? k_dense5_tc_c128_pipe<true, true> : k_dense5_tc_c128_pipe<true, false>)
+                        : (bulk ? k_dense5_tc_c128_pipe<false, true> : k_dense5_tc_c128_pipe<false, false>);
+        fn<<<grid, kC128Threads, kSmemC128Pipe, st>>>((double2 *)s->amp, groups, t, (const uint8_t *)dev_pack,
+                                                     post, status);
     }
     // amplitudes on the padding targets of an embedded cluster keep their
     // fixed values (U (x) 1 leaves zero inputs zero), so only the cluster's own
