@@ -580,11 +580,37 @@ int stats_impl(qs_state *s, double *out, int nstat)
     return QS_OK;
 }
 
+// The state's second stream and its fork/join events, made on first use.
+int side_stream(qs_state *s, cudaStream_t *out)
+{
+    if (!s->side) {
+        cudaStream_t ss;
+        QS_CUDA(cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking), "side stream");
+        cudaEvent_t e[2];
+        for (int i = 0; i < 2; i++) {
+            cudaError_t err = cudaEventCreateWithFlags(&e[i], cudaEventDisableTiming);
+            if (err != cudaSuccess) {
+                for (int j = 0; j < i; j++) cudaEventDestroy(e[j]);
+                cudaStreamDestroy(ss);
+                return cuda_fail(err, "side stream events");
+            }
+        }
+        s->side = ss;
+        s->side_ev[0] = e[0];
+        s->side_ev[1] = e[1];
+    }
+    *out = (cudaStream_t)s->side;
+    return QS_OK;
+}
+
 // stats (optional): also the statistics of qs_stats.  complex64 states with
 // blocks of 1024 take them from the same pass over the state as the block sums
-// (33.9 ms instead of 7.6 + 29.4 ms for 2^20 draws at 32 qubits); otherwise
-// stats_impl runs first (complex128: the fused pass measured 28.6 ms against
-// 7.2 + 19.7 ms, its FP64 and FP32 work not overlapping).
+// (33.9 ms instead of 7.6 + 29.4 ms for 2^20 draws at 32 qubits).  complex128
+// states with blocks of 1024 run the statistics pass (FP32 pipe) on a second
+// stream beside the block sums (FP64 pipe), forked from and joined to the
+// state's stream (one kernel doing both measured 28.6 ms against 7.2 + 19.7
+// ms, its FP64 and FP32 work not overlapping); otherwise stats_impl runs
+// first.
 template <typename C>
 int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double *stats)
 {
@@ -595,11 +621,16 @@ int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double *st
     const int gb = (int)std::min<uint64_t>((nb * 32 + 255) / 256, (uint64_t)sms * 16);
     constexpr bool c64 = sizeof(C) == 8;
     const bool fused = c64 && stats && B == 1024;
-    if (stats && !fused)
+    const bool beside = !c64 && stats && B == 1024;
+    if (stats && !fused && !beside)
         if (int rc = stats_impl<C>(s, stats, 4)) return rc;
-    cudaStream_t st = (cudaStream_t)s->stream;
-    if (fused)
+    cudaStream_t st = (cudaStream_t)s->stream, ss = nullptr;
+    if (fused || beside)
         if (int rc = ensure_fflog(st)) return rc;
+    if (beside)
+        if (int rc = side_stream(s, &ss)) return rc;
+    const int sgrid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)sms * 4);   // stats_impl's grid
+    const size_t stats_bytes = beside ? sizeof(double) * ((size_t)sgrid + 1) * 4 : 0;
     const size_t m_slots = (size_t)std::max<int64_t>(m, 1);
     size_t bytes = sizeof(double) * (2 * nb + 2 * ns) + sizeof(uint64_t) * m_slots;
     if (fused) bytes += sizeof(double) * ((size_t)gb * 4 + 4);
@@ -608,19 +639,30 @@ int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double *st
     // for them, the draws scan the block as before (the same outcomes)
     bool search = !c64 && B == 1024 && m > 0;
     void *scr = nullptr;
-    int rc = qs_state_scratch(s, bytes + (search ? sizeof(double) * N : 0), &scr);
+    int rc = qs_state_scratch(s, bytes + stats_bytes + (search ? sizeof(double) * N : 0), &scr);
     if (rc && search) {
         cudaGetLastError();   // the failed allocation is not an error of the later launches
         search = false;
-        rc = qs_state_scratch(s, bytes, &scr);
+        rc = qs_state_scratch(s, bytes + stats_bytes, &scr);
     }
     if (rc) return rc;
+    // the statistics' partial sums at the end of the scratch
+    double *spart = (double *)((char *)scr + bytes + (search ? sizeof(double) * N : 0));
+    double *sres = spart + (size_t)sgrid * 4;
     double *P = (double *)scr;                       // probabilities, then running sums
     if (search) scr = (void *)(P + N);
     double *S = (double *)scr, *R = S + nb, *T = R + nb, *Q = T + ns;
     uint64_t *dout = (uint64_t *)(Q + ns);
     double *part = (double *)(dout + m_slots), *res = part + (size_t)gb * 4;
     const C *psi = (const C *)s->amp;
+    if (beside) {
+        QS_CUDA(cudaEventRecord((cudaEvent_t)s->side_ev[0], st), "side fork");
+        QS_CUDA(cudaStreamWaitEvent(ss, (cudaEvent_t)s->side_ev[0], 0), "side fork");
+        k_stats_partial<C, 4><<<sgrid, 256, 0, ss>>>(psi, N, spart);
+        k_stats_final<4><<<1, 32, 0, ss>>>(spart, sgrid, sres);
+        QS_CUDA(cudaGetLastError(), "stats launch");
+        QS_CUDA(cudaEventRecord((cudaEvent_t)s->side_ev[1], ss), "side join");
+    }
     if (fused) {
         if constexpr (c64) k_segment_sums_stats<C><<<gb, 256, 0, st>>>(psi, nb, S, part);
         k_stats_final<4><<<1, 32, 0, st>>>(part, gb, res);
@@ -655,8 +697,12 @@ int sample_impl(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double *st
         QS_CUDA(cudaMemcpyAsync(out, dout, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, st), "sample copy");
     if (fused)
         QS_CUDA(cudaMemcpyAsync(stats, res, sizeof(double) * 4, cudaMemcpyDeviceToHost, st), "stats copy");
+    if (beside) {
+        QS_CUDA(cudaStreamWaitEvent(st, (cudaEvent_t)s->side_ev[1], 0), "side join");
+        QS_CUDA(cudaMemcpyAsync(stats, sres, sizeof(double) * 4, cudaMemcpyDeviceToHost, st), "stats copy");
+    }
     QS_CUDA(cudaStreamSynchronize(st), "sampling sync");
-    if (fused) stats[3] *= (double)N;   // mean of (N p)^2 = N sum p^2
+    if (fused || beside) stats[3] *= (double)N;   // mean of (N p)^2 = N sum p^2
     return QS_OK;
 }
 
@@ -780,6 +826,12 @@ extern "C" void qs_free(qs_state *s)
     if (s->scratch) cudaFree(s->scratch);
     if (s->pinned) cudaFreeHost(s->pinned);
     if (s->status) cudaFree(s->status);
+    if (s->side) {
+        cudaStreamSynchronize((cudaStream_t)s->side);
+        cudaStreamDestroy((cudaStream_t)s->side);
+    }
+    for (void *e : s->side_ev)
+        if (e) cudaEventDestroy((cudaEvent_t)e);
     delete s;
 }
 

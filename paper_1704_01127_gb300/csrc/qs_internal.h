@@ -44,6 +44,8 @@ struct qs_state {
     void *pinned = nullptr;       // small pinned host buffer for results
     size_t pinned_bytes = 0;
     int *status = nullptr;        // device word set by kernels whose bounded waits ran out
+    void *side = nullptr;         // cudaStream_t: a second stream for work that overlaps the main one
+    void *side_ev[2] = {nullptr, nullptr};   // cudaEvent_t: fork and join of that stream
     int path = 0;                 // QS_PATH_*
     bool fold_phase = true;       // qs_set_phase_fold
     bool pair_sweeps = false;     // qs_set_pair_sweeps
