@@ -203,7 +203,10 @@ int qs_sample(qs_state *s, uint64_t seed, int64_t m, uint64_t *out);
  * for bit, and the same statistics up to the order of their float-float sums
  * (relative differences near 1e-15).  For complex64 states of 10 qubits or
  * more one pass over the state forms both the block sums of the draws and the
- * statistics; otherwise the statistics take their own pass first.  out: m
+ * statistics; complex128 states of 10 qubits or more run qs_stats' pass on a
+ * second stream of the state beside the block sums (forked from and joined to
+ * the state's stream before the call returns; the statistics then equal
+ * qs_stats' exactly); smaller states take the statistics first.  out: m
  * uint64 in host memory; stats: 4 host doubles as qs_stats.  Errors as
  * qs_stats. */
 int qs_sample_stats(qs_state *s, uint64_t seed, int64_t m, uint64_t *out, double stats[4]);
