@@ -347,6 +347,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 //   B:    4 KB blocks (half h, plane j) at (7 h + j) * 4 KB, so for A plane i
 //         one MMA with N = 32 (7 - i) reads B planes 0..6-i of half h and
 //         writes D_i..D_6 of that half (24 MMAs per half, 48 per tile).
+// kSub (a sweep that widens the support: only M = 2^m of the 32 members of
+// a group can be nonzero): those members take K positions 0 .. M-1 (B's K
+// positions permuted to match when it is copied in), splitters whose K
+// positions all lie past M keep zero planes and only join the barriers, and
+// each half takes ceil(M / 8) K steps per A plane instead of 4.  Every
+// accumulator sum is an exact integer, so the order of K changes no bit.
 // Hand-offs per tile: mbar_planes (splitter thread 0 after the planes are
 // written), mbar_mma[h] (tcgen05.commit after half h's MMAs; half 1's also
 // releases the A planes), mbar_free[h] (one arrival per epilogue thread when
@@ -363,13 +369,14 @@ __host__ __device__ constexpr uint32_t idesc_f16_n(int n)
     return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 }
 
-__device__ __forceinline__ void issue_c128_half(uint32_t tmem, uint32_t a0, uint32_t b0, int h)
+__device__ __forceinline__ void issue_c128_half(uint32_t tmem, uint32_t a0, uint32_t b0, int h, int nks)
 {
     const uint64_t da = smem_desc(a0, kSBO16), db = smem_desc(b0 + h * kSlicesB * kBlockB, kSBO16);
 #pragma unroll
     for (int i = 0; i < kSlices; i++) {
 #pragma unroll
         for (int ks = 0; ks < kK / 16; ks++) {
+            if (ks >= nks) break;   // K columns past the support's members are zero
             const uint32_t koff = ks * 2 * kLBO;
             mma_f16(tmem + 256 * h + kHalfN * i, da + ((uint64_t)(i * kPlaneA + koff) >> 4),
                      db + ((uint64_t)koff >> 4), idesc_f16_n(kHalfN * (kDiags - i)), (i == 0 && ks == 0) ? 0u : 1u);
@@ -398,7 +405,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr size_t kStageC128 = (size_t)kSplitThreads * kMPT * 16;   // raw next tile: 64 KB
 constexpr size_t kSmemC128Pipe = kSmemC128 + kStageC128;
 
-template <bool kPost, bool kBulk>
+template <bool kPost, bool kBulk, bool kSub>
 __global__ void __launch_bounds__(kC128Threads, 1)
 k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const uint8_t *__restrict__ bpack,
                       const qs_post_phase *__restrict__ post, int *__restrict__ status)
@@ -409,6 +416,8 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     uint4 *stage = reinterpret_cast<uint4 *>(smem + kSmemC128);   // [8][512] x 16 B
     __shared__ __align__(8) uint64_t mbar_mma[2], mbar_free[2], mbar_planes, mbar_full;
     __shared__ uint64_t moff[32];         // offset of member x within a group
+    __shared__ uint64_t ioff[32];         // kSub: offset of the member at K position x (support members first)
+    __shared__ int perm[32];              // kSub: member at K position x
     __shared__ uint32_t tmem_base_s;
     __shared__ int rowexp[kSplitParts][kRows];
     // exponent-field terms, added modulo 2^32 (only the sum must fit):
@@ -419,7 +428,27 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     __shared__ PostSmem ps;               // a phase op folded into the sweep (kPost)
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    {
+    // kSub: M = 2^m of the 32 members lie in the support (the others read as
+    // zero); they take K positions 0 .. M-1, in order, and the rows of B^T
+    // follow them, so only the first M K positions of A can be nonzero
+    const int M = kSub ? __popc(t.mmask) : 32;
+    if constexpr (kSub) {
+        if (tid < 32) {
+            const uint32_t below = (1u << tid) - 1u;
+            perm[(t.mmask >> tid) & 1 ? __popc(t.mmask & below) : M + __popc(~t.mmask & below)] = tid;
+        }
+        __syncthreads();
+        if (tid < 32) ioff[tid] = off5(perm[tid], t);
+        // plane-major pack -> half-major blocks, K positions permuted (a
+        // member's two reals are one 4-byte word)
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(bpack);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(B);
+        for (int i = tid; i < kSlicesB * 2 * 1024; i += blockDim.x) {
+            const int blk = i >> 10, n = (i >> 5) & 31, x = i & 31;   // source block 2 j + h, row n, K position x
+            const int j = blk >> 1, h = blk & 1;
+            dst[((h * kSlicesB + j) * kBlockB + cm_off16(n, 2 * x)) >> 2] = src[(blk * kBlockB + cm_off16(n, 2 * perm[x])) >> 2];
+        }
+    } else {
         // plane-major pack (plane j = halves 0, 1) -> half-major blocks
         const uint4 *src = reinterpret_cast<const uint4 *>(bpack);
         uint4 *dst = reinterpret_cast<uint4 *>(B);
@@ -429,6 +458,8 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             const int j = blk >> 1, h = blk & 1;
             dst[(h * kSlicesB + j) * kPerBlock + w] = src[i];
         }
+    }
+    {
         const int *G = reinterpret_cast<const int *>(bpack + kSlicesB * kPlaneB);
         if (tid < kN) colX[tid] = (uint32_t)G[tid] << 20;
         if (tid == 0) {
@@ -464,7 +495,21 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     const uint32_t tmem = tmem_base_s;
     const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
 
-    if (tid < kSplitThreads) {
+    if (kSub && tid < kSplitThreads && kMPT * (tid >> 7) >= M) {
+        // ------------------------------------------------- idle splitters (kSub)
+        // K positions kMPT part .. + kMPT-1 are past M: zero planes, written
+        // once; then only the splitters' barriers, tile by tile
+        const int row = tid & (kRows - 1), part = tid >> 7;
+        for (int c = 0; c < kMPT / 4; c++)
+            for (int sl = 0; sl < kSlices; sl++)
+                *reinterpret_cast<uint4 *>(A + cm_off16(row, 2 * kMPT * part + 8 * c) + sl * kPlaneA) = make_uint4(0u, 0u, 0u, 0u);
+        fence_proxy_async();
+        for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            rowexp[part][row] = 0;
+            bar_split();
+            if (bar_split_or(abort_flag)) break;
+        }
+    } else if (tid < kSplitThreads) {
         // ------------------------------------------------------------ splitters
         const int row = tid & (kRows - 1), part = tid >> 7;
         const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
@@ -478,8 +523,9 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             const double2 *pp = psi + (val ? tile_base(g, t) : 0);
 #pragma unroll
             for (int x = 0; x < kMPT; x++) {
-                const bool vx = val && ((t.mmask >> (kMPT * part + x)) & 1);   // members outside the support are zero
-                cp_async16(stage_a + 16u * kSplitThreads * x, vx ? pp + moff[kMPT * part + x] : psi, vx ? 16u : 0u);
+                // kSub: K positions past M are members outside the support (zero)
+                const bool vx = val && (!kSub || kMPT * part + x < M);
+                cp_async16(stage_a + 16u * kSplitThreads * x, vx ? pp + (kSub ? ioff : moff)[kMPT * part + x] : psi, vx ? 16u : 0u);
             }
             cp_async_commit();
         };
@@ -627,7 +673,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
                         break;
                     }
                     tc_fence_after();
-                    issue_c128_half(tmem, a0, b0, h);
+                    issue_c128_half(tmem, a0, b0, h, (M + 7) >> 3);
                     mma_commit(smem_u32(&mbar_mma[h]));
                 }
                 if (!ok) break;
@@ -745,8 +791,9 @@ __global__ void k_wait_selftest(int *__restrict__ status, long polls)
     if (!done) atomicExch(status, 1);
 }
 
-bool g_attr_set[2][2][64] = {};   // [complex64][folded phase][device]
-bool g_attr_bulk[2][64] = {};     // complex128 bulk-copy instantiations: [folded phase][device]
+bool g_attr_c64[2][64] = {};       // [folded phase][device]
+bool g_attr_c128[2][3][64] = {};   // [folded phase][staging mode][device]
+using C128Kernel = void (*)(double2 *, uint64_t, TileLayout, const uint8_t *, const qs_post_phase *, int *);
 
 }  // namespace
 
@@ -855,14 +902,11 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (dev < 0 || dev >= 64) return qs_fail(QS_EUNSUPPORTED, "device %d", dev);
-    if (!g_attr_set[c64][fold][dev]) {
-        const void *fn = c64 ? (fold ? (const void *)k_dense5_tc_c64<true> : (const void *)k_dense5_tc_c64<false>)
-                             : (fold ? (const void *)k_dense5_tc_c128_pipe<true, false>
-                                     : (const void *)k_dense5_tc_c128_pipe<false, false>);
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(c64 ? kSmemF32 : kSmemC128Pipe));
+    if (c64 && !g_attr_c64[fold][dev]) {
+        const void *fn = fold ? (const void *)k_dense5_tc_c64<true> : (const void *)k_dense5_tc_c64<false>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF32);
         if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
-        g_attr_set[c64][fold][dev] = true;
+        g_attr_c64[fold][dev] = true;
     }
     // the sweep covers the support after it: the support's free bits plus the
     // targets; groups enumerate the free bits that are not targets
@@ -891,12 +935,23 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
     // complex128 tiles of 128 consecutive amplitudes per member (no inserted
     // bit below bit 7), all members read: bulk copies of the stage
     const bool bulk = !c64 && (t.zmask & 0x7Full) == 0 && groups % kRows == 0 && t.mmask == 0xFFFFFFFFu;
-    if (bulk && !g_attr_bulk[fold][dev]) {
-        cudaError_t e = cudaFuncSetAttribute(fold ? (const void *)k_dense5_tc_c128_pipe<true, true>
-                                                  : (const void *)k_dense5_tc_c128_pipe<false, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemC128Pipe);
-        if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
-        g_attr_bulk[fold][dev] = true;
+    // complex128 staging: 0 cp.async (every member in the support), 1 bulk
+    // copies, 2 members outside the support (compacted, fewer K steps)
+    const int mode = bulk ? 1 : t.mmask != 0xFFFFFFFFu ? 2 : 0;
+    C128Kernel c128 = nullptr;
+    if (!c64) {
+        static const C128Kernel fns[2][3] = {
+            {k_dense5_tc_c128_pipe<false, false, false>, k_dense5_tc_c128_pipe<false, true, false>,
+             k_dense5_tc_c128_pipe<false, false, true>},
+            {k_dense5_tc_c128_pipe<true, false, false>, k_dense5_tc_c128_pipe<true, true, false>,
+             k_dense5_tc_c128_pipe<true, false, true>}};
+        c128 = fns[fold][mode];
+        if (!g_attr_c128[fold][mode][dev]) {
+            cudaError_t e = cudaFuncSetAttribute((const void *)c128, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kSmemC128Pipe);
+            if (e != cudaSuccess) return qs_fail(QS_ECUDA, "tc smem attribute: %s", cudaGetErrorString(e));
+            g_attr_c128[fold][mode][dev] = true;
+        }
     }
     int *status;
     int rc = qs_state_status(s, &status);
@@ -913,10 +968,8 @@ int qs_launch_dense5_tc(qs_state *s, const int *sorted_qubits, const void *dev_p
                                                                  (const float *)dev_pack, post, status);
     } else {
         int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms);
-        auto *fn = fold ? (bulk ? k_dense5_tc_c128_pipe<true, true> : k_dense5_tc_c128_pipe<true, false>)
-                        : (bulk ? k_dense5_tc_c128_pipe<false, true> : k_dense5_tc_c128_pipe<false, false>);
-        fn<<<grid, kC128Threads, kSmemC128Pipe, st>>>((double2 *)s->amp, groups, t, (const uint8_t *)dev_pack,
-                                                     post, status);
+        c128<<<grid, kC128Threads, kSmemC128Pipe, st>>>((double2 *)s->amp, groups, t, (const uint8_t *)dev_pack,
+                                                       post, status);
     }
     // amplitudes on the padding targets of an embedded cluster keep their
     // fixed values (U (x) 1 leaves zero inputs zero), so only the cluster's own

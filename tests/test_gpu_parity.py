@@ -715,6 +715,45 @@ def test_tc_c128_fixed_point_paths(targets):
         assert np.all(np.isfinite(out))
 
 
+@pytest.mark.parametrize("x, clusters", [
+    # the support after |x> grows by the qubits a cluster touches first: 5 new
+    # (1 member of 32 in the support), then 1 (qubit 0, every other member),
+    # 2, 3 (members scattered over the group), 4, and an embedded 3-qubit
+    # cluster whose padding qubits lie outside the support
+    (0x2D6B, [(3, 7, 9, 12, 14), (0, 3, 7, 9, 12), (1, 9, 12, 14, 15), (0, 2, 5, 6, 7),
+              (4, 8, 10, 11, 15), (1, 13, 2), (13, 14, 15, 0, 1)]),
+    (0, [(11, 12, 13, 14, 15), (6, 11, 12, 13, 14), (4, 5, 6, 7, 8), (0, 1, 2, 3, 4)]),
+    (0xFFFF, [(0, 1, 2, 3, 4), (2, 3, 4, 5, 6), (5, 6, 7, 8, 9), (9, 10, 14), (11, 12, 13, 15, 0)]),
+])
+def test_tc_c128_support_growth_is_bit_exact(x, clusters):
+    """complex128 sweeps that widen the support after qs_init_basis: only the
+    members inside the support are split (compacted to the first K positions,
+    the unitary's K positions permuted to match) and fewer K steps are
+    issued.  Every accumulator sum is an exact integer, so the result equals
+    bit for bit the same sweeps on the zero-filled basis vector (every member
+    read); both match the oracle."""
+    n = 16
+    e = np.zeros(1 << n, dtype=np.complex128)
+    e[x] = 1
+    Us = [random_unitary(len(q), 70 + i) for i, q in enumerate(clusters)]
+    ref = e.copy()
+    for q, U in zip(clusters, Us):
+        sim.apply_kq(ref, list(q), U)
+    out = {}
+    for lazy in (True, False):
+        with State(n, qs.QS_C128) as s:
+            qs.qs_set_path(s.h, qs.QS_PATH_TENSOR)
+            if lazy:
+                qs.qs_init_basis(s.h, x)
+            else:
+                qs.qs_set_amplitudes(s.h, e)
+            for q, U in zip(clusters, Us):
+                qs.qs_apply_cluster(s.h, list(q), U)
+            out[lazy] = qs.qs_get_amplitudes(s.h)
+    assert np.array_equal(out[True], out[False])
+    assert np.max(np.abs(out[True] - ref)) < len(clusters) * SWEEP_TOL[qs.QS_C128]
+
+
 def test_tc_c128_out_of_range_reported():
     """Amplitudes near 2^1016, whose results could pass the double range, are
     reported (QS_EINVAL at the next synchronising call, once) instead of
