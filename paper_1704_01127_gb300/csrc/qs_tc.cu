@@ -353,6 +353,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 // positions all lie past M keep zero planes and only join the barriers, and
 // each half takes ceil(M / 8) K steps per A plane instead of 4.  Every
 // accumulator sum is an exact integer, so the order of K changes no bit.
+// kPost (a phase op folded into the sweep): the phase of a row splits into a
+// part of its tile, formed one tile ahead by the issuing thread while it
+// waits for the planes (four slots by tile index), and a part of its row,
+// formed once per CTA (a table of 128); the epilogue combines the two.
 // Hand-offs per tile: mbar_planes (splitter thread 0 after the planes are
 // written), mbar_mma[h] (tcgen05.commit after half h's MMAs; half 1's also
 // releases the A planes), mbar_free[h] (one arrival per epilogue thread when
@@ -405,6 +409,56 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr size_t kStageC128 = (size_t)kSplitThreads * kMPT * 16;   // raw next tile: 64 KB
 constexpr size_t kSmemC128Pipe = kSmemC128 + kStageC128;
 
+// The folded phase of a row (kPost) split into the part of its tile and the
+// part of its row.  A row's base is b = H | l: H the base of the tile's first
+// group, l the row's bits among the 7 lowest group positions (`low`).  Then
+//   e(b) = popc(H & c1) + popc(l & c1) + 2 (q_H ^ q_l ^ parity(l & X_H))  (mod 4),
+//   flip(b) = flip(H) ^ flip(l),
+// where q_H, X_H depend on the tile alone (a term whose qubit a is set in H
+// adds parity(H & partners) to q_H and its partners to X_H; a term whose qubit
+// lies in `low` and whose partners meet H an odd number of times adds bit a to
+// X_H) and q_l on the row alone (parity(l & c2) and the terms with both ends
+// in the row's bits).  The tile's part is formed once per tile by the
+// MMA-issuing thread, the row's part once per epilogue thread; X_H is kept as
+// its bits at the `low` positions (bit k: the k-th lowest), so parity(l & X_H)
+// = parity(r & X) for row r of the tile.
+__device__ __forceinline__ void post_tile(const PostSmem &ps, uint64_t H, uint64_t low, uint32_t &X, uint32_t &C)
+{
+    uint32_t q = (uint32_t)__popcll(H & ps.c2) & 1u;
+    uint64_t x = 0;
+#pragma unroll 1
+    for (int i = 0; i < ps.n; i++) {
+        const uint64_t P = ps.part[i];
+        const int a = ps.a[i];
+        const uint32_t hp = (uint32_t)__popcll(H & P) & 1u;
+        if ((H >> a) & 1) {
+            q ^= hp;
+            x ^= P;
+        } else if (((low >> a) & 1) && hp) {
+            x ^= 1ULL << a;
+        }
+    }
+    uint32_t f = 0;
+#pragma unroll
+    for (int j = 0; j < 5; j++) f |= ((uint32_t)__popcll(H & ps.tp[j]) & 1u) << j;
+    uint32_t xc = 0;
+    int k = 0;
+    for (uint64_t w = low; w; w &= w - 1, k++) xc |= (uint32_t)((x >> (__ffsll((long long)w) - 1)) & 1) << k;
+    X = xc;
+    C = ((uint32_t)__popcll(H & ps.c1) & 3u) | q << 2 | f << 3;
+}
+__device__ __forceinline__ uint32_t post_rowpart(const PostSmem &ps, uint64_t l)
+{
+    uint32_t q = (uint32_t)__popcll(l & ps.c2) & 1u;
+#pragma unroll 1
+    for (int i = 0; i < ps.n; i++)
+        if ((l >> ps.a[i]) & 1) q ^= (uint32_t)__popcll(l & ps.part[i]) & 1u;
+    uint32_t f = 0;
+#pragma unroll
+    for (int j = 0; j < 5; j++) f |= ((uint32_t)__popcll(l & ps.tp[j]) & 1u) << j;
+    return ((uint32_t)__popcll(l & ps.c1) & 3u) | q << 2 | f << 3;
+}
+
 template <bool kPost, bool kBulk, bool kSub>
 __global__ void __launch_bounds__(kC128Threads, 1)
 k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t, const uint8_t *__restrict__ bpack,
@@ -426,6 +480,9 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     __shared__ uint32_t colX[kN];         // G_n << 20
     __shared__ volatile int abort_flag;
     __shared__ PostSmem ps;               // a phase op folded into the sweep (kPost)
+    __shared__ uint32_t postX[4];         // kPost: the tile's part of the folded phase (X_H; by tile index mod 4)
+    __shared__ uint32_t postC[4];         // kPost: popc(H & c1) mod 4, q_H, flip(H)
+    __shared__ uint8_t postR[kRows];      // kPost: the same for the row part, by row of the tile
 
     const int tid = threadIdx.x, warp = tid >> 5;
     // kSub: M = 2^m of the 32 members lie in the support (the others read as
@@ -494,6 +551,14 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
     const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
+    if constexpr (kPost) {
+        // the folded phase's row part, row by row (the same in every tile), and
+        // the tile part of this CTA's first tile
+        if (tid < kRows) postR[tid] = (uint8_t)post_rowpart(ps, tile_base(tid, t) ^ tile_base(0, t));
+        if (tid == kRows && blockIdx.x < n_tiles)
+            post_tile(ps, tile_base((uint64_t)blockIdx.x * kRows, t), tile_base(kRows - 1, t) ^ tile_base(0, t), postX[0], postC[0]);
+        __syncthreads();
+    }
 
     if (kSub && tid < kSplitThreads && kMPT * (tid >> 7) >= M) {
         // ------------------------------------------------- idle splitters (kSub)
@@ -655,8 +720,16 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
         // ---------------------------------------------------------------- issuer
         if (tid == kSplitThreads + kEpiThreads) {
             const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+            const uint64_t low = tile_base(kRows - 1, t) ^ tile_base(0, t);
             int it = 0;
             for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, it++) {
+                // the folded phase's tile part for tile it+1, while the planes of
+                // tile it are written: slot (it+1) & 3 last held tile it-3's, which
+                // the epilogue read before releasing tile it-2's half 0 (waited for
+                // by tile it-1's MMAs); it reads tile it+1's after the last MMAs of
+                // tile it complete (committed after this write)
+                if (kPost && tile + gridDim.x < n_tiles)
+                    post_tile(ps, tile_base((tile + gridDim.x) * kRows, t), low, postX[(it + 1) & 3], postC[(it + 1) & 3]);
                 if (!mbar_wait_bounded(smem_u32(&mbar_planes), it & 1) || abort_flag) {
                     atomicExch(status, 1);
                     abort_flag = 1;
@@ -693,7 +766,13 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             const bool valid = g < n_groups;
             double2 *p = psi + (valid ? tile_base(g, t) : 0);
             uint32_t pe = 0, pf = 0;
-            if constexpr (kPost) post_row(ps, (uint64_t)(p - psi), pe, pf);
+            if constexpr (kPost) {
+                // i^pe (-1)^popc(m & pf) for member m of this row
+                const uint32_t X = postX[it & 3], C = postC[it & 3], Crow = postR[row];
+                const uint32_t sq = ((C ^ Crow) >> 2) ^ (uint32_t)__popc((uint32_t)row & X);
+                pe = ((C & 3u) + (Crow & 3u) + 2u * (sq & 1u)) & 3u;
+                pf = ((C ^ Crow) >> 3) & 31u;
+            }
             for (int h = 0; h < 2; h++) {
                 if (!mbar_wait_bounded(smem_u32(&mbar_mma[h]), it & 1) || abort_flag) {
                     atomicExch(status, 1);
