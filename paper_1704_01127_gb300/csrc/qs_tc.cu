@@ -419,9 +419,9 @@ constexpr size_t kSmemC128Pipe = kSmemC128 + kStageC128;
 // lies in `low` and whose partners meet H an odd number of times adds bit a to
 // X_H) and q_l on the row alone (parity(l & c2) and the terms with both ends
 // in the row's bits).  The tile's part is formed once per tile by the
-// MMA-issuing thread, the row's part once per epilogue thread; X_H is kept as
-// its bits at the `low` positions (bit k: the k-th lowest), so parity(l & X_H)
-// = parity(r & X) for row r of the tile.
+// MMA-issuing thread, the row's part once per CTA for each of its 128 rows;
+// X_H is kept as its bits at the `low` positions (bit k: the k-th lowest), so
+// parity(l & X_H) = parity(r & X) for row r of the tile.
 __device__ __forceinline__ void post_tile(const PostSmem &ps, uint64_t H, uint64_t low, uint32_t &X, uint32_t &C)
 {
     uint32_t q = (uint32_t)__popcll(H & ps.c2) & 1u;
