@@ -328,11 +328,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 //   splitters (512 threads, kSplitThreads / 128 per row, kMPT amplitudes
 //     each): copy tile t+1 into a 64 KB stage while tile t is processed
 //     (kBulk: full-state tiles whose member runs are 2 KB, as 32 bulk copies
-//     from lane 0 of each splitter warp once the stage is read; otherwise
-//     16-byte cp.async of each thread's own slots, which hold the issuing
-//     warps up ~3K cycles a tile); find the row exponents and the fixed-point
-//     values of tile t while the MMAs of tile t-1 still read the digit planes,
-//     then write the planes;
+//     from lane 0 of each splitter warp, halfway through its fixed point,
+//     once an mbarrier shows that every splitter warp has read the stage;
+//     otherwise 16-byte cp.async of each thread's own slots, which hold the
+//     issuing warps up ~3K cycles a tile); find the row exponents (kBulk: the
+//     four threads of a row are lanes of one warp, two shuffles; otherwise a
+//     512-thread barrier) and the fixed-point values of tile t while the MMAs
+//     of tile t-1 still read the digit planes, then write the planes;
 //   issuer (one warp, one thread): issues the MMAs.  The tensor pipe takes
 //     few instructions ahead, so the issuing thread waits about as long as
 //     the MMAs run (~4K cycles a tile); on its own warp that wait holds up
@@ -468,7 +470,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
     uint8_t *A = smem;
     uint8_t *B = smem + kSlices * kPlaneA;
     uint4 *stage = reinterpret_cast<uint4 *>(smem + kSmemC128);   // [8][512] x 16 B
-    __shared__ __align__(8) uint64_t mbar_mma[2], mbar_free[2], mbar_planes, mbar_full;
+    __shared__ __align__(8) uint64_t mbar_mma[2], mbar_free[2], mbar_planes, mbar_full, mbar_used;
     __shared__ uint64_t moff[32];         // offset of member x within a group
     __shared__ uint64_t ioff[32];         // kSub: offset of the member at K position x (support members first)
     __shared__ int perm[32];              // kSub: member at K position x
@@ -542,6 +544,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
         }
         mbar_init(smem_u32(&mbar_planes), 1);
         mbar_init(smem_u32(&mbar_full), kSplitThreads / 32);
+        mbar_init(smem_u32(&mbar_used), kSplitThreads / 32);
         fence_mbar_init();
         abort_flag = 0;
     }
@@ -576,7 +579,11 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
         }
     } else if (tid < kSplitThreads) {
         // ------------------------------------------------------------ splitters
-        const int row = tid & (kRows - 1), part = tid >> 7;
+        // kBulk: the four threads of a row are lanes r, r+8, r+16, r+24 of one
+        // warp (warp w: rows 8w .. 8w+7), so the row's exponent is two warp
+        // shuffles; otherwise thread tid is row tid & 127, part tid >> 7
+        const int row = kBulk ? 8 * (tid >> 5) + (tid & 7) : tid & (kRows - 1);
+        const int part = kBulk ? (tid >> 3) & 3 : tid >> 7;
         const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
         const uint32_t one = *(volatile uint32_t *)&g_qs_one;
         const uint32_t stage_a = smem_u32(stage) + 16u * tid;
@@ -627,7 +634,7 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             double2 v[kMPT];
 #pragma unroll
             for (int x = 0; x < kMPT; x++) {
-                const uint4 w = stage[kSplitThreads * x + tid];
+                const uint4 w = stage[kSplitThreads * x + (kBulk ? kRows * part + row : tid)];
                 v[x] = make_double2(__hiloint2double((int)w.y, (int)w.x), __hiloint2double((int)w.w, (int)w.z));
             }
             uint32_t emax = 0;
@@ -639,27 +646,27 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             // emax depends on every slot read above, so the shared loads are
             // complete before the next tile's copies may overwrite the slots
             asm volatile("" ::"r"(emax) : "memory");
-            if constexpr (!bulk) prefetch(tile + gridDim.x);
-            rowexp[part][row] = (int)(emax >> 20);
+            int E;
             if constexpr (bulk) {
-                if (bar_split_or(!full_ok || abort_flag)) {
-                    if (tid == 0) atomicExch(status, 1);
+                // this warp has read its stage slots; the row's exponent from
+                // the four lanes that hold the row
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(smem_u32(&mbar_used));
+                emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, 8));
+                emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, 16));
+                E = (int)(emax >> 20);
+                if (!full_ok) {
+                    if ((tid & 31) == 0) atomicExch(status, 1);
                     abort_flag = 1;
-                    break;
                 }
             } else {
+                prefetch(tile + gridDim.x);
+                rowexp[part][row] = (int)(emax >> 20);
                 bar_split();
-            }
-            // every splitter has read the stage: the next tile's runs
-            if constexpr (bulk) {
-                if (tile + gridDim.x < n_tiles) {
-                    fill(tile + gridDim.x);
-                    pending = it + 1;
-                }
-            }
-            int E = rowexp[0][row];
+                E = rowexp[0][row];
 #pragma unroll
-            for (int q = 1; q < kSplitParts; q++) E = max(E, rowexp[q][row]);
+                for (int q = 1; q < kSplitParts; q++) E = max(E, rowexp[q][row]);
+            }
             // a result's exponent field is that of T (1023 .. 1085 for T != 0)
             // plus E + G_n - 2096.  Rows below ~2^-970 take E >= 1074 - min G_n
             // (no result leaves the normal range; they keep fewer bits, an
@@ -671,6 +678,19 @@ k_dense5_tc_c128_pipe(double2 *__restrict__ psi, uint64_t n_groups, TileLayout t
             uint32_t glo[2 * kMPT], ghi[2 * kMPT], sgn[kMPT];
 #pragma unroll
             for (int x = 0; x < kMPT; x++) {
+                if (bulk && x == kMPT / 2 && full_ok && tile + gridDim.x < n_tiles) {
+                    // every splitter warp has read the stage (by now, as a rule):
+                    // the next tile's runs
+                    if ((tid & 31) == 0) {
+                        if (mbar_wait_bounded(smem_u32(&mbar_used), it & 1)) {
+                            fill(tile + gridDim.x);
+                            pending = it + 1;
+                        } else {
+                            atomicExch(status, 1);
+                            abort_flag = 1;
+                        }
+                    }
+                }
                 mag48(v[x].x, E, E7f, one, glo[2 * x], ghi[2 * x]);
                 mag48(v[x].y, E, E7f, one, glo[2 * x + 1], ghi[2 * x + 1]);
                 // sign bits of re (bit 15) and im (bit 31)
